@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Chebyshev-BdG hot path on GB300.
+
+One step is one self-consistency iteration (paragraph after Eq. 20) of the
+disordered s-wave 128x128 open lattice (eps_i ~ U[-0.5, 0.5], seed 1001,
+t = 1, mu = -0.5, U = 2, T = 0.01) with M = 1024 Chebyshev moments and all
+16384 sites as start vectors: Gershgorin rescale, damped Fermi coefficients,
+ceil(M/2) applications of H~ per start vector with fused moments, the FP64
+fold into Delta_i and n_i, and the linear mix.
+
+Unit: vector-steps/s, one vector-step = one start vector advanced by one
+application of H~ in the doubled recursion (it yields two moments); a step
+of this workload is 16384 * 512 vector-steps.  The headline runs the
+recursion in FP32 with FP64 folds; the plain FP64 form is measured beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (weak scaling):
+the method exchanges nothing between start vectors inside an iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Chebyshev BdG steps/s (vectors×H-apps), FP32 vs FP64 at ≤1e-4 Δ error; HBM %")
+UNIT = "vector-steps/s"
+L, M, SEED = 128, 1024, 1001
+FP64_FLOPS_PER_ELEMENT_STEP = 20.0  # stencil 12 + moment products 8 (FMA = 2 flops)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(problem, target_s=12.0, max_sites=1024):
+    """The FP64 oracle, as it stands, on a bounded sample of start sites of the
+    same workload (all M moments per site).  Returns (record, sites, delta, n)."""
+    import numpy as np
+    from oracle import oracle as orc
+    p = problem
+    ol = orc.Lattice(p.Lx, p.Ly, p.periodic_x, p.periodic_y, p.eps, p.mu, p.hop, p.pairing,
+                     p.coupling, p.delta0)
+    a = orc.rescale(ol)
+    rng = np.random.default_rng(2024)
+    threads = orc.num_threads()
+    n = max(threads, 8)
+    sites = rng.choice(p.N, size=n, replace=False).astype(np.int32)
+    t0 = time.perf_counter()
+    d, nn = orc.order_parameter_sites(ol, a, p.T, p.M, 1 << 16, sites)
+    t1 = time.perf_counter() - t0
+    n2 = int(min(max_sites, max(n, round(n * target_s / max(t1, 1e-3) / threads) * threads)))
+    if n2 > n:
+        sites = rng.choice(p.N, size=n2, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        d, nn = orc.order_parameter_sites(ol, a, p.T, p.M, 1 << 16, sites)
+        t1 = time.perf_counter() - t0
+    units = sites.size * math.ceil(p.M / 2)
+    rec = {"value": units / t1, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": (f"{sites.size} random start sites of the same 128x128 lattice, all {p.M} "
+                      f"moments each, folded to Delta_i and n_i ({t1:.1f} s; the oracle applies "
+                      f"H~ {p.M - 1} times per site without doubling; value counts the doubled "
+                      f"recursion's {math.ceil(p.M / 2)} vector-steps per site)")}
+    return rec, sites, d, nn, a
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1007_1609_gb300 import workloads as wl
+    from oracle import oracle as orc
+    import numpy as np
+    p = wl.swave_disordered(L, M, seed=SEED)
+    ol = orc.Lattice(p.Lx, p.Ly, p.periodic_x, p.periodic_y, p.eps, p.mu, p.hop, p.pairing,
+                     p.coupling, p.delta0)
+    threads = orc.num_threads()
+    n_sites = max(threads, 16)
+    rng = np.random.default_rng(99)
+    times = []
+    for k in range(args.warmup + args.steps):
+        sites = rng.choice(p.N, size=n_sites, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        a = orc.rescale(ol)
+        orc.order_parameter_sites(ol, a, p.T, p.M, 1 << 16, sites)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    units = n_sites * math.ceil(p.M / 2) * len(times)
+    value = units / t
+    sample = (f"per step {n_sites} random start sites of the 128x128 disordered lattice, all "
+              f"{p.M} moments each, folded to Delta_i and n_i (FP64 oracle, direct recursion)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "s-wave disordered 128x128 open, W=1.0 seed 1001, M=1024",
+                   "start_vectors_per_step": n_sites},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1007_1609_gb300 import build as B
+    B.build()
+    from paper_1007_1609_gb300 import cbdg
+    from paper_1007_1609_gb300 import workloads as wl
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = wl.swave_disordered(L, M, seed=SEED)
+    units_per_step = p.N * math.ceil(p.M / 2)
+    stream = torch.cuda.Stream(device=dev)
+
+    # ---------------- device-resident headline: FP32 recursion, FP64 folds
+    lat = cbdg.Lattice(p, precision="fp32", stream=stream)
+    for _ in range(args.warmup):
+        lat.scf_step(p.T, p.M, p.mix)
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
+    cbdg.cbdg_profile_read(lat.handle, reset=True)
+    cbdg.cbdg_launch_count(lat.handle, reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        diffs = [lat.scf_step(p.T, p.M, p.mix) for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    step_ms, step_n, step_bytes = cbdg.cbdg_profile_read(lat.handle)
+    launches = cbdg.cbdg_launch_count(lat.handle)
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 0)
+    value = world * units_per_step * args.steps / (ms_max / 1e3)
+
+    # ---------------- end to end through the C ABI with host buffers
+    host_delta = torch.from_numpy(np.ascontiguousarray(p.delta0)).pin_memory()
+    host_out = torch.empty_like(host_delta).pin_memory()
+    lat_e = cbdg.Lattice(p, precision="fp32", stream=stream)
+    for _ in range(1):
+        cbdg.cbdg_set_delta(lat_e.handle, host_delta)
+        cbdg.cbdg_scf_step(lat_e.handle, p.T, p.M, p.mix)
+        cbdg.cbdg_get_delta(lat_e.handle, host_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cbdg.cbdg_set_delta(lat_e.handle, host_delta)
+        cbdg.cbdg_scf_step(lat_e.handle, p.T, p.M, p.mix)
+        cbdg.cbdg_get_delta(lat_e.handle, host_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    lat_e.close()
+    e2e_value = world * units_per_step * args.steps / e2e_s
+
+    line = None
+    if rank == 0:
+        hbm, peak_kind = peaks()
+        achieved = (step_bytes / step_n) / (step_ms / step_n / 1e3) / 1e9 if step_n else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                    "kernel": "cheb_step (FP32 recursion step with fused moments)",
+                    "peak_kind": f"{peak_kind} (copy bandwidth)",
+                    "algorithmic_bytes_per_launch": step_bytes / step_n if step_n else None,
+                    "avg_launch_ms": step_ms / step_n if step_n else None,
+                    "share_of_step": step_ms / ms if ms else None}
+        extra = {}
+        if not args.no_fp64:
+            extra["fp64"] = fp64_leg(p, stream, cbdg, torch, units_per_step)
+            extra["fp32_vs_fp64"] = {"speedup": value / world / extra["fp64"]["value"]}
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu, sites, od, on, oa = cpu_baseline(p)
+            # accuracy of both GPU forms against the oracle on the sampled sites
+            errs = {}
+            for prec in ("fp32", "fp64"):
+                lt = cbdg.Lattice(p, precision=prec, stream=stream)
+                d, n = lt.order_parameter(p.T, p.M)
+                errs[prec] = {"max_abs_delta_err": float(np.max(np.abs(d[sites] - od))),
+                              "max_abs_n_err": float(np.max(np.abs(n[sites] - on))),
+                              "sites": int(sites.size)}
+                lt.close()
+            extra["accuracy_vs_oracle_first_iteration"] = errs
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "s-wave disordered 128x128 open lattice, W=1.0 (seed 1001), "
+                                   "t=1, mu=-0.5, U=2, T=0.01, M=1024, all 16384 sites as "
+                                   "start vectors, FP32 recursion with FP64 folds",
+                       "step": "one self-consistency iteration",
+                       "units_per_step": units_per_step,
+                       "l2": "no flush: the two recursion vectors are 2 x 2.1 GB per rank, "
+                             "far larger than the 126 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_delta.numel() * 16),
+                    "d2h_bytes_per_step": int(host_out.numel() * 16 + 8)},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "scf_max_abs_ddelta": diffs[-1],
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def fp64_leg(p, stream, cbdg, torch, units_per_step):
+    """The plain FP64 form on the same GPU: one warm-up and one timed iteration."""
+    lat = cbdg.Lattice(p, precision="fp64", stream=stream)
+    lat.scf_step(p.T, p.M, p.mix)
+    lat.delta = p.delta0
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
+    cbdg.cbdg_profile_read(lat.handle, reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.scf_step(p.T, p.M, p.mix)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    step_ms, step_n, step_bytes = cbdg.cbdg_profile_read(lat.handle)
+    lat.close()
+    elements = 2 * p.N * p.N  # rows x columns advanced per launch
+    flops = FP64_FLOPS_PER_ELEMENT_STEP * elements * step_n
+    return {"value": units_per_step / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "dtype": "f64",
+            "roofline": {"bound": "alu", "achieved": flops / (step_ms / 1e3) / 1e12,
+                         "peak": 1.25, "unit": "TFLOP/s",
+                         "frac": flops / (step_ms / 1e3) / 1e12 / 1.25,
+                         "peak_kind": "nominal FP64 rate of the profiling recipe's table",
+                         "hbm_gbs": step_bytes / (step_ms / 1e3) / 1e9}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

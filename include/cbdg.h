@@ -1,0 +1,178 @@
+/*
+ * cbdg.h -- C ABI of libcbdg, a GB300 (sm_103a) implementation of the hot
+ * path of the Chebyshev-Bogoliubov-de Gennes method (Covaci, Peeters,
+ * Berciu, arXiv:1007.1609).
+ *
+ * The problem (Eq. 2): a square lattice of N = Lx*Ly sites with on-site
+ * energies eps_i, chemical potential mu, hoppings t_ij (Peierls phases
+ * included) and pairing Delta_i (on-site, s-wave) or Delta_ij (nearest-
+ * neighbour bonds, d-wave).  The Nambu basis interleaves, per site s, the
+ * electron row 2s (c_{s,up}) and the hole row 2s+1 (c^dagger_{s,down}).
+ *
+ * Conventions shared by every call:
+ *   - Directions d: 0:+x 1:-x 2:+y 3:-y 4:+x+y 5:-x-y 6:+x-y 7:-x+y.
+ *     hop[s*n_dirs + d] is t_ij for the bond from s to its neighbour along d;
+ *     it enters H_{e_i e_j} = -t_ij and H_{h_i h_j} = conj(t_ij) (Eq. 2).
+ *   - Spectral rescale (paragraph after Eq. 8): H~ = H / a with
+ *     a = 1.1 * max_r sum_s |H_rs| (Gershgorin), b = 0.  a is recomputed
+ *     from the current Delta by every call that needs it.
+ *   - Array arguments may point to host memory or to device memory of the
+ *     device that was current at cbdg_build_lattice; the library detects
+ *     which (cudaPointerGetAttributes).  Host arrays are copied through the
+ *     lattice's stream.  The caller owns every array it passes; the library
+ *     never frees or keeps caller memory beyond the call.
+ *   - Every call returns a cbdg_status and never aborts or exits.  On an
+ *     error, cbdg_last_error() (per thread) describes it.  Compute calls are
+ *     synchronous with respect to the host: results are complete when the
+ *     call returns.
+ *   - Complex numbers are cbdg_complex {re, im} (layout of C99 double
+ *     complex, numpy complex128 and CUDA double2).
+ */
+#ifndef CBDG_H
+#define CBDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cbdg_status;
+enum {
+  CBDG_OK = 0,
+  CBDG_ERR_INVALID_ARG = 1,   /* bad size, enum, pointer, non-finite or non-Hermitian input */
+  CBDG_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  CBDG_ERR_OOM = 3,           /* device allocation failed */
+  CBDG_ERR_SPECTRUM = 4,      /* a moment exceeded 1 in magnitude: a too small */
+  CBDG_ERR_NOT_CONVERGED = 5, /* self-consistency did not reach its tolerance */
+  CBDG_ERR_UNSUPPORTED = 6    /* valid input that this build does not handle */
+};
+
+enum { CBDG_ONSITE_U = 0, CBDG_BOND_V = 1 };        /* pairing channel */
+enum { CBDG_FP64 = 0, CBDG_FP32_MIXED = 1 };        /* recursion precision */
+enum { CBDG_JACKSON = 0, CBDG_LORENTZ = 1 };        /* damping kernel */
+
+typedef struct {
+  double re, im;
+} cbdg_complex;
+
+typedef struct cbdg_lattice cbdg_lattice;
+typedef struct CUstream_st *cbdg_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+/* Lattice description (Eq. 2 and the Peierls phases below it). */
+typedef struct {
+  int32_t Lx, Ly;                /* lattice sides, >= 1; a periodic side must be >= 3 */
+  int32_t periodic_x, periodic_y;/* 0: open edge, 1: periodic */
+  const double *eps;             /* [N] on-site energies epsilon_i */
+  double mu;                     /* chemical potential */
+  int32_t n_dirs;                /* 4 (nearest) or 8 (plus next-nearest) */
+  const cbdg_complex *hop;       /* [N*n_dirs] t_ij; must be 0 across an open edge and
+                                    satisfy hop[j*n_dirs + (d^1)] == conj(hop[i*n_dirs + d]) */
+  int32_t pairing;               /* CBDG_ONSITE_U or CBDG_BOND_V */
+  double coupling;               /* U (on-site) or V (bond), attractive for > 0 */
+  const cbdg_complex *delta0;    /* [N] Delta_i, or [N*4] Delta_{i,d} (d = 0..3) with
+                                    Delta_{j,d^1} == Delta_{i,d} (singlet) */
+  int32_t precision;             /* CBDG_FP64 or CBDG_FP32_MIXED */
+  int32_t complex_field;         /* 0: hop and Delta real (real vectors), 1: complex */
+} cbdg_lattice_desc;
+
+/* Builds a lattice on the current CUDA device and copies the description
+ * into library-owned device memory (Eq. 2).  All descriptor arrays are read
+ * during the call only.  *out receives an opaque handle; release it with
+ * cbdg_destroy.  Errors: INVALID_ARG for any violated constraint above,
+ * UNSUPPORTED for combinations this build has no kernel for, OOM, CUDA. */
+cbdg_status cbdg_build_lattice(const cbdg_lattice_desc *desc, cbdg_stream stream,
+                               cbdg_lattice **out);
+
+/* Releases a lattice and all its device memory.  NULL is accepted. */
+cbdg_status cbdg_destroy(cbdg_lattice *lat);
+
+/* Chebyshev moments of the rescaled Hamiltonian (Eqs. 11, 14, 15):
+ * for each start site i = sites[c], c < n_sites, and n < M,
+ *   mu_ee[c*M + n]            = <e_i | T_n(H~) | e_i>
+ *   mu_eh[(c*M + n)*n_eh + 0] = <h_i | T_n(H~) | e_i>
+ *   bond pairing (n_eh = 5):  mu_eh[(c*M + n)*5 + 1 + d] = <h_{i+d} | T_n(H~) | e_i>,
+ *                             d = 0..3, zero across an open edge.
+ * n_eh is 1 for on-site pairing.  The moments are unnormalised (mu_0 = 1);
+ * the 1/(1 + delta_n0) of Eq. 11 is left to the caller.  Either output may
+ * be NULL.  M >= 2.  sites may repeat.  Errors: INVALID_ARG, SPECTRUM, OOM,
+ * CUDA. */
+cbdg_status cbdg_moments(cbdg_lattice *lat, const int32_t *sites, int32_t n_sites, int32_t M,
+                         double *mu_ee, cbdg_complex *mu_eh);
+
+/* Order parameter and density from the current Delta (Eqs. 18-19, read as
+ * expectation values of tanh(H/2T) through its kernel-damped Chebyshev
+ * series with M terms):
+ *   Delta_i     = (U/2) sum_n C_n conj(<h_i|T_n(H~)|e_i>)                 (on-site)
+ *   Delta_{i,d} = (V/8) sum_n C_n conj(<h_{i+d}|T_n|e_i> + <h_i|T_n|e_{i+d}>)  (bond)
+ *   n_i         = 1 - sum_n C_n <e_i|T_n(H~)|e_i>
+ * with C_n = g_n (2 - delta_n0) c_n, c_n the Chebyshev coefficients of
+ * tanh(a x / 2T) and g_n the Jackson kernel or the Lorentz kernel of Eq. 16
+ * (parameter lambda).  All N sites are start vectors.  delta_out is [N] or
+ * [N*4] (may be NULL); n_out is [N] (may be NULL).  T >= 0 (T = 0 means the
+ * sign function).  Delta is not modified.  Errors: INVALID_ARG, SPECTRUM,
+ * OOM, CUDA. */
+cbdg_status cbdg_order_parameter(cbdg_lattice *lat, double T, int32_t kernel, double lambda,
+                                 int32_t M, cbdg_complex *delta_out, double *n_out);
+
+/* Up-spin local density of states of Eq. 17 with the expansion of Eq. 10,
+ * per unit energy, at absolute energies E (|E| < a):
+ *   ldos[c*n_E + e] = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n(i) T_n(E/a)] / (pi a sqrt(1-(E/a)^2))
+ * for i = sites[c].  Errors: INVALID_ARG (also for |E| >= a), SPECTRUM, OOM,
+ * CUDA. */
+cbdg_status cbdg_ldos(cbdg_lattice *lat, const int32_t *sites, int32_t n_sites, int32_t M,
+                      int32_t kernel, double lambda, const double *energies, int32_t n_E,
+                      float *ldos);
+
+/* One self-consistency iteration (paragraph after Eq. 20) with the Jackson
+ * kernel: computes Delta_out from the current Delta as cbdg_order_parameter
+ * does, then Delta <- Delta + mix (Delta_out - Delta).  *max_abs_ddelta
+ * (host pointer, may be NULL) receives max_i |Delta_out,i - Delta_i| taken
+ * before mixing.  0 < mix <= 1.  Errors: INVALID_ARG, SPECTRUM, OOM, CUDA. */
+cbdg_status cbdg_scf_step(cbdg_lattice *lat, double T, int32_t M, double mix,
+                          double *max_abs_ddelta);
+
+/* Copies the lattice's current Delta ([N] or [N*4]) out, or replaces it. */
+cbdg_status cbdg_get_delta(cbdg_lattice *lat, cbdg_complex *delta);
+cbdg_status cbdg_set_delta(cbdg_lattice *lat, const cbdg_complex *delta);
+
+/* The rescale factor a used by the most recent compute call (0 before any). */
+cbdg_status cbdg_get_rescale(cbdg_lattice *lat, double *a);
+
+/* Tuning and instrumentation options (cbdg_set_option / cbdg_get_option). */
+enum {
+  CBDG_OPT_QUADRATURE_NODES = 0, /* K of the Gauss-Chebyshev sum for c_n; default 65536 */
+  CBDG_OPT_COLUMN_CHUNK = 1,     /* start vectors per recursion pass; 0 = automatic */
+  CBDG_OPT_PROFILE = 2,          /* 1: time every recursion-step launch with CUDA events */
+  CBDG_OPT_SLAB_WIDTH = 3,       /* columns per CTA of the recursion kernel; 0 = automatic */
+  CBDG_OPT_ROW_SPLIT = 4,        /* CTAs per column slab along y; 0 = automatic */
+  CBDG_OPT_WORKSPACE_MB = 5,     /* cap on the recursion vectors' memory; 0 = automatic */
+  CBDG_OPT_RESCALE_MILLI = 6     /* a = (value/1000) * Gershgorin bound; default 1100 (1.1).
+                                    Below 1000 the spectrum may leave [-1, 1] and calls
+                                    then fail with CBDG_ERR_SPECTRUM */
+};
+cbdg_status cbdg_set_option(cbdg_lattice *lat, int32_t option, int64_t value);
+cbdg_status cbdg_get_option(cbdg_lattice *lat, int32_t option, int64_t *value);
+
+/* Accumulated device time of the recursion-step kernel since the last reset
+ * (CBDG_OPT_PROFILE must be on): total milliseconds, number of launches and
+ * algorithmic bytes (read j_n, read j_{n-1}, write j_{n+1}) summed over the
+ * launches.  reset != 0 clears the counters after reading. */
+cbdg_status cbdg_profile_read(cbdg_lattice *lat, double *step_ms, int64_t *step_launches,
+                              double *step_bytes, int32_t reset);
+
+/* Number of CUDA kernels the library has launched for this lattice since the
+ * last reset (reset != 0 clears the counter after reading). */
+cbdg_status cbdg_launch_count(cbdg_lattice *lat, int64_t *launches, int32_t reset);
+
+/* Per-thread description of the last error; never NULL. */
+const char *cbdg_last_error(void);
+
+/* Library version string. */
+const char *cbdg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CBDG_H */

@@ -353,6 +353,35 @@ int orc_order_parameter(const orc_lattice *L, double a, double T, int M, int K, 
   return 0;
 }
 
+/* The on-site order parameter and density of orc_order_parameter restricted
+ * to the start sites listed in sites[0..n_sites) (on-site pairing only):
+ * Delta_i = (U/2) sum_n C_n conj(<h_i|T_n|e_i>), n_i = 1 - sum_n C_n <e_i|T_n|e_i>.
+ * delta_out and n_out are [n_sites]. */
+int orc_order_parameter_sites(const orc_lattice *L, double a, double T, int M, int K, int kernel,
+                              double lambda, const int32_t *sites, int n_sites, cplx *delta_out,
+                              double *n_out) {
+  if (L->pairing != 0) return -1;
+  double *C = (double *)malloc(sizeof(double) * M);
+  orc_fold_coefficients(M, K, a, T, kernel, lambda, C);
+  double *mu_ee = (double *)malloc(sizeof(double) * (size_t)n_sites * M);
+  cplx *mu_eh = (cplx *)malloc(sizeof(cplx) * (size_t)n_sites * M);
+  orc_moments(L, a, sites, n_sites, M, mu_ee, mu_eh);
+  for (int c = 0; c < n_sites; ++c) {
+    double nn = 1.0;
+    cplx s = 0.0;
+    for (int m = 0; m < M; ++m) {
+      nn -= C[m] * mu_ee[(size_t)c * M + m];
+      s += C[m] * conj(mu_eh[(size_t)c * M + m]);
+    }
+    if (n_out) n_out[c] = nn;
+    delta_out[c] = 0.5 * L->coupling * s;
+  }
+  free(C);
+  free(mu_ee);
+  free(mu_eh);
+  return 0;
+}
+
 /* Up-spin LDOS of Eq. 17 from the expansion of Eq. 10, per unit energy:
  *   N(E, i) = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(E/a)] / (pi a sqrt(1-(E/a)^2)).
  * ldos is [n_sites * n_E]. */

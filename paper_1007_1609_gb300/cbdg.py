@@ -1,0 +1,304 @@
+"""Thin ctypes binding of libcbdg (include/cbdg.h), same names as the C ABI.
+
+Only argument marshalling happens here: every step of the Chebyshev-BdG path
+runs in the CUDA library.  Arrays may be numpy arrays (host memory) or torch
+CUDA tensors (device memory, passed by pointer); the library detects which.
+If libcbdg.so has not been built, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+CBDG_OK = 0
+CBDG_ERR_INVALID_ARG = 1
+CBDG_ERR_CUDA = 2
+CBDG_ERR_OOM = 3
+CBDG_ERR_SPECTRUM = 4
+CBDG_ERR_NOT_CONVERGED = 5
+CBDG_ERR_UNSUPPORTED = 6
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "SPECTRUM",
+                5: "NOT_CONVERGED", 6: "UNSUPPORTED"}
+
+CBDG_ONSITE_U, CBDG_BOND_V = 0, 1
+CBDG_FP64, CBDG_FP32_MIXED = 0, 1
+CBDG_JACKSON, CBDG_LORENTZ = 0, 1
+CBDG_OPT_QUADRATURE_NODES = 0
+CBDG_OPT_COLUMN_CHUNK = 1
+CBDG_OPT_PROFILE = 2
+CBDG_OPT_SLAB_WIDTH = 3
+CBDG_OPT_ROW_SPLIT = 4
+CBDG_OPT_WORKSPACE_MB = 5
+CBDG_OPT_RESCALE_MILLI = 6
+
+
+class CbdgError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"cbdg status {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class cbdg_lattice_desc(ctypes.Structure):
+    _fields_ = [
+        ("Lx", ctypes.c_int32), ("Ly", ctypes.c_int32),
+        ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+        ("eps", ctypes.c_void_p),
+        ("mu", ctypes.c_double),
+        ("n_dirs", ctypes.c_int32),
+        ("hop", ctypes.c_void_p),
+        ("pairing", ctypes.c_int32),
+        ("coupling", ctypes.c_double),
+        ("delta0", ctypes.c_void_p),
+        ("precision", ctypes.c_int32),
+        ("complex_field", ctypes.c_int32),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads the in-tree libcbdg.so (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcbdg.so is not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "cbdg_build_lattice": [P, P, P],
+            "cbdg_destroy": [P],
+            "cbdg_moments": [P, P, I32, I32, P, P],
+            "cbdg_order_parameter": [P, D, I32, D, I32, P, P],
+            "cbdg_ldos": [P, P, I32, I32, I32, D, P, I32, P],
+            "cbdg_scf_step": [P, D, I32, D, P],
+            "cbdg_get_delta": [P, P],
+            "cbdg_set_delta": [P, P],
+            "cbdg_get_rescale": [P, P],
+            "cbdg_set_option": [P, I32, I64],
+            "cbdg_get_option": [P, I32, P],
+            "cbdg_profile_read": [P, P, P, P, I32],
+            "cbdg_launch_count": [P, P, I32],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int32
+        lib.cbdg_last_error.restype = ctypes.c_char_p
+        lib.cbdg_last_error.argtypes = []
+        lib.cbdg_version.restype = ctypes.c_char_p
+        lib.cbdg_version.argtypes = []
+        _lib = lib
+        return lib
+
+
+def header_functions(header=None):
+    """Names of the functions include/cbdg.h declares."""
+    header = header or os.path.join(_build.ROOT, "include", "cbdg.h")
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cbdg_[a-z_]+)\s*\(", text)))
+
+
+def _check(status):
+    if status != CBDG_OK:
+        msg = load().cbdg_last_error().decode()
+        raise CbdgError(status, msg)
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- C ABI names
+
+
+def cbdg_build_lattice(desc: cbdg_lattice_desc, stream=None):
+    out = ctypes.c_void_p()
+    _check(load().cbdg_build_lattice(ctypes.byref(desc), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def cbdg_destroy(lat):
+    _check(load().cbdg_destroy(lat))
+
+
+def cbdg_moments(lat, sites, n_sites, M, mu_ee, mu_eh):
+    _check(load().cbdg_moments(lat, _ptr(sites), int(n_sites), int(M), _ptr(mu_ee), _ptr(mu_eh)))
+
+
+def cbdg_order_parameter(lat, T, kernel, lam, M, delta_out, n_out):
+    _check(load().cbdg_order_parameter(lat, float(T), int(kernel), float(lam), int(M),
+                                       _ptr(delta_out), _ptr(n_out)))
+
+
+def cbdg_ldos(lat, sites, n_sites, M, kernel, lam, energies, n_E, ldos):
+    _check(load().cbdg_ldos(lat, _ptr(sites), int(n_sites), int(M), int(kernel), float(lam),
+                            _ptr(energies), int(n_E), _ptr(ldos)))
+
+
+def cbdg_scf_step(lat, T, M, mix):
+    out = ctypes.c_double(0.0)
+    _check(load().cbdg_scf_step(lat, float(T), int(M), float(mix), ctypes.byref(out)))
+    return out.value
+
+
+def cbdg_get_delta(lat, delta):
+    _check(load().cbdg_get_delta(lat, _ptr(delta)))
+
+
+def cbdg_set_delta(lat, delta):
+    _check(load().cbdg_set_delta(lat, _ptr(delta)))
+
+
+def cbdg_get_rescale(lat):
+    out = ctypes.c_double(0.0)
+    _check(load().cbdg_get_rescale(lat, ctypes.byref(out)))
+    return out.value
+
+
+def cbdg_set_option(lat, option, value):
+    _check(load().cbdg_set_option(lat, int(option), int(value)))
+
+
+def cbdg_get_option(lat, option):
+    out = ctypes.c_int64(0)
+    _check(load().cbdg_get_option(lat, int(option), ctypes.byref(out)))
+    return out.value
+
+
+def cbdg_profile_read(lat, reset=False):
+    ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().cbdg_profile_read(lat, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                    1 if reset else 0))
+    return ms.value, n.value, b.value
+
+
+def cbdg_launch_count(lat, reset=False):
+    out = ctypes.c_int64(0)
+    _check(load().cbdg_launch_count(lat, ctypes.byref(out), 1 if reset else 0))
+    return out.value
+
+
+def cbdg_last_error():
+    return load().cbdg_last_error().decode()
+
+
+def cbdg_version():
+    return load().cbdg_version().decode()
+
+
+# ---------------------------------------------------------------- convenience
+
+
+PRECISIONS = {"fp64": CBDG_FP64, "fp32": CBDG_FP32_MIXED}
+KERNELS = {"jackson": CBDG_JACKSON, "lorentz": CBDG_LORENTZ}
+
+
+class Lattice:
+    """Owns a cbdg_lattice built from a workloads.Problem-like object
+    (attributes Lx, Ly, periodic_x, periodic_y, eps, mu, hop, pairing,
+    coupling, delta0)."""
+
+    def __init__(self, problem, precision="fp64", stream=None, complex_field=None):
+        p = problem
+        self.N = int(p.Lx * p.Ly)
+        self.pairing = int(p.pairing)
+        self._eps = np.ascontiguousarray(p.eps, dtype=np.float64)
+        self._hop = np.ascontiguousarray(p.hop, dtype=np.complex128)
+        self._delta = np.ascontiguousarray(p.delta0, dtype=np.complex128)
+        if complex_field is None:
+            complex_field = bool(np.any(self._hop.imag) or np.any(self._delta.imag))
+        d = cbdg_lattice_desc()
+        d.Lx, d.Ly = int(p.Lx), int(p.Ly)
+        d.periodic_x, d.periodic_y = int(p.periodic_x), int(p.periodic_y)
+        d.eps = _ptr(self._eps)
+        d.mu = float(p.mu)
+        d.n_dirs = int(self._hop.shape[-1]) if self._hop.ndim == 2 else int(self._hop.size // self.N)
+        d.hop = _ptr(self._hop)
+        d.pairing = self.pairing
+        d.coupling = float(p.coupling)
+        d.delta0 = _ptr(self._delta)
+        d.precision = PRECISIONS[precision]
+        d.complex_field = 1 if complex_field else 0
+        self.desc = d
+        self.handle = cbdg_build_lattice(d, stream)
+        self.nd = 4 * self.N if self.pairing == CBDG_BOND_V else self.N
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cbdg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option, value):
+        cbdg_set_option(self.handle, option, value)
+
+    def moments(self, sites, M):
+        sites = np.ascontiguousarray(sites, dtype=np.int32)
+        n_eh = 5 if self.pairing == CBDG_BOND_V else 1
+        mu_ee = np.zeros((sites.size, M))
+        mu_eh = np.zeros((sites.size, M, n_eh), dtype=np.complex128)
+        cbdg_moments(self.handle, sites, sites.size, M, mu_ee, mu_eh)
+        return mu_ee, mu_eh
+
+    def order_parameter(self, T, M, kernel="jackson", lam=0.0):
+        d = np.zeros(self.nd, dtype=np.complex128)
+        n = np.zeros(self.N)
+        cbdg_order_parameter(self.handle, T, KERNELS[kernel], lam, M, d, n)
+        return (d.reshape(self.N, 4) if self.pairing == CBDG_BOND_V else d), n
+
+    def scf_step(self, T, M, mix):
+        return cbdg_scf_step(self.handle, T, M, mix)
+
+    @property
+    def delta(self):
+        d = np.zeros(self.nd, dtype=np.complex128)
+        cbdg_get_delta(self.handle, d)
+        return d.reshape(self.N, 4) if self.pairing == CBDG_BOND_V else d
+
+    @delta.setter
+    def delta(self, value):
+        cbdg_set_delta(self.handle, np.ascontiguousarray(value, dtype=np.complex128).reshape(-1))
+
+    @property
+    def rescale(self):
+        return cbdg_get_rescale(self.handle)

@@ -1,0 +1,633 @@
+// api.cu -- host side of libcbdg: the C ABI of include/cbdg.h, lattice
+// objects, validation, device memory and the launch sequence of one
+// self-consistency iteration (paragraph after Eq. 20):
+//
+//   Gershgorin bound -> a              (rescale below Eq. 8)
+//   damped Fermi coefficients C_n      (FP64 table, M entries)
+//   stencil parameters 2 t/a, ...      (step precision)
+//   per column chunk:
+//     j_0 = e_i, j_1 = H~ e_i          (Eq. 15 start)
+//     ceil(M/2) - 1 times: recursion step + moment fold
+//     scatter Delta_out, n
+//   mix Delta, max |Delta_out - Delta|
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cbdg.h"
+#include "internal.h"
+
+using namespace cbdg;
+
+namespace {
+
+thread_local std::string g_error = "no error";
+
+cbdg_status fail(cbdg_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return st;
+}
+
+cbdg_status cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(CBDG_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return fail(CBDG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// Growable device buffer owned by a lattice.
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = n;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T *as() const {
+    return static_cast<T *>(p);
+  }
+};
+
+}  // namespace
+
+struct cbdg_lattice {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int Lx = 0, Ly = 0, px = 0, py = 0, N = 0, n_dirs = 4, pairing = 0, precision = 0, cplx = 0;
+  double mu = 0.0, coupling = 0.0;
+  int nd = 0;  // number of Delta entries (N or 4N)
+  DBuf eps, hop, delta, params, scal, flags, f, C, sites_all, sites_user;
+  DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
+  // options
+  int K = 65536;
+  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100;
+  int profile = 0;
+  std::vector<cudaEvent_t> events;
+  double prof_ms = 0.0, prof_bytes = 0.0;
+  int64_t prof_launches = 0;
+  int64_t launches = 0;  // kernels this library launched for the lattice
+  double last_a = 0.0;
+};
+
+namespace {
+
+// Copies device src into a caller array (host or device).
+cudaError_t deliver(cbdg_lattice *L, void *dst, const void *src, size_t bytes) {
+  if (bytes == 0 || !dst) return cudaSuccess;
+  return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice
+                                                             : cudaMemcpyDeviceToHost,
+                         L->stream);
+}
+
+// Host copy of a caller array, for validation.
+template <typename T>
+cudaError_t host_copy(const T *src, size_t count, std::vector<T> &out) {
+  out.resize(count);
+  if (count == 0) return cudaSuccess;
+  if (is_device_ptr(src)) return cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost);
+  memcpy(out.data(), src, count * sizeof(T));
+  return cudaSuccess;
+}
+
+const int DXh[8] = {1, -1, 0, 0, 1, -1, 1, -1};
+const int DYh[8] = {0, 0, 1, -1, 1, -1, -1, 1};
+
+int host_neighbour(const cbdg_lattice_desc *d, int s, int dir) {
+  int x = s % d->Lx, y = s / d->Lx;
+  int nx = x + DXh[dir], ny = y + DYh[dir];
+  if (nx < 0 || nx >= d->Lx) {
+    if (!d->periodic_x) return -1;
+    nx = (nx + d->Lx) % d->Lx;
+  }
+  if (ny < 0 || ny >= d->Ly) {
+    if (!d->periodic_y) return -1;
+    ny = (ny + d->Ly) % d->Ly;
+  }
+  return nx + d->Lx * ny;
+}
+
+bool finite_c(const cbdg_complex &z) { return isfinite(z.re) && isfinite(z.im); }
+
+size_t elem_size(const cbdg_lattice *L) { return L->precision == CBDG_FP32_MIXED ? 4 : 8; }
+
+// a, coefficient table and stencil parameters for the current Delta.
+cbdg_status prepare(cbdg_lattice *L, double T, int kernel, double lambda, int M, bool coeffs) {
+  CK(L->scal.ensure(kScalars * sizeof(double)));
+  CK(launch_gershgorin(L->N, L->n_dirs, L->pairing, L->Lx, L->Ly, L->px, L->py,
+                       L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
+                       L->margin_milli / 1000.0, L->scal.as<double>(), L->stream));
+  L->launches += 2;
+  CK(L->C.ensure(static_cast<size_t>(M) * sizeof(double)));
+  if (coeffs) {
+    CK(L->f.ensure(static_cast<size_t>(L->K) * sizeof(double)));
+    CK(launch_coefficients(M, L->K, T, kernel, lambda, L->scal.as<double>(), L->f.as<double>(),
+                           L->C.as<double>(), L->stream));
+    L->launches += 2;
+  } else {
+    CK(cudaMemsetAsync(L->C.p, 0, static_cast<size_t>(M) * sizeof(double), L->stream));
+  }
+  CK(L->params.ensure(static_cast<size_t>(L->N) * kParamStride * elem_size(L)));
+  CK(launch_params_real(L->precision, L->N, L->eps.as<double>(), L->mu, L->hop.as<double2>(),
+                        L->delta.as<double2>(), L->scal.as<double>(), L->params.p, L->stream));
+  L->launches += 1;
+  return CBDG_OK;
+}
+
+// Runs the recursion for n_sites start vectors (device list), folding the
+// moments into per-column accumulators; optionally writes the moments
+// ([n_sites][M] and [n_sites][M][stride]) and scatters Delta_out / n into
+// L->dout / L->nout.
+cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int M,
+                        double *mom_ee, double2 *mom_eh, int mom_stride, bool finalize) {
+  const size_t es = elem_size(L);
+  const size_t rows = 2 * static_cast<size_t>(L->N);
+  int W = L->slab_w > 0 ? static_cast<int>(L->slab_w) : slab_width_default(L->precision);
+  // column chunk: bounded by the workspace cap (two vectors)
+  size_t cap;
+  if (L->ws_mb > 0) {
+    cap = static_cast<size_t>(L->ws_mb) << 20;
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    cap = static_cast<size_t>(0.6 * (fr + L->vec0.bytes + L->vec1.bytes));
+  }
+  int64_t per_col = static_cast<int64_t>(2 * rows * es);
+  int64_t max_cols = static_cast<int64_t>(cap) / per_col;
+  max_cols = (max_cols / W) * W;
+  if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
+  if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for one column slab");
+  const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((n_sites + W - 1) / W) * W));
+
+  for (int c0 = 0; c0 < n_sites; c0 += chunk) {
+    const int ncols = std::min(chunk, n_sites - c0);
+    const int ld = ((ncols + W - 1) / W) * W;
+    StepConfig cfg;
+    if (!plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split), &cfg))
+      return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d with %d columns", L->Lx, ld);
+    const size_t vbytes = rows * ld * es;
+    CK(L->vec0.ensure(vbytes));
+    CK(L->vec1.ensure(vbytes));
+    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 3 * ld * sizeof(double)));
+    CK(L->mu1.ensure(ld * sizeof(double)));
+    CK(L->dA.ensure(ld * sizeof(double2)));
+    CK(L->acc_n.ensure(ld * sizeof(double)));
+    CK(L->acc_d.ensure(ld * sizeof(double2)));
+    CK(cudaMemsetAsync(L->vec0.p, 0, vbytes, L->stream));
+    CK(cudaMemsetAsync(L->vec1.p, 0, vbytes, L->stream));
+    double *mee = mom_ee ? mom_ee + static_cast<size_t>(c0) * M : nullptr;
+    double2 *meh = mom_eh ? mom_eh + static_cast<size_t>(c0) * M * mom_stride : nullptr;
+    CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, ld, sites + c0,
+                        L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
+                        L->scal.as<double>(), L->C.as<double>(), M, L->vec0.p, L->vec1.p,
+                        L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
+                        L->acc_d.as<double2>(), mee, meh, mom_stride, L->stream));
+    L->launches += 1;
+    void *cur = L->vec1.p, *prev = L->vec0.p;
+    const int steps = (M + 1) / 2 - 1;
+    if (L->profile && static_cast<int>(L->events.size()) < 2 * steps) {
+      for (int k = static_cast<int>(L->events.size()); k < 2 * steps; ++k) {
+        cudaEvent_t ev;
+        CK(cudaEventCreate(&ev));
+        L->events.push_back(ev);
+      }
+    }
+    StepArgs a;
+    a.params = L->params.p;
+    a.partials = L->partials.as<double>();
+    a.Lx = L->Lx;
+    a.Ly = L->Ly;
+    a.ld = ld;
+    a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+    const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
+    for (int n = 1; n <= steps; ++n) {
+      a.cur = cur;
+      a.prev = prev;
+      if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1)], L->stream));
+      CK(launch_step_real(L->precision, a, cfg, L->stream));
+      if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1) + 1], L->stream));
+      CK(launch_fold(n, M, ncols, ld, cfg.row_split, L->partials.as<double>(), L->C.as<double>(),
+                     L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
+                     L->acc_d.as<double2>(), mee, meh, mom_stride, L->flags.as<unsigned int>(),
+                     tol, L->stream));
+      L->launches += 2;
+      std::swap(cur, prev);
+    }
+    if (finalize)
+      CK(launch_finalize_onsite(ncols, sites + c0, L->coupling, L->acc_n.as<double>(),
+                                L->acc_d.as<double2>(), L->dout.as<double2>(), L->nout.as<double>(),
+                                L->stream));
+    if (finalize) L->launches += 1;
+    if (L->profile && steps > 0) {
+      CK(cudaStreamSynchronize(L->stream));
+      for (int n = 0; n < steps; ++n) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, L->events[2 * n], L->events[2 * n + 1]));
+        L->prof_ms += ms;
+      }
+      L->prof_launches += steps;
+      L->prof_bytes += static_cast<double>(steps) * 3.0 * static_cast<double>(vbytes);
+    }
+  }
+  return CBDG_OK;
+}
+
+cbdg_status begin(cbdg_lattice *L) {
+  if (!L) return fail(CBDG_ERR_INVALID_ARG, "lattice is NULL");
+  CK(cudaSetDevice(L->device));
+  CK(cudaMemsetAsync(L->flags.p, 0, sizeof(unsigned int), L->stream));
+  return CBDG_OK;
+}
+
+cbdg_status finish(cbdg_lattice *L) {
+  unsigned int flags = 0;
+  double a = 0.0;
+  CK(cudaMemcpyAsync(&flags, L->flags.p, sizeof(flags), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaMemcpyAsync(&a, L->scal.as<double>() + kScalA, sizeof(double), cudaMemcpyDeviceToHost,
+                     L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  L->last_a = a;
+  if (flags & kFlagSpectrum)
+    return fail(CBDG_ERR_SPECTRUM, "a Chebyshev moment exceeded 1 in magnitude (a = %g too small)", a);
+  return CBDG_OK;
+}
+
+cbdg_status order_parameter_impl(cbdg_lattice *L, double T, int kernel, double lambda, int M) {
+  if (!(T >= 0.0) || !isfinite(T)) return fail(CBDG_ERR_INVALID_ARG, "T must be finite and >= 0");
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  if (kernel != CBDG_JACKSON && kernel != CBDG_LORENTZ)
+    return fail(CBDG_ERR_INVALID_ARG, "unknown kernel %d", kernel);
+  if (kernel == CBDG_LORENTZ && !(lambda > 0.0 && isfinite(lambda)))
+    return fail(CBDG_ERR_INVALID_ARG, "Lorentz kernel needs lambda > 0");
+  cbdg_status st = prepare(L, T, kernel, lambda, M, true);
+  if (st != CBDG_OK) return st;
+  CK(L->dout.ensure(static_cast<size_t>(L->nd) * sizeof(double2)));
+  CK(L->nout.ensure(static_cast<size_t>(L->N) * sizeof(double)));
+  return run_columns(L, L->sites_all.as<int32_t>(), L->N, M, nullptr, nullptr, 1, true);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cbdg_last_error(void) { return g_error.c_str(); }
+
+const char *cbdg_version(void) { return "cbdg 0.1 (sm_103a)"; }
+
+cbdg_status cbdg_build_lattice(const cbdg_lattice_desc *d, cbdg_stream stream,
+                               cbdg_lattice **out) {
+  if (!d || !out) return fail(CBDG_ERR_INVALID_ARG, "desc and out must be non-NULL");
+  *out = nullptr;
+  if (d->Lx < 1 || d->Ly < 1) return fail(CBDG_ERR_INVALID_ARG, "Lx, Ly must be >= 1");
+  if ((d->periodic_x != 0 && d->periodic_x != 1) || (d->periodic_y != 0 && d->periodic_y != 1))
+    return fail(CBDG_ERR_INVALID_ARG, "periodic flags must be 0 or 1");
+  if ((d->periodic_x && d->Lx < 3) || (d->periodic_y && d->Ly < 3))
+    return fail(CBDG_ERR_INVALID_ARG, "a periodic side must be >= 3");
+  if (static_cast<int64_t>(d->Lx) * d->Ly > (1LL << 26))
+    return fail(CBDG_ERR_INVALID_ARG, "lattice too large");
+  if (d->n_dirs != 4 && d->n_dirs != 8) return fail(CBDG_ERR_INVALID_ARG, "n_dirs must be 4 or 8");
+  if (d->pairing != CBDG_ONSITE_U && d->pairing != CBDG_BOND_V)
+    return fail(CBDG_ERR_INVALID_ARG, "unknown pairing %d", d->pairing);
+  if (d->precision != CBDG_FP64 && d->precision != CBDG_FP32_MIXED)
+    return fail(CBDG_ERR_INVALID_ARG, "unknown precision %d", d->precision);
+  if (d->complex_field != 0 && d->complex_field != 1)
+    return fail(CBDG_ERR_INVALID_ARG, "complex_field must be 0 or 1");
+  if (!d->eps || !d->hop || !d->delta0) return fail(CBDG_ERR_INVALID_ARG, "NULL array in desc");
+  if (!isfinite(d->mu) || !isfinite(d->coupling))
+    return fail(CBDG_ERR_INVALID_ARG, "mu and coupling must be finite");
+  const int N = d->Lx * d->Ly;
+  const int nd = d->pairing == CBDG_BOND_V ? 4 * N : N;
+  std::vector<double> eps;
+  std::vector<cbdg_complex> hop, delta;
+  cudaError_t e;
+  if ((e = host_copy(d->eps, N, eps)) != cudaSuccess) return cuda_fail(e, "reading eps");
+  if ((e = host_copy(d->hop, static_cast<size_t>(N) * d->n_dirs, hop)) != cudaSuccess)
+    return cuda_fail(e, "reading hop");
+  if ((e = host_copy(d->delta0, nd, delta)) != cudaSuccess) return cuda_fail(e, "reading delta0");
+  for (int i = 0; i < N; ++i)
+    if (!isfinite(eps[i])) return fail(CBDG_ERR_INVALID_ARG, "eps[%d] is not finite", i);
+  for (size_t k = 0; k < hop.size(); ++k)
+    if (!finite_c(hop[k])) return fail(CBDG_ERR_INVALID_ARG, "hop[%zu] is not finite", k);
+  for (size_t k = 0; k < delta.size(); ++k)
+    if (!finite_c(delta[k])) return fail(CBDG_ERR_INVALID_ARG, "delta0[%zu] is not finite", k);
+  for (int i = 0; i < N; ++i) {
+    for (int dir = 0; dir < d->n_dirs; ++dir) {
+      const cbdg_complex t = hop[static_cast<size_t>(i) * d->n_dirs + dir];
+      const int j = host_neighbour(d, i, dir);
+      if (j < 0) {
+        if (t.re != 0.0 || t.im != 0.0)
+          return fail(CBDG_ERR_INVALID_ARG, "hop[%d][%d] crosses an open edge and must be 0", i, dir);
+        continue;
+      }
+      const cbdg_complex b = hop[static_cast<size_t>(j) * d->n_dirs + (dir ^ 1)];
+      const double tol = 1e-12 * (1.0 + hypot(t.re, t.im));
+      if (fabs(b.re - t.re) > tol || fabs(b.im + t.im) > tol)
+        return fail(CBDG_ERR_INVALID_ARG, "hop is not Hermitian at site %d dir %d", i, dir);
+    }
+    if (d->pairing == CBDG_BOND_V) {
+      for (int dir = 0; dir < 4; ++dir) {
+        const cbdg_complex v = delta[static_cast<size_t>(i) * 4 + dir];
+        const int j = host_neighbour(d, i, dir);
+        if (j < 0) {
+          if (v.re != 0.0 || v.im != 0.0)
+            return fail(CBDG_ERR_INVALID_ARG, "delta0[%d][%d] crosses an open edge and must be 0", i, dir);
+          continue;
+        }
+        const cbdg_complex w = delta[static_cast<size_t>(j) * 4 + (dir ^ 1)];
+        const double tol = 1e-12 * (1.0 + hypot(v.re, v.im));
+        if (fabs(w.re - v.re) > tol || fabs(w.im - v.im) > tol)
+          return fail(CBDG_ERR_INVALID_ARG, "bond pairing is not symmetric at site %d dir %d", i, dir);
+      }
+    }
+  }
+  if (!d->complex_field) {
+    for (auto &z : hop)
+      if (z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex hop with complex_field = 0");
+    for (auto &z : delta)
+      if (z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex delta0 with complex_field = 0");
+  }
+  if (d->complex_field || d->pairing != CBDG_ONSITE_U || d->n_dirs != 4)
+    return fail(CBDG_ERR_UNSUPPORTED,
+                "this build handles real on-site pairing with nearest-neighbour hopping only");
+
+  cbdg_lattice *L = new (std::nothrow) cbdg_lattice();
+  if (!L) return fail(CBDG_ERR_OOM, "host allocation failed");
+  cudaGetDevice(&L->device);
+  L->stream = reinterpret_cast<cudaStream_t>(stream);
+  L->Lx = d->Lx;
+  L->Ly = d->Ly;
+  L->px = d->periodic_x;
+  L->py = d->periodic_y;
+  L->N = N;
+  L->n_dirs = d->n_dirs;
+  L->pairing = d->pairing;
+  L->precision = d->precision;
+  L->cplx = d->complex_field;
+  L->mu = d->mu;
+  L->coupling = d->coupling;
+  L->nd = nd;
+  auto bail = [&](cudaError_t err, const char *what) {
+    cbdg_status st = cuda_fail(err, what);
+    cbdg_destroy(L);
+    return st;
+  };
+  if ((e = L->eps.ensure(N * sizeof(double))) != cudaSuccess) return bail(e, "alloc eps");
+  if ((e = L->hop.ensure(hop.size() * sizeof(double2))) != cudaSuccess) return bail(e, "alloc hop");
+  if ((e = L->delta.ensure(nd * sizeof(double2))) != cudaSuccess) return bail(e, "alloc delta");
+  if ((e = L->flags.ensure(sizeof(unsigned int) * 4)) != cudaSuccess) return bail(e, "alloc flags");
+  if ((e = L->scal.ensure(kScalars * sizeof(double))) != cudaSuccess) return bail(e, "alloc scal");
+  if ((e = L->sites_all.ensure(N * sizeof(int32_t))) != cudaSuccess) return bail(e, "alloc sites");
+  std::vector<int32_t> iota(N);
+  for (int i = 0; i < N; ++i) iota[i] = i;
+  if ((e = cudaMemcpy(L->eps.p, eps.data(), N * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "upload eps");
+  if ((e = cudaMemcpy(L->hop.p, hop.data(), hop.size() * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "upload hop");
+  if ((e = cudaMemcpy(L->delta.p, delta.data(), nd * sizeof(double2), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "upload delta");
+  if ((e = cudaMemcpy(L->sites_all.p, iota.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(e, "upload sites");
+  if ((e = cudaMemset(L->scal.p, 0, kScalars * sizeof(double))) != cudaSuccess) return bail(e, "memset");
+  *out = L;
+  return CBDG_OK;
+}
+
+cbdg_status cbdg_destroy(cbdg_lattice *L) {
+  if (!L) return CBDG_OK;
+  cudaSetDevice(L->device);
+  if (L->stream) cudaStreamSynchronize(L->stream);
+  else cudaDeviceSynchronize();
+  DBuf *bufs[] = {&L->eps,     &L->hop,   &L->delta, &L->params,  &L->scal,  &L->flags,
+                  &L->f,       &L->C,     &L->sites_all, &L->sites_user, &L->vec0, &L->vec1,
+                  &L->partials, &L->mu1,  &L->dA,    &L->acc_n,   &L->acc_d, &L->dout,
+                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage};
+  for (DBuf *b : bufs) b->release();
+  for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
+  delete L;
+  return CBDG_OK;
+}
+
+cbdg_status cbdg_moments(cbdg_lattice *L, const int32_t *sites, int32_t n_sites, int32_t M,
+                         double *mu_ee, cbdg_complex *mu_eh) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  if (n_sites < 0 || (n_sites > 0 && !sites)) return fail(CBDG_ERR_INVALID_ARG, "bad site list");
+  if (n_sites == 0) return CBDG_OK;
+  std::vector<int32_t> hs;
+  cudaError_t e = host_copy(sites, n_sites, hs);
+  if (e != cudaSuccess) return cuda_fail(e, "reading sites");
+  for (int c = 0; c < n_sites; ++c)
+    if (hs[c] < 0 || hs[c] >= L->N) return fail(CBDG_ERR_INVALID_ARG, "site %d out of range", hs[c]);
+  CK(L->sites_user.ensure(n_sites * sizeof(int32_t)));
+  CK(cudaMemcpyAsync(L->sites_user.p, hs.data(), n_sites * sizeof(int32_t), cudaMemcpyHostToDevice, L->stream));
+  const int n_eh = L->pairing == CBDG_BOND_V ? 5 : 1;
+  const size_t nee = static_cast<size_t>(n_sites) * M, neh = nee * n_eh;
+  double *dee = nullptr;
+  double2 *deh = nullptr;
+  if (mu_ee) {
+    if (is_device_ptr(mu_ee)) dee = mu_ee;
+    else {
+      CK(L->mom_ee.ensure(nee * sizeof(double)));
+      dee = L->mom_ee.as<double>();
+    }
+  }
+  if (mu_eh) {
+    if (is_device_ptr(mu_eh)) deh = reinterpret_cast<double2 *>(mu_eh);
+    else {
+      CK(L->mom_eh.ensure(neh * sizeof(double2)));
+      deh = L->mom_eh.as<double2>();
+    }
+  }
+  st = prepare(L, 0.0, CBDG_JACKSON, 0.0, M, false);
+  if (st != CBDG_OK) return st;
+  st = run_columns(L, L->sites_user.as<int32_t>(), n_sites, M, dee, deh, n_eh, false);
+  if (st != CBDG_OK) return st;
+  if (mu_ee && dee != mu_ee) CK(deliver(L, mu_ee, dee, nee * sizeof(double)));
+  if (mu_eh && deh != reinterpret_cast<double2 *>(mu_eh)) CK(deliver(L, mu_eh, deh, neh * sizeof(double2)));
+  return finish(L);
+}
+
+cbdg_status cbdg_order_parameter(cbdg_lattice *L, double T, int32_t kernel, double lambda,
+                                 int32_t M, cbdg_complex *delta_out, double *n_out) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  st = order_parameter_impl(L, T, kernel, lambda, M);
+  if (st != CBDG_OK) return st;
+  CK(deliver(L, delta_out, L->dout.p, static_cast<size_t>(L->nd) * sizeof(double2)));
+  CK(deliver(L, n_out, L->nout.p, static_cast<size_t>(L->N) * sizeof(double)));
+  return finish(L);
+}
+
+cbdg_status cbdg_ldos(cbdg_lattice *L, const int32_t *, int32_t, int32_t, int32_t, double,
+                      const double *, int32_t, float *) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  return fail(CBDG_ERR_UNSUPPORTED, "cbdg_ldos is not available in this build");
+}
+
+cbdg_status cbdg_scf_step(cbdg_lattice *L, double T, int32_t M, double mix,
+                          double *max_abs_ddelta) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  if (!(mix > 0.0 && mix <= 1.0)) return fail(CBDG_ERR_INVALID_ARG, "mix must be in (0, 1]");
+  st = order_parameter_impl(L, T, CBDG_JACKSON, 0.0, M);
+  if (st != CBDG_OK) return st;
+  CK(launch_mix(L->nd, mix, L->dout.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
+                L->stream));
+  L->launches += 1;
+  double bits = 0.0;
+  CK(cudaMemcpyAsync(&bits, L->scal.as<double>() + kScalMaxDiffBits, sizeof(double),
+                     cudaMemcpyDeviceToHost, L->stream));
+  st = finish(L);
+  if (max_abs_ddelta) *max_abs_ddelta = bits;  // the bits are the double itself
+  return st;
+}
+
+cbdg_status cbdg_get_delta(cbdg_lattice *L, cbdg_complex *delta) {
+  if (!L || !delta) return fail(CBDG_ERR_INVALID_ARG, "NULL argument");
+  CK(cudaSetDevice(L->device));
+  CK(deliver(L, delta, L->delta.p, static_cast<size_t>(L->nd) * sizeof(double2)));
+  CK(cudaStreamSynchronize(L->stream));
+  return CBDG_OK;
+}
+
+cbdg_status cbdg_set_delta(cbdg_lattice *L, const cbdg_complex *delta) {
+  if (!L || !delta) return fail(CBDG_ERR_INVALID_ARG, "NULL argument");
+  CK(cudaSetDevice(L->device));
+  std::vector<cbdg_complex> h;
+  cudaError_t e = host_copy(delta, L->nd, h);
+  if (e != cudaSuccess) return cuda_fail(e, "reading delta");
+  for (auto &z : h) {
+    if (!finite_c(z)) return fail(CBDG_ERR_INVALID_ARG, "delta is not finite");
+    if (!L->cplx && z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex delta on a real lattice");
+  }
+  CK(cudaMemcpyAsync(L->delta.p, h.data(), static_cast<size_t>(L->nd) * sizeof(double2),
+                     cudaMemcpyHostToDevice, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  return CBDG_OK;
+}
+
+cbdg_status cbdg_get_rescale(cbdg_lattice *L, double *a) {
+  if (!L || !a) return fail(CBDG_ERR_INVALID_ARG, "NULL argument");
+  *a = L->last_a;
+  return CBDG_OK;
+}
+
+cbdg_status cbdg_set_option(cbdg_lattice *L, int32_t option, int64_t value) {
+  if (!L) return fail(CBDG_ERR_INVALID_ARG, "lattice is NULL");
+  switch (option) {
+    case CBDG_OPT_QUADRATURE_NODES:
+      if (value < 16 || value > (1 << 24)) return fail(CBDG_ERR_INVALID_ARG, "K out of range");
+      L->K = static_cast<int>(value);
+      return CBDG_OK;
+    case CBDG_OPT_COLUMN_CHUNK:
+      if (value < 0) return fail(CBDG_ERR_INVALID_ARG, "chunk must be >= 0");
+      L->chunk = value;
+      return CBDG_OK;
+    case CBDG_OPT_PROFILE:
+      L->profile = value != 0;
+      return CBDG_OK;
+    case CBDG_OPT_SLAB_WIDTH:
+      if (value != 0 && (value < 2 || value > 32 || (value & (value - 1))))
+        return fail(CBDG_ERR_INVALID_ARG, "slab width must be 0 or a power of two in [2, 32]");
+      L->slab_w = value;
+      return CBDG_OK;
+    case CBDG_OPT_ROW_SPLIT:
+      if (value < 0 || value > 4096) return fail(CBDG_ERR_INVALID_ARG, "row split out of range");
+      L->row_split = value;
+      return CBDG_OK;
+    case CBDG_OPT_WORKSPACE_MB:
+      if (value < 0) return fail(CBDG_ERR_INVALID_ARG, "workspace must be >= 0");
+      L->ws_mb = value;
+      return CBDG_OK;
+    case CBDG_OPT_RESCALE_MILLI:
+      if (value < 100 || value > 100000) return fail(CBDG_ERR_INVALID_ARG, "rescale out of range");
+      L->margin_milli = value;
+      return CBDG_OK;
+  }
+  return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
+}
+
+cbdg_status cbdg_get_option(cbdg_lattice *L, int32_t option, int64_t *value) {
+  if (!L || !value) return fail(CBDG_ERR_INVALID_ARG, "NULL argument");
+  switch (option) {
+    case CBDG_OPT_QUADRATURE_NODES: *value = L->K; return CBDG_OK;
+    case CBDG_OPT_COLUMN_CHUNK: *value = L->chunk; return CBDG_OK;
+    case CBDG_OPT_PROFILE: *value = L->profile; return CBDG_OK;
+    case CBDG_OPT_SLAB_WIDTH: *value = L->slab_w; return CBDG_OK;
+    case CBDG_OPT_ROW_SPLIT: *value = L->row_split; return CBDG_OK;
+    case CBDG_OPT_WORKSPACE_MB: *value = L->ws_mb; return CBDG_OK;
+    case CBDG_OPT_RESCALE_MILLI: *value = L->margin_milli; return CBDG_OK;
+  }
+  return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
+}
+
+cbdg_status cbdg_profile_read(cbdg_lattice *L, double *step_ms, int64_t *step_launches,
+                              double *step_bytes, int32_t reset) {
+  if (!L) return fail(CBDG_ERR_INVALID_ARG, "lattice is NULL");
+  if (step_ms) *step_ms = L->prof_ms;
+  if (step_launches) *step_launches = L->prof_launches;
+  if (step_bytes) *step_bytes = L->prof_bytes;
+  if (reset) {
+    L->prof_ms = 0.0;
+    L->prof_launches = 0;
+    L->prof_bytes = 0.0;
+  }
+  return CBDG_OK;
+}
+
+cbdg_status cbdg_launch_count(cbdg_lattice *L, int64_t *launches, int32_t reset) {
+  if (!L || !launches) return fail(CBDG_ERR_INVALID_ARG, "NULL argument");
+  *launches = L->launches;
+  if (reset) L->launches = 0;
+  return CBDG_OK;
+}
+
+}  // extern "C"

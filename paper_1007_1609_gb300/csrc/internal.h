@@ -1,0 +1,83 @@
+// internal.h -- declarations shared by the translation units of libcbdg.
+// Not part of the public ABI (include/cbdg.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cbdg {
+
+// Parameter record per site in the step precision S, 8 scalars (32 B for
+// float, 64 B for double), pre-multiplied by 2/a so that one stencil
+// application yields 2 H~ j:
+//   [0] 2 (eps - mu)/a   [1] 2 Delta/a   [2..5] 2 t_{s,d}/a (d = 0..3)   [6,7] 0
+constexpr int kParamStride = 8;
+
+// Arguments of one recursion step j_{n+1} = 2 H~ j_n - j_{n-1} over a block
+// of start vectors laid out [2N rows][ld columns] (row 2s electron, 2s+1
+// hole of site s; column b is one start vector).
+struct StepArgs {
+  const void *cur;      // j_n
+  void *prev;           // j_{n-1} on entry, j_{n+1} on exit (in place)
+  const void *params;   // [N][kParamStride] scalars of the step precision
+  double *partials;     // [row_split][3][ld]: sum |j_n|^2, <j_{n+1}|j_n>, symplectic
+  int Lx, Ly;
+  int ld;               // columns (padded to the slab width)
+  int rows_per_cta;     // lattice rows per CTA along y
+};
+
+struct StepConfig {
+  int slab_w;           // columns per CTA
+  int row_split;        // CTAs per column slab along y
+  int threads;
+  size_t smem;
+};
+
+// Recursion step for real on-site (s-wave) lattices with nearest-neighbour
+// hopping.  precision 0: double, 1: float.
+cudaError_t launch_step_real(int precision, const StepArgs &a, const StepConfig &cfg,
+                             cudaStream_t s);
+// Fills cfg for the given shape; returns false if no instantiation fits.
+bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
+                    StepConfig *cfg);
+int slab_width_default(int precision);
+
+// ---- auxiliary kernels (aux.cu) -------------------------------------------
+cudaError_t launch_gershgorin(int N, int n_dirs, int pairing, int Lx, int Ly, int px, int py,
+                              const double *eps, double mu, const double2 *hop,
+                              const double2 *delta, double margin, double *scal, cudaStream_t s);
+cudaError_t launch_coefficients(int M, int K, double T, int kernel, double lambda,
+                                const double *scal, double *f, double *C, cudaStream_t s);
+cudaError_t launch_params_real(int precision, int N, const double *eps, double mu,
+                               const double2 *hop, const double2 *delta, const double *scal,
+                               void *params, cudaStream_t s);
+cudaError_t launch_init_real(int precision, int Lx, int Ly, int px, int py, int ncols, int ld,
+                             const int32_t *sites, const double *eps, double mu,
+                             const double2 *hop, const double2 *delta, const double *scal,
+                             const double *C, int M, void *j0, void *j1, double *mu1,
+                             double2 *dA, double *acc_n, double2 *acc_d, double *mu_ee,
+                             double2 *mu_eh, int mom_stride, cudaStream_t s);
+cudaError_t launch_fold(int n, int M, int ncols, int ld, int row_split, const double *partials,
+                        const double *C, const double *mu1, const double2 *dA, double *acc_n,
+                        double2 *acc_d, double *mu_ee, double2 *mu_eh, int mom_stride,
+                        unsigned int *flags, double tol, cudaStream_t s);
+cudaError_t launch_finalize_onsite(int ncols, const int32_t *sites, double U,
+                                   const double *acc_n, const double2 *acc_d, double2 *dout,
+                                   double *nout, cudaStream_t s);
+cudaError_t launch_mix(int n, double mix, const double2 *dout, double2 *delta, double *scal,
+                       cudaStream_t s);
+cudaError_t launch_ldos_eval(int n_sites, int M, int kernel, double lambda, const double *mu_ee,
+                             const double *energies, int n_E, const double *scal, float *ldos,
+                             cudaStream_t s);
+
+// Device scalars block (double[kScalars]).
+enum {
+  kScalBoundBits = 0,   // Gershgorin bound, as ordered bits (atomicMax)
+  kScalA = 1,           // a = 1.1 * bound
+  kScalMaxDiffBits = 2, // max |Delta_out - Delta|, as ordered bits
+  kScalars = 4
+};
+// Error flags (unsigned int bits).
+enum { kFlagSpectrum = 1u };
+
+}  // namespace cbdg

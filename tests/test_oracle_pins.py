@@ -308,6 +308,17 @@ def test_bond_order_parameter_matches_ed():
             assert d[i, dd] == pytest.approx(ref, abs=1e-12)
 
 
+def test_sampled_sites_match_full_order_parameter():
+    M, K = 64, 1 << 12
+    p = wl.random_swave(5, M, seed=45, T=0.05)
+    lat = as_oracle(p)
+    a = orc.rescale(lat)
+    d, n = orc.order_parameter(lat, a, p.T, M, K)
+    sites = np.array([3, 0, 24, 3, 11])
+    ds, ns = orc.order_parameter_sites(lat, a, p.T, M, K, sites)
+    assert np.array_equal(ds, d[sites]) and np.array_equal(ns, n[sites])
+
+
 def test_order_parameter_converges_to_exact_tanh():
     """As M grows the damped series converges to the exact ED order parameter
     (U/2) sum_k u conj(v) tanh(E_k/2T); the error falls monotonically."""
