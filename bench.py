@@ -209,7 +209,7 @@ def run_gb300(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    p = wl.swave_disordered(L, M, seed=SEED)
+    p = wl.swave_disordered(args.lattice, args.moments, seed=SEED)
     units_per_step = p.N * math.ceil(p.M / 2)
     stream = torch.cuda.Stream(device=dev)
 
@@ -244,21 +244,23 @@ def run_gb300(args):
     # ---------------- end to end through the C ABI with host buffers
     host_delta = torch.from_numpy(np.ascontiguousarray(p.delta0)).pin_memory()
     host_out = torch.empty_like(host_delta).pin_memory()
-    lat_e = cbdg.Lattice(p, precision="fp32", stream=stream)
-    for _ in range(1):
-        cbdg.cbdg_set_delta(lat_e.handle, host_delta)
-        cbdg.cbdg_scf_step(lat_e.handle, p.T, p.M, p.mix)
-        cbdg.cbdg_get_delta(lat_e.handle, host_out)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        cbdg.cbdg_set_delta(lat_e.handle, host_delta)
-        cbdg.cbdg_scf_step(lat_e.handle, p.T, p.M, p.mix)
-        cbdg.cbdg_get_delta(lat_e.handle, host_out)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    lat_e.close()
-    e2e_value = world * units_per_step * args.steps / e2e_s
+    e2e_value = None
+    if not args.no_e2e:
+        lat_e = cbdg.Lattice(p, precision="fp32", stream=stream)
+        for _ in range(1):
+            cbdg.cbdg_set_delta(lat_e.handle, host_delta)
+            cbdg.cbdg_scf_step(lat_e.handle, p.T, p.M, p.mix)
+            cbdg.cbdg_get_delta(lat_e.handle, host_out)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            cbdg.cbdg_set_delta(lat_e.handle, host_delta)
+            cbdg.cbdg_scf_step(lat_e.handle, p.T, p.M, p.mix)
+            cbdg.cbdg_get_delta(lat_e.handle, host_out)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        lat_e.close()
+        e2e_value = world * units_per_step * args.steps / e2e_s
 
     line = None
     if rank == 0:
@@ -293,8 +295,8 @@ def run_gb300(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "s-wave disordered 128x128 open lattice, W=1.0 (seed 1001), "
-                                   "t=1, mu=-0.5, U=2, T=0.01, M=1024, all 16384 sites as "
+            "config": {"workload": f"s-wave disordered {p.Lx}x{p.Ly} open lattice, W=1.0 (seed 1001), "
+                                   f"t=1, mu=-0.5, U=2, T=0.01, M={p.M}, all {p.N} sites as "
                                    "start vectors, FP32 recursion with FP64 folds",
                        "step": "one self-consistency iteration",
                        "units_per_step": units_per_step,
@@ -303,8 +305,9 @@ def run_gb300(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_delta.numel() * 16),
-                    "d2h_bytes_per_step": int(host_out.numel() * 16 + 8)},
+            "e2e": None if e2e_value is None else {
+                "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(host_delta.numel() * 16),
+                "d2h_bytes_per_step": int(host_out.numel() * 16 + 8)},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
             "scf_max_abs_ddelta": diffs[-1],
@@ -355,6 +358,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lattice", type=int, default=L,
+                    help="lattice side (profiling of smaller cases; the metric is quoted at 128)")
+    ap.add_argument("--moments", type=int, default=M)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
