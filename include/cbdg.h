@@ -147,9 +147,11 @@ enum {
   CBDG_OPT_SLAB_WIDTH = 3,       /* columns per CTA of the recursion kernel; 0 = automatic */
   CBDG_OPT_ROW_SPLIT = 4,        /* CTAs per column slab along y; 0 = automatic */
   CBDG_OPT_WORKSPACE_MB = 5,     /* cap on the recursion vectors' memory; 0 = automatic */
-  CBDG_OPT_RESCALE_MILLI = 6     /* a = (value/1000) * Gershgorin bound; default 1100 (1.1).
+  CBDG_OPT_RESCALE_MILLI = 6,    /* a = (value/1000) * Gershgorin bound; default 1100 (1.1).
                                     Below 1000 the spectrum may leave [-1, 1] and calls
                                     then fail with CBDG_ERR_SPECTRUM */
+  CBDG_OPT_PIPELINE_DEPTH = 7    /* lattice rows the recursion kernel stages ahead (1..4);
+                                    0 = automatic */
 };
 cbdg_status cbdg_set_option(cbdg_lattice *lat, int32_t option, int64_t value);
 cbdg_status cbdg_get_option(cbdg_lattice *lat, int32_t option, int64_t *value);

@@ -36,6 +36,7 @@ CBDG_OPT_SLAB_WIDTH = 3
 CBDG_OPT_ROW_SPLIT = 4
 CBDG_OPT_WORKSPACE_MB = 5
 CBDG_OPT_RESCALE_MILLI = 6
+CBDG_OPT_PIPELINE_DEPTH = 7
 
 
 class CbdgError(RuntimeError):

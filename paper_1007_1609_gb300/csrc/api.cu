@@ -107,7 +107,7 @@ struct cbdg_lattice {
   DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
   // options
   int K = 65536;
-  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100;
+  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0;
   int profile = 0;
   std::vector<cudaEvent_t> events;
   double prof_ms = 0.0, prof_bytes = 0.0;
@@ -209,7 +209,8 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     const int ncols = std::min(chunk, n_sites - c0);
     const int ld = ((ncols + W - 1) / W) * W;
     StepConfig cfg;
-    if (!plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split), &cfg))
+    if (!plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
+                        static_cast<int>(L->depth), &cfg))
       return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d with %d columns", L->Lx, ld);
     const size_t vbytes = rows * ld * es;
     CK(L->vec0.ensure(vbytes));
@@ -223,7 +224,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     CK(cudaMemsetAsync(L->vec1.p, 0, vbytes, L->stream));
     double *mee = mom_ee ? mom_ee + static_cast<size_t>(c0) * M : nullptr;
     double2 *meh = mom_eh ? mom_eh + static_cast<size_t>(c0) * M * mom_stride : nullptr;
-    CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, ld, sites + c0,
+    CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, cfg.slab_w, sites + c0,
                         L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
                         L->scal.as<double>(), L->C.as<double>(), M, L->vec0.p, L->vec1.p,
                         L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
@@ -241,6 +242,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     StepArgs a;
     a.params = L->params.p;
     a.partials = L->partials.as<double>();
+    a.flags = L->flags.as<unsigned int>();
     a.Lx = L->Lx;
     a.Ly = L->Ly;
     a.ld = ld;
@@ -293,6 +295,8 @@ cbdg_status finish(cbdg_lattice *L) {
                      L->stream));
   CK(cudaStreamSynchronize(L->stream));
   L->last_a = a;
+  if (flags & kFlagTimeout)
+    return fail(CBDG_ERR_CUDA, "a recursion kernel gave up waiting for a staged copy");
   if (flags & kFlagSpectrum)
     return fail(CBDG_ERR_SPECTRUM, "a Chebyshev moment exceeded 1 in magnitude (a = %g too small)", a);
   return CBDG_OK;
@@ -591,6 +595,10 @@ cbdg_status cbdg_set_option(cbdg_lattice *L, int32_t option, int64_t value) {
       if (value < 100 || value > 100000) return fail(CBDG_ERR_INVALID_ARG, "rescale out of range");
       L->margin_milli = value;
       return CBDG_OK;
+    case CBDG_OPT_PIPELINE_DEPTH:
+      if (value < 0 || value > 4) return fail(CBDG_ERR_INVALID_ARG, "depth must be in [0, 4]");
+      L->depth = value;
+      return CBDG_OK;
   }
   return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
 }
@@ -605,6 +613,7 @@ cbdg_status cbdg_get_option(cbdg_lattice *L, int32_t option, int64_t *value) {
     case CBDG_OPT_ROW_SPLIT: *value = L->row_split; return CBDG_OK;
     case CBDG_OPT_WORKSPACE_MB: *value = L->ws_mb; return CBDG_OK;
     case CBDG_OPT_RESCALE_MILLI: *value = L->margin_milli; return CBDG_OK;
+    case CBDG_OPT_PIPELINE_DEPTH: *value = L->depth; return CBDG_OK;
   }
   return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
 }

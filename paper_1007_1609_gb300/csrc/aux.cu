@@ -114,7 +114,7 @@ __device__ __forceinline__ int neighbour(int Lx, int Ly, int px, int py, int x, 
 // the fold: mu_0 = 1, mu_1 = (eps_i - mu)/a, <h_i|e_i> = 0,
 // <h_i|H~|e_i> = conj(Delta_i)/a.
 template <typename S>
-__global__ void init_real_kernel(int Lx, int Ly, int px, int py, int ncols, int ld,
+__global__ void init_real_kernel(int Lx, int Ly, int px, int py, int ncols, int W,
                                  const int32_t *sites, const double *eps, double mu,
                                  const double2 *hop, const double2 *delta, const double *scal,
                                  const double *C, int M, S *j0, S *j1, double *mu1, double2 *dA,
@@ -125,17 +125,19 @@ __global__ void init_real_kernel(int Lx, int Ly, int px, int py, int ncols, int 
   const double a = scal[kScalA];
   const int i = sites[b];
   const int x = i % Lx, y = i / Lx;
+  const size_t rows = 2 * static_cast<size_t>(Lx) * Ly;
   const double m1 = (eps[i] - mu) / a;
   const double2 dl = delta[i];
-  j0[(2 * static_cast<size_t>(i)) * ld + b] = static_cast<S>(1);
-  j1[(2 * static_cast<size_t>(i)) * ld + b] = static_cast<S>(m1);
-  j1[(2 * static_cast<size_t>(i) + 1) * ld + b] = static_cast<S>(dl.x / a);
+  j0[blocked_index(2 * static_cast<size_t>(i), b, rows, W)] = static_cast<S>(1);
+  j1[blocked_index(2 * static_cast<size_t>(i), b, rows, W)] = static_cast<S>(m1);
+  j1[blocked_index(2 * static_cast<size_t>(i) + 1, b, rows, W)] = static_cast<S>(dl.x / a);
   const int DX[4] = {1, -1, 0, 0}, DY[4] = {0, 0, 1, -1};
   for (int d = 0; d < 4; ++d) {
     const int j = neighbour(Lx, Ly, px, py, x, y, DX[d], DY[d]);
     if (j < 0) continue;
     // H_{e_j e_i} = -t_{j -> i} = -conj(t_{i -> j})
-    j1[(2 * static_cast<size_t>(j)) * ld + b] = static_cast<S>(-hop[static_cast<size_t>(i) * 4 + d].x / a);
+    j1[blocked_index(2 * static_cast<size_t>(j), b, rows, W)] =
+        static_cast<S>(-hop[static_cast<size_t>(i) * 4 + d].x / a);
   }
   mu1[b] = m1;
   dA[b] = make_double2(dl.x / a, -dl.y / a);  // conj(Delta_i)/a
@@ -256,7 +258,7 @@ cudaError_t launch_params_real(int precision, int N, const double *eps, double m
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_real(int precision, int Lx, int Ly, int px, int py, int ncols, int ld,
+cudaError_t launch_init_real(int precision, int Lx, int Ly, int px, int py, int ncols, int W,
                              const int32_t *sites, const double *eps, double mu,
                              const double2 *hop, const double2 *delta, const double *scal,
                              const double *C, int M, void *j0, void *j1, double *mu1,
@@ -265,12 +267,12 @@ cudaError_t launch_init_real(int precision, int Lx, int Ly, int px, int py, int 
   if (ncols <= 0) return cudaSuccess;
   if (precision == 1)
     init_real_kernel<float><<<blocks(ncols, 128), 128, 0, s>>>(
-        Lx, Ly, px, py, ncols, ld, sites, eps, mu, hop, delta, scal, C, M,
+        Lx, Ly, px, py, ncols, W, sites, eps, mu, hop, delta, scal, C, M,
         static_cast<float *>(j0), static_cast<float *>(j1), mu1, dA, acc_n, acc_d, mu_ee, mu_eh,
         mom_stride);
   else
     init_real_kernel<double><<<blocks(ncols, 128), 128, 0, s>>>(
-        Lx, Ly, px, py, ncols, ld, sites, eps, mu, hop, delta, scal, C, M,
+        Lx, Ly, px, py, ncols, W, sites, eps, mu, hop, delta, scal, C, M,
         static_cast<double *>(j0), static_cast<double *>(j1), mu1, dA, acc_n, acc_d, mu_ee, mu_eh,
         mom_stride);
   return cudaGetLastError();

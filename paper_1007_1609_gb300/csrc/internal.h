@@ -14,24 +14,33 @@ namespace cbdg {
 constexpr int kParamStride = 8;
 
 // Arguments of one recursion step j_{n+1} = 2 H~ j_n - j_{n-1} over a block
-// of start vectors laid out [2N rows][ld columns] (row 2s electron, 2s+1
-// hole of site s; column b is one start vector).
+// of ld start vectors.  Vectors use the slab-blocked layout: column slab
+// c = b / W is a row-major [2N][W] block at offset c * 2N * W, so element
+// (row r, column b) sits at (b / W) * 2N*W + r*W + (b % W); row 2s is the
+// electron and 2s+1 the hole of site s = x + Lx*y.
 struct StepArgs {
   const void *cur;      // j_n
   void *prev;           // j_{n-1} on entry, j_{n+1} on exit (in place)
   const void *params;   // [N][kParamStride] scalars of the step precision
   double *partials;     // [row_split][3][ld]: sum |j_n|^2, <j_{n+1}|j_n>, symplectic
+  unsigned int *flags;  // error bits (kFlagTimeout when a staged copy never arrived)
   int Lx, Ly;
-  int ld;               // columns (padded to the slab width)
+  int ld;               // columns (a multiple of the slab width)
   int rows_per_cta;     // lattice rows per CTA along y
 };
 
 struct StepConfig {
-  int slab_w;           // columns per CTA
+  int slab_w;           // columns per CTA (W)
+  int depth;            // lattice rows staged ahead (D)
   int row_split;        // CTAs per column slab along y
   int threads;
   size_t smem;
 };
+
+// Offset of element (row r, column b) in the slab-blocked layout.
+__host__ __device__ inline size_t blocked_index(size_t r, size_t b, size_t rows, int W) {
+  return (b / W) * rows * W + r * W + (b % W);
+}
 
 // Recursion step for real on-site (s-wave) lattices with nearest-neighbour
 // hopping.  precision 0: double, 1: float.
@@ -39,7 +48,7 @@ cudaError_t launch_step_real(int precision, const StepArgs &a, const StepConfig 
                              cudaStream_t s);
 // Fills cfg for the given shape; returns false if no instantiation fits.
 bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
-                    StepConfig *cfg);
+                    int want_depth, StepConfig *cfg);
 int slab_width_default(int precision);
 
 // ---- auxiliary kernels (aux.cu) -------------------------------------------
@@ -51,7 +60,7 @@ cudaError_t launch_coefficients(int M, int K, double T, int kernel, double lambd
 cudaError_t launch_params_real(int precision, int N, const double *eps, double mu,
                                const double2 *hop, const double2 *delta, const double *scal,
                                void *params, cudaStream_t s);
-cudaError_t launch_init_real(int precision, int Lx, int Ly, int px, int py, int ncols, int ld,
+cudaError_t launch_init_real(int precision, int Lx, int Ly, int px, int py, int ncols, int W,
                              const int32_t *sites, const double *eps, double mu,
                              const double2 *hop, const double2 *delta, const double *scal,
                              const double *C, int M, void *j0, void *j1, double *mu1,
@@ -78,6 +87,6 @@ enum {
   kScalars = 4
 };
 // Error flags (unsigned int bits).
-enum { kFlagSpectrum = 1u };
+enum { kFlagSpectrum = 1u, kFlagTimeout = 2u };
 
 }  // namespace cbdg

@@ -8,19 +8,27 @@
 //     A = <j_n|j_n>,  B = <j_{n+1}|j_n>,  C = sum_s (u'_s v_s - v'_s u_s)
 // where (u, v) are the electron / hole rows of j_n and (u', v') of j_{n+1}.
 //
-// Layout: vectors are [2N rows][ld columns], row 2s electron and 2s+1 hole
-// of site s = x + Lx*y, so lattice row y is the contiguous block of 2*Lx
-// vector rows [2*Lx*y, 2*Lx*(y+1)).  A CTA owns a slab of W columns and a
-// range of lattice rows, and marches along y: a ring of four shared-memory
-// slots holds the j_n rows y-1, y, y+1 (and y+2 in flight), staged with
-// cp.async 16-byte copies together with the row's parameter records, so
-// every element of j_n is read from HBM once per step and every stencil
-// neighbour comes from shared memory.  j_{n-1} is streamed through registers
-// one row ahead; j_{n+1} is stored straight to HBM.  Each Hamiltonian
-// parameter is read once per row for all W columns.  Column sums use Kahan
-// compensation in FP32 and are reduced across the CTA in FP64 in a fixed
-// order (deterministic, no atomics).
+// Layout (slab-blocked [2N x B]): the B start vectors are cut into slabs of
+// W columns and each slab is stored as its own row-major [2N][W] block,
+//     element (row r, column b) at (b / W) * 2N*W + r*W + (b % W),
+// with row 2s the electron and 2s+1 the hole of site s = x + Lx*y.  Lattice
+// row y of one slab is therefore one contiguous 2*Lx*W-element block, which
+// streams from HBM as a single run.
+//
+// A CTA owns one slab and a range of lattice rows and marches along y.  A
+// pipeline D rows deep stages, per lattice row, the j_n block, the j_{n-1}
+// block and the row's parameter records into shared-memory rings (3 + D
+// slots for j_n: rows y-1, y, y+1 plus D in flight; 2 + D for j_{n-1}) with
+// TMA bulk copies (cp.async.bulk) issued by one thread and completing on one
+// mbarrier per slot; every wait is bounded in time and a lost copy sets an
+// error flag instead of hanging.  Every element of j_n and j_{n-1} is read from HBM once per step
+// and every stencil neighbour comes from shared memory; each Hamiltonian
+// parameter is read once per row for all W columns; j_{n+1} is stored
+// straight to HBM.  Column sums use Kahan compensation in FP32 (plain FP64
+// sums in FP64) and are reduced across the CTA in FP64 in a fixed order:
+// deterministic, no atomics.
 #include <algorithm>
+#include <cmath>
 
 #include "internal.h"
 
@@ -40,16 +48,49 @@ struct Vec<double> {
   static constexpr int N = 2;
 };
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-  unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// One bulk copy global -> shared (TMA, untiled), completing on mbarrier bar.
+// Addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(unsigned dst, const void *src, unsigned bytes,
+                                          unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for phase `parity` of bar to complete; gives up after ~limit_ns
+// (returns false) so that a lost copy can never hang the GPU.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u && global_ns() - t0 > limit_ns) return false;
+  }
 }
 
 // Compensated (Kahan) accumulator in FP32; plain accumulation in FP64.
@@ -72,99 +113,108 @@ struct Acc<float> {
 };
 
 template <typename V, typename S>
-__device__ __forceinline__ S &comp(V &v, int j) {
-  return reinterpret_cast<S *>(&v)[j];
+__device__ __forceinline__ S comp(const V &v, int j) {
+  return reinterpret_cast<const S *>(&v)[j];
+}
+template <typename V, typename S>
+__device__ __forceinline__ void set_comp(V &v, int j, S x) {
+  reinterpret_cast<S *>(&v)[j] = x;
 }
 
-constexpr int kRing = 4;
-
-template <typename S, int W, int NT, int MAXX>
+template <typename S, int W, int NT, int MAXX, int D>
 __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
   using V = typename Vec<S>::T;
   constexpr int VEC = Vec<S>::N;
   constexpr int QUADS = W / VEC;       // 16-byte chunks per row segment
   constexpr int XSLOTS = NT / QUADS;   // threads along x
-  constexpr int PV = 16 / sizeof(S);   // scalars per 16-byte chunk
+  constexpr int JS = 3 + D;            // j_n ring slots
+  constexpr int OS = 2 + D;            // j_{n-1} ring slots
   static_assert(W % VEC == 0 && NT % QUADS == 0, "bad slab shape");
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S *sv = reinterpret_cast<S *>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[3 + D];
+  __shared__ int abort_flag;
   const int Lx = a.Lx, Ly = a.Ly;
-  const size_t ld = static_cast<size_t>(a.ld);
-  const int vslot = 2 * Lx * W;
-  const int pslot = Lx * kParamStride;
-  S *sp = sv + kRing * vslot;
+  const int rowel = 2 * Lx * W;        // elements of one lattice row of a slab
+  const int pel = Lx * kParamStride;   // parameter scalars of one lattice row
+  S *sj = reinterpret_cast<S *>(smem_raw);
+  S *so = sj + JS * rowel;
+  S *sp = so + OS * rowel;
 
   const int t = threadIdx.x;
   const int q = t % QUADS;
   const int xs = t / QUADS;
-  const int c0 = blockIdx.x * W;
   const int y0 = blockIdx.y * a.rows_per_cta;
   const int rows = min(a.rows_per_cta, Ly - y0);
-  const S *cur = static_cast<const S *>(a.cur);
-  S *prev = static_cast<S *>(a.prev);
+  const size_t slab = static_cast<size_t>(blockIdx.x) * (static_cast<size_t>(2) * Lx * Ly * W);
+  const S *cur = static_cast<const S *>(a.cur) + slab;
+  S *prev = static_cast<S *>(a.prev) + slab;
   const S *par = static_cast<const S *>(a.params);
+  const unsigned row_bytes = static_cast<unsigned>(rowel * sizeof(S));
+  const unsigned par_bytes = static_cast<unsigned>(pel * sizeof(S));
+  constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
-  // Stage lattice row (y0 - 1 + k) of j_n and its parameters into slot k % 4.
+  if (t == 0) {
+    for (int k = 0; k < JS; ++k) mbar_init(smem_addr(&bars[k]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+
+  // Load k (issued by thread 0, one TMA bulk copy per block): j_n and the
+  // parameters of lattice row y0 - 1 + k (periodic wrap; an open edge has
+  // zero hopping on the wrapped bond), plus j_{n-1} of the computed row
+  // y0 + k - 1 when that row belongs to this CTA.  All complete on bars[k % JS].
   auto issue = [&](int k) {
     int y = y0 - 1 + k;
     y = (y < 0) ? y + Ly : (y >= Ly ? y - Ly : y);
-    const int slot = k % kRing;
-    const S *src = cur + static_cast<size_t>(2 * Lx) * y * ld + c0;
-    S *dst = sv + slot * vslot;
-    for (int c = t; c < 2 * Lx * QUADS; c += NT) {
-      const int r = c / QUADS, qq = c - r * QUADS;
-      cp_async16(dst + r * W + qq * VEC, src + r * ld + qq * VEC);
-    }
-    const S *psrc = par + static_cast<size_t>(y) * Lx * kParamStride;
-    S *pdst = sp + slot * pslot;
-    for (int c = t; c < pslot / PV; c += NT) cp_async16(pdst + c * PV, psrc + c * PV);
+    const int r = k - 1;
+    const bool with_old = (r >= 0 && r < rows);
+    const unsigned bar = smem_addr(&bars[k % JS]);
+    mbar_expect_tx(bar, row_bytes + par_bytes + (with_old ? row_bytes : 0u));
+    bulk_load(smem_addr(sj + (k % JS) * rowel), cur + static_cast<size_t>(y) * rowel, row_bytes, bar);
+    bulk_load(smem_addr(sp + (k % JS) * pel), par + static_cast<size_t>(y) * pel, par_bytes, bar);
+    if (with_old)
+      bulk_load(smem_addr(so + (r % OS) * rowel), prev + static_cast<size_t>(y0 + r) * rowel,
+                row_bytes, bar);
   };
-  // j_{n-1} of lattice row y0 + i for this thread's sites.
-  auto load_old = [&](int i, V *ou, V *ov) {
-    const size_t rowbase = static_cast<size_t>(2) * ((y0 + i) * static_cast<size_t>(Lx));
-#pragma unroll
-    for (int k = 0; k < MAXX; ++k) {
-      const int x = xs + k * XSLOTS;
-      if (x < Lx) {
-        const S *p = prev + (rowbase + 2 * x) * ld + c0 + q * VEC;
-        ou[k] = __ldcs(reinterpret_cast<const V *>(p));
-        ov[k] = __ldcs(reinterpret_cast<const V *>(p + ld));
-      }
-    }
-  };
-
-  issue(0);
-  cp_async_commit();
-  issue(1);
-  cp_async_commit();
-  issue(2);
-  cp_async_commit();
-
-  V ou[MAXX], ov[MAXX];
-  load_old(0, ou, ov);
+  int issued = 0;  // loads issued so far (thread 0's view; loads are issued in order)
+  if (t == 0) {
+    for (int k = 0; k < D + 2 && k <= rows + 1; ++k) issue(k);
+  }
+  issued = min(D + 2, rows + 2);
 
   Acc<S> accA[VEC], accB[VEC], accC[VEC];
 
+  int waited = 0;  // loads this thread has seen complete
+  bool ok = true;
   for (int i = 0; i < rows; ++i) {
-    if (i + 3 <= rows + 1) issue(i + 3);
-    cp_async_commit();  // possibly empty: keeps one group per iteration
-    V nu[MAXX], nv[MAXX];
-    if (i + 1 < rows) load_old(i + 1, nu, nv);
-    cp_async_wait<1>();  // groups up to i + 2 (rows y-1, y, y+1) have landed
+    if (i + 2 + D <= rows + 1) {
+      if (t == 0) issue(i + 2 + D);
+      issued = i + 3 + D;
+    }
+    // loads up to i + 2: rows y-1, y, y+1 of j_n and j_{n-1} of y
+    for (; waited <= i + 2; ++waited) {
+      if (!mbar_wait(smem_addr(&bars[waited % JS]), (waited / JS) & 1u, kWaitLimitNs)) {
+        ok = false;
+        break;
+      }
+    }
+    if (!ok) atomicOr(&abort_flag, 1);
     __syncthreads();
+    if (abort_flag) break;
 
-    const S *rm = sv + (i % kRing) * vslot;        // lattice row y - 1
-    const S *rc = sv + ((i + 1) % kRing) * vslot;  // y
-    const S *rp = sv + ((i + 2) % kRing) * vslot;  // y + 1
-    const S *pc = sp + ((i + 1) % kRing) * pslot;
-    const size_t rowbase = static_cast<size_t>(2) * ((y0 + i) * static_cast<size_t>(Lx));
+    const S *rm = sj + (i % JS) * rowel;        // lattice row y - 1
+    const S *rc = sj + ((i + 1) % JS) * rowel;  // y
+    const S *rp = sj + ((i + 2) % JS) * rowel;  // y + 1
+    const S *ro = so + (i % OS) * rowel;        // j_{n-1} of y
+    const S *pc = sp + ((i + 1) % JS) * pel;
+    S *out = prev + static_cast<size_t>(y0 + i) * rowel;
     const int off = q * VEC;
 #pragma unroll
     for (int k = 0; k < MAXX; ++k) {
       const int x = xs + k * XSLOTS;
       if (x < Lx) {
-        // periodic wrap of the index; an open edge has t = 0 on that bond
         const int xl = (x == 0) ? Lx - 1 : x - 1;
         const int xr = (x == Lx - 1) ? 0 : x + 1;
         const V u = *reinterpret_cast<const V *>(rc + (2 * x) * W + off);
@@ -177,41 +227,47 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
         const V vu = *reinterpret_cast<const V *>(rp + (2 * x + 1) * W + off);
         const V ud = *reinterpret_cast<const V *>(rm + (2 * x) * W + off);
         const V vd = *reinterpret_cast<const V *>(rm + (2 * x + 1) * W + off);
+        const V uo = *reinterpret_cast<const V *>(ro + (2 * x) * W + off);
+        const V vo = *reinterpret_cast<const V *>(ro + (2 * x + 1) * W + off);
         const S *pp = pc + x * kParamStride;
         const S e = pp[0], d = pp[1], t0 = pp[2], t1 = pp[3], t2 = pp[4], t3 = pp[5];
         V un, vn;
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
-          const S uj = comp<const V, const S>(u, j), vj = comp<const V, const S>(v, j);
+          const S uj = comp<V, S>(u, j), vj = comp<V, S>(v, j);
           // 2 H~ j_n: electron row  (eps-mu) u + Delta v - sum_d t_d u_d
           //           hole row      Delta u - (eps-mu) v + sum_d t_d v_d
           const S hu = e * uj + d * vj -
-                       (t0 * comp<const V, const S>(ur, j) + t1 * comp<const V, const S>(ul, j) +
-                        t2 * comp<const V, const S>(uu, j) + t3 * comp<const V, const S>(ud, j));
+                       (t0 * comp<V, S>(ur, j) + t1 * comp<V, S>(ul, j) +
+                        t2 * comp<V, S>(uu, j) + t3 * comp<V, S>(ud, j));
           const S hv = d * uj - e * vj +
-                       (t0 * comp<const V, const S>(vr, j) + t1 * comp<const V, const S>(vl, j) +
-                        t2 * comp<const V, const S>(vu, j) + t3 * comp<const V, const S>(vd, j));
-          const S unj = hu - comp<V, S>(ou[k], j);
-          const S vnj = hv - comp<V, S>(ov[k], j);
-          comp<V, S>(un, j) = unj;
-          comp<V, S>(vn, j) = vnj;
+                       (t0 * comp<V, S>(vr, j) + t1 * comp<V, S>(vl, j) +
+                        t2 * comp<V, S>(vu, j) + t3 * comp<V, S>(vd, j));
+          const S unj = hu - comp<V, S>(uo, j);
+          const S vnj = hv - comp<V, S>(vo, j);
+          set_comp<V, S>(un, j, unj);
+          set_comp<V, S>(vn, j, vnj);
           accA[j].add(uj * uj + vj * vj);
           accB[j].add(unj * uj + vnj * vj);
           accC[j].add(unj * vj - vnj * uj);
         }
-        S *dst = prev + (rowbase + 2 * x) * ld + c0 + off;
-        __stcs(reinterpret_cast<V *>(dst), un);
-        __stcs(reinterpret_cast<V *>(dst + ld), vn);
+        __stcs(reinterpret_cast<V *>(out + (2 * x) * W + off), un);
+        __stcs(reinterpret_cast<V *>(out + (2 * x + 1) * W + off), vn);
       }
     }
-    __syncthreads();  // slot (i % 4) is refilled by the next iteration
-#pragma unroll
-    for (int k = 0; k < MAXX; ++k) {
-      ou[k] = nu[k];
-      ov[k] = nv[k];
-    }
+    __syncthreads();  // the slots of load i are refilled by the next iteration
   }
-  cp_async_wait<0>();
+  if (abort_flag) {
+    // A copy did not arrive in time: report it, let the copies in flight
+    // land (bounded again) so no TMA write targets freed shared memory, and
+    // leave without writing partial sums.
+    if (t == 0) {
+      atomicOr(a.flags, kFlagTimeout);
+      for (int k = waited; k < issued; ++k)
+        if (!mbar_wait(smem_addr(&bars[k % JS]), (k / JS) & 1u, kWaitLimitNs)) break;
+    }
+    return;
+  }
   __syncthreads();
 
   // Fixed-order CTA reduction of the column sums, in FP64.
@@ -223,129 +279,148 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
     red[(2 * XSLOTS + xs) * W + q * VEC + j] = accC[j].value();
   }
   __syncthreads();
+  const size_t c0 = static_cast<size_t>(blockIdx.x) * W;
   for (int idx = t; idx < 3 * W; idx += NT) {
     const int k = idx / W, col = idx - k * W;
     double s = 0.0;
     for (int z = 0; z < XSLOTS; ++z) s += red[(k * XSLOTS + z) * W + col];
-    a.partials[(static_cast<size_t>(blockIdx.y) * 3 + k) * ld + c0 + col] = s;
+    a.partials[(static_cast<size_t>(blockIdx.y) * 3 + k) * a.ld + c0 + col] = s;
   }
-}
-
-template <typename S, int W, int NT, int MAXX>
-size_t smem_bytes(int Lx) {
-  constexpr int QUADS = W / Vec<S>::N;
-  constexpr int XSLOTS = NT / QUADS;
-  size_t ring = static_cast<size_t>(kRing) * (2 * Lx * W + Lx * kParamStride) * sizeof(S);
-  size_t red = static_cast<size_t>(3) * XSLOTS * W * sizeof(double);
-  return std::max(ring, red);
-}
-
-template <typename S, int W, int NT, int MAXX>
-cudaError_t launch_one(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
-  auto k = step_real_kernel<S, W, NT, MAXX>;
-  static bool attr_set = false;  // per instantiation; set once per process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  dim3 grid(a.ld / W, cfg.row_split);
-  k<<<grid, NT, cfg.smem, s>>>(a);
-  return cudaGetLastError();
 }
 
 constexpr int kThreads = 256;
+// Dynamic shared memory cap: the 227 KB per-CTA opt-in limit less room for
+// the kernel's static mbarriers.
+constexpr int kMaxDynSmem = 227 * 1024 - 1024;
 
-// Largest x-extent each instantiation handles: MAXX * XSLOTS.
+template <typename S, int W, int D>
+size_t smem_bytes(int Lx) {
+  constexpr int QUADS = W / Vec<S>::N;
+  constexpr int XSLOTS = kThreads / QUADS;
+  const size_t rowel = static_cast<size_t>(2) * Lx * W;
+  const size_t ring = ((3 + D) * rowel + (2 + D) * rowel +
+                       (3 + D) * static_cast<size_t>(Lx) * kParamStride) * sizeof(S);
+  const size_t red = static_cast<size_t>(3) * XSLOTS * W * sizeof(double);
+  return std::max(ring, red);
+}
+
+template <typename S, int W, int MAXX, int D>
+cudaError_t launch_one(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
+  auto k = step_real_kernel<S, W, kThreads, MAXX, D>;
+  static int attr_dev = -1;  // set once per instantiation and device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  dim3 grid(a.ld / W, cfg.row_split);
+  k<<<grid, kThreads, cfg.smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename S, int W>
 int xslots() {
   return kThreads / (W / Vec<S>::N);
 }
 
-template <typename S, int W>
+template <typename S, int W, int D>
 cudaError_t dispatch_maxx(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
   const int xsl = xslots<S, W>();
-  if (a.Lx <= 1 * xsl) return launch_one<S, W, kThreads, 1>(a, cfg, s);
-  if (a.Lx <= 2 * xsl) return launch_one<S, W, kThreads, 2>(a, cfg, s);
-  if (a.Lx <= 4 * xsl) return launch_one<S, W, kThreads, 4>(a, cfg, s);
-  if (a.Lx <= 8 * xsl) return launch_one<S, W, kThreads, 8>(a, cfg, s);
+  if (a.Lx <= 1 * xsl) return launch_one<S, W, 1, D>(a, cfg, s);
+  if (a.Lx <= 2 * xsl) return launch_one<S, W, 2, D>(a, cfg, s);
+  if (a.Lx <= 4 * xsl) return launch_one<S, W, 4, D>(a, cfg, s);
+  if (a.Lx <= 8 * xsl) return launch_one<S, W, 8, D>(a, cfg, s);
   return cudaErrorInvalidValue;
 }
 
 template <typename S, int W>
-size_t smem_for(int Lx) {
-  return smem_bytes<S, W, kThreads, 1>(Lx);  // MAXX does not change the footprint
+cudaError_t dispatch_depth(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
+  switch (cfg.depth) {
+    case 1: return dispatch_maxx<S, W, 1>(a, cfg, s);
+    case 2: return dispatch_maxx<S, W, 2>(a, cfg, s);
+    case 3: return dispatch_maxx<S, W, 3>(a, cfg, s);
+    case 4: return dispatch_maxx<S, W, 4>(a, cfg, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename S>
-size_t smem_dispatch(int W, int Lx) {
+size_t smem_dispatch(int W, int D, int Lx) {
   constexpr int V = Vec<S>::N;
+#define CBDG_SMEM_CASE(w)                                                       \
+  case w:                                                                       \
+    return D == 1   ? smem_bytes<S, w, 1>(Lx)                                   \
+           : D == 2 ? smem_bytes<S, w, 2>(Lx)                                   \
+           : D == 3 ? smem_bytes<S, w, 3>(Lx)                                   \
+                    : smem_bytes<S, w, 4>(Lx);
   switch (W) {
-    case V: return smem_for<S, V>(Lx);
-    case 2 * V: return smem_for<S, 2 * V>(Lx);
-    case 4 * V: return smem_for<S, 4 * V>(Lx);
-    case 8 * V: return smem_for<S, 8 * V>(Lx);
+    CBDG_SMEM_CASE(V)
+    CBDG_SMEM_CASE(2 * V)
+    CBDG_SMEM_CASE(4 * V)
+    CBDG_SMEM_CASE(8 * V)
   }
+#undef CBDG_SMEM_CASE
   return 0;
 }
 
 template <typename S>
 int max_lx(int W) {
-  constexpr int V = Vec<S>::N;
-  return 8 * kThreads / (W / V);
+  return 8 * kThreads / (W / Vec<S>::N);
 }
 
 }  // namespace
 
-int slab_width_default(int precision) { return precision == 1 ? 32 : 16; }
+int slab_width_default(int precision) { return precision == 1 ? 8 : 4; }
 
 bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
-                    StepConfig *cfg) {
+                    int want_depth, StepConfig *cfg) {
   const int vecn = precision == 1 ? 4 : 2;
   int W = want_w > 0 ? want_w : slab_width_default(precision);
-  // the slab must divide the padded column count and fit in shared memory
-  auto smem = [&](int w) {
-    return precision == 1 ? smem_dispatch<float>(w, Lx) : smem_dispatch<double>(w, Lx);
+  const int d0 = want_depth > 0 ? std::min(want_depth, 4) : 2;
+  int D = d0;
+  auto smem = [&](int w, int d) {
+    return precision == 1 ? smem_dispatch<float>(w, d, Lx) : smem_dispatch<double>(w, d, Lx);
   };
   auto lxmax = [&](int w) { return precision == 1 ? max_lx<float>(w) : max_lx<double>(w); };
-  while (W > vecn && (smem(W) == 0 || smem(W) > 227 * 1024 || ld % W != 0 || Lx > lxmax(W)))
-    W /= 2;
-  if (W < vecn || smem(W) == 0 || smem(W) > 227 * 1024 || ld % W != 0 || Lx > lxmax(W))
-    return false;
+  auto fits = [&](int w, int d) {
+    const size_t b = smem(w, d);
+    return b != 0 && b <= kMaxDynSmem && ld % w == 0 && Lx <= lxmax(w);
+  };
+  while (!fits(W, D)) {
+    if (D > 1) {
+      D -= 1;
+    } else if (W > vecn) {
+      W /= 2;
+      D = d0;
+    } else {
+      return false;
+    }
+  }
   const int slabs = ld / W;
   int split = want_split;
   if (split <= 0) {
-    // Model: time ~ waves(ceil) / waves(exact) * (1 + 2/(3*rows_per_cta)) (halo rows
-    // re-read j_n, one of three streams).  Pick the best split in 1..16.
+    // One CTA per slab marches over all rows (no halo re-reads) unless that
+    // leaves the GPU with fewer than two waves of CTAs; then split rows, but
+    // keep at least 8 rows per CTA.
     int dev = 0;
     cudaGetDevice(&dev);
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t sm_bytes = 228 * 1024;
-    int per_sm = static_cast<int>(sm_bytes / (smem(W) + 1024));
+    int per_sm = static_cast<int>((228 * 1024) / (smem(W, D) + 1024));
     per_sm = std::max(1, std::min(per_sm, 2048 / kThreads));
-    const double slots = static_cast<double>(sms) * per_sm;
-    double best = 1e30;
+    const int slots = sms * per_sm;
     split = 1;
-    for (int s = 1; s <= 16 && s <= Ly; ++s) {
-      const int rpc = (Ly + s - 1) / s;
-      const int eff = (Ly + rpc - 1) / rpc;
-      const double tiles = static_cast<double>(slabs) * eff;
-      const double waves = std::ceil(tiles / slots);
-      const double cost = waves * slots / tiles * (1.0 + 2.0 / (3.0 * rpc)) *
-                          (tiles < slots ? slots / tiles : 1.0);
-      if (cost < best - 1e-9) {
-        best = cost;
-        split = s;
-      }
-    }
+    while (slabs * split < 2 * slots && (Ly + 2 * split - 1) / (2 * split) >= 8) split *= 2;
   }
   split = std::max(1, std::min(split, Ly));
   const int rpc = (Ly + split - 1) / split;
   cfg->slab_w = W;
+  cfg->depth = D;
   cfg->row_split = (Ly + rpc - 1) / rpc;
   cfg->threads = kThreads;
-  cfg->smem = smem(W);
+  cfg->smem = smem(W, D);
   return true;
 }
 
@@ -353,17 +428,17 @@ cudaError_t launch_step_real(int precision, const StepArgs &a, const StepConfig 
                              cudaStream_t s) {
   if (precision == 1) {
     switch (cfg.slab_w) {
-      case 4: return dispatch_maxx<float, 4>(a, cfg, s);
-      case 8: return dispatch_maxx<float, 8>(a, cfg, s);
-      case 16: return dispatch_maxx<float, 16>(a, cfg, s);
-      case 32: return dispatch_maxx<float, 32>(a, cfg, s);
+      case 4: return dispatch_depth<float, 4>(a, cfg, s);
+      case 8: return dispatch_depth<float, 8>(a, cfg, s);
+      case 16: return dispatch_depth<float, 16>(a, cfg, s);
+      case 32: return dispatch_depth<float, 32>(a, cfg, s);
     }
   } else {
     switch (cfg.slab_w) {
-      case 2: return dispatch_maxx<double, 2>(a, cfg, s);
-      case 4: return dispatch_maxx<double, 4>(a, cfg, s);
-      case 8: return dispatch_maxx<double, 8>(a, cfg, s);
-      case 16: return dispatch_maxx<double, 16>(a, cfg, s);
+      case 2: return dispatch_depth<double, 2>(a, cfg, s);
+      case 4: return dispatch_depth<double, 4>(a, cfg, s);
+      case 8: return dispatch_depth<double, 8>(a, cfg, s);
+      case 16: return dispatch_depth<double, 16>(a, cfg, s);
     }
   }
   return cudaErrorInvalidValue;

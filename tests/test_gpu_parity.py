@@ -133,7 +133,8 @@ def test_fp32_converged_delta_within_1e4():
 
 @pytest.mark.parametrize("opts", [
     dict(slab_width=4), dict(slab_width=8, row_split=3), dict(slab_width=32, row_split=2),
-    dict(column_chunk=40), dict(row_split=5), dict(workspace_mb=1)])
+    dict(column_chunk=40), dict(row_split=5), dict(workspace_mb=1), dict(pipeline_depth=1),
+    dict(slab_width=2, pipeline_depth=2)])
 def test_tiling_options_give_same_result(opts):
     p = rect(12, 10, 40, seed=13, periodic=0)
     sites = np.arange(p.N, dtype=np.int32)
