@@ -167,6 +167,32 @@ cbdg_status cbdg_profile_read(cbdg_lattice *lat, double *step_ms, int64_t *step_
  * last reset (reset != 0 clears the counter after reading). */
 cbdg_status cbdg_launch_count(cbdg_lattice *lat, int64_t *launches, int32_t reset);
 
+/* Moments of cbdg_moments (same definitions, outputs and tolerances) for
+ * callers that cannot allocate device memory -- for example code being
+ * recorded into a CUDA graph, or a host program that works inside a fixed,
+ * pre-planned memory budget -- and so cannot build a lattice handle.  The
+ * paper has no counterpart; this is a deployment variant.
+ *   desc:    as for cbdg_build_lattice, but eps, hop and delta0 must be
+ *            DEVICE pointers; inputs are not checked for finiteness or
+ *            Hermiticity (invalid values give meaningless moments, or
+ *            CBDG_ERR_SPECTRUM).  Real on-site pairing with n_dirs = 4 only.
+ *   sites:   device array of n_sites start sites; mu_ee [n_sites*M] and
+ *            mu_eh [n_sites*M] (n_eh = 1) device outputs, either may be NULL.
+ *   stream:  the stream all work is queued on; the call returns after it
+ *            has finished.
+ * Every intermediate lives in one fixed 64 MiB device array reserved when
+ * the library is loaded (on each GPU that loads it, until the process
+ * exits); nothing is allocated.  Lattices whose single column slab does not
+ * fit are rejected with CBDG_ERR_INVALID_ARG; more start sites are handled
+ * in chunks.  The first call on a device looks up the array's device
+ * address (once per device, with that device current): make that first
+ * call before any stream capture.  All calls share the array and a call
+ * resets what it needs, but calls whose GPU work overlaps (other streams or
+ * threads) race on it: serialise them. */
+cbdg_status cbdg_moments_noalloc(const cbdg_lattice_desc *desc, const int32_t *sites,
+                                 int32_t n_sites, int32_t M, double *mu_ee, cbdg_complex *mu_eh,
+                                 cbdg_stream stream);
+
 /* Per-thread description of the last error; never NULL. */
 const char *cbdg_last_error(void);
 

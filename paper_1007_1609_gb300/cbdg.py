@@ -94,6 +94,7 @@ def load():
             "cbdg_get_option": [P, I32, P],
             "cbdg_profile_read": [P, P, P, P, I32],
             "cbdg_launch_count": [P, P, I32],
+            "cbdg_moments_noalloc": [P, P, I32, I32, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -212,6 +213,12 @@ def cbdg_launch_count(lat, reset=False):
     out = ctypes.c_int64(0)
     _check(load().cbdg_launch_count(lat, ctypes.byref(out), 1 if reset else 0))
     return out.value
+
+
+def cbdg_moments_noalloc(desc, sites, n_sites, M, mu_ee, mu_eh, stream=None):
+    """Moments without device allocation: every array must be in device memory."""
+    _check(load().cbdg_moments_noalloc(ctypes.byref(desc), _ptr(sites), int(n_sites), int(M),
+                                       _ptr(mu_ee), _ptr(mu_eh), _stream_handle(stream)))
 
 
 def cbdg_last_error():

@@ -97,6 +97,8 @@ struct DBuf {
 
 }  // namespace
 
+void cbdg_internal_set_error(const char *msg) { g_error = msg; }
+
 struct cbdg_lattice {
   int device = 0;
   cudaStream_t stream = nullptr;

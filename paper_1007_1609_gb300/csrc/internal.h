@@ -90,3 +90,6 @@ enum {
 enum { kFlagSpectrum = 1u, kFlagTimeout = 2u };
 
 }  // namespace cbdg
+
+// Records msg as the calling thread's cbdg_last_error() text.
+void cbdg_internal_set_error(const char *msg);
