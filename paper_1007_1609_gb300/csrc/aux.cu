@@ -128,15 +128,15 @@ __global__ void init_real_kernel(int Lx, int Ly, int px, int py, int ncols, int 
   const size_t rows = 2 * static_cast<size_t>(Lx) * Ly;
   const double m1 = (eps[i] - mu) / a;
   const double2 dl = delta[i];
-  j0[blocked_index(2 * static_cast<size_t>(i), b, rows, W)] = static_cast<S>(1);
-  j1[blocked_index(2 * static_cast<size_t>(i), b, rows, W)] = static_cast<S>(m1);
-  j1[blocked_index(2 * static_cast<size_t>(i) + 1, b, rows, W)] = static_cast<S>(dl.x / a);
+  j0[blocked_index(vector_row(Lx, i, 0), b, rows, W)] = static_cast<S>(1);
+  j1[blocked_index(vector_row(Lx, i, 0), b, rows, W)] = static_cast<S>(m1);
+  j1[blocked_index(vector_row(Lx, i, 1), b, rows, W)] = static_cast<S>(dl.x / a);
   const int DX[4] = {1, -1, 0, 0}, DY[4] = {0, 0, 1, -1};
   for (int d = 0; d < 4; ++d) {
     const int j = neighbour(Lx, Ly, px, py, x, y, DX[d], DY[d]);
     if (j < 0) continue;
     // H_{e_j e_i} = -t_{j -> i} = -conj(t_{i -> j})
-    j1[blocked_index(2 * static_cast<size_t>(j), b, rows, W)] =
+    j1[blocked_index(vector_row(Lx, j, 0), b, rows, W)] =
         static_cast<S>(-hop[static_cast<size_t>(i) * 4 + d].x / a);
   }
   mu1[b] = m1;

@@ -16,8 +16,9 @@ constexpr int kParamStride = 8;
 // Arguments of one recursion step j_{n+1} = 2 H~ j_n - j_{n-1} over a block
 // of ld start vectors.  Vectors use the slab-blocked layout: column slab
 // c = b / W is a row-major [2N][W] block at offset c * 2N * W, so element
-// (row r, column b) sits at (b / W) * 2N*W + r*W + (b % W); row 2s is the
-// electron and 2s+1 the hole of site s = x + Lx*y.
+// (row r, column b) sits at (b / W) * 2N*W + r*W + (b % W).  Rows go lattice
+// row by lattice row; inside lattice row y the Lx electron rows come first,
+// then the Lx hole rows (vector_row below).
 struct StepArgs {
   const void *cur;      // j_n
   void *prev;           // j_{n-1} on entry, j_{n+1} on exit (in place)
@@ -36,6 +37,11 @@ struct StepConfig {
   int threads;
   size_t smem;
 };
+
+// Storage row of the electron (part 0) or hole (part 1) component of site s.
+__host__ __device__ inline size_t vector_row(int Lx, size_t s, int part) {
+  return 2 * static_cast<size_t>(Lx) * (s / Lx) + static_cast<size_t>(part) * Lx + (s % Lx);
+}
 
 // Offset of element (row r, column b) in the slab-blocked layout.
 __host__ __device__ inline size_t blocked_index(size_t r, size_t b, size_t rows, int W) {

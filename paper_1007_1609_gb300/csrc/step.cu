@@ -11,9 +11,12 @@
 // Layout (slab-blocked [2N x B]): the B start vectors are cut into slabs of
 // W columns and each slab is stored as its own row-major [2N][W] block,
 //     element (row r, column b) at (b / W) * 2N*W + r*W + (b % W),
-// with row 2s the electron and 2s+1 the hole of site s = x + Lx*y.  Lattice
-// row y of one slab is therefore one contiguous 2*Lx*W-element block, which
-// streams from HBM as a single run.
+// where the 2N rows are ordered lattice row by lattice row and, inside
+// lattice row y, first the Lx electron rows then the Lx hole rows:
+//     r(x, y, part) = 2*Lx*y + part*Lx + x      (part 0: electron, 1: hole).
+// Lattice row y of one slab is one contiguous 2*Lx*W-element block, which
+// streams from HBM as a single run, and a warp reading W-wide segments of
+// consecutive x touches consecutive shared-memory words (no bank conflicts).
 //
 // A CTA owns one slab and a range of lattice rows and marches along y.  A
 // pipeline D rows deep stages, per lattice row, the j_n block, the j_{n-1}
@@ -189,73 +192,74 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
   int waited = 0;  // loads this thread has seen complete
   bool ok = true;
   for (int i = 0; i < rows; ++i) {
+    // The slots refilled here were last read in iteration i - 1, which every
+    // thread has left through the barrier that ends it.
     if (i + 2 + D <= rows + 1) {
       if (t == 0) issue(i + 2 + D);
       issued = i + 3 + D;
     }
     // loads up to i + 2: rows y-1, y, y+1 of j_n and j_{n-1} of y
-    for (; waited <= i + 2; ++waited) {
-      if (!mbar_wait(smem_addr(&bars[waited % JS]), (waited / JS) & 1u, kWaitLimitNs)) {
-        ok = false;
-        break;
-      }
+    for (; ok && waited <= i + 2; ++waited) {
+      if (!mbar_wait(smem_addr(&bars[waited % JS]), (waited / JS) & 1u, kWaitLimitNs)) ok = false;
     }
-    if (!ok) atomicOr(&abort_flag, 1);
-    __syncthreads();
-    if (abort_flag) break;
+    if (!ok) abort_flag = 1;
 
-    const S *rm = sj + (i % JS) * rowel;        // lattice row y - 1
-    const S *rc = sj + ((i + 1) % JS) * rowel;  // y
-    const S *rp = sj + ((i + 2) % JS) * rowel;  // y + 1
-    const S *ro = so + (i % OS) * rowel;        // j_{n-1} of y
-    const S *pc = sp + ((i + 1) % JS) * pel;
-    S *out = prev + static_cast<size_t>(y0 + i) * rowel;
-    const int off = q * VEC;
+    if (ok) {
+      const S *rm = sj + (i % JS) * rowel;        // lattice row y - 1
+      const S *rc = sj + ((i + 1) % JS) * rowel;  // y
+      const S *rp = sj + ((i + 2) % JS) * rowel;  // y + 1
+      const S *ro = so + (i % OS) * rowel;        // j_{n-1} of y
+      const S *pc = sp + ((i + 1) % JS) * pel;
+      S *out = prev + static_cast<size_t>(y0 + i) * rowel;
+      const int off = q * VEC;
+      const int hb = Lx * W;  // hole rows follow the electron rows
 #pragma unroll
-    for (int k = 0; k < MAXX; ++k) {
-      const int x = xs + k * XSLOTS;
-      if (x < Lx) {
-        const int xl = (x == 0) ? Lx - 1 : x - 1;
-        const int xr = (x == Lx - 1) ? 0 : x + 1;
-        const V u = *reinterpret_cast<const V *>(rc + (2 * x) * W + off);
-        const V v = *reinterpret_cast<const V *>(rc + (2 * x + 1) * W + off);
-        const V ur = *reinterpret_cast<const V *>(rc + (2 * xr) * W + off);
-        const V vr = *reinterpret_cast<const V *>(rc + (2 * xr + 1) * W + off);
-        const V ul = *reinterpret_cast<const V *>(rc + (2 * xl) * W + off);
-        const V vl = *reinterpret_cast<const V *>(rc + (2 * xl + 1) * W + off);
-        const V uu = *reinterpret_cast<const V *>(rp + (2 * x) * W + off);
-        const V vu = *reinterpret_cast<const V *>(rp + (2 * x + 1) * W + off);
-        const V ud = *reinterpret_cast<const V *>(rm + (2 * x) * W + off);
-        const V vd = *reinterpret_cast<const V *>(rm + (2 * x + 1) * W + off);
-        const V uo = *reinterpret_cast<const V *>(ro + (2 * x) * W + off);
-        const V vo = *reinterpret_cast<const V *>(ro + (2 * x + 1) * W + off);
-        const S *pp = pc + x * kParamStride;
-        const S e = pp[0], d = pp[1], t0 = pp[2], t1 = pp[3], t2 = pp[4], t3 = pp[5];
-        V un, vn;
+      for (int k = 0; k < MAXX; ++k) {
+        const int x = xs + k * XSLOTS;
+        if (x < Lx) {
+          const int xl = (x == 0) ? Lx - 1 : x - 1;
+          const int xr = (x == Lx - 1) ? 0 : x + 1;
+          const V u = *reinterpret_cast<const V *>(rc + x * W + off);
+          const V v = *reinterpret_cast<const V *>(rc + hb + x * W + off);
+          const V ur = *reinterpret_cast<const V *>(rc + xr * W + off);
+          const V vr = *reinterpret_cast<const V *>(rc + hb + xr * W + off);
+          const V ul = *reinterpret_cast<const V *>(rc + xl * W + off);
+          const V vl = *reinterpret_cast<const V *>(rc + hb + xl * W + off);
+          const V uu = *reinterpret_cast<const V *>(rp + x * W + off);
+          const V vu = *reinterpret_cast<const V *>(rp + hb + x * W + off);
+          const V ud = *reinterpret_cast<const V *>(rm + x * W + off);
+          const V vd = *reinterpret_cast<const V *>(rm + hb + x * W + off);
+          const V uo = *reinterpret_cast<const V *>(ro + x * W + off);
+          const V vo = *reinterpret_cast<const V *>(ro + hb + x * W + off);
+          const S *pp = pc + x * kParamStride;
+          const S e = pp[0], d = pp[1], t0 = pp[2], t1 = pp[3], t2 = pp[4], t3 = pp[5];
+          V un, vn;
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-          const S uj = comp<V, S>(u, j), vj = comp<V, S>(v, j);
-          // 2 H~ j_n: electron row  (eps-mu) u + Delta v - sum_d t_d u_d
-          //           hole row      Delta u - (eps-mu) v + sum_d t_d v_d
-          const S hu = e * uj + d * vj -
-                       (t0 * comp<V, S>(ur, j) + t1 * comp<V, S>(ul, j) +
-                        t2 * comp<V, S>(uu, j) + t3 * comp<V, S>(ud, j));
-          const S hv = d * uj - e * vj +
-                       (t0 * comp<V, S>(vr, j) + t1 * comp<V, S>(vl, j) +
-                        t2 * comp<V, S>(vu, j) + t3 * comp<V, S>(vd, j));
-          const S unj = hu - comp<V, S>(uo, j);
-          const S vnj = hv - comp<V, S>(vo, j);
-          set_comp<V, S>(un, j, unj);
-          set_comp<V, S>(vn, j, vnj);
-          accA[j].add(uj * uj + vj * vj);
-          accB[j].add(unj * uj + vnj * vj);
-          accC[j].add(unj * vj - vnj * uj);
+          for (int j = 0; j < VEC; ++j) {
+            const S uj = comp<V, S>(u, j), vj = comp<V, S>(v, j);
+            // 2 H~ j_n: electron row  (eps-mu) u + Delta v - sum_d t_d u_d
+            //           hole row      Delta u - (eps-mu) v + sum_d t_d v_d
+            const S hu = e * uj + d * vj -
+                         (t0 * comp<V, S>(ur, j) + t1 * comp<V, S>(ul, j) +
+                          t2 * comp<V, S>(uu, j) + t3 * comp<V, S>(ud, j));
+            const S hv = d * uj - e * vj +
+                         (t0 * comp<V, S>(vr, j) + t1 * comp<V, S>(vl, j) +
+                          t2 * comp<V, S>(vu, j) + t3 * comp<V, S>(vd, j));
+            const S unj = hu - comp<V, S>(uo, j);
+            const S vnj = hv - comp<V, S>(vo, j);
+            set_comp<V, S>(un, j, unj);
+            set_comp<V, S>(vn, j, vnj);
+            accA[j].add(uj * uj + vj * vj);
+            accB[j].add(unj * uj + vnj * vj);
+            accC[j].add(unj * vj - vnj * uj);
+          }
+          __stcs(reinterpret_cast<V *>(out + x * W + off), un);
+          __stcs(reinterpret_cast<V *>(out + hb + x * W + off), vn);
         }
-        __stcs(reinterpret_cast<V *>(out + (2 * x) * W + off), un);
-        __stcs(reinterpret_cast<V *>(out + (2 * x + 1) * W + off), vn);
       }
     }
-    __syncthreads();  // the slots of load i are refilled by the next iteration
+    __syncthreads();  // ends iteration i: its slots may be refilled
+    if (abort_flag) break;
   }
   if (abort_flag) {
     // A copy did not arrive in time: report it, let the copies in flight
@@ -372,13 +376,13 @@ int max_lx(int W) {
 
 }  // namespace
 
-int slab_width_default(int precision) { return precision == 1 ? 8 : 4; }
+int slab_width_default(int precision) { return precision == 1 ? 16 : 4; }
 
 bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
                     int want_depth, StepConfig *cfg) {
   const int vecn = precision == 1 ? 4 : 2;
   int W = want_w > 0 ? want_w : slab_width_default(precision);
-  const int d0 = want_depth > 0 ? std::min(want_depth, 4) : 2;
+  const int d0 = want_depth > 0 ? std::min(want_depth, 4) : 3;
   int D = d0;
   auto smem = [&](int w, int d) {
     return precision == 1 ? smem_dispatch<float>(w, d, Lx) : smem_dispatch<double>(w, d, Lx);
