@@ -39,6 +39,25 @@ L, M, SEED = 128, 1024, 1001
 FP64_FLOPS_PER_ELEMENT_STEP = 20.0  # stencil 12 + moment products 8 (FMA = 2 flops)
 
 
+def recorded_traffic():
+    """DRAM bytes per step-kernel launch from the committed ncu summary, or
+    None when the kernel source changed since those counters were taken."""
+    import glob
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in ("paper_1007_1609_gb300/csrc/step.cu", "paper_1007_1609_gb300/csrc/internal.h"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    for path in glob.glob(os.path.join(ROOT, "profiles", "step_real_kernel_fp32_*.md")):
+        text = open(path).read()
+        m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+        if m and m.group(2) == digest:
+            return int(m.group(1)), os.path.relpath(path, ROOT)
+    return None, None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -266,8 +285,12 @@ def run_gb300(args):
     if rank == 0:
         hbm, peak_kind = peaks()
         achieved = (step_bytes / step_n) / (step_ms / step_n / 1e3) / 1e9 if step_n else None
+        traffic, traffic_src = recorded_traffic()
+        if args.lattice != L or args.moments != M:
+            traffic, traffic_src = None, None  # recorded for the 128x128, M=1024 launch only
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                    "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                    "traffic_source": traffic_src,
                     "kernel": "cheb_step (FP32 recursion step with fused moments)",
                     "peak_kind": f"{peak_kind} (copy bandwidth)",
                     "algorithmic_bytes_per_launch": step_bytes / step_n if step_n else None,
