@@ -144,7 +144,9 @@ enum {
   CBDG_OPT_QUADRATURE_NODES = 0, /* K of the Gauss-Chebyshev sum for c_n; default 65536 */
   CBDG_OPT_COLUMN_CHUNK = 1,     /* start vectors per recursion pass; 0 = automatic */
   CBDG_OPT_PROFILE = 2,          /* 1: time every recursion-step launch with CUDA events */
-  CBDG_OPT_SLAB_WIDTH = 3,       /* columns per CTA of the recursion kernel; 0 = automatic */
+  CBDG_OPT_SLAB_WIDTH = 3,       /* columns per CTA of the recursion kernel (power of two,
+                                    at most 32; the planner narrows it to what fits);
+                                    0 = automatic */
   CBDG_OPT_ROW_SPLIT = 4,        /* CTAs per column slab along y; 0 = automatic */
   CBDG_OPT_WORKSPACE_MB = 5,     /* cap on the recursion vectors' memory; 0 = automatic */
   CBDG_OPT_RESCALE_MILLI = 6,    /* a = (value/1000) * Gershgorin bound; default 1100 (1.1).

@@ -85,6 +85,7 @@ def _load():
             lib.orc_order_parameter.argtypes = [P, D, D, I, I, I, D, P, P]
             lib.orc_ldos.argtypes = [P, D, P, I, I, I, D, P, I, P]
             lib.orc_order_parameter_sites.argtypes = [P, D, D, I, I, I, D, P, I, P, P]
+            lib.orc_order_parameter_bonds.argtypes = [P, D, D, I, I, I, D, P, I, P, P]
             lib.orc_scf.argtypes = [P, D, I, I, D, D, I, P, P, P]
             lib.orc_jacobi_eigh.argtypes = [I, P, P, P, D, I]
             lib.orc_scf_map_gradient.argtypes = [P, D, P, I, P, P, P, P]
@@ -223,6 +224,20 @@ def order_parameter_sites(lat: Lattice, a: float, T: float, M: int, K: int, site
     if rc != 0:
         raise ValueError("on-site pairing only")
     return d, n
+
+
+def order_parameter_bonds(lat: Lattice, a: float, T: float, M: int, K: int, sites, kernel: int = 0,
+                          lam: float = 0.0):
+    """Bond Delta [n, 4] and n at the listed sites only (sampled parity)."""
+    sites = np.ascontiguousarray(sites, dtype=np.int32)
+    d = np.zeros(sites.size * 4, dtype=np.complex128)
+    n = np.zeros(sites.size)
+    c = lat._c()
+    rc = _load().orc_order_parameter_bonds(ctypes.byref(c), float(a), float(T), M, K, int(kernel),
+                                           float(lam), _ptr(sites), sites.size, _ptr(d), _ptr(n))
+    if rc != 0:
+        raise ValueError("bond pairing only")
+    return d.reshape(sites.size, 4), n
 
 
 def ldos(lat: Lattice, a: float, sites, M: int, energies, kernel: int = 0, lam: float = 0.0):

@@ -107,6 +107,7 @@ struct cbdg_lattice {
   int nd = 0;  // number of Delta entries (N or 4N)
   DBuf eps, hop, delta, params, scal, flags, f, C, sites_all, sites_user;
   DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
+  DBuf acc_site_n, acc_site_b;
   // options
   int K = 65536;
   int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0;
@@ -157,7 +158,25 @@ int host_neighbour(const cbdg_lattice_desc *d, int s, int dir) {
 
 bool finite_c(const cbdg_complex &z) { return isfinite(z.re) && isfinite(z.im); }
 
+// Recursion kernel family for the lattice:
+//   kReal:   real on-site pairing, nearest neighbours (step.cu), doubling;
+//   kCplx:   complex field and/or next-nearest hopping, on-site pairing
+//            (step_cplx.cu), doubling;
+//   kDirect: bond pairing (step_cplx.cu), every moment read directly.
+enum Mode { kReal = 0, kCplx = 1, kDirect = 2 };
+
+Mode mode_of(const cbdg_lattice *L) {
+  if (L->pairing == CBDG_BOND_V) return kDirect;
+  if (L->cplx || L->n_dirs == 8) return kCplx;
+  return kReal;
+}
+
 size_t elem_size(const cbdg_lattice *L) { return L->precision == CBDG_FP32_MIXED ? 4 : 8; }
+
+// bytes of one vector element (complex for the general kernels)
+size_t vec_elem_size(const cbdg_lattice *L) {
+  return elem_size(L) * (mode_of(L) == kReal ? 1 : 2);
+}
 
 // a, coefficient table and stencil parameters for the current Delta.
 cbdg_status prepare(cbdg_lattice *L, double T, int kernel, double lambda, int M, bool coeffs) {
@@ -175,22 +194,32 @@ cbdg_status prepare(cbdg_lattice *L, double T, int kernel, double lambda, int M,
   } else {
     CK(cudaMemsetAsync(L->C.p, 0, static_cast<size_t>(M) * sizeof(double), L->stream));
   }
-  CK(L->params.ensure(static_cast<size_t>(L->N) * kParamStride * elem_size(L)));
-  CK(launch_params_real(L->precision, L->N, L->eps.as<double>(), L->mu, L->hop.as<double2>(),
-                        L->delta.as<double2>(), L->scal.as<double>(), L->params.p, L->stream));
+  if (mode_of(L) == kReal) {
+    CK(L->params.ensure(static_cast<size_t>(L->N) * kParamStride * elem_size(L)));
+    CK(launch_params_real(L->precision, L->N, L->eps.as<double>(), L->mu, L->hop.as<double2>(),
+                          L->delta.as<double2>(), L->scal.as<double>(), L->params.p, L->stream));
+  } else {
+    CK(L->params.ensure(static_cast<size_t>(L->N) * kCplxParamStride * elem_size(L)));
+    CK(launch_params_cplx(L->precision, L->N, L->n_dirs, L->pairing, L->eps.as<double>(), L->mu,
+                          L->hop.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
+                          L->params.p, L->stream));
+  }
   L->launches += 1;
   return CBDG_OK;
 }
 
 // Runs the recursion for n_sites start vectors (device list), folding the
 // moments into per-column accumulators; optionally writes the moments
-// ([n_sites][M] and [n_sites][M][stride]) and scatters Delta_out / n into
-// L->dout / L->nout.
+// ([n_sites][M] and [n_sites][M][stride]).  With finalize, Delta_out and n
+// go to L->dout / L->nout; then the site list must be 0..N-1 in order
+// (bond pairing pairs the accumulators of neighbouring start sites).
 cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int M,
                         double *mom_ee, double2 *mom_eh, int mom_stride, bool finalize) {
-  const size_t es = elem_size(L);
+  const Mode mode = mode_of(L);
+  const size_t es = vec_elem_size(L);
   const size_t rows = 2 * static_cast<size_t>(L->N);
-  int W = L->slab_w > 0 ? static_cast<int>(L->slab_w) : slab_width_default(L->precision);
+  const int Wdef = mode == kReal ? slab_width_default(L->precision) : slab_width_default_cplx(L->precision);
+  int W = L->slab_w > 0 ? static_cast<int>(L->slab_w) : Wdef;
   // column chunk: bounded by the workspace cap (two vectors)
   size_t cap;
   if (L->ws_mb > 0) {
@@ -206,34 +235,72 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
   if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
   if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for one column slab");
   const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((n_sites + W - 1) / W) * W));
+  const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
+  if (mode == kDirect && finalize) {
+    // per-site accumulators for the bond fold, filled chunk by chunk
+    CK(L->acc_site_n.ensure(static_cast<size_t>(L->N) * sizeof(double)));
+    CK(L->acc_site_b.ensure(static_cast<size_t>(L->N) * 4 * sizeof(double2)));
+  }
 
   for (int c0 = 0; c0 < n_sites; c0 += chunk) {
     const int ncols = std::min(chunk, n_sites - c0);
     const int ld = ((ncols + W - 1) / W) * W;
     StepConfig cfg;
-    if (!plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
-                        static_cast<int>(L->depth), &cfg))
+    const bool planned =
+        mode == kReal ? plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
+                                       static_cast<int>(L->depth), &cfg)
+                      : plan_step_cplx(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
+                                       static_cast<int>(L->depth), &cfg);
+    if (!planned)
       return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d with %d columns", L->Lx, ld);
+    const int nsum = mode == kReal ? 3 : 4;
     const size_t vbytes = rows * ld * es;
     CK(L->vec0.ensure(vbytes));
     CK(L->vec1.ensure(vbytes));
-    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 3 * ld * sizeof(double)));
+    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * nsum * ld * sizeof(double)));
     CK(L->mu1.ensure(ld * sizeof(double)));
     CK(L->dA.ensure(ld * sizeof(double2)));
     CK(L->acc_n.ensure(ld * sizeof(double)));
-    CK(L->acc_d.ensure(ld * sizeof(double2)));
+    CK(L->acc_d.ensure(ld * 4 * sizeof(double2)));
     CK(cudaMemsetAsync(L->vec0.p, 0, vbytes, L->stream));
     CK(cudaMemsetAsync(L->vec1.p, 0, vbytes, L->stream));
     double *mee = mom_ee ? mom_ee + static_cast<size_t>(c0) * M : nullptr;
     double2 *meh = mom_eh ? mom_eh + static_cast<size_t>(c0) * M * mom_stride : nullptr;
-    CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, cfg.slab_w, sites + c0,
-                        L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
-                        L->scal.as<double>(), L->C.as<double>(), M, L->vec0.p, L->vec1.p,
-                        L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
-                        L->acc_d.as<double2>(), mee, meh, mom_stride, L->stream));
-    L->launches += 1;
+    double *accn = L->acc_n.as<double>();
+    double2 *accb = L->acc_d.as<double2>();
+    if (mode == kDirect && finalize) {
+      accn = L->acc_site_n.as<double>() + c0;
+      accb = L->acc_site_b.as<double2>() + static_cast<size_t>(c0) * 4;
+    }
+    if (mode == kReal) {
+      CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, cfg.slab_w, sites + c0,
+                          L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
+                          L->scal.as<double>(), L->C.as<double>(), M, L->vec0.p, L->vec1.p,
+                          L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
+                          L->acc_d.as<double2>(), mee, meh, mom_stride, L->stream));
+      L->launches += 1;
+    } else {
+      CK(launch_init_cplx(L->precision, L->Lx, L->Ly, L->px, L->py, L->n_dirs, L->pairing, ncols,
+                          cfg.slab_w, sites + c0, L->eps.as<double>(), L->mu, L->hop.as<double2>(),
+                          L->delta.as<double2>(), L->scal.as<double>(), L->C.as<double>(), M,
+                          L->vec0.p, L->vec1.p, L->mu1.as<double>(), L->dA.as<double2>(),
+                          L->acc_n.as<double>(), L->acc_d.as<double2>(), mee, meh, mom_stride,
+                          L->stream));
+      L->launches += 1;
+      if (mode == kDirect) {
+        CK(cudaMemsetAsync(accn, 0, ncols * sizeof(double), L->stream));
+        CK(cudaMemsetAsync(accb, 0, static_cast<size_t>(ncols) * 4 * sizeof(double2), L->stream));
+        for (int m = 0; m < 2 && m < M; ++m) {
+          CK(launch_gather(L->precision, m, M, L->Lx, L->Ly, L->px, L->py, ncols, cfg.slab_w,
+                           sites + c0, m == 0 ? L->vec0.p : L->vec1.p, L->C.as<double>(), accn,
+                           accb, mee, meh, L->flags.as<unsigned int>(), tol, L->stream));
+          L->launches += 1;
+        }
+      }
+    }
     void *cur = L->vec1.p, *prev = L->vec0.p;
-    const int steps = (M + 1) / 2 - 1;
+    // doubling: step n yields moments 2n, 2n+1; direct: step n yields j_{n+1}
+    const int steps = mode == kDirect ? M - 2 : (M + 1) / 2 - 1;
     if (L->profile && static_cast<int>(L->events.size()) < 2 * steps) {
       for (int k = static_cast<int>(L->events.size()); k < 2 * steps; ++k) {
         cudaEvent_t ev;
@@ -249,25 +316,36 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     a.Ly = L->Ly;
     a.ld = ld;
     a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
-    const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
     for (int n = 1; n <= steps; ++n) {
       a.cur = cur;
       a.prev = prev;
       if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1)], L->stream));
-      CK(launch_step_real(L->precision, a, cfg, L->stream));
+      if (mode == kReal) CK(launch_step_real(L->precision, a, cfg, L->stream));
+      else CK(launch_step_cplx(L->precision, L->n_dirs == 8, mode == kDirect, a, cfg, L->stream));
       if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1) + 1], L->stream));
-      CK(launch_fold(n, M, ncols, ld, cfg.row_split, L->partials.as<double>(), L->C.as<double>(),
-                     L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
-                     L->acc_d.as<double2>(), mee, meh, mom_stride, L->flags.as<unsigned int>(),
-                     tol, L->stream));
+      if (mode == kReal)
+        CK(launch_fold(n, M, ncols, ld, cfg.row_split, L->partials.as<double>(), L->C.as<double>(),
+                       L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
+                       L->acc_d.as<double2>(), mee, meh, mom_stride, L->flags.as<unsigned int>(),
+                       tol, L->stream));
+      else if (mode == kCplx)
+        CK(launch_fold_cplx(n, M, ncols, ld, cfg.row_split, L->partials.as<double>(),
+                            L->C.as<double>(), L->mu1.as<double>(), L->dA.as<double2>(),
+                            L->acc_n.as<double>(), L->acc_d.as<double2>(), mee, meh, mom_stride,
+                            L->flags.as<unsigned int>(), tol, L->stream));
+      else
+        CK(launch_gather(L->precision, n + 1, M, L->Lx, L->Ly, L->px, L->py, ncols, cfg.slab_w,
+                         sites + c0, prev, L->C.as<double>(), accn, accb, mee, meh,
+                         L->flags.as<unsigned int>(), tol, L->stream));
       L->launches += 2;
       std::swap(cur, prev);
     }
-    if (finalize)
+    if (finalize && mode != kDirect) {
       CK(launch_finalize_onsite(ncols, sites + c0, L->coupling, L->acc_n.as<double>(),
                                 L->acc_d.as<double2>(), L->dout.as<double2>(), L->nout.as<double>(),
                                 L->stream));
-    if (finalize) L->launches += 1;
+      L->launches += 1;
+    }
     if (L->profile && steps > 0) {
       CK(cudaStreamSynchronize(L->stream));
       for (int n = 0; n < steps; ++n) {
@@ -278,6 +356,12 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
       L->prof_launches += steps;
       L->prof_bytes += static_cast<double>(steps) * 3.0 * static_cast<double>(vbytes);
     }
+  }
+  if (finalize && mode == kDirect) {
+    CK(launch_finalize_bond(L->N, L->Lx, L->Ly, L->px, L->py, L->coupling,
+                            L->acc_site_n.as<double>(), L->acc_site_b.as<double2>(),
+                            L->dout.as<double2>(), L->nout.as<double>(), L->stream));
+    L->launches += 1;
   }
   return CBDG_OK;
 }
@@ -398,9 +482,6 @@ cbdg_status cbdg_build_lattice(const cbdg_lattice_desc *d, cbdg_stream stream,
     for (auto &z : delta)
       if (z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex delta0 with complex_field = 0");
   }
-  if (d->complex_field || d->pairing != CBDG_ONSITE_U || d->n_dirs != 4)
-    return fail(CBDG_ERR_UNSUPPORTED,
-                "this build handles real on-site pairing with nearest-neighbour hopping only");
 
   cbdg_lattice *L = new (std::nothrow) cbdg_lattice();
   if (!L) return fail(CBDG_ERR_OOM, "host allocation failed");
@@ -452,7 +533,7 @@ cbdg_status cbdg_destroy(cbdg_lattice *L) {
   DBuf *bufs[] = {&L->eps,     &L->hop,   &L->delta, &L->params,  &L->scal,  &L->flags,
                   &L->f,       &L->C,     &L->sites_all, &L->sites_user, &L->vec0, &L->vec1,
                   &L->partials, &L->mu1,  &L->dA,    &L->acc_n,   &L->acc_d, &L->dout,
-                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage};
+                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
   delete L;
@@ -581,8 +662,8 @@ cbdg_status cbdg_set_option(cbdg_lattice *L, int32_t option, int64_t value) {
       L->profile = value != 0;
       return CBDG_OK;
     case CBDG_OPT_SLAB_WIDTH:
-      if (value != 0 && (value < 2 || value > 32 || (value & (value - 1))))
-        return fail(CBDG_ERR_INVALID_ARG, "slab width must be 0 or a power of two in [2, 32]");
+      if (value != 0 && (value < 1 || value > 32 || (value & (value - 1))))
+        return fail(CBDG_ERR_INVALID_ARG, "slab width must be 0 or a power of two in [1, 32]");
       L->slab_w = value;
       return CBDG_OK;
     case CBDG_OPT_ROW_SPLIT:

@@ -12,6 +12,10 @@ namespace cbdg {
 // application yields 2 H~ j:
 //   [0] 2 (eps - mu)/a   [1] 2 Delta/a   [2..5] 2 t_{s,d}/a (d = 0..3)   [6,7] 0
 constexpr int kParamStride = 8;
+// General (complex / next-nearest / bond) parameter record, 32 scalars per site:
+//   [0] 2(eps-mu)/a  [2,3] 2 Delta_i/a  [4+2d, 5+2d] 2 t_{i,d}/a (d < 8)
+//   [20+2d, 21+2d] 2 Delta_{i,d}/a (d < 4); the rest 0.
+constexpr int kCplxParamStride = 32;
 
 // Arguments of one recursion step j_{n+1} = 2 H~ j_n - j_{n-1} over a block
 // of ld start vectors.  Vectors use the slab-blocked layout: column slab
@@ -56,6 +60,35 @@ cudaError_t launch_step_real(int precision, const StepArgs &a, const StepConfig 
 bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
                     int want_depth, StepConfig *cfg);
 int slab_width_default(int precision);
+
+// Recursion step for the general lattice (complex vectors; nnn: 8 hopping
+// directions; bond: nearest-neighbour pairing, which skips the column sums).
+// The partial sums, when formed, are [row_split][4][ld].
+cudaError_t launch_step_cplx(int precision, int nnn, int bond, const StepArgs &a,
+                             const StepConfig &cfg, cudaStream_t s);
+bool plan_step_cplx(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
+                    int want_depth, StepConfig *cfg);
+int slab_width_default_cplx(int precision);
+cudaError_t launch_params_cplx(int precision, int N, int n_dirs, int pairing, const double *eps,
+                               double mu, const double2 *hop, const double2 *delta,
+                               const double *scal, void *params, cudaStream_t s);
+cudaError_t launch_init_cplx(int precision, int Lx, int Ly, int px, int py, int n_dirs, int pairing,
+                             int ncols, int W, const int32_t *sites, const double *eps, double mu,
+                             const double2 *hop, const double2 *delta, const double *scal,
+                             const double *C, int M, void *j0, void *j1, double *mu1, double2 *dA,
+                             double *acc_n, double2 *acc_d, double *mu_ee, double2 *mu_eh,
+                             int mom_stride, cudaStream_t s);
+cudaError_t launch_fold_cplx(int n, int M, int ncols, int ld, int row_split, const double *partials,
+                             const double *C, const double *mu1, const double2 *dA, double *acc_n,
+                             double2 *acc_d, double *mu_ee, double2 *mu_eh, int mom_stride,
+                             unsigned int *flags, double tol, cudaStream_t s);
+cudaError_t launch_gather(int precision, int m, int M, int Lx, int Ly, int px, int py, int ncols,
+                          int W, const int32_t *sites, const void *j, const double *C,
+                          double *acc_n, double2 *acc_b, double *mu_ee, double2 *mu_eh,
+                          unsigned int *flags, double tol, cudaStream_t s);
+cudaError_t launch_finalize_bond(int N, int Lx, int Ly, int px, int py, double V,
+                                 const double *acc_n, const double2 *acc_b, double2 *dout,
+                                 double *nout, cudaStream_t s);
 
 // ---- auxiliary kernels (aux.cu) -------------------------------------------
 cudaError_t launch_gershgorin(int N, int n_dirs, int pairing, int Lx, int Ly, int px, int py,

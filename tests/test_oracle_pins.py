@@ -319,6 +319,17 @@ def test_sampled_sites_match_full_order_parameter():
     assert np.array_equal(ds, d[sites]) and np.array_equal(ns, n[sites])
 
 
+def test_sampled_bonds_match_full_order_parameter():
+    M, K = 48, 1 << 12
+    p = wl.random_dwave(5, M, seed=46, flux_quanta=2.0)
+    lat = as_oracle(p)
+    a = orc.rescale(lat)
+    d, n = orc.order_parameter(lat, a, p.T, M, K)
+    sites = np.array([7, 0, 24, 13])
+    ds, ns = orc.order_parameter_bonds(lat, a, p.T, M, K, sites)
+    assert np.allclose(ds, d[sites], atol=1e-15) and np.allclose(ns, n[sites], atol=1e-15)
+
+
 def test_order_parameter_converges_to_exact_tanh():
     """As M grows the damped series converges to the exact ED order parameter
     (U/2) sum_k u conj(v) tanh(E_k/2T); the error falls monotonically."""
