@@ -118,11 +118,24 @@ cbdg_status cbdg_order_parameter(cbdg_lattice *lat, double T, int32_t kernel, do
 /* Up-spin local density of states of Eq. 17 with the expansion of Eq. 10,
  * per unit energy, at absolute energies E (|E| < a):
  *   ldos[c*n_E + e] = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n(i) T_n(E/a)] / (pi a sqrt(1-(E/a)^2))
- * for i = sites[c].  Errors: INVALID_ARG (also for |E| >= a), SPECTRUM, OOM,
- * CUDA. */
+ * for i = sites[c], g_n the Jackson or Lorentz (lambda) kernel.  The
+ * moments come from the recursion; the sum over n is a dense
+ * [n_sites x M] . [M x n_E] contraction on the tensor cores
+ * (cbdg_contract_tf32x3).  Errors: INVALID_ARG (also for |E| >= a),
+ * SPECTRUM, OOM, CUDA. */
 cbdg_status cbdg_ldos(cbdg_lattice *lat, const int32_t *sites, int32_t n_sites, int32_t M,
                       int32_t kernel, double lambda, const double *energies, int32_t n_E,
                       float *ldos);
+
+/* Dense contraction behind cbdg_ldos, on the tensor cores (tcgen05,
+ * kind::tf32) with each operand split into TF32 head and tail (3 products,
+ * about 21 significant bits, FP32 accumulation):
+ *   D[i*ldd + j] = sum_{l<k} A[i*lda + l] * B[j*ldb + l],  i < m, j < n.
+ * A, B, D are device pointers on the current device; lda and ldb are
+ * multiples of 4 (>= k), A and B 16-byte aligned, ldd >= n.  Runs on
+ * `stream` and returns after completion.  Errors: INVALID_ARG, CUDA. */
+cbdg_status cbdg_contract_tf32x3(const float *A, int32_t lda, const float *B, int32_t ldb, float *D,
+                                 int32_t ldd, int32_t m, int32_t n, int32_t k, cbdg_stream stream);
 
 /* One self-consistency iteration (paragraph after Eq. 20) with the Jackson
  * kernel: computes Delta_out from the current Delta as cbdg_order_parameter

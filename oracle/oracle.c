@@ -430,18 +430,15 @@ int orc_order_parameter_bonds(const orc_lattice *L, double a, double T, int M, i
   return 0;
 }
 
-/* Up-spin LDOS of Eq. 17 from the expansion of Eq. 10, per unit energy:
+/* Up-spin LDOS of Eq. 17 from the expansion of Eq. 10, per unit energy, from
+ * given moments mu_ee [n_sites*M]:
  *   N(E, i) = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(E/a)] / (pi a sqrt(1-(E/a)^2)).
  * ldos is [n_sites * n_E]. */
-int orc_ldos(const orc_lattice *L, double a, const int32_t *sites, int n_sites, int M,
-             int kernel, double lambda, const double *energies, int n_E, double *ldos) {
-  int n_eh = (L->pairing == 1) ? 5 : 1;
+int orc_ldos_from_moments(const double *mu_ee, int n_sites, int M, double a, int kernel,
+                          double lambda, const double *energies, int n_E, double *ldos) {
   double *g = (double *)malloc(sizeof(double) * M);
   if (kernel == 0) orc_jackson(M, g);
   else orc_lorentz(M, lambda, g);
-  double *mu_ee = (double *)malloc(sizeof(double) * (size_t)n_sites * M);
-  cplx *mu_eh = (cplx *)malloc(sizeof(cplx) * (size_t)n_sites * M * n_eh);
-  orc_moments(L, a, sites, n_sites, M, mu_ee, mu_eh);
   for (int c = 0; c < n_sites; ++c) {
     for (int e = 0; e < n_E; ++e) {
       double x = energies[e] / a;
@@ -452,6 +449,18 @@ int orc_ldos(const orc_lattice *L, double a, const int32_t *sites, int n_sites, 
     }
   }
   free(g);
+  return 0;
+}
+
+/* The LDOS at the listed start sites: moments by the direct recursion, then
+ * orc_ldos_from_moments. */
+int orc_ldos(const orc_lattice *L, double a, const int32_t *sites, int n_sites, int M,
+             int kernel, double lambda, const double *energies, int n_E, double *ldos) {
+  int n_eh = (L->pairing == 1) ? 5 : 1;
+  double *mu_ee = (double *)malloc(sizeof(double) * (size_t)n_sites * M);
+  cplx *mu_eh = (cplx *)malloc(sizeof(cplx) * (size_t)n_sites * M * n_eh);
+  orc_moments(L, a, sites, n_sites, M, mu_ee, mu_eh);
+  orc_ldos_from_moments(mu_ee, n_sites, M, a, kernel, lambda, energies, n_E, ldos);
   free(mu_ee);
   free(mu_eh);
   return 0;

@@ -84,6 +84,7 @@ def _load():
             lib.orc_moments.argtypes = [P, D, P, I, I, P, P]
             lib.orc_order_parameter.argtypes = [P, D, D, I, I, I, D, P, P]
             lib.orc_ldos.argtypes = [P, D, P, I, I, I, D, P, I, P]
+            lib.orc_ldos_from_moments.argtypes = [P, I, I, D, I, D, P, I, P]
             lib.orc_order_parameter_sites.argtypes = [P, D, D, I, I, I, D, P, I, P, P]
             lib.orc_order_parameter_bonds.argtypes = [P, D, D, I, I, I, D, P, I, P, P]
             lib.orc_scf.argtypes = [P, D, I, I, D, D, I, P, P, P]
@@ -247,6 +248,16 @@ def ldos(lat: Lattice, a: float, sites, M: int, energies, kernel: int = 0, lam: 
     c = lat._c()
     _load().orc_ldos(ctypes.byref(c), float(a), _ptr(sites), sites.size, M, int(kernel), float(lam),
                      _ptr(energies), energies.size, _ptr(out))
+    return out
+
+
+def ldos_from_moments(mu_ee, a: float, energies, kernel: int = 0, lam: float = 0.0):
+    """LDOS (Eq. 17) at the given energies from oracle moments mu_ee [n_sites, M]."""
+    mu_ee = np.ascontiguousarray(mu_ee, dtype=np.float64)
+    energies = np.ascontiguousarray(energies, dtype=np.float64)
+    out = np.zeros((mu_ee.shape[0], energies.size))
+    _load().orc_ldos_from_moments(_ptr(mu_ee), mu_ee.shape[0], mu_ee.shape[1], float(a), int(kernel),
+                                  float(lam), _ptr(energies), energies.size, _ptr(out))
     return out
 
 

@@ -95,6 +95,7 @@ def load():
             "cbdg_profile_read": [P, P, P, P, I32],
             "cbdg_launch_count": [P, P, I32],
             "cbdg_moments_noalloc": [P, P, I32, I32, P, P, P],
+            "cbdg_contract_tf32x3": [P, I32, P, I32, P, I32, I32, I32, I32, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -221,6 +222,11 @@ def cbdg_moments_noalloc(desc, sites, n_sites, M, mu_ee, mu_eh, stream=None):
                                        _ptr(mu_ee), _ptr(mu_eh), _stream_handle(stream)))
 
 
+def cbdg_contract_tf32x3(A, lda, B, ldb, D, ldd, m, n, k, stream=None):
+    _check(load().cbdg_contract_tf32x3(_ptr(A), int(lda), _ptr(B), int(ldb), _ptr(D), int(ldd),
+                                       int(m), int(n), int(k), _stream_handle(stream)))
+
+
 def cbdg_last_error():
     return load().cbdg_last_error().decode()
 
@@ -293,6 +299,13 @@ class Lattice:
         n = np.zeros(self.N)
         cbdg_order_parameter(self.handle, T, KERNELS[kernel], lam, M, d, n)
         return (d.reshape(self.N, 4) if self.pairing == CBDG_BOND_V else d), n
+
+    def ldos(self, sites, M, energies, kernel="jackson", lam=0.0):
+        sites = np.ascontiguousarray(sites, dtype=np.int32)
+        energies = np.ascontiguousarray(energies, dtype=np.float64)
+        out = np.zeros((sites.size, energies.size), dtype=np.float32)
+        cbdg_ldos(self.handle, sites, sites.size, M, KERNELS[kernel], lam, energies, energies.size, out)
+        return out
 
     def scf_step(self, T, M, mix):
         return cbdg_scf_step(self.handle, T, M, mix)

@@ -592,11 +592,93 @@ cbdg_status cbdg_order_parameter(cbdg_lattice *L, double T, int32_t kernel, doub
   return finish(L);
 }
 
-cbdg_status cbdg_ldos(cbdg_lattice *L, const int32_t *, int32_t, int32_t, int32_t, double,
-                      const double *, int32_t, float *) {
+cbdg_status cbdg_ldos(cbdg_lattice *L, const int32_t *sites, int32_t n_sites, int32_t M,
+                      int32_t kernel, double lambda, const double *energies, int32_t n_E,
+                      float *ldos) {
   cbdg_status st = begin(L);
   if (st != CBDG_OK) return st;
-  return fail(CBDG_ERR_UNSUPPORTED, "cbdg_ldos is not available in this build");
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  if (kernel != CBDG_JACKSON && kernel != CBDG_LORENTZ)
+    return fail(CBDG_ERR_INVALID_ARG, "unknown kernel %d", kernel);
+  if (kernel == CBDG_LORENTZ && !(lambda > 0.0 && isfinite(lambda)))
+    return fail(CBDG_ERR_INVALID_ARG, "Lorentz kernel needs lambda > 0");
+  if (n_sites < 0 || n_E < 0 || (n_sites > 0 && !sites) || (n_E > 0 && !energies) ||
+      (n_sites > 0 && n_E > 0 && !ldos))
+    return fail(CBDG_ERR_INVALID_ARG, "bad site or energy list");
+  if (n_sites == 0 || n_E == 0) return CBDG_OK;
+  std::vector<int32_t> hs;
+  std::vector<double> he;
+  cudaError_t e = host_copy(sites, n_sites, hs);
+  if (e != cudaSuccess) return cuda_fail(e, "reading sites");
+  e = host_copy(energies, n_E, he);
+  if (e != cudaSuccess) return cuda_fail(e, "reading energies");
+  for (int c = 0; c < n_sites; ++c)
+    if (hs[c] < 0 || hs[c] >= L->N) return fail(CBDG_ERR_INVALID_ARG, "site %d out of range", hs[c]);
+  st = prepare(L, 0.0, CBDG_JACKSON, 0.0, M, false);
+  if (st != CBDG_OK) return st;
+  double a = 0.0;
+  CK(cudaMemcpyAsync(&a, L->scal.as<double>() + kScalA, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  for (int k = 0; k < n_E; ++k)
+    if (!(fabs(he[k]) < a))
+      return fail(CBDG_ERR_INVALID_ARG, "energy %g outside the rescaled band (-a, a), a = %g", he[k], a);
+  CK(L->sites_user.ensure(n_sites * sizeof(int32_t)));
+  CK(cudaMemcpyAsync(L->sites_user.p, hs.data(), n_sites * sizeof(int32_t), cudaMemcpyHostToDevice, L->stream));
+  const int n_eh = L->pairing == CBDG_BOND_V ? 5 : 1;
+  const size_t nee = static_cast<size_t>(n_sites) * M;
+  CK(L->mom_ee.ensure(nee * sizeof(double)));
+  st = run_columns(L, L->sites_user.as<int32_t>(), n_sites, M, L->mom_ee.as<double>(), nullptr, n_eh, false);
+  if (st != CBDG_OK) return st;
+  // contraction operands: moments [n_sites][ldk] and weights [n_E][ldk] in FP32
+  const int ldk = (M + 3) / 4 * 4;
+  const size_t a_bytes = static_cast<size_t>(n_sites) * ldk * sizeof(float);
+  const size_t w_bytes = static_cast<size_t>(n_E) * ldk * sizeof(float);
+  const size_t d_bytes = static_cast<size_t>(n_sites) * n_E * sizeof(float);
+  const size_t e_bytes = static_cast<size_t>(n_E) * sizeof(double);
+  auto r256 = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+  CK(L->stage.ensure(r256(a_bytes) + r256(w_bytes) + r256(d_bytes) + r256(e_bytes)));
+  unsigned char *sb = L->stage.as<unsigned char>();
+  float *dA = reinterpret_cast<float *>(sb);
+  float *dW = reinterpret_cast<float *>(sb + r256(a_bytes));
+  float *dD = reinterpret_cast<float *>(sb + r256(a_bytes) + r256(w_bytes));
+  double *dE = reinterpret_cast<double *>(sb + r256(a_bytes) + r256(w_bytes) + r256(d_bytes));
+  CK(cudaMemcpyAsync(dE, he.data(), e_bytes, cudaMemcpyHostToDevice, L->stream));
+  CK(launch_moments_to_f32(n_sites, M, ldk, L->mom_ee.as<double>(), dA, L->stream));
+  CK(launch_ldos_weights(n_E, M, ldk, kernel, lambda, dE, L->scal.as<double>(), dW, L->stream));
+  float *dst = is_device_ptr(ldos) ? ldos : dD;
+  CK(launch_contract_tf32x3(dA, ldk, dW, ldk, dst, n_E, n_sites, n_E, M,
+                            L->flags.as<unsigned int>(), L->stream));
+  L->launches += 3;
+  if (dst != ldos) CK(deliver(L, ldos, dD, d_bytes));
+  return finish(L);
+}
+
+cbdg_status cbdg_contract_tf32x3(const float *A, int32_t lda, const float *B, int32_t ldb, float *D,
+                                 int32_t ldd, int32_t m, int32_t n, int32_t k, cbdg_stream stream) {
+  if (m < 0 || n < 0 || k < 0) return fail(CBDG_ERR_INVALID_ARG, "negative size");
+  if (m == 0 || n == 0) return CBDG_OK;
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(D))
+    return fail(CBDG_ERR_INVALID_ARG, "A, B and D must be device pointers");
+  if (lda < k || ldb < k || ldd < n || (lda & 3) || (ldb & 3) ||
+      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
+    return fail(CBDG_ERR_INVALID_ARG,
+                "lda, ldb must be >= k and multiples of 4, A and B 16-byte aligned, ldd >= n");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (k == 0) {
+    for (int r = 0; r < m; ++r)
+      CK(cudaMemsetAsync(D + static_cast<size_t>(r) * ldd, 0, n * sizeof(float), s));
+    CK(cudaStreamSynchronize(s));
+    return CBDG_OK;
+  }
+  unsigned *flags = nullptr;
+  CK(contract_flag_address(&flags));
+  CK(cudaMemsetAsync(flags, 0, sizeof(unsigned), s));
+  CK(launch_contract_tf32x3(A, lda, B, ldb, D, ldd, m, n, k, flags, s));
+  unsigned h = 0;
+  CK(cudaMemcpyAsync(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h & kFlagTimeout) return fail(CBDG_ERR_CUDA, "the contraction kernel gave up waiting for its tensor cores");
+  return CBDG_OK;
 }
 
 cbdg_status cbdg_scf_step(cbdg_lattice *L, double T, int32_t M, double mix,

@@ -128,6 +128,18 @@ enum {
 // Error flags (unsigned int bits).
 enum { kFlagSpectrum = 1u, kFlagTimeout = 2u };
 
+// Dense D[m][n] = sum_k A[m][k] B[n][k] (row strides lda, ldb multiples of 4,
+// 16-byte aligned) on tcgen05 tensor cores with the 3xTF32 split.
+cudaError_t launch_contract_tf32x3(const float *A, int lda, const float *B, int ldb, float *D,
+                                   int ldd, int m, int n, int k, unsigned *flags, cudaStream_t s);
+// Device address of the stand-alone contraction's error word (this device).
+cudaError_t contract_flag_address(unsigned **out);
+cudaError_t launch_ldos_weights(int n_E, int M, int ld, int kernel, double lambda,
+                                const double *energies, const double *scal, float *W,
+                                cudaStream_t s);
+cudaError_t launch_moments_to_f32(int rows, int M, int ld, const double *mu, float *out,
+                                  cudaStream_t s);
+
 }  // namespace cbdg
 
 // Records msg as the calling thread's cbdg_last_error() text.

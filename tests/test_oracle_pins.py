@@ -436,6 +436,8 @@ def test_ldos_matches_ed_and_is_normalised():
         # int N(E) dE with E = a cos th: Gauss-Chebyshev weights pi/Kq * a sqrt(1-x^2)
         total = (r * np.pi / Kq * a * np.sqrt(1 - xq ** 2)).sum()
         assert total == pytest.approx(1.0, abs=1e-10)
+    mu_ee, _ = orc.moments(lat, a, sites, M)
+    assert np.array_equal(orc.ldos_from_moments(mu_ee, a, E), rho)
 
 
 def test_gauge_covariance():
