@@ -178,6 +178,30 @@ cbdg_status cbdg_get_option(cbdg_lattice *lat, int32_t option, int64_t *value);
 cbdg_status cbdg_profile_read(cbdg_lattice *lat, double *step_ms, int64_t *step_launches,
                               double *step_bytes, int32_t reset);
 
+/* Ensembles: many independent lattices (disorder realisations of uneven
+ * size) iterated to self-consistency together.  Every member: real on-site
+ * pairing, 4 directions, open edges, CBDG_FP32_MIXED, sides <= 128, and one
+ * shared mu and U.  Each iteration is one persistent launch over (sample,
+ * 16-column slab) work items plus small batched kernels (rescale, Fermi
+ * coefficients by K-node quadrature, parameters, mixing, convergence),
+ * captured once as a CUDA graph and replayed.  Not in the paper: a batching
+ * layer over its self-consistency loop (paragraph after Eq. 20). */
+typedef struct cbdg_ensemble cbdg_ensemble;
+cbdg_status cbdg_build_ensemble(const cbdg_lattice_desc *descs, int32_t n, cbdg_stream stream,
+                                cbdg_ensemble **out);
+cbdg_status cbdg_ensemble_destroy(cbdg_ensemble *ens);
+/* Runs up to max_iter iterations (Jackson kernel, M moments, linear mixing
+ * `mix`); a sample stops once max_i |Delta_out - Delta| < tol (the mix of
+ * that iteration is applied).  *iters_out = iterations run; converged_mask
+ * [n] (host) = 1 for converged samples.  Returns CBDG_ERR_NOT_CONVERGED if
+ * any sample is left, with all outputs filled. */
+cbdg_status cbdg_ensemble_scf(cbdg_ensemble *ens, double T, int32_t M, double mix, double tol,
+                              int32_t max_iter, int32_t *iters_out, int32_t *converged_mask);
+/* Copies sample `sample`'s current Delta ([N], host or device) out. */
+cbdg_status cbdg_ensemble_get_delta(cbdg_ensemble *ens, int32_t sample, cbdg_complex *delta);
+/* CBDG_OPT_QUADRATURE_NODES only (default 16384). */
+cbdg_status cbdg_ensemble_set_option(cbdg_ensemble *ens, int32_t option, int64_t value);
+
 /* Number of CUDA kernels the library has launched for this lattice since the
  * last reset (reset != 0 clears the counter after reading). */
 cbdg_status cbdg_launch_count(cbdg_lattice *lat, int64_t *launches, int32_t reset);

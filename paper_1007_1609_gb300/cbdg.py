@@ -96,6 +96,11 @@ def load():
             "cbdg_launch_count": [P, P, I32],
             "cbdg_moments_noalloc": [P, P, I32, I32, P, P, P],
             "cbdg_contract_tf32x3": [P, I32, P, I32, P, I32, I32, I32, I32, P],
+            "cbdg_build_ensemble": [P, I32, P, P],
+            "cbdg_ensemble_destroy": [P],
+            "cbdg_ensemble_scf": [P, D, I32, D, D, I32, P, P],
+            "cbdg_ensemble_get_delta": [P, I32, P],
+            "cbdg_ensemble_set_option": [P, I32, I64],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -227,6 +232,35 @@ def cbdg_contract_tf32x3(A, lda, B, ldb, D, ldd, m, n, k, stream=None):
                                        int(m), int(n), int(k), _stream_handle(stream)))
 
 
+def cbdg_build_ensemble(descs, stream=None):
+    arr = (cbdg_lattice_desc * len(descs))(*descs)
+    out = ctypes.c_void_p()
+    _check(load().cbdg_build_ensemble(arr, len(descs), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def cbdg_ensemble_destroy(ens):
+    _check(load().cbdg_ensemble_destroy(ens))
+
+
+def cbdg_ensemble_scf(ens, T, M, mix, tol, max_iter, converged_mask):
+    """Returns (status, iterations); NOT_CONVERGED is returned, not raised."""
+    it = ctypes.c_int32(0)
+    st = load().cbdg_ensemble_scf(ens, float(T), int(M), float(mix), float(tol), int(max_iter),
+                                  ctypes.byref(it), _ptr(converged_mask))
+    if st not in (CBDG_OK, CBDG_ERR_NOT_CONVERGED):
+        _check(st)
+    return st, it.value
+
+
+def cbdg_ensemble_get_delta(ens, sample, delta):
+    _check(load().cbdg_ensemble_get_delta(ens, int(sample), _ptr(delta)))
+
+
+def cbdg_ensemble_set_option(ens, option, value):
+    _check(load().cbdg_ensemble_set_option(ens, int(option), int(value)))
+
+
 def cbdg_last_error():
     return load().cbdg_last_error().decode()
 
@@ -236,6 +270,66 @@ def cbdg_version():
 
 
 # ---------------------------------------------------------------- convenience
+
+
+def make_desc(problem, precision="fp64", complex_field=None):
+    """A cbdg_lattice_desc for a workloads.Problem-like object; returns
+    (desc, arrays) -- keep `arrays` alive while the descriptor is used."""
+    p = problem
+    eps = np.ascontiguousarray(p.eps, dtype=np.float64)
+    hop = np.ascontiguousarray(p.hop, dtype=np.complex128)
+    delta = np.ascontiguousarray(p.delta0, dtype=np.complex128)
+    if complex_field is None:
+        complex_field = bool(np.any(hop.imag) or np.any(delta.imag))
+    d = cbdg_lattice_desc()
+    d.Lx, d.Ly = int(p.Lx), int(p.Ly)
+    d.periodic_x, d.periodic_y = int(p.periodic_x), int(p.periodic_y)
+    d.eps, d.hop, d.delta0 = _ptr(eps), _ptr(hop), _ptr(delta)
+    d.mu = float(p.mu)
+    d.n_dirs = int(hop.shape[-1]) if hop.ndim == 2 else int(hop.size // eps.size)
+    d.pairing = int(p.pairing)
+    d.coupling = float(p.coupling)
+    d.precision = PRECISIONS[precision]
+    d.complex_field = 1 if complex_field else 0
+    return d, (eps, hop, delta)
+
+
+class Ensemble:
+    """Independent lattices iterated to self-consistency together (FP32)."""
+
+    def __init__(self, problems, stream=None):
+        self._keep = []
+        descs = []
+        for p in problems:
+            d, arrays = make_desc(p, precision="fp32", complex_field=False)
+            descs.append(d)
+            self._keep.append(arrays)
+        self.sizes = [int(p.Lx * p.Ly) for p in problems]
+        self.handle = cbdg_build_ensemble(descs, stream)
+
+    def set_option(self, option, value):
+        cbdg_ensemble_set_option(self.handle, option, value)
+
+    def scf(self, T, M, mix, tol, max_iter):
+        mask = np.zeros(len(self.sizes), dtype=np.int32)
+        st, it = cbdg_ensemble_scf(self.handle, T, M, mix, tol, max_iter, mask)
+        return st == CBDG_OK, it, mask
+
+    def delta(self, sample):
+        d = np.zeros(self.sizes[sample], dtype=np.complex128)
+        cbdg_ensemble_get_delta(self.handle, sample, d)
+        return d
+
+    def close(self):
+        if getattr(self, "handle", None):
+            cbdg_ensemble_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 PRECISIONS = {"fp64": CBDG_FP64, "fp32": CBDG_FP32_MIXED}
