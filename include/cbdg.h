@@ -145,6 +145,26 @@ cbdg_status cbdg_contract_tf32x3(const float *A, int32_t lda, const float *B, in
 cbdg_status cbdg_scf_step(cbdg_lattice *lat, double T, int32_t M, double mix,
                           double *max_abs_ddelta);
 
+/* Reverse-mode gradient of one self-consistency map Delta_out(eps, t, Delta_in)
+ * (Eq. 19 through the recursion of Eq. 15) for real on-site pairing with
+ * 4 directions, with the rescale a and the coefficients C_n frozen at their
+ * values for the current Delta (a Gershgorin value, or the fixed one).
+ * Given dL_ddelta_out [N] (real part used), writes
+ *   dL_deps[i]         = dL/deps_i
+ *   dL_dhop[i*4 + d]   = dL/dt for the undirected bond (i, i+d), moving both
+ *                        directed entries together (stored on both; 0 across
+ *                        an open edge)
+ *   dL_ddelta_in[i]    = dL/dDelta_i  (the input Delta of the map)
+ * Any output may be NULL.  The forward recursion runs without doubling,
+ * keeps checkpoints of (j_{kS}, j_{kS+1}) every S = ceil(sqrt(M)) steps and
+ * recomputes each segment during the reverse sweep
+ *   lam_m = y_m + 2 H~ lam_{m+1} - lam_{m+2},  y_m = w_i (U/2) C_m h_i.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Not in the paper (it has no
+ * derivatives); added for gradient-based inverse design on Delta. */
+cbdg_status cbdg_order_parameter_backward(cbdg_lattice *lat, double T, int32_t M,
+                                          const cbdg_complex *dL_ddelta_out, double *dL_deps,
+                                          double *dL_dhop, double *dL_ddelta_in);
+
 /* Copies the lattice's current Delta ([N] or [N*4]) out, or replaces it. */
 cbdg_status cbdg_get_delta(cbdg_lattice *lat, cbdg_complex *delta);
 cbdg_status cbdg_set_delta(cbdg_lattice *lat, const cbdg_complex *delta);
@@ -165,8 +185,11 @@ enum {
   CBDG_OPT_RESCALE_MILLI = 6,    /* a = (value/1000) * Gershgorin bound; default 1100 (1.1).
                                     Below 1000 the spectrum may leave [-1, 1] and calls
                                     then fail with CBDG_ERR_SPECTRUM */
-  CBDG_OPT_PIPELINE_DEPTH = 7    /* lattice rows the recursion kernel stages ahead (1..4);
+  CBDG_OPT_PIPELINE_DEPTH = 7,   /* lattice rows the recursion kernel stages ahead (1..4);
                                     0 = automatic */
+  CBDG_OPT_FIXED_RESCALE_PICO = 8 /* > 0: use a = value * 1e-12 instead of the Gershgorin
+                                    rescale (frozen a, e.g. for finite differences);
+                                    0 = Gershgorin (default) */
 };
 cbdg_status cbdg_set_option(cbdg_lattice *lat, int32_t option, int64_t value);
 cbdg_status cbdg_get_option(cbdg_lattice *lat, int32_t option, int64_t *value);

@@ -37,6 +37,7 @@ CBDG_OPT_ROW_SPLIT = 4
 CBDG_OPT_WORKSPACE_MB = 5
 CBDG_OPT_RESCALE_MILLI = 6
 CBDG_OPT_PIPELINE_DEPTH = 7
+CBDG_OPT_FIXED_RESCALE_PICO = 8
 
 
 class CbdgError(RuntimeError):
@@ -96,6 +97,7 @@ def load():
             "cbdg_launch_count": [P, P, I32],
             "cbdg_moments_noalloc": [P, P, I32, I32, P, P, P],
             "cbdg_contract_tf32x3": [P, I32, P, I32, P, I32, I32, I32, I32, P],
+            "cbdg_order_parameter_backward": [P, D, I32, P, P, P, P],
             "cbdg_build_ensemble": [P, I32, P, P],
             "cbdg_ensemble_destroy": [P],
             "cbdg_ensemble_scf": [P, D, I32, D, D, I32, P, P],
@@ -230,6 +232,11 @@ def cbdg_moments_noalloc(desc, sites, n_sites, M, mu_ee, mu_eh, stream=None):
 def cbdg_contract_tf32x3(A, lda, B, ldb, D, ldd, m, n, k, stream=None):
     _check(load().cbdg_contract_tf32x3(_ptr(A), int(lda), _ptr(B), int(ldb), _ptr(D), int(ldd),
                                        int(m), int(n), int(k), _stream_handle(stream)))
+
+
+def cbdg_order_parameter_backward(lat, T, M, dL_ddelta_out, dL_deps, dL_dhop, dL_ddelta_in):
+    _check(load().cbdg_order_parameter_backward(lat, float(T), int(M), _ptr(dL_ddelta_out),
+                                                _ptr(dL_deps), _ptr(dL_dhop), _ptr(dL_ddelta_in)))
 
 
 def cbdg_build_ensemble(descs, stream=None):
@@ -417,3 +424,16 @@ class Lattice:
     @property
     def rescale(self):
         return cbdg_get_rescale(self.handle)
+
+    def freeze_rescale(self, a):
+        """Use a fixed a (None: back to the Gershgorin rescale)."""
+        cbdg_set_option(self.handle, CBDG_OPT_FIXED_RESCALE_PICO, 0 if a is None else int(round(a * 1e12)))
+
+    def backward(self, T, M, dL_ddelta_out):
+        """Gradients (eps [N], hop [N, 4], delta_in [N]) of one map (see the C ABI)."""
+        w = np.ascontiguousarray(dL_ddelta_out, dtype=np.complex128)
+        g_eps = np.zeros(self.N)
+        g_hop = np.zeros(self.N * 4)
+        g_delta = np.zeros(self.N)
+        cbdg_order_parameter_backward(self.handle, T, M, w, g_eps, g_hop, g_delta)
+        return g_eps, g_hop.reshape(self.N, 4), g_delta

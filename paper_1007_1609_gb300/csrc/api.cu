@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <complex>
 #include <new>
 #include <string>
@@ -107,10 +108,10 @@ struct cbdg_lattice {
   int nd = 0;  // number of Delta entries (N or 4N)
   DBuf eps, hop, delta, params, scal, flags, f, C, sites_all, sites_user;
   DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
-  DBuf acc_site_n, acc_site_b;
+  DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out;
   // options
   int K = 65536;
-  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0;
+  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0, fixed_a_pico = 0;
   int profile = 0;
   std::vector<cudaEvent_t> events;
   double prof_ms = 0.0, prof_bytes = 0.0;
@@ -181,10 +182,16 @@ size_t vec_elem_size(const cbdg_lattice *L) {
 // a, coefficient table and stencil parameters for the current Delta.
 cbdg_status prepare(cbdg_lattice *L, double T, int kernel, double lambda, int M, bool coeffs) {
   CK(L->scal.ensure(kScalars * sizeof(double)));
-  CK(launch_gershgorin(L->N, L->n_dirs, L->pairing, L->Lx, L->Ly, L->px, L->py,
-                       L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
-                       L->margin_milli / 1000.0, L->scal.as<double>(), L->stream));
-  L->launches += 2;
+  if (L->fixed_a_pico > 0) {
+    const double a = static_cast<double>(L->fixed_a_pico) * 1e-12;
+    CK(cudaMemcpyAsync(L->scal.as<double>() + kScalA, &a, sizeof(double), cudaMemcpyHostToDevice, L->stream));
+    CK(cudaStreamSynchronize(L->stream));  // a lives on this stack frame
+  } else {
+    CK(launch_gershgorin(L->N, L->n_dirs, L->pairing, L->Lx, L->Ly, L->px, L->py,
+                         L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
+                         L->margin_milli / 1000.0, L->scal.as<double>(), L->stream));
+    L->launches += 2;
+  }
   CK(L->C.ensure(static_cast<size_t>(M) * sizeof(double)));
   if (coeffs) {
     CK(L->f.ensure(static_cast<size_t>(L->K) * sizeof(double)));
@@ -533,7 +540,7 @@ cbdg_status cbdg_destroy(cbdg_lattice *L) {
   DBuf *bufs[] = {&L->eps,     &L->hop,   &L->delta, &L->params,  &L->scal,  &L->flags,
                   &L->f,       &L->C,     &L->sites_all, &L->sites_user, &L->vec0, &L->vec1,
                   &L->partials, &L->mu1,  &L->dA,    &L->acc_n,   &L->acc_d, &L->dout,
-                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b};
+                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b, &L->adj_ck, &L->adj_seg, &L->adj_lam, &L->adj_part, &L->adj_w, &L->adj_out};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
   delete L;
@@ -699,6 +706,170 @@ cbdg_status cbdg_scf_step(cbdg_lattice *L, double T, int32_t M, double mix,
   return st;
 }
 
+cbdg_status cbdg_order_parameter_backward(cbdg_lattice *L, double T, int32_t M,
+                                          const cbdg_complex *dL_ddelta_out, double *dL_deps,
+                                          double *dL_dhop, double *dL_ddelta_in) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  if (mode_of(L) != kReal)
+    return fail(CBDG_ERR_UNSUPPORTED, "the adjoint handles real on-site pairing with 4 directions");
+  if (!(T >= 0.0) || !isfinite(T)) return fail(CBDG_ERR_INVALID_ARG, "T must be finite and >= 0");
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  if (!dL_ddelta_out) return fail(CBDG_ERR_INVALID_ARG, "dL_ddelta_out is NULL");
+  const int N = L->N;
+  // w_i = Re dL/dDelta_out,i (Delta is real here)
+  std::vector<cbdg_complex> hw;
+  cudaError_t e = host_copy(dL_ddelta_out, N, hw);
+  if (e != cudaSuccess) return cuda_fail(e, "reading dL_ddelta_out");
+  std::vector<double> w(N);
+  for (int i = 0; i < N; ++i) {
+    if (!isfinite(hw[i].re)) return fail(CBDG_ERR_INVALID_ARG, "dL_ddelta_out is not finite");
+    w[i] = hw[i].re;
+  }
+  st = prepare(L, T, CBDG_JACKSON, 0.0, M, true);
+  if (st != CBDG_OK) return st;
+  CK(L->adj_w.ensure(N * sizeof(double)));
+  CK(cudaMemcpyAsync(L->adj_w.p, w.data(), N * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  std::vector<double> hC(M);
+  CK(cudaMemcpyAsync(hC.data(), L->C.p, M * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+
+  const size_t es = elem_size(L);
+  const size_t rows = 2 * static_cast<size_t>(N);
+  const int W = slab_width_default(L->precision);
+  const int S = std::max(2, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(M)))));
+  const int nseg = (M + S - 1) / S;
+  // per column: 2 checkpoint vectors per segment, S segment vectors, 2 forward, 2 adjoint
+  const int64_t per_col = static_cast<int64_t>((2 * nseg + S + 4) * rows * es);
+  size_t cap;
+  if (L->ws_mb > 0) {
+    cap = static_cast<size_t>(L->ws_mb) << 20;
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    cap = static_cast<size_t>(0.5 * (fr + L->adj_ck.bytes + L->adj_seg.bytes + L->adj_lam.bytes +
+                                     L->vec0.bytes + L->vec1.bytes));
+  }
+  int64_t max_cols = (static_cast<int64_t>(cap) / per_col / W) * W;
+  if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
+  if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for the adjoint");
+  const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((N + W - 1) / W) * W));
+  const int groups = 64;
+  CK(L->adj_part.ensure(static_cast<size_t>(groups) * N * 12 * sizeof(double)));
+  CK(cudaMemsetAsync(L->adj_part.p, 0, static_cast<size_t>(groups) * N * 12 * sizeof(double), L->stream));
+  const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
+  (void)tol;
+
+  for (int c0 = 0; c0 < N; c0 += chunk) {
+    const int ncols = std::min(chunk, N - c0);
+    const int ld = ((ncols + W - 1) / W) * W;
+    StepConfig cfg;
+    if (!plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
+                        static_cast<int>(L->depth), &cfg) || cfg.slab_w != W)
+      return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d for the adjoint", L->Lx);
+    const size_t vb = rows * ld * es;
+    CK(L->vec0.ensure(vb));
+    CK(L->vec1.ensure(vb));
+    CK(L->adj_ck.ensure(2 * nseg * vb));
+    CK(L->adj_seg.ensure(static_cast<size_t>(S) * vb));
+    CK(L->adj_lam.ensure(2 * vb));
+    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 3 * ld * sizeof(double)));
+    CK(L->mu1.ensure(ld * sizeof(double)));
+    CK(L->dA.ensure(ld * sizeof(double2)));
+    CK(L->acc_n.ensure(ld * sizeof(double)));
+    CK(L->acc_d.ensure(ld * 4 * sizeof(double2)));
+    const int32_t *sites = L->sites_all.as<int32_t>() + c0;
+    unsigned char *ck = L->adj_ck.as<unsigned char>();
+    unsigned char *seg = L->adj_seg.as<unsigned char>();
+    auto ckv = [&](int k, int which) { return ck + (2 * static_cast<size_t>(k) + which) * vb; };
+    auto segv = [&](int r) { return seg + static_cast<size_t>(r) * vb; };
+    StepArgs a;
+    a.params = L->params.p;
+    a.partials = L->partials.as<double>();
+    a.flags = L->flags.as<unsigned int>();
+    a.Lx = L->Lx;
+    a.Ly = L->Ly;
+    a.ld = ld;
+    a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+    // j_{m} = 2 H~ j_{m-1} - j_{m-2} written over dst, which must hold j_{m-2}
+    auto step = [&](void *cur, void *prev_inout) -> cbdg_status {
+      a.cur = cur;
+      a.prev = prev_inout;
+      CK(launch_step_real(L->precision, a, cfg, L->stream));
+      L->launches += 1;
+      return CBDG_OK;
+    };
+    // ---- forward with checkpoints (j_{kS}, j_{kS+1})
+    CK(cudaMemsetAsync(L->vec0.p, 0, vb, L->stream));
+    CK(cudaMemsetAsync(L->vec1.p, 0, vb, L->stream));
+    CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, W, sites, L->eps.as<double>(),
+                        L->mu, L->hop.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
+                        L->C.as<double>(), M, L->vec0.p, L->vec1.p, L->mu1.as<double>(),
+                        L->dA.as<double2>(), L->acc_n.as<double>(), L->acc_d.as<double2>(), nullptr,
+                        nullptr, 1, L->stream));
+    L->launches += 1;
+    // checkpoint k holds j_{kS} (slot 0) and j_{kS+1} (slot 1, when kS+1 < M)
+    CK(cudaMemcpyAsync(ckv(0, 0), L->vec0.p, vb, cudaMemcpyDeviceToDevice, L->stream));
+    CK(cudaMemcpyAsync(ckv(0, 1), L->vec1.p, vb, cudaMemcpyDeviceToDevice, L->stream));
+    void *jm2 = L->vec0.p, *jm1 = L->vec1.p;  // j_{m-2}, j_{m-1} before step m
+    const int m_last = (nseg - 1) * S + 1;     // no later j is ever needed from the forward pass
+    for (int m = 2; m < M && m <= m_last; ++m) {
+      st = step(jm1, jm2);  // jm2 <- j_m
+      if (st != CBDG_OK) return st;
+      std::swap(jm1, jm2);  // jm1 = j_m
+      if (m % S == 0) CK(cudaMemcpyAsync(ckv(m / S, 0), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+      if ((m - 1) % S == 0 && m - 1 >= S)
+        CK(cudaMemcpyAsync(ckv((m - 1) / S, 1), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+    }
+    // ---- reverse: lam_m for m = M-1 .. 1, gradient f_m lam_m (x) j_{m-1}
+    void *lam1 = L->adj_lam.p;                                  // lam_{m+1}
+    void *lam2 = L->adj_lam.as<unsigned char>() + vb;          // lam_{m+2}
+    CK(cudaMemsetAsync(lam1, 0, vb, L->stream));
+    CK(cudaMemsetAsync(lam2, 0, vb, L->stream));
+    const double halfU = 0.5 * L->coupling;
+    bool first = true;
+    for (int k = nseg - 1; k >= 0; --k) {
+      // recompute j_{kS} .. j_{kS+S-1} (those below M) into the segment
+      const int r_end = std::min(S, M - k * S);
+      CK(cudaMemcpyAsync(segv(0), ckv(k, 0), vb, cudaMemcpyDeviceToDevice, L->stream));
+      if (r_end > 1) CK(cudaMemcpyAsync(segv(1), ckv(k, 1), vb, cudaMemcpyDeviceToDevice, L->stream));
+      for (int r = 2; r < r_end; ++r) {
+        CK(cudaMemcpyAsync(segv(r), segv(r - 2), vb, cudaMemcpyDeviceToDevice, L->stream));
+        st = step(segv(r - 1), segv(r));
+        if (st != CBDG_OK) return st;
+      }
+      // m - 1 in [kS, kS + r_end - 1]  ->  m in [kS + 1, kS + r_end], m <= M - 1
+      const int m_hi = std::min(M - 1, k * S + r_end), m_lo = k * S + 1;
+      for (int m = m_hi; m >= m_lo; --m) {
+        if (first) {
+          // lam_{M-1} = y_{M-1}
+          first = false;
+        } else {
+          st = step(lam1, lam2);  // lam2 <- 2 H~ lam_{m+1} - lam_{m+2} = lam_m without source
+          if (st != CBDG_OK) return st;
+          std::swap(lam1, lam2);  // lam1 = lam_m, lam2 = lam_{m+1}
+        }
+        CK(launch_adjoint_source(L->precision, L->Lx, L->Ly, ncols, W, sites, L->adj_w.as<double>(),
+                                 halfU * hC[m], lam1, L->stream));
+        CK(launch_adjoint_accumulate(L->precision, L->Lx, L->Ly, L->px, L->py, ld, W, groups, lam1,
+                                     segv(m - 1 - k * S), m == 1 ? 1.0 : 2.0,
+                                     L->adj_part.as<double>(), L->stream));
+        L->launches += 2;
+      }
+    }
+  }
+  // gradients
+  CK(L->adj_out.ensure(static_cast<size_t>(N) * 6 * sizeof(double)));
+  double *ge = L->adj_out.as<double>(), *gd = ge + N, *gh = ge + 2 * N;
+  CK(launch_adjoint_final(L->Lx, L->Ly, L->px, L->py, groups, L->adj_part.as<double>(),
+                          L->scal.as<double>(), ge, gh, gd, L->stream));
+  L->launches += 1;
+  CK(deliver(L, dL_deps, ge, N * sizeof(double)));
+  CK(deliver(L, dL_ddelta_in, gd, N * sizeof(double)));
+  CK(deliver(L, dL_dhop, gh, static_cast<size_t>(N) * 4 * sizeof(double)));
+  return finish(L);
+}
+
 cbdg_status cbdg_get_delta(cbdg_lattice *L, cbdg_complex *delta) {
   if (!L || !delta) return fail(CBDG_ERR_INVALID_ARG, "NULL argument");
   CK(cudaSetDevice(L->device));
@@ -764,6 +935,10 @@ cbdg_status cbdg_set_option(cbdg_lattice *L, int32_t option, int64_t value) {
       if (value < 0 || value > 4) return fail(CBDG_ERR_INVALID_ARG, "depth must be in [0, 4]");
       L->depth = value;
       return CBDG_OK;
+    case CBDG_OPT_FIXED_RESCALE_PICO:
+      if (value < 0) return fail(CBDG_ERR_INVALID_ARG, "fixed rescale must be >= 0");
+      L->fixed_a_pico = value;
+      return CBDG_OK;
   }
   return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
 }
@@ -779,6 +954,7 @@ cbdg_status cbdg_get_option(cbdg_lattice *L, int32_t option, int64_t *value) {
     case CBDG_OPT_WORKSPACE_MB: *value = L->ws_mb; return CBDG_OK;
     case CBDG_OPT_RESCALE_MILLI: *value = L->margin_milli; return CBDG_OK;
     case CBDG_OPT_PIPELINE_DEPTH: *value = L->depth; return CBDG_OK;
+    case CBDG_OPT_FIXED_RESCALE_PICO: *value = L->fixed_a_pico; return CBDG_OK;
   }
   return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
 }

@@ -132,6 +132,17 @@ enum { kFlagSpectrum = 1u, kFlagTimeout = 2u };
 // 16-byte aligned) on tcgen05 tensor cores with the 3xTF32 split.
 cudaError_t launch_contract_tf32x3(const float *A, int lda, const float *B, int ldb, float *D,
                                    int ldd, int m, int n, int k, unsigned *flags, cudaStream_t s);
+// Adjoint of one self-consistency map (adjoint.cu).
+cudaError_t launch_adjoint_source(int precision, int Lx, int Ly, int ncols, int W,
+                                  const int32_t *sites, const double *w, double scale_m, void *lam,
+                                  cudaStream_t s);
+cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int py, int ld, int W,
+                                      int groups, const void *lam, const void *j, double f,
+                                      double *part, cudaStream_t s);
+cudaError_t launch_adjoint_final(int Lx, int Ly, int px, int py, int groups, const double *part,
+                                 const double *scal, double *g_eps, double *g_hop, double *g_delta,
+                                 cudaStream_t s);
+
 // Device address of the stand-alone contraction's error word (this device).
 cudaError_t contract_flag_address(unsigned **out);
 cudaError_t launch_ldos_weights(int n_E, int M, int ld, int kernel, double lambda,
