@@ -187,10 +187,22 @@ enum {
                                     then fail with CBDG_ERR_SPECTRUM */
   CBDG_OPT_PIPELINE_DEPTH = 7,   /* lattice rows the recursion kernel stages ahead (1..4);
                                     0 = automatic */
-  CBDG_OPT_FIXED_RESCALE_PICO = 8 /* > 0: use a = value * 1e-12 instead of the Gershgorin
+  CBDG_OPT_FIXED_RESCALE_PICO = 8, /* > 0: use a = value * 1e-12 instead of the Gershgorin
                                     rescale (frozen a, e.g. for finite differences);
                                     0 = Gershgorin (default) */
+  CBDG_OPT_WAIT_LIMIT_MS = 9,    /* limit of every wait of the recursion kernels on a staged
+                                    copy (default 2000); on expiry the call returns
+                                    CBDG_ERR_CUDA and the lattice stays usable */
+  CBDG_OPT_TEST_STALL_COPY = 10, /* test hook for failure detection: 1 makes the first staged
+                                    row of each recursion CTA wait for 16 bytes that never
+                                    arrive, so the wait runs out; 0 (default) off */
+  CBDG_OPT_AUTOTUNE = 11         /* 1: time candidate tiles (slab width, depth, row split) on
+                                    the first pass of each lattice shape and keep the fastest
+                                    (cached per process); 0 (default): static plan */
 };
+/* Read-only (cbdg_get_option): the tile of the last recursion pass, packed as
+ * slab width | depth << 16 | row split << 32. */
+enum { CBDG_INFO_LAST_TILE = 100 };
 cbdg_status cbdg_set_option(cbdg_lattice *lat, int32_t option, int64_t value);
 cbdg_status cbdg_get_option(cbdg_lattice *lat, int32_t option, int64_t *value);
 

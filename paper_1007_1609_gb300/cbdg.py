@@ -38,6 +38,10 @@ CBDG_OPT_WORKSPACE_MB = 5
 CBDG_OPT_RESCALE_MILLI = 6
 CBDG_OPT_PIPELINE_DEPTH = 7
 CBDG_OPT_FIXED_RESCALE_PICO = 8
+CBDG_OPT_WAIT_LIMIT_MS = 9
+CBDG_OPT_TEST_STALL_COPY = 10
+CBDG_OPT_AUTOTUNE = 11
+CBDG_INFO_LAST_TILE = 100
 
 
 class CbdgError(RuntimeError):
@@ -386,6 +390,11 @@ class Lattice:
 
     def set_option(self, option, value):
         cbdg_set_option(self.handle, option, value)
+
+    def last_tile(self):
+        """(slab width, pipeline depth, row split) of the last recursion pass."""
+        v = cbdg_get_option(self.handle, CBDG_INFO_LAST_TILE)
+        return v & 0xFFFF, (v >> 16) & 0xFFFF, v >> 32
 
     def moments(self, sites, M):
         sites = np.ascontiguousarray(sites, dtype=np.int32)

@@ -19,6 +19,9 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -111,12 +114,14 @@ struct cbdg_lattice {
   DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out;
   // options
   int K = 65536;
-  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0, fixed_a_pico = 0;
+  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0, fixed_a_pico = 0, wait_ms = 2000, stall = 0, autotune = 0;
   int profile = 0;
   std::vector<cudaEvent_t> events;
   double prof_ms = 0.0, prof_bytes = 0.0;
   int64_t prof_launches = 0;
   int64_t launches = 0;  // kernels this library launched for the lattice
+  int tuned_w = 0, tuned_d = 0, tuned_split = 0;
+  StepConfig last_cfg{};
   double last_a = 0.0;
 };
 
@@ -215,6 +220,108 @@ cbdg_status prepare(cbdg_lattice *L, double T, int kernel, double lambda, int M,
   return CBDG_OK;
 }
 
+// ---- autotuner: measured choice of (slab width, pipeline depth, row split)
+struct TuneKey {
+  int mode, precision, Lx, Ly, nsum;
+  int64_t ncols;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(mode, precision, Lx, Ly, nsum, ncols) <
+           std::tie(o.mode, o.precision, o.Lx, o.Ly, o.nsum, o.ncols);
+  }
+};
+struct TuneVal {
+  int W, D, split;
+  float ms;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+// Times every candidate tile for one recursion step on the lattice's own
+// vector buffers (their contents are about to be reset) and returns the
+// fastest.  Cached per process and lattice shape.
+cbdg_status autotune(cbdg_lattice *L, int mode, int n_sites, TuneVal *out) {
+  const TuneKey key{mode, L->precision, L->Lx, L->Ly, L->n_dirs * 2 + L->pairing, n_sites};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *out = it->second;
+      return CBDG_OK;
+    }
+  }
+  const bool real = mode == kReal;
+  const size_t es = elem_size(L) * (real ? 1 : 2);
+  const size_t rows = 2 * static_cast<size_t>(L->N);
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  const size_t cap = static_cast<size_t>(0.6 * (fr + L->vec0.bytes + L->vec1.bytes));
+  int64_t ld = ((static_cast<int64_t>(n_sites) + 31) / 32) * 32;
+  ld = std::min<int64_t>(ld, (static_cast<int64_t>(cap / (2 * rows * es)) / 32) * 32);
+  if (ld < 32) return fail(CBDG_ERR_OOM, "workspace too small to tune");
+  const size_t vb = rows * ld * es;
+  CK(L->vec0.ensure(vb));
+  CK(L->vec1.ensure(vb));
+  CK(cudaMemsetAsync(L->vec0.p, 0, vb, L->stream));
+  CK(cudaMemsetAsync(L->vec1.p, 0, vb, L->stream));
+  std::vector<int> Ws = real ? (L->precision == 1 ? std::vector<int>{4, 8, 16, 32} : std::vector<int>{2, 4, 8, 16})
+                             : (L->precision == 1 ? std::vector<int>{2, 4, 8} : std::vector<int>{1, 2, 4});
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  TuneVal best{0, 0, 0, 1e30f};
+  for (int W : Ws) {
+    for (int D = 1; D <= (real ? 4 : 3); ++D) {
+      for (int split : {0, 1, 2}) {
+        StepConfig cfg;
+        const bool ok = real ? plan_step_real(L->precision, L->Lx, L->Ly, static_cast<int>(ld), W, split, D, &cfg)
+                             : plan_step_cplx(L->precision, L->Lx, L->Ly, static_cast<int>(ld), W, split, D, &cfg);
+        if (!ok || cfg.slab_w != W || cfg.depth != D) continue;
+        if (split > 0 && cfg.row_split != split) continue;
+        const int nsum = real ? 3 : 4;
+        CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * nsum * ld * sizeof(double)));
+        StepArgs a;
+        a.cur = L->vec1.p;
+        a.prev = L->vec0.p;
+        a.params = L->params.p;
+        a.partials = L->partials.as<double>();
+        a.flags = L->flags.as<unsigned int>();
+        a.wait_ns = static_cast<unsigned long long>(L->wait_ms) * 1000000ull;
+        a.stall_tx = 0;
+        a.Lx = L->Lx;
+        a.Ly = L->Ly;
+        a.ld = static_cast<int>(ld);
+        a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+        auto launch = [&]() {
+          return real ? launch_step_real(L->precision, a, cfg, L->stream)
+                      : launch_step_cplx(L->precision, L->n_dirs == 8, mode == kDirect, a, cfg, L->stream);
+        };
+        CK(launch());
+        float t_best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+          CK(cudaEventRecord(e0, L->stream));
+          CK(launch());
+          CK(cudaEventRecord(e1, L->stream));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          t_best = std::min(t_best, ms);
+        }
+        L->launches += 4;
+        if (t_best < best.ms) best = TuneVal{W, D, cfg.row_split, t_best};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best.W == 0) return fail(CBDG_ERR_UNSUPPORTED, "no tile fits this lattice");
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best;
+  }
+  *out = best;
+  return CBDG_OK;
+}
+
 // Runs the recursion for n_sites start vectors (device list), folding the
 // moments into per-column accumulators; optionally writes the moments
 // ([n_sites][M] and [n_sites][M][stride]).  With finalize, Delta_out and n
@@ -227,6 +334,18 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
   const size_t rows = 2 * static_cast<size_t>(L->N);
   const int Wdef = mode == kReal ? slab_width_default(L->precision) : slab_width_default_cplx(L->precision);
   int W = L->slab_w > 0 ? static_cast<int>(L->slab_w) : Wdef;
+  int want_split = static_cast<int>(L->row_split), want_depth = static_cast<int>(L->depth);
+  if (L->autotune && L->slab_w == 0 && L->row_split == 0 && L->depth == 0 && n_sites > 0) {
+    TuneVal tv;
+    cbdg_status ts = autotune(L, mode, n_sites, &tv);
+    if (ts != CBDG_OK) return ts;
+    W = tv.W;
+    want_split = tv.split;
+    want_depth = tv.D;
+    L->tuned_w = tv.W;
+    L->tuned_d = tv.D;
+    L->tuned_split = tv.split;
+  }
   // column chunk: bounded by the workspace cap (two vectors)
   size_t cap;
   if (L->ws_mb > 0) {
@@ -254,10 +373,9 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     const int ld = ((ncols + W - 1) / W) * W;
     StepConfig cfg;
     const bool planned =
-        mode == kReal ? plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
-                                       static_cast<int>(L->depth), &cfg)
-                      : plan_step_cplx(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
-                                       static_cast<int>(L->depth), &cfg);
+        mode == kReal ? plan_step_real(L->precision, L->Lx, L->Ly, ld, W, want_split, want_depth, &cfg)
+                      : plan_step_cplx(L->precision, L->Lx, L->Ly, ld, W, want_split, want_depth, &cfg);
+    L->last_cfg = cfg;
     if (!planned)
       return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d with %d columns", L->Lx, ld);
     const int nsum = mode == kReal ? 3 : 4;
@@ -319,6 +437,8 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     a.params = L->params.p;
     a.partials = L->partials.as<double>();
     a.flags = L->flags.as<unsigned int>();
+    a.wait_ns = static_cast<unsigned long long>(L->wait_ms) * 1000000ull;
+    a.stall_tx = L->stall ? 16u : 0u;
     a.Lx = L->Lx;
     a.Ly = L->Ly;
     a.ld = ld;
@@ -389,7 +509,7 @@ cbdg_status finish(cbdg_lattice *L) {
   CK(cudaStreamSynchronize(L->stream));
   L->last_a = a;
   if (flags & kFlagTimeout)
-    return fail(CBDG_ERR_CUDA, "a recursion kernel gave up waiting for a staged copy");
+    return fail(CBDG_ERR_CUDA, "a recursion kernel gave up waiting for a staged copy (results discarded)");
   if (flags & kFlagSpectrum)
     return fail(CBDG_ERR_SPECTRUM, "a Chebyshev moment exceeded 1 in magnitude (a = %g too small)", a);
   return CBDG_OK;
@@ -787,6 +907,8 @@ cbdg_status cbdg_order_parameter_backward(cbdg_lattice *L, double T, int32_t M,
     a.params = L->params.p;
     a.partials = L->partials.as<double>();
     a.flags = L->flags.as<unsigned int>();
+    a.wait_ns = static_cast<unsigned long long>(L->wait_ms) * 1000000ull;
+    a.stall_tx = L->stall ? 16u : 0u;
     a.Lx = L->Lx;
     a.Ly = L->Ly;
     a.ld = ld;
@@ -939,6 +1061,16 @@ cbdg_status cbdg_set_option(cbdg_lattice *L, int32_t option, int64_t value) {
       if (value < 0) return fail(CBDG_ERR_INVALID_ARG, "fixed rescale must be >= 0");
       L->fixed_a_pico = value;
       return CBDG_OK;
+    case CBDG_OPT_WAIT_LIMIT_MS:
+      if (value < 1 || value > 60000) return fail(CBDG_ERR_INVALID_ARG, "wait limit out of range");
+      L->wait_ms = value;
+      return CBDG_OK;
+    case CBDG_OPT_TEST_STALL_COPY:
+      L->stall = value != 0;
+      return CBDG_OK;
+    case CBDG_OPT_AUTOTUNE:
+      L->autotune = value != 0;
+      return CBDG_OK;
   }
   return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
 }
@@ -955,6 +1087,13 @@ cbdg_status cbdg_get_option(cbdg_lattice *L, int32_t option, int64_t *value) {
     case CBDG_OPT_RESCALE_MILLI: *value = L->margin_milli; return CBDG_OK;
     case CBDG_OPT_PIPELINE_DEPTH: *value = L->depth; return CBDG_OK;
     case CBDG_OPT_FIXED_RESCALE_PICO: *value = L->fixed_a_pico; return CBDG_OK;
+    case CBDG_OPT_WAIT_LIMIT_MS: *value = L->wait_ms; return CBDG_OK;
+    case CBDG_OPT_TEST_STALL_COPY: *value = L->stall; return CBDG_OK;
+    case CBDG_OPT_AUTOTUNE: *value = L->autotune; return CBDG_OK;
+    case CBDG_INFO_LAST_TILE:
+      *value = static_cast<int64_t>(L->last_cfg.slab_w) | (static_cast<int64_t>(L->last_cfg.depth) << 16) |
+               (static_cast<int64_t>(L->last_cfg.row_split) << 32);
+      return CBDG_OK;
   }
   return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
 }

@@ -29,6 +29,8 @@ struct StepArgs {
   const void *params;   // [N][kParamStride] scalars of the step precision
   double *partials;     // [row_split][3][ld]: sum |j_n|^2, <j_{n+1}|j_n>, symplectic
   unsigned int *flags;  // error bits (kFlagTimeout when a staged copy never arrived)
+  unsigned long long wait_ns;  // limit of every wait on a staged copy
+  unsigned stall_tx;    // test hook: extra bytes the first staged row expects (never arrive)
   int Lx, Ly;
   int ld;               // columns (a multiple of the slab width)
   int rows_per_cta;     // lattice rows per CTA along y

@@ -188,6 +188,8 @@ extern "C" cbdg_status cbdg_moments_noalloc(const cbdg_lattice_desc *d, const in
     a.params = params;
     a.partials = partials;
     a.flags = flags;
+    a.wait_ns = 2000000000ull;
+    a.stall_tx = 0;
     a.Lx = d->Lx;
     a.Ly = d->Ly;
     a.ld = ld;

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
   const S *par = static_cast<const S *>(a.params);
   const unsigned row_bytes = static_cast<unsigned>(rowel * sizeof(S));
   const unsigned par_bytes = static_cast<unsigned>(pel * sizeof(S));
-  constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+  const unsigned long long kWaitLimitNs = a.wait_ns;
 
   if (t == 0) {
     for (int k = 0; k < JS; ++k) mbar_init(smem_addr(&bars[k]), 1);
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
     const int r = k - 1;
     const bool with_old = (r >= 0 && r < rows);
     const unsigned bar = smem_addr(&bars[k % JS]);
-    mbar_expect_tx(bar, row_bytes + par_bytes + (with_old ? row_bytes : 0u));
+    mbar_expect_tx(bar, row_bytes + par_bytes + (with_old ? row_bytes : 0u) + (k == 0 ? a.stall_tx : 0u));
     bulk_load(smem_addr(sj + (k % JS) * rowel), cur + static_cast<size_t>(y) * rowel, row_bytes, bar);
     bulk_load(smem_addr(sp + (k % JS) * pel), par + static_cast<size_t>(y) * pel, par_bytes, bar);
     if (with_old)

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
   S *prev = static_cast<S *>(a.prev) + slab;
   const S *par = static_cast<const S *>(a.params);
   const unsigned row_bytes = static_cast<unsigned>(rowel * sizeof(S));
-  constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+  const unsigned long long kWaitLimitNs = a.wait_ns;
 
   if (t == 0) {
     for (int k = 0; k < JS; ++k) mbar_init(smem_addr(&bars[k]), 1);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
     const int r = k - 1;
     const bool with_old = (r >= 0 && r < rows);
     const unsigned bar = smem_addr(&bars[k % JS]);
-    mbar_expect_tx(bar, row_bytes + (with_old ? row_bytes : 0u));
+    mbar_expect_tx(bar, row_bytes + (with_old ? row_bytes : 0u) + (k == 0 ? a.stall_tx : 0u));
     bulk_load(smem_addr(sj + (k % JS) * rowel), cur + static_cast<size_t>(y) * rowel, row_bytes, bar);
     if (with_old)
       bulk_load(smem_addr(so + (r % OS) * rowel), prev + static_cast<size_t>(y0 + r) * rowel,

@@ -224,3 +224,36 @@ def test_full_size_disordered_128_sampled(precision):
     # properties at every site: |Delta| bounded by U/2, 0 <= n <= 2
     assert np.all(np.abs(d) <= 0.5 * p.coupling + 1e-9)
     assert np.all((n > -1e-9) & (n < 2 + 1e-9))
+
+
+def test_lost_copy_times_out_and_lattice_stays_usable():
+    """Failure detection without a fault: the test hook makes every recursion
+    CTA wait for 16 bytes that never arrive; the wait runs out after 20 ms,
+    the call reports CBDG_ERR_CUDA, and the same lattice then computes
+    correct moments."""
+    p = rect(8, 8, 24, seed=41, periodic=0)
+    lat = gpu_lattice(p, "fp64", wait_limit_ms=20, test_stall_copy=1)
+    sites = np.arange(p.N, dtype=np.int32)
+    with pytest.raises(cbdg.CbdgError) as ei:
+        lat.moments(sites, p.M)
+    assert ei.value.status == cbdg.CBDG_ERR_CUDA and "gave up waiting" in str(ei.value)
+    lat.set_option(cbdg.CBDG_OPT_TEST_STALL_COPY, 0)
+    ee, eh = lat.moments(sites, p.M)
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, p.M)
+    assert max_abs(ee, oee) < 1e-11 and max_abs(eh, oeh) < 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_autotuned_tile(precision):
+    p = rect(40, 24, 48, seed=43, periodic=0)
+    sites = np.arange(p.N, dtype=np.int32)
+    ref = gpu_lattice(p, precision).moments(sites, p.M)
+    lat = gpu_lattice(p, precision, autotune=1)
+    got = lat.moments(sites, p.M)
+    W, D, split = lat.last_tile()
+    assert W in (1, 2, 4, 8, 16, 32) and 1 <= D <= 4 and split >= 1
+    tol = TOL[precision][0]
+    assert max_abs(got[0], ref[0]) < tol and max_abs(got[1], ref[1]) < tol
+    again = lat.moments(sites, p.M)  # cached tile: bitwise repeatable
+    assert lat.last_tile() == (W, D, split)
+    assert np.array_equal(again[0], got[0])
