@@ -300,6 +300,8 @@ def run_gb300(args):
         if not args.no_fp64:
             extra["fp64"] = fp64_leg(p, stream, cbdg, torch, units_per_step)
             extra["fp32_vs_fp64"] = {"speedup": value / world / extra["fp64"]["value"]}
+        if not args.no_extras:
+            extra["other_stages"] = extra_legs(cbdg, wl, torch, stream, hbm)
         cpu = None
         if not args.no_cpu_baseline:
             cpu, sites, od, on, oa = cpu_baseline(p)
@@ -345,6 +347,106 @@ def run_gb300(args):
     return 0
 
 
+def leg_contraction(cbdg, torch, stream, shape=(65536, 2048, 512)):
+    """LDOS contraction on the tensor cores at the vortex-lattice shape:
+    [65536 sites x 2048 moments] . [2048 x 512 energies], 3xTF32."""
+    m, k, n = shape
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn((m, k), generator=g, device="cuda", dtype=torch.float32)
+    B = torch.randn((n, k), generator=g, device="cuda", dtype=torch.float32)
+    D = torch.empty((m, n), device="cuda", dtype=torch.float32)
+    cbdg.cbdg_contract_tf32x3(A, k, B, k, D, n, m, n, k, stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        cbdg.cbdg_contract_tf32x3(A, k, B, k, D, n, m, n, k, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    tflops = 3 * 2.0 * m * n * k / (ms * 1e-3) / 1e12
+    peak = bf16_peak() * 0.5
+    return {"shape": [m, k, n], "ms": ms, "tflops": tflops,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak,
+                         "peak_kind": "measured bf16 dense burst x 0.5 (nominal tf32/bf16 ratio)",
+                         "note": "3 TF32 products per term (hi*hi + hi*lo + lo*hi)"}}
+
+
+def leg_dwave(cbdg, wl, stream, hbm):
+    """General recursion step (complex64, t', bond pairing, Peierls field) on
+    the 256x256 vortex lattice, a 4096-column chunk."""
+    import numpy as np
+    pv = wl.dwave_vortex(256, 34)
+    lat = cbdg.Lattice(pv, precision="fp32", stream=stream, complex_field=True)
+    sites = np.arange(4096, dtype=np.int32) * 16
+    lat.moments(sites, 8)
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
+    cbdg.cbdg_profile_read(lat.handle, reset=True)
+    lat.moments(sites, pv.M)
+    sms, sn, sb = cbdg.cbdg_profile_read(lat.handle)
+    tile = lat.last_tile()
+    lat.close()
+    return {"lattice": "256x256 periodic, t'=-0.3, 2 h/2e flux, bond pairing, complex64",
+            "columns": 4096, "launches": sn, "avg_launch_ms": sms / sn, "tile": list(tile),
+            "roofline": {"bound": "hbm", "achieved": sb / (sms * 1e-3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": sb / (sms * 1e-3) / 1e9 / hbm}}
+
+
+def leg_ensemble(cbdg, wl, stream):
+    """256 disordered lattices (sides 32..96, M = 512): one graph-replayed
+    self-consistency iteration."""
+    probs = wl.ensemble()
+    ens = cbdg.Ensemble(probs, stream=stream)
+    t0 = time.perf_counter()
+    ens.scf(0.01, 512, 0.5, 0.0, 1)  # includes the graph capture
+    t1 = time.perf_counter()
+    ens.scf(0.01, 512, 0.5, 0.0, 1)
+    t2 = time.perf_counter()
+    ens.close()
+    units = sum(p.N for p in probs) * 256
+    algo_bytes = sum(3 * 2 * p.N * 4 * p.N * 255 for p in probs)  # 3 streams x 2N x 4 B, N columns, 255 steps
+    return {"samples": len(probs), "s_per_iteration": t2 - t1, "first_call_s": t1 - t0,
+            "vector_steps_per_s": units / (t2 - t1), "algorithmic_gbs": algo_bytes / (t2 - t1) / 1e9}
+
+
+def leg_adjoint(cbdg, wl, stream):
+    """Gradient of one self-consistency map, 64x64, M = 512 (FP64 and FP32)."""
+    import numpy as np
+    pg = wl.gradient_case()
+    out = {}
+    for prec in ("fp64", "fp32"):
+        lg = cbdg.Lattice(pg, precision=prec, stream=stream)
+        d, _ = lg.order_parameter(pg.T, pg.M)
+        w = (2.0 * (d.real - pg.extra["target"])).astype(np.complex128)
+        lg.backward(pg.T, pg.M, w)
+        t0 = time.perf_counter()
+        lg.backward(pg.T, pg.M, w)
+        out[f"{prec}_s"] = time.perf_counter() - t0
+        lg.close()
+    return out
+
+
+def extra_legs(cbdg, wl, torch, stream, hbm, only=None):
+    """Other hot-path stages at their workload sizes (not the headline)."""
+    legs = {
+        "contraction": lambda: leg_contraction(cbdg, torch, stream),
+        "dwave": lambda: leg_dwave(cbdg, wl, stream, hbm),
+        "ensemble": lambda: leg_ensemble(cbdg, wl, stream),
+        "adjoint": lambda: leg_adjoint(cbdg, wl, stream),
+    }
+    return {name: fn() for name, fn in legs.items() if only is None or only == name}
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def fp64_leg(p, stream, cbdg, torch, units_per_step):
     """The plain FP64 form on the same GPU: one warm-up and one timed iteration."""
     lat = cbdg.Lattice(p, precision="fp64", stream=stream)
@@ -382,12 +484,26 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--stage", default=None, choices=["contraction", "dwave", "ensemble", "adjoint"],
+                    help="measure only this stage and print its record (profiling runs)")
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")
     ap.add_argument("--moments", type=int, default=M)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.stage is not None:
+        import torch
+        from paper_1007_1609_gb300 import build as B
+        B.build()
+        from paper_1007_1609_gb300 import cbdg
+        from paper_1007_1609_gb300 import workloads as wl
+        stream = torch.cuda.Stream()
+        hbm, _ = peaks()
+        rec = extra_legs(cbdg, wl, torch, stream, hbm, only=args.stage)
+        print(json.dumps({"stage": args.stage, **rec}), flush=True)
+        return 0
     return run_gb300(args)
 
 
