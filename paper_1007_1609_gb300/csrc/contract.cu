@@ -6,14 +6,17 @@
 // (x = hi + lo); D accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor
 // memory ("3xTF32"), which carries about 21 significant bits per product.
 //
-// Tiling: a CTA computes a 128 x 256 tile of D.  Per K-block of 32 (128
-// bytes of FP32 per row) the CTA stages A_hi, A_lo (128 rows) and B_hi, B_lo
-// (256 rows) in shared memory in the canonical K-major 128-byte-swizzled
-// layout (row r at r*128 bytes, 16-byte chunk c at position c ^ (r & 7),
-// tiles 1024-byte aligned); one thread issues 4 k-steps x 3 products of
-// tcgen05.mma (M = 128, N = 256, K = 8) into a 128-lane x 256-column FP32
-// accumulator in tensor memory and commits to an mbarrier; the epilogue
-// reads the accumulator with tcgen05.ld (each warp its 32-lane quarter).
+// Tiling: a CTA computes a 128 x 128 tile of D.  Per K-block of 32 (128
+// bytes of FP32 per row) the CTA stages A_hi, A_lo, B_hi, B_lo (128 rows
+// each) in shared memory in the canonical K-major 128-byte-swizzled layout
+// (row r at r*128 bytes, 16-byte chunk c at position c ^ (r & 7), tiles
+// 1024-byte aligned); one thread issues 4 k-steps x 3 products of
+// tcgen05.mma (M = 128, N = 128, K = 8) into a 128-lane x 128-column FP32
+// accumulator in tensor memory and commits to an mbarrier.  The tensor
+// cores accumulate in FP32 with truncation, so every 8 K-blocks the
+// accumulator is drained with tcgen05.ld (each warp its 32-lane quarter)
+// into an FP64 tile in shared memory and restarted: the error of the sum
+// then grows with 96 accumulations, not with all K/8 * 3 of them.
 // Every wait is bounded; on expiry the CTA records an error bit, still
 // waits (bounded) for its tensor-core work and frees its tensor memory.
 #include <math.h>
@@ -24,10 +27,11 @@ namespace cbdg {
 namespace {
 
 constexpr int kTileM = 128;
-constexpr int kTileN = 256;
+constexpr int kTileN = 128;
+constexpr int kFlushBlocks = 8;  // K-blocks per FP32 accumulation group
 constexpr int kBlockK = 32;  // FP32 elements per 128-byte row
 constexpr int kThreads = 128;
-constexpr unsigned kTmemCols = 256;
+constexpr unsigned kTmemCols = 128;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
@@ -97,13 +101,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     contract_kernel(const float *__restrict__ A, int lda, const float *__restrict__ B, int ldb,
                     float *__restrict__ D, int ldd, int m, int n, int k, unsigned *flags) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned tiles: A_hi, A_lo (16 KB each), B_hi, B_lo (32 KB each)
+  // 1024-byte aligned tiles: A_hi, A_lo, B_hi, B_lo (16 KB each), then the
+  // FP64 accumulator, column-major [kTileN][kTileM] (conflict-free per row)
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   unsigned char *a_hi = base;
   unsigned char *a_lo = a_hi + kTileM * 128;
   unsigned char *b_hi = a_lo + kTileM * 128;
   unsigned char *b_lo = b_hi + kTileN * 128;
+  double *acc64 = reinterpret_cast<double *>(b_lo + kTileN * 128);
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ unsigned tmem_slot;
   __shared__ int abort_flag;
@@ -128,6 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const unsigned tmem = tmem_slot;
+  for (int idx = t; idx < kTileM * kTileN; idx += kThreads) acc64[idx] = 0.0;
 
   const int kblocks = (k + kBlockK - 1) / kBlockK;
   int committed = 0;
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const unsigned off = ks * 32;
         const unsigned long long dah = smem_desc(ah + off), dal = smem_desc(al + off);
         const unsigned long long dbh = smem_desc(bh + off), dbl = smem_desc(bl + off);
-        const unsigned acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
+        const unsigned acc0 = (kb % kFlushBlocks > 0 || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -216,28 +223,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (abort_flag) break;
+    if (kb % kFlushBlocks == kFlushBlocks - 1 || kb == kblocks - 1) {
+      // drain the FP32 group sum into the FP64 tile (row = warp*32 + lane)
+      const int r = warp * 32 + lane;
+      for (int c0 = 0; c0 < kTileN; c0 += 16) {
+        unsigned v[16];
+        const unsigned taddr = tmem + (static_cast<unsigned>(warp * 32) << 16) + static_cast<unsigned>(c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+              "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc64[(c0 + j) * kTileM + r] += static_cast<double>(__uint_as_float(v[j]));
+      }
+      // the next MMA overwrites the accumulator: order the loads before it
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
   }
 
   if (!abort_flag && kblocks > 0) {
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows m0 + 32w + lane)
     const int row = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < kTileN; c0 += 16) {
-      unsigned r[16];
-      const unsigned taddr = tmem + (static_cast<unsigned>(warp * 32) << 16) + static_cast<unsigned>(c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-            "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (row < m) {
-        float *out = D + static_cast<size_t>(row) * ldd + n0 + c0;
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (n0 + c0 + j < n) out[j] = __uint_as_float(r[j]);
-      }
+    if (row < m) {
+      float *out = D + static_cast<size_t>(row) * ldd + n0;
+      for (int j = 0; j < kTileN && n0 + j < n; ++j)
+        out[j] = static_cast<float>(acc64[j * kTileM + warp * 32 + lane]);
     }
   } else if (abort_flag) {
     if (t == 0) {
@@ -255,7 +270,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-constexpr size_t kSmem = 1024 + static_cast<size_t>(2 * kTileM + 2 * kTileN) * 128;
+constexpr size_t kSmem = 1024 + static_cast<size_t>(2 * kTileM + 2 * kTileN) * 128 +
+                         static_cast<size_t>(kTileM) * kTileN * sizeof(double);
 
 // error word of the stand-alone contraction entry point
 static __device__ unsigned g_contract_flag;
