@@ -45,11 +45,8 @@ def recorded_traffic():
     import glob
     import hashlib
     import re
-    h = hashlib.sha256()
-    for f in ("paper_1007_1609_gb300/csrc/step.cu", "paper_1007_1609_gb300/csrc/internal.h"):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    digest = h.hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_1007_1609_gb300/csrc/step.cu"), "rb") as fh:
+        digest = hashlib.sha256(fh.read()).hexdigest()[:16]
     for path in glob.glob(os.path.join(ROOT, "profiles", "step_real_kernel_fp32_*.md")):
         text = open(path).read()
         m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+kernel_source_sha256_16:\s*([0-9a-f]+)", text)
