@@ -138,6 +138,9 @@ __device__ __forceinline__ Cx<S> pc(const S *p, int k) {
 
 template <typename S, int W, int NT, int MAXX, int D, bool NNN, bool BOND, bool SUMS>
 __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
+  // FP32: parameter rows ride the TMA pipeline with j_{n-1}; FP64 (bound by
+  // its arithmetic) reads them through the read-only cache.
+  constexpr bool PSTAGE = sizeof(S) == 4;
   using V = typename CVec<S>::T;
   constexpr int VC = CVec<S>::N;       // complex elements per 16-byte vector
   constexpr int QUADS = W / VC;        // 16-byte chunks per row segment
@@ -153,6 +156,8 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
   const int rowel = 2 * Lx * W * 2;    // scalars of one lattice row of a slab (complex)
   S *sj = reinterpret_cast<S *>(smem_raw);
   S *so = sj + JS * rowel;
+  const int pel = Lx * kCplxParamStride;  // parameter scalars of one lattice row
+  S *sp = so + OS * rowel;                  // [OS][pel] when PSTAGE
 
   const int t = threadIdx.x;
   const int q = t % QUADS;
@@ -164,6 +169,7 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
   S *prev = static_cast<S *>(a.prev) + slab;
   const S *par = static_cast<const S *>(a.params);
   const unsigned row_bytes = static_cast<unsigned>(rowel * sizeof(S));
+  const unsigned par_bytes = PSTAGE ? static_cast<unsigned>(pel * sizeof(S)) : 0u;
   const unsigned long long kWaitLimitNs = a.wait_ns;
 
   if (t == 0) {
@@ -179,11 +185,14 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
     const int r = k - 1;
     const bool with_old = (r >= 0 && r < rows);
     const unsigned bar = smem_addr(&bars[k % JS]);
-    mbar_expect_tx(bar, row_bytes + (with_old ? row_bytes : 0u) + (k == 0 ? a.stall_tx : 0u));
+    mbar_expect_tx(bar, row_bytes + (with_old ? row_bytes + par_bytes : 0u) + (k == 0 ? a.stall_tx : 0u));
     bulk_load(smem_addr(sj + (k % JS) * rowel), cur + static_cast<size_t>(y) * rowel, row_bytes, bar);
-    if (with_old)
+    if (with_old) {
       bulk_load(smem_addr(so + (r % OS) * rowel), prev + static_cast<size_t>(y0 + r) * rowel,
                 row_bytes, bar);
+      if (PSTAGE)
+        bulk_load(smem_addr(sp + (r % OS) * pel), par + static_cast<size_t>(y0 + r) * pel, par_bytes, bar);
+    }
   };
   int issued = min(D + 2, rows + 2);
   if (t == 0)
@@ -220,9 +229,10 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
           auto ld = [&](const S *row, int xx, int part) {
             return *reinterpret_cast<const V *>(row + part * hb + xx * W * 2 + off);
           };
-          const S *pp = par + (static_cast<size_t>(y) * Lx + x) * kCplxParamStride;
-          const S e = __ldg(pp + 0);
-          const Cx<S> dl = pc(pp, 2);
+          const S *pp = PSTAGE ? sp + (i % OS) * pel + x * kCplxParamStride
+                               : par + (static_cast<size_t>(y) * Lx + x) * kCplxParamStride;
+          const S e = PSTAGE ? pp[0] : __ldg(pp + 0);
+          const Cx<S> dl = PSTAGE ? Cx<S>{pp[2], pp[3]} : pc(pp, 2);
           // neighbour rows/columns per direction 0:+x 1:-x 2:+y 3:-y 4:+x+y 5:-x-y 6:+x-y 7:-x+y
           const S *nrow[8] = {rc, rc, rp, rm, rp, rm, rm, rp};
           const int ncol[8] = {xr, xl, x, x, xr, xl, xr, xl};
@@ -240,14 +250,14 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
 #pragma unroll
           for (int dd = 0; dd < (NNN ? 8 : 4); ++dd) {
             const V ud = ld(nrow[dd], ncol[dd], 0), vd = ld(nrow[dd], ncol[dd], 1);
-            const Cx<S> td = pc(pp, 4 + 2 * dd);
+            const Cx<S> td = PSTAGE ? Cx<S>{pp[4 + 2 * dd], pp[5 + 2 * dd]} : pc(pp, 4 + 2 * dd);
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
               Cx<S> hu = cget<V, S>(un, j), hv = cget<V, S>(vn, j);
               hu = csub(hu, cmul(td, cget<V, S>(ud, j)));
               hv = cadd(hv, cmulc(td, cget<V, S>(vd, j)));
               if (BOND && dd < 4) {
-                const Cx<S> bd = pc(pp, 20 + 2 * dd);
+                const Cx<S> bd = PSTAGE ? Cx<S>{pp[20 + 2 * dd], pp[21 + 2 * dd]} : pc(pp, 20 + 2 * dd);
                 hu = cadd(hu, cmul(bd, cget<V, S>(vd, j)));
                 hv = cadd(hv, cmulc(bd, cget<V, S>(ud, j)));
               }
@@ -314,7 +324,8 @@ size_t smem_bytes(int Lx) {
   constexpr int QUADS = W / CVec<S>::N;
   constexpr int XSLOTS = kThreads / QUADS;
   const size_t rowel = static_cast<size_t>(2) * Lx * W * 2;
-  const size_t ring = ((3 + D) + (2 + D)) * rowel * sizeof(S);
+  const size_t pel = sizeof(S) == 4 ? static_cast<size_t>(Lx) * kCplxParamStride : 0;
+  const size_t ring = (((3 + D) + (2 + D)) * rowel + (2 + D) * pel) * sizeof(S);
   const size_t red = static_cast<size_t>(4) * XSLOTS * W * sizeof(double);
   return std::max(ring, red);
 }
