@@ -131,6 +131,17 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """Max of a per-rank float over all ranks (the timing rule for N > 1)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(problem, target_s=12.0, max_sites=1024):
     """The FP64 oracle, as it stands, on a bounded sample of start sites of the
     same workload (all M moments per site).  Returns (record, sites, delta, n)."""
@@ -246,12 +257,7 @@ def run_gb300(args):
         torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     step_ms, step_n, step_bytes = cbdg.cbdg_profile_read(lat.handle)
     launches = cbdg.cbdg_launch_count(lat.handle)
     cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 0)
