@@ -196,9 +196,12 @@ enum {
   CBDG_OPT_TEST_STALL_COPY = 10, /* test hook for failure detection: 1 makes the first staged
                                     row of each recursion CTA wait for 16 bytes that never
                                     arrive, so the wait runs out; 0 (default) off */
-  CBDG_OPT_AUTOTUNE = 11         /* 1: time candidate tiles (slab width, depth, row split) on
+  CBDG_OPT_AUTOTUNE = 11,        /* 1: time candidate tiles (slab width, depth, row split) on
                                     the first pass of each lattice shape and keep the fastest
                                     (cached per process); 0 (default): static plan */
+  CBDG_OPT_TEMPORAL_STEPS = 12   /* recursion steps per pass over the vectors (temporal
+                                    blocking), 1..4, for real on-site FP32 lattices with open
+                                    y edges; 1 = one step per pass; 0 = library default */
 };
 /* Read-only (cbdg_get_option): the tile of the last recursion pass, packed as
  * slab width | depth << 16 | row split << 32. */

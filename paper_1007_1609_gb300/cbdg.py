@@ -41,6 +41,7 @@ CBDG_OPT_FIXED_RESCALE_PICO = 8
 CBDG_OPT_WAIT_LIMIT_MS = 9
 CBDG_OPT_TEST_STALL_COPY = 10
 CBDG_OPT_AUTOTUNE = 11
+CBDG_OPT_TEMPORAL_STEPS = 12
 CBDG_INFO_LAST_TILE = 100
 
 

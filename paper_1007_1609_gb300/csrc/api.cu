@@ -114,7 +114,7 @@ struct cbdg_lattice {
   DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out;
   // options
   int K = 65536;
-  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0, fixed_a_pico = 0, wait_ms = 2000, stall = 0, autotune = 0;
+  int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0, fixed_a_pico = 0, wait_ms = 2000, stall = 0, autotune = 0, temporal = 0;
   int profile = 0;
   std::vector<cudaEvent_t> events;
   double prof_ms = 0.0, prof_bytes = 0.0;
@@ -163,6 +163,9 @@ int host_neighbour(const cbdg_lattice_desc *d, int s, int dir) {
 }
 
 bool finite_c(const cbdg_complex &z) { return isfinite(z.re) && isfinite(z.im); }
+
+// Recursion steps per HBM pass used when CBDG_OPT_TEMPORAL_STEPS is 0.
+constexpr int64_t kDefaultTemporalSteps = 1;
 
 // Recursion kernel family for the lattice:
 //   kReal:   real on-site pairing, nearest neighbours (step.cu), doubling;
@@ -378,11 +381,20 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     L->last_cfg = cfg;
     if (!planned)
       return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d with %d columns", L->Lx, ld);
+    // temporal blocking: K steps per HBM pass (real FP32, open y edges)
+    StepConfig mcfg;
+    int Kt = 1;
+    const int64_t want_k = L->temporal == 0 ? kDefaultTemporalSteps : L->temporal;
+    // both kernels run on the same slab-blocked layout, so they share the slab width
+    if (!(mode == kReal && L->precision == CBDG_FP32_MIXED && !L->py && want_k >= 2 &&
+          (cfg.slab_w == 8 || cfg.slab_w == 16) &&
+          plan_step_multi(L->Lx, L->Ly, ld, cfg.slab_w, static_cast<int>(want_k), want_depth, &mcfg, &Kt)))
+      Kt = 1;
     const int nsum = mode == kReal ? 3 : 4;
     const size_t vbytes = rows * ld * es;
     CK(L->vec0.ensure(vbytes));
     CK(L->vec1.ensure(vbytes));
-    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * nsum * ld * sizeof(double)));
+    CK(L->partials.ensure(static_cast<size_t>(std::max(cfg.row_split, Kt)) * nsum * ld * sizeof(double)));
     CK(L->mu1.ensure(ld * sizeof(double)));
     CK(L->dA.ensure(ld * sizeof(double2)));
     CK(L->acc_n.ensure(ld * sizeof(double)));
@@ -424,6 +436,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
       }
     }
     void *cur = L->vec1.p, *prev = L->vec0.p;
+    std::vector<double> launch_bytes;
     // doubling: step n yields moments 2n, 2n+1; direct: step n yields j_{n+1}
     const int steps = mode == kDirect ? M - 2 : (M + 1) / 2 - 1;
     if (L->profile && static_cast<int>(L->events.size()) < 2 * steps) {
@@ -443,13 +456,36 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     a.Ly = L->Ly;
     a.ld = ld;
     a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
-    for (int n = 1; n <= steps; ++n) {
+    int launch_idx = 0;
+    for (int n = 1; n <= steps;) {
       a.cur = cur;
       a.prev = prev;
-      if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1)], L->stream));
+      if (Kt >= 2 && steps - n + 1 >= Kt) {
+        // steps n .. n+Kt-1 in one pass; (prev, cur) end as (j_{n+Kt-1}, j_{n+Kt})
+        a.rows_per_cta = L->Ly;
+        if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx], L->stream));
+        CK(launch_step_multi(a, mcfg, Kt, L->stream));
+        if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx + 1], L->stream));
+        L->launches += 1;
+        for (int lv = 0; lv < Kt; ++lv) {
+          CK(launch_fold(n + lv, M, ncols, ld, 1, L->partials.as<double>() + static_cast<size_t>(lv) * 3 * ld,
+                         L->C.as<double>(), L->mu1.as<double>(), L->dA.as<double2>(),
+                         L->acc_n.as<double>(), L->acc_d.as<double2>(), mee, meh, mom_stride,
+                         L->flags.as<unsigned int>(), tol, L->stream));
+          L->launches += 1;
+        }
+        a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+        launch_bytes.push_back(4.0 * static_cast<double>(vbytes));
+        ++launch_idx;
+        n += Kt;
+        continue;
+      }
+      if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx], L->stream));
       if (mode == kReal) CK(launch_step_real(L->precision, a, cfg, L->stream));
       else CK(launch_step_cplx(L->precision, L->n_dirs == 8, mode == kDirect, a, cfg, L->stream));
-      if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1) + 1], L->stream));
+      if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx + 1], L->stream));
+      launch_bytes.push_back(3.0 * static_cast<double>(vbytes));
+      ++launch_idx;
       if (mode == kReal)
         CK(launch_fold(n, M, ncols, ld, cfg.row_split, L->partials.as<double>(), L->C.as<double>(),
                        L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
@@ -466,6 +502,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
                          L->flags.as<unsigned int>(), tol, L->stream));
       L->launches += 2;
       std::swap(cur, prev);
+      ++n;
     }
     if (finalize && mode != kDirect) {
       CK(launch_finalize_onsite(ncols, sites + c0, L->coupling, L->acc_n.as<double>(),
@@ -473,15 +510,15 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
                                 L->stream));
       L->launches += 1;
     }
-    if (L->profile && steps > 0) {
+    if (L->profile && launch_idx > 0) {
       CK(cudaStreamSynchronize(L->stream));
-      for (int n = 0; n < steps; ++n) {
+      for (int k = 0; k < launch_idx; ++k) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, L->events[2 * n], L->events[2 * n + 1]));
+        CK(cudaEventElapsedTime(&ms, L->events[2 * k], L->events[2 * k + 1]));
         L->prof_ms += ms;
+        L->prof_bytes += launch_bytes[k];
       }
-      L->prof_launches += steps;
-      L->prof_bytes += static_cast<double>(steps) * 3.0 * static_cast<double>(vbytes);
+      L->prof_launches += launch_idx;
     }
   }
   if (finalize && mode == kDirect) {
@@ -1071,6 +1108,10 @@ cbdg_status cbdg_set_option(cbdg_lattice *L, int32_t option, int64_t value) {
     case CBDG_OPT_AUTOTUNE:
       L->autotune = value != 0;
       return CBDG_OK;
+    case CBDG_OPT_TEMPORAL_STEPS:
+      if (value < 0 || value > 4) return fail(CBDG_ERR_INVALID_ARG, "temporal steps must be in [0, 4]");
+      L->temporal = value;
+      return CBDG_OK;
   }
   return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
 }
@@ -1090,6 +1131,7 @@ cbdg_status cbdg_get_option(cbdg_lattice *L, int32_t option, int64_t *value) {
     case CBDG_OPT_WAIT_LIMIT_MS: *value = L->wait_ms; return CBDG_OK;
     case CBDG_OPT_TEST_STALL_COPY: *value = L->stall; return CBDG_OK;
     case CBDG_OPT_AUTOTUNE: *value = L->autotune; return CBDG_OK;
+    case CBDG_OPT_TEMPORAL_STEPS: *value = L->temporal; return CBDG_OK;
     case CBDG_INFO_LAST_TILE:
       *value = static_cast<int64_t>(L->last_cfg.slab_w) | (static_cast<int64_t>(L->last_cfg.depth) << 16) |
                (static_cast<int64_t>(L->last_cfg.row_split) << 32);

@@ -63,6 +63,14 @@ bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_
                     int want_depth, StepConfig *cfg);
 int slab_width_default(int precision);
 
+// K recursion steps per pass (temporal blocking) for real on-site FP32
+// lattices with open y edges; one CTA per slab (row split 1).  Partial sums
+// are [K][3][ld].  plan_step_multi returns false when the shape has no
+// instantiation or the rings do not fit in shared memory.
+bool plan_step_multi(int Lx, int Ly, int ld, int want_w, int want_k, int want_depth,
+                     StepConfig *cfg, int *k_out);
+cudaError_t launch_step_multi(const StepArgs &a, const StepConfig &cfg, int K, cudaStream_t s);
+
 // Recursion step for the general lattice (complex vectors; nnn: 8 hopping
 // directions; bond: nearest-neighbour pairing, which skips the column sums).
 // The partial sums, when formed, are [row_split][4][ld].

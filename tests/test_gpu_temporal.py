@@ -1,0 +1,97 @@
+"""Temporal blocking (several recursion steps of Eq. 15 per pass over the
+vectors) against the FP64 oracle.
+
+The multi-step kernel serves real on-site FP32 lattices with open edges along
+y; everything else falls back to one step per pass.  Tolerances are those of
+the FP32 recursion: 1e-5 on moments and 1e-4 on Delta_i.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1007_1609_gb300 import cbdg
+from paper_1007_1609_gb300 import workloads as wl
+from tests._common import as_oracle, gpu_available, max_abs
+from tests.test_gpu_parity import K, gpu_lattice, rect
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+TOL_MOM, TOL_DELTA = 1e-5, 1e-4
+
+
+def recursion_launches(lat, sites, M):
+    lat.set_option(cbdg.CBDG_OPT_PROFILE, 1)
+    cbdg.cbdg_profile_read(lat.handle, reset=True)
+    out = lat.moments(sites, M)
+    _, n, _ = cbdg.cbdg_profile_read(lat.handle, reset=True)
+    return out, n
+
+
+@pytest.mark.parametrize("slab", [8, 16])
+@pytest.mark.parametrize("depth", [1, 2])
+@pytest.mark.parametrize("steps", [2, 3, 4])
+@pytest.mark.parametrize("case", [(7, 5, 33), (40, 24, 48), (80, 3, 17), (3, 2, 64), (64, 9, 10)])
+def test_moments_match_oracle(case, steps, depth, slab):
+    Lx, Ly, M = case
+    p = rect(Lx, Ly, M, seed=Lx * 31 + Ly, periodic=0)
+    sites = np.arange(p.N, dtype=np.int32)
+    lat = gpu_lattice(p, "fp32", temporal_steps=steps, pipeline_depth=depth, slab_width=slab)
+    (ee, eh), launches = recursion_launches(lat, sites, M)
+    n_steps = (M + 1) // 2 - 1
+    # the grouped launches ran: K steps per pass, then single steps for the rest
+    assert launches == n_steps // steps + n_steps % steps
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, M)
+    assert max_abs(ee, oee) < TOL_MOM, max_abs(ee, oee)
+    assert max_abs(eh, oeh) < TOL_MOM, max_abs(eh, oeh)
+    lat.close()
+
+
+@pytest.mark.parametrize("steps", [2, 4])
+def test_same_as_one_step_per_pass(steps):
+    """Same arithmetic in the same order per level: the multi-step result
+    equals the one-step-per-pass result to FP32 rounding of the sums."""
+    p = rect(33, 17, 65, seed=5, periodic=0)
+    sites = np.arange(p.N, dtype=np.int32)[::-1].copy()
+    one = gpu_lattice(p, "fp32", temporal_steps=1).moments(sites, p.M)
+    got = gpu_lattice(p, "fp32", temporal_steps=steps).moments(sites, p.M)
+    assert max_abs(got[0], one[0]) < 1e-6 and max_abs(got[1], one[1]) < 1e-6
+
+
+def test_periodic_y_falls_back_to_one_step():
+    p = rect(6, 9, 40, seed=4, periodic=1)
+    sites = np.arange(p.N, dtype=np.int32)
+    lat = gpu_lattice(p, "fp32", temporal_steps=4)
+    (ee, eh), launches = recursion_launches(lat, sites, p.M)
+    assert launches == (p.M + 1) // 2 - 1
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, p.M)
+    assert max_abs(ee, oee) < TOL_MOM and max_abs(eh, oeh) < TOL_MOM
+
+
+def test_option_range():
+    p = rect(4, 4, 8, seed=2, periodic=0)
+    lat = gpu_lattice(p, "fp32")
+    for bad in (-1, 5):
+        with pytest.raises(cbdg.CbdgError):
+            lat.set_option(cbdg.CBDG_OPT_TEMPORAL_STEPS, bad)
+    lat.set_option(cbdg.CBDG_OPT_TEMPORAL_STEPS, 3)
+    assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_OPT_TEMPORAL_STEPS) == 3
+
+
+@pytest.mark.parametrize("steps,slab", [(2, 16), (4, 8)])
+def test_full_size_disordered_128_sampled(steps, slab):
+    """The 128x128 disordered workload at M = 1024, all 16384 start vectors:
+    Delta_out and n at sampled sites vs the oracle."""
+    p = wl.swave_disordered(128, 1024, seed=1001)
+    lat = gpu_lattice(p, "fp32", temporal_steps=steps, slab_width=slab, profile=1)
+    d, n = lat.order_parameter(p.T, p.M)
+    _, launches, _ = cbdg.cbdg_profile_read(lat.handle, reset=True)
+    assert launches == 511 // steps + 511 % steps
+    ol = as_oracle(p)
+    rng = np.random.default_rng(11)
+    sample = np.concatenate([[0, 127, 128 * 64 + 64, p.N - 1],
+                             rng.choice(p.N, 6, replace=False)]).astype(np.int32)
+    od, on = orc.order_parameter_sites(ol, lat.rescale, p.T, p.M, K, sample)
+    assert max_abs(d[sample], od) < TOL_DELTA, max_abs(d[sample], od)
+    assert max_abs(n[sample], on) < TOL_DELTA, max_abs(n[sample], on)
+    assert np.all(np.abs(d) <= 0.5 * p.coupling + 1e-9)
