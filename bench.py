@@ -39,15 +39,16 @@ L, M, SEED = 128, 1024, 1001
 FP64_FLOPS_PER_ELEMENT_STEP = 20.0  # stencil 12 + moment products 8 (FMA = 2 flops)
 
 
-def recorded_traffic():
-    """DRAM bytes per step-kernel launch from the committed ncu summary, or
-    None when the kernel source changed since those counters were taken."""
+def recorded_traffic(source="step.cu", pattern="step_real_kernel_fp32_*.md"):
+    """DRAM bytes per launch of a recursion kernel from the committed ncu
+    summary, or None when the kernel source changed since those counters were
+    taken."""
     import glob
     import hashlib
     import re
-    with open(os.path.join(ROOT, "paper_1007_1609_gb300/csrc/step.cu"), "rb") as fh:
+    with open(os.path.join(ROOT, "paper_1007_1609_gb300/csrc", source), "rb") as fh:
         digest = hashlib.sha256(fh.read()).hexdigest()[:16]
-    for path in glob.glob(os.path.join(ROOT, "profiles", "step_real_kernel_fp32_*.md")):
+    for path in glob.glob(os.path.join(ROOT, "profiles", pattern)):
         text = open(path).read()
         m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+kernel_source_sha256_16:\s*([0-9a-f]+)", text)
         if m and m.group(2) == digest:
@@ -242,6 +243,8 @@ def run_gb300(args):
 
     # ---------------- device-resident headline: FP32 recursion, FP64 folds
     lat = cbdg.Lattice(p, precision="fp32", stream=stream)
+    if args.temporal is not None:
+        lat.set_option(cbdg.CBDG_OPT_TEMPORAL_STEPS, args.temporal)
     for _ in range(args.warmup):
         lat.scf_step(p.T, p.M, p.mix)
     cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
@@ -260,6 +263,7 @@ def run_gb300(args):
     ms_max = max_over_ranks(ms, world, dev)
     step_ms, step_n, step_bytes = cbdg.cbdg_profile_read(lat.handle)
     launches = cbdg.cbdg_launch_count(lat.handle)
+    k_used = cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL)
     cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 0)
     value = world * units_per_step * args.steps / (ms_max / 1e3)
 
@@ -269,6 +273,8 @@ def run_gb300(args):
     e2e_value = None
     if not args.no_e2e:
         lat_e = cbdg.Lattice(p, precision="fp32", stream=stream)
+        if args.temporal is not None:
+            lat_e.set_option(cbdg.CBDG_OPT_TEMPORAL_STEPS, args.temporal)
         for _ in range(1):
             cbdg.cbdg_set_delta(lat_e.handle, host_delta)
             cbdg.cbdg_scf_step(lat_e.handle, p.T, p.M, p.mix)
@@ -288,15 +294,24 @@ def run_gb300(args):
     if rank == 0:
         hbm, peak_kind = peaks()
         achieved = (step_bytes / step_n) / (step_ms / step_n / 1e3) / 1e9 if step_n else None
-        traffic, traffic_src = recorded_traffic()
+        if k_used >= 2:
+            traffic, traffic_src = recorded_traffic("step_multi.cu", "step_multi_kernel_fp32_*.md")
+            kernel = (f"step_multi_kernel: FP32, {k_used} recursion steps per pass over the vectors "
+                      "(reads j_(n-1), j_n; writes the last two), moment products fused; the "
+                      "leftover odd step of each iteration runs step_real_kernel")
+        else:
+            traffic, traffic_src = recorded_traffic()
+            kernel = "step_real_kernel: FP32 recursion step with fused moment products"
         if args.lattice != L or args.moments != M:
             traffic, traffic_src = None, None  # recorded for the 128x128, M=1024 launch only
+        vec_bytes = 2 * p.N * p.N * 4  # one FP32 block of all start vectors
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                     "traffic_source": traffic_src,
-                    "kernel": "cheb_step (FP32 recursion step with fused moments)",
+                    "kernel": kernel, "steps_per_pass": int(k_used),
                     "peak_kind": f"{peak_kind} (copy bandwidth)",
-                    "algorithmic_bytes_per_launch": step_bytes / step_n if step_n else None,
+                    "algorithmic_bytes_per_launch": (4 if k_used >= 2 else 3) * vec_bytes,
+                    "recursion_launches_per_step": step_n / args.steps if args.steps else None,
                     "avg_launch_ms": step_ms / step_n if step_n else None,
                     "share_of_step": step_ms / ms if ms else None}
         extra = {}
@@ -493,6 +508,8 @@ def main():
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")
     ap.add_argument("--moments", type=int, default=M)
+    ap.add_argument("--temporal", type=int, default=None,
+                    help="recursion steps per pass over the vectors (1..4; default: library choice)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

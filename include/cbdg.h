@@ -199,13 +199,21 @@ enum {
   CBDG_OPT_AUTOTUNE = 11,        /* 1: time candidate tiles (slab width, depth, row split) on
                                     the first pass of each lattice shape and keep the fastest
                                     (cached per process); 0 (default): static plan */
-  CBDG_OPT_TEMPORAL_STEPS = 12   /* recursion steps per pass over the vectors (temporal
+  CBDG_OPT_TEMPORAL_STEPS = 12   /* recursion steps K per pass over the vectors (temporal
                                     blocking), 1..4, for real on-site FP32 lattices with open
-                                    y edges; 1 = one step per pass; 0 = library default */
+                                    y edges: one pass reads j_{n-1}, j_n and writes
+                                    j_{n+K-1}, j_{n+K}; 1 = one step per pass; 0 (default) =
+                                    2.  Shapes the multi-step kernel does not serve run one
+                                    step per pass: periodic y, FP64, complex fields, slab
+                                    widths other than 8 and 16, Lx above 64 (K = 2: 128) at
+                                    slab width 16 or above 128 (K = 2: 256) at slab width 8,
+                                    and rings that do not fit in shared memory */
 };
 /* Read-only (cbdg_get_option): the tile of the last recursion pass, packed as
  * slab width | depth << 16 | row split << 32. */
 enum { CBDG_INFO_LAST_TILE = 100 };
+/* Read-only: recursion steps per pass (K) used by the last pass. */
+enum { CBDG_INFO_LAST_TEMPORAL = 101 };
 cbdg_status cbdg_set_option(cbdg_lattice *lat, int32_t option, int64_t value);
 cbdg_status cbdg_get_option(cbdg_lattice *lat, int32_t option, int64_t *value);
 

@@ -43,6 +43,7 @@ CBDG_OPT_TEST_STALL_COPY = 10
 CBDG_OPT_AUTOTUNE = 11
 CBDG_OPT_TEMPORAL_STEPS = 12
 CBDG_INFO_LAST_TILE = 100
+CBDG_INFO_LAST_TEMPORAL = 101
 
 
 class CbdgError(RuntimeError):

@@ -122,6 +122,7 @@ struct cbdg_lattice {
   int64_t launches = 0;  // kernels this library launched for the lattice
   int tuned_w = 0, tuned_d = 0, tuned_split = 0;
   StepConfig last_cfg{};
+  int last_temporal = 1;
   double last_a = 0.0;
 };
 
@@ -164,8 +165,9 @@ int host_neighbour(const cbdg_lattice_desc *d, int s, int dir) {
 
 bool finite_c(const cbdg_complex &z) { return isfinite(z.re) && isfinite(z.im); }
 
-// Recursion steps per HBM pass used when CBDG_OPT_TEMPORAL_STEPS is 0.
-constexpr int64_t kDefaultTemporalSteps = 1;
+// Recursion steps per HBM pass used when CBDG_OPT_TEMPORAL_STEPS is 0: two
+// steps per pass read and write 4 vectors where two single steps move 6.
+constexpr int64_t kDefaultTemporalSteps = 2;
 
 // Recursion kernel family for the lattice:
 //   kReal:   real on-site pairing, nearest neighbours (step.cu), doubling;
@@ -390,6 +392,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
           (cfg.slab_w == 8 || cfg.slab_w == 16) &&
           plan_step_multi(L->Lx, L->Ly, ld, cfg.slab_w, static_cast<int>(want_k), want_depth, &mcfg, &Kt)))
       Kt = 1;
+    L->last_temporal = Kt;
     const int nsum = mode == kReal ? 3 : 4;
     const size_t vbytes = rows * ld * es;
     CK(L->vec0.ensure(vbytes));
@@ -1132,6 +1135,7 @@ cbdg_status cbdg_get_option(cbdg_lattice *L, int32_t option, int64_t *value) {
     case CBDG_OPT_TEST_STALL_COPY: *value = L->stall; return CBDG_OK;
     case CBDG_OPT_AUTOTUNE: *value = L->autotune; return CBDG_OK;
     case CBDG_OPT_TEMPORAL_STEPS: *value = L->temporal; return CBDG_OK;
+    case CBDG_INFO_LAST_TEMPORAL: *value = L->last_temporal; return CBDG_OK;
     case CBDG_INFO_LAST_TILE:
       *value = static_cast<int64_t>(L->last_cfg.slab_w) | (static_cast<int64_t>(L->last_cfg.depth) << 16) |
                (static_cast<int64_t>(L->last_cfg.row_split) << 32);

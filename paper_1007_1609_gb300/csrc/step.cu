@@ -96,19 +96,23 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigne
   }
 }
 
-// Compensated (Kahan) accumulator in FP32; plain accumulation in FP64.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Accumulates a1*b1 + a2*b2: compensated (Kahan) in FP32, with the products
+// and the compensation term fused into two FMAs; plain accumulation in FP64.
 template <typename S>
 struct Acc {
   S s = 0;
-  __device__ __forceinline__ void add(S x) { s += x; }
+  __device__ __forceinline__ void add2(S a1, S b1, S a2, S b2) { s = fma_rn(a1, b1, fma_rn(a2, b2, s)); }
   __device__ __forceinline__ double value() const { return s; }
 };
 template <>
 struct Acc<float> {
   float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    float y = __fsub_rn(x, c);
-    float t = __fadd_rn(s, y);
+  __device__ __forceinline__ void add2(float a1, float b1, float a2, float b2) {
+    const float y = fma_rn(a1, b1, fma_rn(a2, b2, -c));
+    const float t = __fadd_rn(s, y);
     c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
   }
@@ -237,21 +241,19 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
 #pragma unroll
           for (int j = 0; j < VEC; ++j) {
             const S uj = comp<V, S>(u, j), vj = comp<V, S>(v, j);
-            // 2 H~ j_n: electron row  (eps-mu) u + Delta v - sum_d t_d u_d
-            //           hole row      Delta u - (eps-mu) v + sum_d t_d v_d
-            const S hu = e * uj + d * vj -
-                         (t0 * comp<V, S>(ur, j) + t1 * comp<V, S>(ul, j) +
-                          t2 * comp<V, S>(uu, j) + t3 * comp<V, S>(ud, j));
-            const S hv = d * uj - e * vj +
-                         (t0 * comp<V, S>(vr, j) + t1 * comp<V, S>(vl, j) +
-                          t2 * comp<V, S>(vu, j) + t3 * comp<V, S>(vd, j));
-            const S unj = hu - comp<V, S>(uo, j);
-            const S vnj = hv - comp<V, S>(vo, j);
+            // 2 H~ j_n - j_{n-1}:
+            //   electron row  (eps-mu) u + Delta v - sum_d t_d u_d - u_old
+            //   hole row      Delta u - (eps-mu) v + sum_d t_d v_d - v_old
+            // each one chain of six FMAs
+            const S unj = fma_rn(e, uj, fma_rn(d, vj, -fma_rn(t3, comp<V, S>(ud, j), fma_rn(t2, comp<V, S>(uu, j),
+                              fma_rn(t1, comp<V, S>(ul, j), fma_rn(t0, comp<V, S>(ur, j), comp<V, S>(uo, j)))))));
+            const S vnj = fma_rn(d, uj, fma_rn(-e, vj, fma_rn(t3, comp<V, S>(vd, j), fma_rn(t2, comp<V, S>(vu, j),
+                              fma_rn(t1, comp<V, S>(vl, j), fma_rn(t0, comp<V, S>(vr, j), -comp<V, S>(vo, j)))))));
             set_comp<V, S>(un, j, unj);
             set_comp<V, S>(vn, j, vnj);
-            accA[j].add(uj * uj + vj * vj);
-            accB[j].add(unj * uj + vnj * vj);
-            accC[j].add(unj * vj - vnj * uj);
+            accA[j].add2(uj, uj, vj, vj);
+            accB[j].add2(unj, uj, vnj, vj);
+            accC[j].add2(unj, vj, -vnj, uj);
           }
           __stcs(reinterpret_cast<V *>(out + x * W + off), un);
           __stcs(reinterpret_cast<V *>(out + hb + x * W + off), vn);
