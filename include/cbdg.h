@@ -129,13 +129,36 @@ cbdg_status cbdg_ldos(cbdg_lattice *lat, const int32_t *sites, int32_t n_sites, 
 
 /* Dense contraction behind cbdg_ldos, on the tensor cores (tcgen05,
  * kind::tf32) with each operand split into TF32 head and tail (3 products,
- * about 21 significant bits, FP32 accumulation):
+ * about 21 significant bits; FP32 accumulation, re-based every 256 terms of
+ * the k sum so that the tensor cores' truncating accumulation stays short):
  *   D[i*ldd + j] = sum_{l<k} A[i*lda + l] * B[j*ldb + l],  i < m, j < n.
- * A, B, D are device pointers on the current device; lda and ldb are
- * multiples of 4 (>= k), A and B 16-byte aligned, ldd >= n.  Runs on
- * `stream` and returns after completion.  Errors: INVALID_ARG, CUDA. */
+ * A, B, D are device pointers on the current device; lda, ldb >= k,
+ * ldd >= n.  The split planes live in a library-owned stream-ordered pool
+ * (2 (m + n) kp floats, kp = cbdg_contract_kp(k)).  Runs on `stream` and
+ * returns after completion.  Errors: INVALID_ARG, OOM, CUDA. */
 cbdg_status cbdg_contract_tf32x3(const float *A, int32_t lda, const float *B, int32_t ldb, float *D,
                                  int32_t ldd, int32_t m, int32_t n, int32_t k, cbdg_stream stream);
+
+/* Row length of the split planes for a contraction over k terms: k rounded
+ * up to 32 (one 128-byte K-block).  Returns 0 for k <= 0. */
+int32_t cbdg_contract_kp(int32_t k);
+
+/* Splits src [rows][ld] (device, FP32, ld >= k) into TF32 planes hi and lo
+ * [rows][kp], kp = cbdg_contract_kp(k): hi = TF32(x) and lo = TF32(x - hi),
+ * both rounded to nearest, zero for columns k .. kp-1.  hi and lo are device
+ * pointers, 16-byte aligned.  For an operand reused across contractions
+ * (e.g. a weight table), split it once.  Runs on `stream`, returns without
+ * waiting.  Errors: INVALID_ARG, CUDA. */
+cbdg_status cbdg_split_tf32(const float *src, int32_t ld, int32_t rows, int32_t k, float *hi, float *lo,
+                            cbdg_stream stream);
+
+/* cbdg_contract_tf32x3 on operands already split by cbdg_split_tf32:
+ * a_hi, a_lo [m][kp] and b_hi, b_lo [n][kp] (device, 16-byte aligned, kp a
+ * positive multiple of 32); D as above.  Runs on `stream` and returns after
+ * completion.  Errors: INVALID_ARG, CUDA. */
+cbdg_status cbdg_contract_tf32x3_planes(const float *a_hi, const float *a_lo, const float *b_hi,
+                                        const float *b_lo, int32_t kp, float *D, int32_t ldd, int32_t m,
+                                        int32_t n, cbdg_stream stream);
 
 /* One self-consistency iteration (paragraph after Eq. 20) with the Jackson
  * kernel: computes Delta_out from the current Delta as cbdg_order_parameter

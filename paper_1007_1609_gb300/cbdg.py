@@ -103,6 +103,9 @@ def load():
             "cbdg_launch_count": [P, P, I32],
             "cbdg_moments_noalloc": [P, P, I32, I32, P, P, P],
             "cbdg_contract_tf32x3": [P, I32, P, I32, P, I32, I32, I32, I32, P],
+            "cbdg_contract_kp": [I32],
+            "cbdg_split_tf32": [P, I32, I32, I32, P, P, P],
+            "cbdg_contract_tf32x3_planes": [P, P, P, P, I32, P, I32, I32, I32, P],
             "cbdg_order_parameter_backward": [P, D, I32, P, P, P, P],
             "cbdg_build_ensemble": [P, I32, P, P],
             "cbdg_ensemble_destroy": [P],
@@ -238,6 +241,20 @@ def cbdg_moments_noalloc(desc, sites, n_sites, M, mu_ee, mu_eh, stream=None):
 def cbdg_contract_tf32x3(A, lda, B, ldb, D, ldd, m, n, k, stream=None):
     _check(load().cbdg_contract_tf32x3(_ptr(A), int(lda), _ptr(B), int(ldb), _ptr(D), int(ldd),
                                        int(m), int(n), int(k), _stream_handle(stream)))
+
+
+def cbdg_contract_kp(k):
+    return int(load().cbdg_contract_kp(int(k)))
+
+
+def cbdg_split_tf32(src, ld, rows, k, hi, lo, stream=None):
+    _check(load().cbdg_split_tf32(_ptr(src), int(ld), int(rows), int(k), _ptr(hi), _ptr(lo),
+                                  _stream_handle(stream)))
+
+
+def cbdg_contract_tf32x3_planes(a_hi, a_lo, b_hi, b_lo, kp, D, ldd, m, n, stream=None):
+    _check(load().cbdg_contract_tf32x3_planes(_ptr(a_hi), _ptr(a_lo), _ptr(b_hi), _ptr(b_lo), int(kp),
+                                              _ptr(D), int(ldd), int(m), int(n), _stream_handle(stream)))
 
 
 def cbdg_order_parameter_backward(lat, T, M, dL_ddelta_out, dL_deps, dL_dhop, dL_ddelta_in):

@@ -796,29 +796,43 @@ cbdg_status cbdg_ldos(cbdg_lattice *L, const int32_t *sites, int32_t n_sites, in
   CK(L->mom_ee.ensure(nee * sizeof(double)));
   st = run_columns(L, L->sites_user.as<int32_t>(), n_sites, M, L->mom_ee.as<double>(), nullptr, n_eh, false);
   if (st != CBDG_OK) return st;
-  // contraction operands: moments [n_sites][ldk] and weights [n_E][ldk] in FP32
-  const int ldk = (M + 3) / 4 * 4;
-  const size_t a_bytes = static_cast<size_t>(n_sites) * ldk * sizeof(float);
-  const size_t w_bytes = static_cast<size_t>(n_E) * ldk * sizeof(float);
+  // contraction operands as TF32 head / tail planes: moments [n_sites][kp], weights [n_E][kp]
+  const int kp = contract_kp(M);
+  const size_t a_bytes = static_cast<size_t>(n_sites) * kp * sizeof(float);
+  const size_t w_bytes = static_cast<size_t>(n_E) * kp * sizeof(float);
   const size_t d_bytes = static_cast<size_t>(n_sites) * n_E * sizeof(float);
   const size_t e_bytes = static_cast<size_t>(n_E) * sizeof(double);
   auto r256 = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
-  CK(L->stage.ensure(r256(a_bytes) + r256(w_bytes) + r256(d_bytes) + r256(e_bytes)));
+  CK(L->stage.ensure(2 * r256(a_bytes) + 2 * r256(w_bytes) + r256(d_bytes) + r256(e_bytes)));
   unsigned char *sb = L->stage.as<unsigned char>();
-  float *dA = reinterpret_cast<float *>(sb);
-  float *dW = reinterpret_cast<float *>(sb + r256(a_bytes));
-  float *dD = reinterpret_cast<float *>(sb + r256(a_bytes) + r256(w_bytes));
-  double *dE = reinterpret_cast<double *>(sb + r256(a_bytes) + r256(w_bytes) + r256(d_bytes));
+  float *a_hi = reinterpret_cast<float *>(sb);
+  float *a_lo = reinterpret_cast<float *>(sb + r256(a_bytes));
+  float *w_hi = reinterpret_cast<float *>(sb + 2 * r256(a_bytes));
+  float *w_lo = reinterpret_cast<float *>(sb + 2 * r256(a_bytes) + r256(w_bytes));
+  float *dD = reinterpret_cast<float *>(sb + 2 * r256(a_bytes) + 2 * r256(w_bytes));
+  double *dE = reinterpret_cast<double *>(sb + 2 * r256(a_bytes) + 2 * r256(w_bytes) + r256(d_bytes));
   CK(cudaMemcpyAsync(dE, he.data(), e_bytes, cudaMemcpyHostToDevice, L->stream));
-  CK(launch_moments_to_f32(n_sites, M, ldk, L->mom_ee.as<double>(), dA, L->stream));
-  CK(launch_ldos_weights(n_E, M, ldk, kernel, lambda, dE, L->scal.as<double>(), dW, L->stream));
+  CK(launch_split_tf32_f64(L->mom_ee.as<double>(), static_cast<size_t>(M), n_sites, M, kp, a_hi, a_lo,
+                           L->stream));
+  CK(launch_ldos_weights(n_E, M, kp, kernel, lambda, dE, L->scal.as<double>(), w_hi, w_lo, L->stream));
   float *dst = is_device_ptr(ldos) ? ldos : dD;
-  CK(launch_contract_tf32x3(dA, ldk, dW, ldk, dst, n_E, n_sites, n_E, M,
+  CK(launch_contract_planes(a_hi, a_lo, w_hi, w_lo, kp, dst, n_E, n_sites, n_E,
                             L->flags.as<unsigned int>(), L->stream));
   L->launches += 3;
   if (dst != ldos) CK(deliver(L, ldos, dD, d_bytes));
   return finish(L);
 }
+
+namespace {
+cbdg_status contract_finish(unsigned *flags, cudaStream_t s) {
+  unsigned h = 0;
+  CK(cudaMemcpyAsync(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h & kFlagTimeout) return fail(CBDG_ERR_CUDA, "the contraction kernel gave up waiting for its tensor cores");
+  return CBDG_OK;
+}
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+}  // namespace
 
 cbdg_status cbdg_contract_tf32x3(const float *A, int32_t lda, const float *B, int32_t ldb, float *D,
                                  int32_t ldd, int32_t m, int32_t n, int32_t k, cbdg_stream stream) {
@@ -826,10 +840,7 @@ cbdg_status cbdg_contract_tf32x3(const float *A, int32_t lda, const float *B, in
   if (m == 0 || n == 0) return CBDG_OK;
   if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(D))
     return fail(CBDG_ERR_INVALID_ARG, "A, B and D must be device pointers");
-  if (lda < k || ldb < k || ldd < n || (lda & 3) || (ldb & 3) ||
-      (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
-    return fail(CBDG_ERR_INVALID_ARG,
-                "lda, ldb must be >= k and multiples of 4, A and B 16-byte aligned, ldd >= n");
+  if (lda < k || ldb < k || ldd < n) return fail(CBDG_ERR_INVALID_ARG, "need lda, ldb >= k and ldd >= n");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (k == 0) {
     for (int r = 0; r < m; ++r)
@@ -840,12 +851,42 @@ cbdg_status cbdg_contract_tf32x3(const float *A, int32_t lda, const float *B, in
   unsigned *flags = nullptr;
   CK(contract_flag_address(&flags));
   CK(cudaMemsetAsync(flags, 0, sizeof(unsigned), s));
-  CK(launch_contract_tf32x3(A, lda, B, ldb, D, ldd, m, n, k, flags, s));
-  unsigned h = 0;
-  CK(cudaMemcpyAsync(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (h & kFlagTimeout) return fail(CBDG_ERR_CUDA, "the contraction kernel gave up waiting for its tensor cores");
+  cudaError_t e = launch_contract_tf32x3(A, lda, B, ldb, D, ldd, m, n, k, flags, s);
+  if (e == cudaErrorMemoryAllocation) return cuda_fail(e, "scratch for the split operands");
+  CK(e);
+  return contract_finish(flags, s);
+}
+
+int32_t cbdg_contract_kp(int32_t k) { return k <= 0 ? 0 : contract_kp(k); }
+
+cbdg_status cbdg_split_tf32(const float *src, int32_t ld, int32_t rows, int32_t k, float *hi, float *lo,
+                            cbdg_stream stream) {
+  if (rows < 0 || k < 0 || ld < k) return fail(CBDG_ERR_INVALID_ARG, "need rows, k >= 0 and ld >= k");
+  if (rows == 0 || k == 0) return CBDG_OK;
+  if (!is_device_ptr(src) || !is_device_ptr(hi) || !is_device_ptr(lo) || !aligned16(hi) || !aligned16(lo))
+    return fail(CBDG_ERR_INVALID_ARG, "src, hi and lo must be device pointers, hi and lo 16-byte aligned");
+  CK(launch_split_tf32(src, static_cast<size_t>(ld), rows, k, contract_kp(k), hi, lo,
+                       reinterpret_cast<cudaStream_t>(stream)));
   return CBDG_OK;
+}
+
+cbdg_status cbdg_contract_tf32x3_planes(const float *a_hi, const float *a_lo, const float *b_hi,
+                                        const float *b_lo, int32_t kp, float *D, int32_t ldd, int32_t m,
+                                        int32_t n, cbdg_stream stream) {
+  if (m < 0 || n < 0 || kp <= 0 || kp % 32 || ldd < n)
+    return fail(CBDG_ERR_INVALID_ARG, "need m, n >= 0, kp a positive multiple of 32 and ldd >= n");
+  if (m == 0 || n == 0) return CBDG_OK;
+  const float *planes[4] = {a_hi, a_lo, b_hi, b_lo};
+  for (const float *p : planes)
+    if (!is_device_ptr(p) || !aligned16(p))
+      return fail(CBDG_ERR_INVALID_ARG, "the planes must be 16-byte aligned device pointers");
+  if (!is_device_ptr(D)) return fail(CBDG_ERR_INVALID_ARG, "D must be a device pointer");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned *flags = nullptr;
+  CK(contract_flag_address(&flags));
+  CK(cudaMemsetAsync(flags, 0, sizeof(unsigned), s));
+  CK(launch_contract_planes(a_hi, a_lo, b_hi, b_lo, kp, D, ldd, m, n, flags, s));
+  return contract_finish(flags, s);
 }
 
 cbdg_status cbdg_scf_step(cbdg_lattice *L, double T, int32_t M, double mix,

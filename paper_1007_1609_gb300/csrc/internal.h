@@ -138,10 +138,21 @@ enum {
 // Error flags (unsigned int bits).
 enum { kFlagSpectrum = 1u, kFlagTimeout = 2u };
 
-// Dense D[m][n] = sum_k A[m][k] B[n][k] (row strides lda, ldb multiples of 4,
-// 16-byte aligned) on tcgen05 tensor cores with the 3xTF32 split.
+// Dense D[m][n] = sum_k A[m][k] B[n][k] on tcgen05 tensor cores with the
+// 3xTF32 split (contract.cu).  launch_contract_tf32x3 splits FP32 operands
+// into TF32 hi / lo planes [rows][kp] (kp = contract_kp(k), zero padded) in
+// stream-ordered scratch and contracts them; callers that build operands
+// themselves write the planes directly (launch_split_tf32*) and call
+// launch_contract_planes.
 cudaError_t launch_contract_tf32x3(const float *A, int lda, const float *B, int ldb, float *D,
                                    int ldd, int m, int n, int k, unsigned *flags, cudaStream_t s);
+int contract_kp(int k);
+cudaError_t launch_split_tf32(const float *src, size_t ld, int rows, int k, int kp, float *hi, float *lo,
+                              cudaStream_t s);
+cudaError_t launch_split_tf32_f64(const double *src, size_t ld, int rows, int k, int kp, float *hi,
+                                  float *lo, cudaStream_t s);
+cudaError_t launch_contract_planes(const float *a_hi, const float *a_lo, const float *b_hi, const float *b_lo,
+                                   int kp, float *D, int ldd, int m, int n, unsigned *flags, cudaStream_t s);
 // Adjoint of one self-consistency map (adjoint.cu).
 cudaError_t launch_adjoint_source(int precision, int Lx, int Ly, int ncols, int W,
                                   const int32_t *sites, const double *w, double scale_m, void *lam,
@@ -155,11 +166,10 @@ cudaError_t launch_adjoint_final(int Lx, int Ly, int px, int py, int groups, con
 
 // Device address of the stand-alone contraction's error word (this device).
 cudaError_t contract_flag_address(unsigned **out);
+// LDOS weights of Eq. 17 as TF32 head / tail planes [n_E][ld].
 cudaError_t launch_ldos_weights(int n_E, int M, int ld, int kernel, double lambda,
-                                const double *energies, const double *scal, float *W,
+                                const double *energies, const double *scal, float *w_hi, float *w_lo,
                                 cudaStream_t s);
-cudaError_t launch_moments_to_f32(int rows, int M, int ld, const double *mu, float *out,
-                                  cudaStream_t s);
 
 }  // namespace cbdg
 

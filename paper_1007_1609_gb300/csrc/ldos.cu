@@ -1,9 +1,8 @@
 // ldos.cu -- the LDOS weight table of Eq. 17 with the expansion of Eq. 10,
 //   W[e][n] = g_n (2 - delta_n0) T_n(E_e / a) / (pi a sqrt(1 - (E_e/a)^2)),
-// built in FP64 and stored in FP32 for the tensor-core contraction
-// LDOS[site][e] = sum_n mu_n(site) W[e][n], and the FP64 -> FP32 copy of
-// the moments.  Both operands are K-major (n contiguous) with a row stride
-// padded to a multiple of 4 so that 16-byte loads stay aligned.
+// built in FP64 and stored as the TF32 head / tail planes that the
+// tensor-core contraction LDOS[site][e] = sum_n mu_n(site) W[e][n] reads
+// (K-major, row stride kp = M rounded up to 32, zero padded).
 #include <math.h>
 
 #include "internal.h"
@@ -13,13 +12,19 @@ namespace {
 
 inline int blocks(long long n, int t) { return static_cast<int>((n + t - 1) / t); }
 
+__device__ __forceinline__ float tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __global__ void ldos_weights_kernel(int n_E, int M, int ld, int kernel, double lambda,
-                                    const double *energies, const double *scal, float *W) {
+                                    const double *energies, const double *scal, float *w_hi, float *w_lo) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= static_cast<long long>(n_E) * ld) return;
   const int e = static_cast<int>(idx / ld);
   const int n = static_cast<int>(idx % ld);
-  float w = 0.f;
+  double w = 0.0;
   if (n < M) {
     const double a = scal[kScalA];
     const double x = energies[e] / a;
@@ -32,33 +37,21 @@ __global__ void ldos_weights_kernel(int n_E, int M, int ld, int kernel, double l
     }
     const double th = acos(x);
     const double tn = cos(n * th);
-    w = static_cast<float>(g * (n == 0 ? 1.0 : 2.0) * tn / (M_PI * a * sqrt(1.0 - x * x)));
+    w = g * (n == 0 ? 1.0 : 2.0) * tn / (M_PI * a * sqrt(1.0 - x * x));
   }
-  W[static_cast<size_t>(e) * ld + n] = w;
-}
-
-__global__ void moments_to_f32_kernel(int rows, int M, int ld, const double *mu, float *out) {
-  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= static_cast<long long>(rows) * ld) return;
-  const int r = static_cast<int>(idx / ld);
-  const int n = static_cast<int>(idx % ld);
-  out[static_cast<size_t>(r) * ld + n] = n < M ? static_cast<float>(mu[static_cast<size_t>(r) * M + n]) : 0.f;
+  const float h = tf32_rna(static_cast<float>(w));
+  w_hi[static_cast<size_t>(e) * ld + n] = h;
+  w_lo[static_cast<size_t>(e) * ld + n] = tf32_rna(static_cast<float>(w - static_cast<double>(h)));
 }
 
 }  // namespace
 
 cudaError_t launch_ldos_weights(int n_E, int M, int ld, int kernel, double lambda,
-                                const double *energies, const double *scal, float *W,
+                                const double *energies, const double *scal, float *w_hi, float *w_lo,
                                 cudaStream_t s) {
   if (n_E <= 0) return cudaSuccess;
-  ldos_weights_kernel<<<blocks(static_cast<long long>(n_E) * ld, 256), 256, 0, s>>>(n_E, M, ld, kernel, lambda, energies, scal, W);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_moments_to_f32(int rows, int M, int ld, const double *mu, float *out,
-                                  cudaStream_t s) {
-  if (rows <= 0) return cudaSuccess;
-  moments_to_f32_kernel<<<blocks(static_cast<long long>(rows) * ld, 256), 256, 0, s>>>(rows, M, ld, mu, out);
+  ldos_weights_kernel<<<blocks(static_cast<long long>(n_E) * ld, 256), 256, 0, s>>>(n_E, M, ld, kernel, lambda,
+                                                                                     energies, scal, w_hi, w_lo);
   return cudaGetLastError();
 }
 

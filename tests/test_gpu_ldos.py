@@ -34,7 +34,7 @@ def contract(A, B):
 
 
 @pytest.mark.parametrize("m,n,k", [(128, 256, 32), (1, 1, 1), (300, 300, 100), (129, 257, 33),
-                                   (640, 512, 2048)])
+                                   (640, 512, 2048), (200, 520, 600)])
 def test_contraction_matches_fp64_product(m, n, k):
     rng = np.random.default_rng(m * 7 + n + k)
     A = rng.standard_normal((m, k)).astype(np.float32).astype(np.float64)
@@ -45,6 +45,42 @@ def test_contraction_matches_fp64_product(m, n, k):
     err = np.abs(D - ref) / scale
     # 3xTF32 products (~2^-21) plus FP32 accumulation over k terms (~sqrt(k) 2^-24)
     assert err.max() < 1e-5, (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_contraction_unaligned_rows_and_presplit_planes():
+    """Odd row strides and an offset base (no alignment), then the same
+    product through split-once planes: identical bits."""
+    import torch
+    rng = np.random.default_rng(5)
+    m, n, k, ld = 150, 70, 77, 79
+    Ah = rng.standard_normal((m, ld)).astype(np.float32)
+    Bh = rng.standard_normal((n, ld)).astype(np.float32)
+    A_buf = torch.zeros(m * ld + 1, dtype=torch.float32, device="cuda")
+    A_buf[1:] = torch.from_numpy(Ah.ravel())
+    A = A_buf[1:]  # 4-byte aligned only
+    B = torch.from_numpy(Bh).cuda()
+    D = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    cbdg.cbdg_contract_tf32x3(A, ld, B, ld, D, n, m, n, k)
+    ref = Ah[:, :k].astype(np.float64) @ Bh[:, :k].astype(np.float64).T
+    scale = np.abs(Ah[:, :k]).astype(np.float64) @ np.abs(Bh[:, :k]).astype(np.float64).T
+    assert (np.abs(D.cpu().numpy() - ref) / scale).max() < 1e-5
+    kp = cbdg.cbdg_contract_kp(k)
+    assert kp == 96 and cbdg.cbdg_contract_kp(0) == 0 and cbdg.cbdg_contract_kp(32) == 32
+    ahi, alo = (torch.empty((m, kp), dtype=torch.float32, device="cuda") for _ in range(2))
+    bhi, blo = (torch.empty((n, kp), dtype=torch.float32, device="cuda") for _ in range(2))
+    cbdg.cbdg_split_tf32(A, ld, m, k, ahi, alo)
+    cbdg.cbdg_split_tf32(B, ld, n, k, bhi, blo)
+    # the planes hold TF32 values (low 13 mantissa bits clear), hi + lo ~ x, zero padding
+    for p in (ahi, alo):
+        assert int((p.view(torch.int32) & 0x1FFF).abs().sum()) == 0
+    assert torch.all(ahi[:, k:] == 0) and torch.all(alo[:, k:] == 0)
+    x = torch.from_numpy(Ah[:, :k]).cuda()
+    assert float(((ahi[:, :k] + alo[:, :k]) - x).abs().max()) <= float(x.abs().max()) * 2.0 ** -21
+    D2 = torch.empty_like(D)
+    cbdg.cbdg_contract_tf32x3_planes(ahi, alo, bhi, blo, kp, D2, n, m, n)
+    assert torch.equal(D, D2)
+    with pytest.raises(cbdg.CbdgError):
+        cbdg.cbdg_contract_tf32x3_planes(ahi, alo, bhi, blo, 48, D2, n, m, n)
 
 
 def test_contraction_structured_layout():
