@@ -406,13 +406,13 @@ def leg_contraction(cbdg, torch, stream, shape=(65536, 2048, 512)):
                          "note": "contract_kernel alone; 3 TF32 products per term (hi*hi + hi*lo + lo*hi)"}}
 
 
-def leg_dwave(cbdg, wl, stream, hbm):
+def leg_dwave(cbdg, wl, stream, hbm, columns=4096):
     """General recursion step (complex64, t', bond pairing, Peierls field) on
-    the 256x256 vortex lattice, a 4096-column chunk."""
+    the 256x256 vortex lattice, a chunk of `columns` start sites."""
     import numpy as np
     pv = wl.dwave_vortex(256, 34)
     lat = cbdg.Lattice(pv, precision="fp32", stream=stream, complex_field=True)
-    sites = np.arange(4096, dtype=np.int32) * 16
+    sites = (np.arange(columns, dtype=np.int64) * (pv.N // columns)).astype(np.int32)
     lat.moments(sites, 8)
     cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
     cbdg.cbdg_profile_read(lat.handle, reset=True)
@@ -421,7 +421,7 @@ def leg_dwave(cbdg, wl, stream, hbm):
     tile = lat.last_tile()
     lat.close()
     return {"lattice": "256x256 periodic, t'=-0.3, 2 h/2e flux, bond pairing, complex64",
-            "columns": 4096, "launches": sn, "avg_launch_ms": sms / sn, "tile": list(tile),
+            "columns": int(columns), "launches": sn, "avg_launch_ms": sms / sn, "tile": list(tile),
             "roofline": {"bound": "hbm", "achieved": sb / (sms * 1e-3) / 1e9, "peak": hbm,
                          "unit": "GB/s", "frac": sb / (sms * 1e-3) / 1e9 / hbm}}
 
@@ -460,11 +460,11 @@ def leg_adjoint(cbdg, wl, stream):
     return out
 
 
-def extra_legs(cbdg, wl, torch, stream, hbm, only=None):
+def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096):
     """Other hot-path stages at their workload sizes (not the headline)."""
     legs = {
         "contraction": lambda: leg_contraction(cbdg, torch, stream),
-        "dwave": lambda: leg_dwave(cbdg, wl, stream, hbm),
+        "dwave": lambda: leg_dwave(cbdg, wl, stream, hbm, columns),
         "ensemble": lambda: leg_ensemble(cbdg, wl, stream),
         "adjoint": lambda: leg_adjoint(cbdg, wl, stream),
     }
@@ -522,6 +522,8 @@ def main():
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")
     ap.add_argument("--moments", type=int, default=M)
+    ap.add_argument("--columns", type=int, default=4096,
+                    help="start vectors of the d-wave stage (--stage dwave)")
     ap.add_argument("--temporal", type=int, default=None,
                     help="recursion steps per pass over the vectors (1..4; default: library choice)")
     args = ap.parse_args()
@@ -535,7 +537,7 @@ def main():
         from paper_1007_1609_gb300 import workloads as wl
         stream = torch.cuda.Stream()
         hbm, _ = peaks()
-        rec = extra_legs(cbdg, wl, torch, stream, hbm, only=args.stage)
+        rec = extra_legs(cbdg, wl, torch, stream, hbm, only=args.stage, columns=args.columns)
         print(json.dumps({"stage": args.stage, **rec}), flush=True)
         return 0
     return run_gb300(args)

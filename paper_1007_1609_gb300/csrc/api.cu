@@ -217,7 +217,7 @@ cbdg_status prepare(cbdg_lattice *L, double T, int kernel, double lambda, int M,
                           L->delta.as<double2>(), L->scal.as<double>(), L->params.p, L->stream));
   } else {
     CK(L->params.ensure(static_cast<size_t>(L->N) * kCplxParamStride * elem_size(L)));
-    CK(launch_params_cplx(L->precision, L->N, L->n_dirs, L->pairing, L->eps.as<double>(), L->mu,
+    CK(launch_params_cplx(L->precision, L->N, L->Lx, L->n_dirs, L->pairing, L->eps.as<double>(), L->mu,
                           L->hop.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
                           L->params.p, L->stream));
   }

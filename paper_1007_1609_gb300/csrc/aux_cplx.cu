@@ -27,29 +27,31 @@ __device__ __forceinline__ int nbr(int Lx, int Ly, int px, int py, int s, int d)
 // [0] 2(eps-mu)/a  [2,3] 2 Delta_i/a  [4+2d, 5+2d] 2 t_{i,d}/a (d < 8)
 // [20+2d, 21+2d] 2 Delta_{i,d}/a (d < 4, bond pairing); the rest 0.
 template <typename S>
-__global__ void params_cplx_kernel(int N, int n_dirs, int pairing, const double *eps, double mu,
+__global__ void params_cplx_kernel(int N, int Lx, int n_dirs, int pairing, const double *eps, double mu,
                                    const double2 *hop, const double2 *delta, const double *scal,
                                    S *p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double s2 = 2.0 / scal[kScalA];
-  S *r = p + static_cast<size_t>(i) * kCplxParamStride;
-  for (int k = 0; k < kCplxParamStride; ++k) r[k] = 0;
-  r[0] = static_cast<S>(s2 * (eps[i] - mu));
+  const int x = i % Lx, y = i / Lx;
+  auto f = [&](int k, double re, double im) {
+    S *q = p + ((static_cast<size_t>(y) * kCplxFields + k) * Lx + x) * 2;
+    q[0] = static_cast<S>(re);
+    q[1] = static_cast<S>(im);
+  };
+  for (int k = 0; k < kCplxFields; ++k) f(k, 0.0, 0.0);
+  f(kCpE, s2 * (eps[i] - mu), 0.0);
   if (pairing == 0) {
-    r[2] = static_cast<S>(s2 * delta[i].x);
-    r[3] = static_cast<S>(s2 * delta[i].y);
+    f(kCpDelta, s2 * delta[i].x, s2 * delta[i].y);
   } else {
     for (int d = 0; d < 4; ++d) {
       const double2 b = delta[static_cast<size_t>(i) * 4 + d];
-      r[20 + 2 * d] = static_cast<S>(s2 * b.x);
-      r[21 + 2 * d] = static_cast<S>(s2 * b.y);
+      f(kCpBond + d, s2 * b.x, s2 * b.y);
     }
   }
   for (int d = 0; d < n_dirs; ++d) {
     const double2 t = hop[static_cast<size_t>(i) * n_dirs + d];
-    r[4 + 2 * d] = static_cast<S>(s2 * t.x);
-    r[5 + 2 * d] = static_cast<S>(s2 * t.y);
+    f(kCpHop + d, s2 * t.x, s2 * t.y);
   }
 }
 
@@ -212,14 +214,14 @@ __global__ void finalize_bond_kernel(int N, int Lx, int Ly, int px, int py, doub
 
 }  // namespace
 
-cudaError_t launch_params_cplx(int precision, int N, int n_dirs, int pairing, const double *eps,
+cudaError_t launch_params_cplx(int precision, int N, int Lx, int n_dirs, int pairing, const double *eps,
                                double mu, const double2 *hop, const double2 *delta,
                                const double *scal, void *params, cudaStream_t s) {
   if (precision == 1)
-    params_cplx_kernel<float><<<blocks(N, 128), 128, 0, s>>>(N, n_dirs, pairing, eps, mu, hop, delta,
+    params_cplx_kernel<float><<<blocks(N, 128), 128, 0, s>>>(N, Lx, n_dirs, pairing, eps, mu, hop, delta,
                                                              scal, static_cast<float *>(params));
   else
-    params_cplx_kernel<double><<<blocks(N, 128), 128, 0, s>>>(N, n_dirs, pairing, eps, mu, hop,
+    params_cplx_kernel<double><<<blocks(N, 128), 128, 0, s>>>(N, Lx, n_dirs, pairing, eps, mu, hop,
                                                               delta, scal, static_cast<double *>(params));
   return cudaGetLastError();
 }

@@ -12,10 +12,17 @@ namespace cbdg {
 // application yields 2 H~ j:
 //   [0] 2 (eps - mu)/a   [1] 2 Delta/a   [2..5] 2 t_{s,d}/a (d = 0..3)   [6,7] 0
 constexpr int kParamStride = 8;
-// General (complex / next-nearest / bond) parameter record, 32 scalars per site:
-//   [0] 2(eps-mu)/a  [2,3] 2 Delta_i/a  [4+2d, 5+2d] 2 t_{i,d}/a (d < 8)
-//   [20+2d, 21+2d] 2 Delta_{i,d}/a (d < 4); the rest 0.
-constexpr int kCplxParamStride = 32;
+// General (complex / next-nearest / bond) parameters: 14 complex fields per
+// site, stored field-major inside each lattice row, field f of site (x, y)
+// (real, imaginary) at
+//   params[((y * kCplxFields + f) * Lx + x) * 2 + {0, 1}]
+// so that a lattice row is one contiguous block of kCplxParamStride * Lx
+// scalars and threads on consecutive x read consecutive pairs.  Fields:
+//   [0] (2(eps-mu)/a, 0)  [1] 2 Delta_i/a  [2+d] 2 t_{i,d}/a (d < 8)
+//   [10+d] 2 Delta_{i,d}/a (d < 4)
+constexpr int kCplxFields = 14;
+constexpr int kCplxParamStride = 2 * kCplxFields;
+constexpr int kCpE = 0, kCpDelta = 1, kCpHop = 2, kCpBond = 10;
 
 // Arguments of one recursion step j_{n+1} = 2 H~ j_n - j_{n-1} over a block
 // of ld start vectors.  Vectors use the slab-blocked layout: column slab
@@ -79,7 +86,7 @@ cudaError_t launch_step_cplx(int precision, int nnn, int bond, const StepArgs &a
 bool plan_step_cplx(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
                     int want_depth, StepConfig *cfg);
 int slab_width_default_cplx(int precision);
-cudaError_t launch_params_cplx(int precision, int N, int n_dirs, int pairing, const double *eps,
+cudaError_t launch_params_cplx(int precision, int N, int Lx, int n_dirs, int pairing, const double *eps,
                                double mu, const double2 *hop, const double2 *delta,
                                const double *scal, void *params, cudaStream_t s);
 cudaError_t launch_init_cplx(int precision, int Lx, int Ly, int px, int py, int n_dirs, int pairing,

@@ -9,9 +9,11 @@
 //
 // Vectors are complex (float2 / double2) in the slab-blocked layout of the
 // real kernel (rows electron-then-hole inside each lattice row), staged by
-// TMA bulk copies on mbarriers with bounded waits.  Parameters ([N][32]
-// scalars) are read through the read-only cache: all CTAs share them and
-// they stay resident in L2.
+// TMA bulk copies on mbarriers with bounded waits.  Parameters (14 complex
+// fields per site, field-major inside each lattice row) stay resident in L2: the FP32
+// kernel stages each row with the j_{n-1} row, the FP64 kernel reads them
+// through the read-only cache; either way threads on consecutive x read
+// consecutive words.
 //
 // With on-site pairing the doubling identities apply and the kernel fuses
 // four column sums (|j_n|^2, Re<j_{n+1}|j_n>, and the complex symplectic sum
@@ -130,10 +132,25 @@ __device__ __forceinline__ void cset(V &v, int j, Cx<S> z) {
   p[2 * j + 1] = z.im;
 }
 
-// Parameter record [kCplxParamStride] scalars per site (see internal.h).
 template <typename S>
-__device__ __forceinline__ Cx<S> pc(const S *p, int k) {
-  return {__ldg(p + k), __ldg(p + k + 1)};
+struct Pair;
+template <>
+struct Pair<float> {
+  using T = float2;
+};
+template <>
+struct Pair<double> {
+  using T = double2;
+};
+// Complex field k of a site's parameters, one 8- or 16-byte load; p points at
+// field 0 of the site inside its lattice row, fields are 2 Lx scalars apart
+// (see internal.h).
+template <typename S, bool LDG>
+__device__ __forceinline__ Cx<S> pcx(const S *p, int k, int Lx) {
+  using P = typename Pair<S>::T;
+  const P *q = reinterpret_cast<const P *>(p + static_cast<size_t>(k) * 2 * Lx);
+  const P v = LDG ? __ldg(q) : *q;
+  return {v.x, v.y};
 }
 
 template <typename S, int W, int NT, int MAXX, int D, bool NNN, bool BOND, bool SUMS>
@@ -229,10 +246,9 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
           auto ld = [&](const S *row, int xx, int part) {
             return *reinterpret_cast<const V *>(row + part * hb + xx * W * 2 + off);
           };
-          const S *pp = PSTAGE ? sp + (i % OS) * pel + x * kCplxParamStride
-                               : par + (static_cast<size_t>(y) * Lx + x) * kCplxParamStride;
-          const S e = PSTAGE ? pp[0] : __ldg(pp + 0);
-          const Cx<S> dl = PSTAGE ? Cx<S>{pp[2], pp[3]} : pc(pp, 2);
+          const S *pp = PSTAGE ? sp + (i % OS) * pel + 2 * x : par + static_cast<size_t>(y) * pel + 2 * x;
+          const S e = pcx<S, !PSTAGE>(pp, kCpE, Lx).re;
+          const Cx<S> dl = pcx<S, !PSTAGE>(pp, kCpDelta, Lx);
           // neighbour rows/columns per direction 0:+x 1:-x 2:+y 3:-y 4:+x+y 5:-x-y 6:+x-y 7:-x+y
           const S *nrow[8] = {rc, rc, rp, rm, rp, rm, rm, rp};
           const int ncol[8] = {xr, xl, x, x, xr, xl, xr, xl};
@@ -250,14 +266,14 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
 #pragma unroll
           for (int dd = 0; dd < (NNN ? 8 : 4); ++dd) {
             const V ud = ld(nrow[dd], ncol[dd], 0), vd = ld(nrow[dd], ncol[dd], 1);
-            const Cx<S> td = PSTAGE ? Cx<S>{pp[4 + 2 * dd], pp[5 + 2 * dd]} : pc(pp, 4 + 2 * dd);
+            const Cx<S> td = pcx<S, !PSTAGE>(pp, kCpHop + dd, Lx);
+            const Cx<S> bd = (BOND && dd < 4) ? pcx<S, !PSTAGE>(pp, kCpBond + dd, Lx) : Cx<S>{0, 0};
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
               Cx<S> hu = cget<V, S>(un, j), hv = cget<V, S>(vn, j);
               hu = csub(hu, cmul(td, cget<V, S>(ud, j)));
               hv = cadd(hv, cmulc(td, cget<V, S>(vd, j)));
               if (BOND && dd < 4) {
-                const Cx<S> bd = PSTAGE ? Cx<S>{pp[20 + 2 * dd], pp[21 + 2 * dd]} : pc(pp, 20 + 2 * dd);
                 hu = cadd(hu, cmul(bd, cget<V, S>(vd, j)));
                 hv = cadd(hv, cmulc(bd, cget<V, S>(ud, j)));
               }
