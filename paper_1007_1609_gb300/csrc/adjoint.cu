@@ -14,9 +14,16 @@
 // (j_{kS}, j_{kS+1}) taken every S ~ sqrt(M) steps of the forward pass.
 //
 // This file holds the kernels: the source scatter, the pattern-restricted
-// accumulation (one thread per (site, column group), 12 FP64 sums per site:
-// e-e, h-h, e-h, h-e on site and e-e, h-h to each of the 4 neighbours; fixed
-// order, no atomics) and the final contraction with dH/dparameter.
+// accumulation (12 sums per site: e-e, h-h, e-h, h-e on site and e-e, h-h
+// to each of the 4 neighbours; fixed order, no atomics) and the final
+// contraction with dH/dparameter.  The accumulation streams lattice rows of
+// the slab-blocked vectors like the recursion kernels: a CTA owns one lattice
+// row and a group of column slabs, a thread one site and VEC columns, every
+// load is a coalesced 16-byte vector; FP32 vectors are summed in FP32 with
+// Kahan compensation, FP64 vectors in FP64, and the column lanes of a site
+// are combined by warp shuffles in FP64.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace cbdg {
@@ -35,51 +42,118 @@ __global__ void adjoint_source_kernel(int Lx, int Ly, int ncols, int W, const in
   lam[k] = static_cast<S>(static_cast<double>(lam[k]) + w[i] * scale_m);
 }
 
-// part[g][site][12] += f * sum_{b in group g} lam(r, b) j(s, b) on the pattern.
 template <typename S>
-__global__ void adjoint_accumulate_kernel(int Lx, int Ly, int px, int py, int ld, int W,
-                                          int cols_per_group, const S *lam, const S *j, double f,
-                                          double *part) {
-  const int N = Lx * Ly;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int g = blockIdx.y;
-  if (i >= N) return;
-  const int x = i % Lx, y = i / Lx;
-  const size_t rows = 2 * static_cast<size_t>(N);
-  const int DX[4] = {1, -1, 0, 0}, DY[4] = {0, 0, 1, -1};
-  int nb[4];
-  for (int d = 0; d < 4; ++d) {
-    int nx = x + DX[d], ny = y + DY[d];
-    bool ok = true;
-    if (nx < 0 || nx >= Lx) {
-      ok = px != 0;
-      nx = (nx + Lx) % Lx;
-    }
-    if (ny < 0 || ny >= Ly) {
-      ok = ok && py != 0;
-      ny = (ny + Ly) % Ly;
-    }
-    nb[d] = ok ? nx + Lx * ny : -1;
+struct SumOf {
+  S s = 0;
+  __device__ __forceinline__ void add(S x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct SumOf<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
   }
-  const size_t re = vector_row(Lx, i, 0), rh = vector_row(Lx, i, 1);
-  double acc[12];
-  for (int k = 0; k < 12; ++k) acc[k] = 0.0;
-  const int b0 = g * cols_per_group, b1 = min(ld, b0 + cols_per_group);
-  for (int b = b0; b < b1; ++b) {
-    const double le = lam[blocked_index(re, b, rows, W)], lh = lam[blocked_index(rh, b, rows, W)];
-    const double je = j[blocked_index(re, b, rows, W)], jh = j[blocked_index(rh, b, rows, W)];
-    acc[0] += le * je;
-    acc[1] += lh * jh;
-    acc[2] += le * jh;
-    acc[3] += lh * je;
-    for (int d = 0; d < 4; ++d) {
-      if (nb[d] < 0) continue;
-      acc[4 + d] += le * static_cast<double>(j[blocked_index(vector_row(Lx, nb[d], 0), b, rows, W)]);
-      acc[8 + d] += lh * static_cast<double>(j[blocked_index(vector_row(Lx, nb[d], 1), b, rows, W)]);
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <typename S, int VEC>
+struct alignas(sizeof(S) * VEC) Pack {
+  S v[VEC];
+};
+
+// part[g][site][12] += f * sum_{b in group g} lam(r, b) j(s, b) on the pattern.
+// Grid (Ly, groups); group g covers column slabs [g * spg, (g + 1) * spg).
+template <typename S, int W>
+__global__ void __launch_bounds__(256) adjoint_accumulate_kernel(int Lx, int Ly, int px, int py, int ld,
+                                                                 int spg, const S *__restrict__ lam,
+                                                                 const S *__restrict__ j, double f,
+                                                                 double *part) {
+  constexpr int VEC = (W * sizeof(S) >= 16) ? 16 / static_cast<int>(sizeof(S)) : W;
+  constexpr int QUADS = W / VEC, XSLOTS = 256 / QUADS;
+  using P = Pack<S, VEC>;
+  const int N = Lx * Ly, y = blockIdx.x, g = blockIdx.y;
+  const int t = threadIdx.x, q = t % QUADS, xs = t / QUADS;
+  const size_t slab_el = static_cast<size_t>(2) * N * W;
+  const int s0 = g * spg, s1 = min(ld / W, s0 + spg);
+  const int off = q * VEC;
+  for (int xb = 0; xb < Lx; xb += XSLOTS) {  // warp-uniform: the shuffles below need every lane
+    const int x = xb + xs;
+    const bool valid = x < Lx;
+    int nx[4], ny[4];
+    bool has[4];
+    {
+      const int DX[4] = {1, -1, 0, 0}, DY[4] = {0, 0, 1, -1};
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        int a = x + DX[d], b = y + DY[d];
+        bool ok = valid;
+        if (a < 0 || a >= Lx) {
+          ok = ok && px != 0;
+          a = (a + Lx) % Lx;
+        }
+        if (b < 0 || b >= Ly) {
+          ok = ok && py != 0;
+          b = (b + Ly) % Ly;
+        }
+        nx[d] = a;
+        ny[d] = b;
+        has[d] = ok;
+      }
+    }
+    SumOf<S> acc[12];
+    if (valid) {
+      for (int c = s0; c < s1; ++c) {
+        const S *lb = lam + c * slab_el, *jb = j + c * slab_el;
+        const size_t re = static_cast<size_t>(2 * Lx * y + x) * W + off, rh = re + static_cast<size_t>(Lx) * W;
+        const P le = *reinterpret_cast<const P *>(lb + re), lh = *reinterpret_cast<const P *>(lb + rh);
+        const P je = *reinterpret_cast<const P *>(jb + re), jh = *reinterpret_cast<const P *>(jb + rh);
+        // FP32: the VEC lane products of a sum first (cheap), then one
+        // compensated add; FP64 (bound by its FMA rate): one FMA per product
+        auto dot = [&](int k, const P &a, const P &b) {
+          if constexpr (sizeof(S) == 8) {
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) acc[k].s = fma(a.v[l], b.v[l], acc[k].s);
+          } else {
+            S p = a.v[0] * b.v[0];
+#pragma unroll
+            for (int l = 1; l < VEC; ++l) p = fmaf(a.v[l], b.v[l], p);
+            acc[k].add(p);
+          }
+        };
+        dot(0, le, je);
+        dot(1, lh, jh);
+        dot(2, le, jh);
+        dot(3, lh, je);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          if (!has[d]) continue;
+          const size_t ne = static_cast<size_t>(2 * Lx * ny[d] + nx[d]) * W + off;
+          const P de = *reinterpret_cast<const P *>(jb + ne);
+          const P dh = *reinterpret_cast<const P *>(jb + ne + static_cast<size_t>(Lx) * W);
+          dot(4 + d, le, de);
+          dot(8 + d, lh, dh);
+        }
+      }
+    }
+    // combine the QUADS column lanes of each site (adjacent lanes), FP64
+    double tot[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double v = acc[k].value();
+#pragma unroll
+      for (int o = 1; o < QUADS; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      tot[k] = v;
+    }
+    if (valid && q == 0) {
+      double *pp = part + (static_cast<size_t>(g) * N + static_cast<size_t>(y) * Lx + x) * 12;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) pp[k] += f * tot[k];
     }
   }
-  double *p = part + (static_cast<size_t>(g) * N + i) * 12;
-  for (int k = 0; k < 12; ++k) p[k] += f * acc[k];
 }
 
 // dL/deps_i = (G_ee - G_hh)/a, dL/dDelta_i = (G_eh + G_he)/a,
@@ -138,21 +212,44 @@ cudaError_t launch_adjoint_source(int precision, int Lx, int Ly, int ncols, int 
   return cudaGetLastError();
 }
 
+int adjoint_groups(int Ly, int ld, int W) {
+  // about 8 CTAs per SM of 152 (several resident per SM, so an uneven last
+  // round costs little), at least 8 slabs per group
+  const int slabs = std::max(1, ld / W);
+  const int want = std::max(1, (8 * 152 + Ly - 1) / Ly);
+  return std::max(1, std::min(want, slabs / 8));
+}
+
+template <typename S, int W>
+cudaError_t accumulate_w(int Lx, int Ly, int px, int py, int ld, int groups, const void *lam, const void *j,
+                         double f, double *part, cudaStream_t s) {
+  const int slabs = ld / W;
+  const int spg = (slabs + groups - 1) / groups;
+  dim3 grid(Ly, groups);
+  adjoint_accumulate_kernel<S, W><<<grid, 256, 0, s>>>(Lx, Ly, px, py, ld, spg, static_cast<const S *>(lam),
+                                                      static_cast<const S *>(j), f, part);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t accumulate_s(int Lx, int Ly, int px, int py, int ld, int W, int groups, const void *lam,
+                         const void *j, double f, double *part, cudaStream_t s) {
+  switch (W) {
+    case 1: return accumulate_w<S, 1>(Lx, Ly, px, py, ld, groups, lam, j, f, part, s);
+    case 2: return accumulate_w<S, 2>(Lx, Ly, px, py, ld, groups, lam, j, f, part, s);
+    case 4: return accumulate_w<S, 4>(Lx, Ly, px, py, ld, groups, lam, j, f, part, s);
+    case 8: return accumulate_w<S, 8>(Lx, Ly, px, py, ld, groups, lam, j, f, part, s);
+    case 16: return accumulate_w<S, 16>(Lx, Ly, px, py, ld, groups, lam, j, f, part, s);
+    case 32: return accumulate_w<S, 32>(Lx, Ly, px, py, ld, groups, lam, j, f, part, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int py, int ld, int W,
                                       int groups, const void *lam, const void *j, double f,
                                       double *part, cudaStream_t s) {
-  const int N = Lx * Ly;
-  const int cpg = (ld + groups - 1) / groups;
-  dim3 grid(blocks(N, 128), groups);
-  if (precision == 1)
-    adjoint_accumulate_kernel<float><<<grid, 128, 0, s>>>(Lx, Ly, px, py, ld, W, cpg,
-                                                          static_cast<const float *>(lam),
-                                                          static_cast<const float *>(j), f, part);
-  else
-    adjoint_accumulate_kernel<double><<<grid, 128, 0, s>>>(Lx, Ly, px, py, ld, W, cpg,
-                                                           static_cast<const double *>(lam),
-                                                           static_cast<const double *>(j), f, part);
-  return cudaGetLastError();
+  return precision == 1 ? accumulate_s<float>(Lx, Ly, px, py, ld, W, groups, lam, j, f, part, s)
+                        : accumulate_s<double>(Lx, Ly, px, py, ld, W, groups, lam, j, f, part, s);
 }
 
 cudaError_t launch_adjoint_final(int Lx, int Ly, int px, int py, int groups, const double *part,

@@ -955,7 +955,7 @@ cbdg_status cbdg_order_parameter_backward(cbdg_lattice *L, double T, int32_t M,
   if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
   if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for the adjoint");
   const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((N + W - 1) / W) * W));
-  const int groups = 64;
+  const int groups = adjoint_groups(L->Ly, ((std::min(chunk, N) + W - 1) / W) * W, W);
   CK(L->adj_part.ensure(static_cast<size_t>(groups) * N * 12 * sizeof(double)));
   CK(cudaMemsetAsync(L->adj_part.p, 0, static_cast<size_t>(groups) * N * 12 * sizeof(double), L->stream));
   const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
@@ -1037,9 +1037,13 @@ cbdg_status cbdg_order_parameter_backward(cbdg_lattice *L, double T, int32_t M,
       CK(cudaMemcpyAsync(segv(0), ckv(k, 0), vb, cudaMemcpyDeviceToDevice, L->stream));
       if (r_end > 1) CK(cudaMemcpyAsync(segv(1), ckv(k, 1), vb, cudaMemcpyDeviceToDevice, L->stream));
       for (int r = 2; r < r_end; ++r) {
-        CK(cudaMemcpyAsync(segv(r), segv(r - 2), vb, cudaMemcpyDeviceToDevice, L->stream));
-        st = step(segv(r - 1), segv(r));
-        if (st != CBDG_OK) return st;
+        // j_r = 2 H~ j_{r-1} - j_{r-2}, out of place (the segment keeps j_{r-2})
+        a.cur = segv(r - 1);
+        a.prev = segv(r - 2);
+        a.out = segv(r);
+        CK(launch_step_real(L->precision, a, cfg, L->stream));
+        a.out = nullptr;
+        L->launches += 1;
       }
       // m - 1 in [kS, kS + r_end - 1]  ->  m in [kS + 1, kS + r_end], m <= M - 1
       const int m_hi = std::min(M - 1, k * S + r_end), m_lo = k * S + 1;

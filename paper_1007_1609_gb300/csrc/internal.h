@@ -41,6 +41,7 @@ struct StepArgs {
   int Lx, Ly;
   int ld;               // columns (a multiple of the slab width)
   int rows_per_cta;     // lattice rows per CTA along y
+  void *out = nullptr;  // real one-step kernel only: j_{n+1} goes here when set (prev is kept)
 };
 
 struct StepConfig {
@@ -164,6 +165,8 @@ cudaError_t launch_contract_planes(const float *a_hi, const float *a_lo, const f
 cudaError_t launch_adjoint_source(int precision, int Lx, int Ly, int ncols, int W,
                                   const int32_t *sites, const double *w, double scale_m, void *lam,
                                   cudaStream_t s);
+// Column groups of the accumulation for ld columns at slab width W on Ly rows.
+int adjoint_groups(int Ly, int ld, int W);
 cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int py, int ld, int W,
                                       int groups, const void *lam, const void *j, double f,
                                       double *part, cudaStream_t s);

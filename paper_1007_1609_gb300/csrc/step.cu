@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
   const size_t slab = static_cast<size_t>(blockIdx.x) * (static_cast<size_t>(2) * Lx * Ly * W);
   const S *cur = static_cast<const S *>(a.cur) + slab;
   S *prev = static_cast<S *>(a.prev) + slab;
+  S *const dst = a.out ? static_cast<S *>(a.out) + slab : prev;  // j_{n+1}
   const S *par = static_cast<const S *>(a.params);
   const unsigned row_bytes = static_cast<unsigned>(rowel * sizeof(S));
   const unsigned par_bytes = static_cast<unsigned>(pel * sizeof(S));
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
       const S *rp = sj + ((i + 2) % JS) * rowel;  // y + 1
       const S *ro = so + (i % OS) * rowel;        // j_{n-1} of y
       const S *pc = sp + ((i + 1) % JS) * pel;
-      S *out = prev + static_cast<size_t>(y0 + i) * rowel;
+      S *out = dst + static_cast<size_t>(y0 + i) * rowel;
       const int off = q * VEC;
       const int hb = Lx * W;  // hole rows follow the electron rows
 #pragma unroll
