@@ -460,9 +460,33 @@ def leg_adjoint(cbdg, wl, stream):
     return out
 
 
+def leg_tiny(cbdg, wl, stream):
+    """The 16x16 clean lattice (M = 256, all 256 sites): 10 mixed
+    self-consistency iterations from uniform Delta = 0.5, replayed as CUDA
+    graphs.  The whole recursion runs in shared memory (one launch per
+    iteration); "*_streamed" is the same with the HBM-streaming kernels."""
+    p = wl.swave_clean(16, 256)
+    out = {}
+    for prec, resident in (("fp64", 1), ("fp32", 1), ("fp64", 0), ("fp32", 0)):
+        lat = cbdg.Lattice(p, precision=prec, stream=stream)
+        lat.set_option(cbdg.CBDG_OPT_RESIDENT, resident)
+        lat.scf_step(p.T, p.M, p.mix)  # warm-up (tables, buffers)
+        lat.delta = p.delta0
+        t0 = time.perf_counter()
+        for _ in range(10):
+            diff = lat.scf_step(p.T, p.M, p.mix)
+        dt = time.perf_counter() - t0
+        out[prec if resident else prec + "_streamed"] = {
+            "ms_10_iterations": dt * 1e3, "ms_per_iteration": dt * 1e2,
+            "vector_steps_per_s": 10 * p.N * ((p.M + 1) // 2) / dt, "last_max_abs_ddelta": diff}
+        lat.close()
+    return out
+
+
 def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096):
     """Other hot-path stages at their workload sizes (not the headline)."""
     legs = {
+        "tiny": lambda: leg_tiny(cbdg, wl, stream),
         "contraction": lambda: leg_contraction(cbdg, torch, stream),
         "dwave": lambda: leg_dwave(cbdg, wl, stream, hbm, columns),
         "ensemble": lambda: leg_ensemble(cbdg, wl, stream),
@@ -517,7 +541,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--stage", default=None, choices=["contraction", "dwave", "ensemble", "adjoint"],
+    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint"],
                     help="measure only this stage and print its record (profiling runs)")
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")

@@ -222,15 +222,27 @@ enum {
   CBDG_OPT_AUTOTUNE = 11,        /* 1: time candidate tiles (slab width, depth, row split) on
                                     the first pass of each lattice shape and keep the fastest
                                     (cached per process); 0 (default): static plan */
-  CBDG_OPT_TEMPORAL_STEPS = 12   /* recursion steps K per pass over the vectors (temporal
+  CBDG_OPT_TEMPORAL_STEPS = 12,  /* recursion steps K per pass over the vectors (temporal
                                     blocking), 1..4, for real on-site FP32 lattices with open
-                                    y edges: one pass reads j_{n-1}, j_n and writes
-                                    j_{n+K-1}, j_{n+K}; 1 = one step per pass; 0 (default) =
+                                    y edges: one pass reads j_(n-1), j_n and writes
+                                    j_(n+K-1), j_(n+K); 1 = one step per pass; 0 (default) =
                                     2.  Shapes the multi-step kernel does not serve run one
                                     step per pass: periodic y, FP64, complex fields, slab
                                     widths other than 8 and 16, Lx above 64 (K = 2: 128) at
                                     slab width 16 or above 128 (K = 2: 256) at slab width 8,
                                     and rings that do not fit in shared memory */
+  CBDG_OPT_GRAPH = 13,           /* 1 (default): cbdg_scf_step captures its iteration as a
+                                    CUDA graph on the second call with the same (T, M, mix)
+                                    and replays it afterwards (not while profiling,
+                                    autotuning, with a fixed rescale or the stall hook); any
+                                    option change or buffer reallocation drops the graph;
+                                    0: always launch directly */
+  CBDG_OPT_RESIDENT = 14         /* 1 (default): real on-site lattices whose two vectors per
+                                    column slab, stencil parameters and coefficient table
+                                    fit in one SM's shared memory (about 2300 sites in FP64,
+                                    4700 in FP32) run the whole recursion on chip, one
+                                    launch per pass (unless a tile option, autotuning or the
+                                    stall hook is set); 0: the streamed kernels */
 };
 /* Read-only (cbdg_get_option): the tile of the last recursion pass, packed as
  * slab width | depth << 16 | row split << 32. */

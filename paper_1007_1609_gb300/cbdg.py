@@ -42,6 +42,8 @@ CBDG_OPT_WAIT_LIMIT_MS = 9
 CBDG_OPT_TEST_STALL_COPY = 10
 CBDG_OPT_AUTOTUNE = 11
 CBDG_OPT_TEMPORAL_STEPS = 12
+CBDG_OPT_GRAPH = 13
+CBDG_OPT_RESIDENT = 14
 CBDG_INFO_LAST_TILE = 100
 CBDG_INFO_LAST_TEMPORAL = 101
 

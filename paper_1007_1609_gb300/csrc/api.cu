@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <map>
@@ -72,11 +73,16 @@ bool is_device_ptr(const void *p) {
 }
 
 // Growable device buffer owned by a lattice.
+// Bumped whenever any library buffer is (re)allocated: a captured graph
+// records the value and is discarded once it changes (its pointers may be stale).
+std::atomic<uint64_t> g_buffer_generation{0};
+
 struct DBuf {
   void *p = nullptr;
   size_t bytes = 0;
   cudaError_t ensure(size_t n) {
     if (n <= bytes) return cudaSuccess;
+    g_buffer_generation.fetch_add(1);
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
@@ -124,6 +130,26 @@ struct cbdg_lattice {
   StepConfig last_cfg{};
   int last_temporal = 1;
   double last_a = 0.0;
+  // CUDA-graph replay of self-consistency iterations (CBDG_OPT_GRAPH)
+  int64_t use_graph = 1;
+  int64_t resident = 1;  // CBDG_OPT_RESIDENT
+  struct ScfKey {
+    double T = 0.0, mix = 0.0;
+    int M = 0;
+    uint64_t gen = 0;
+    bool valid = false;
+    bool same(double t, int m, double x, uint64_t g) const {
+      return valid && T == t && M == m && mix == x && gen == g;
+    }
+  } graph_key, warm_key;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;  // the iteration is captured here, replayed on `stream`
+  int64_t graph_launches = 0;
+  void drop_graph() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    graph_exec = nullptr;
+    graph_key.valid = warm_key.valid = false;
+  }
 };
 
 namespace {
@@ -204,7 +230,7 @@ cbdg_status prepare(cbdg_lattice *L, double T, int kernel, double lambda, int M,
   }
   CK(L->C.ensure(static_cast<size_t>(M) * sizeof(double)));
   if (coeffs) {
-    CK(L->f.ensure(static_cast<size_t>(L->K) * sizeof(double)));
+    CK(L->f.ensure(coefficient_work(M, L->K) * sizeof(double)));
     CK(launch_coefficients(M, L->K, T, kernel, lambda, L->scal.as<double>(), L->f.as<double>(),
                            L->C.as<double>(), L->stream));
     L->launches += 2;
@@ -340,7 +366,13 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
   const int Wdef = mode == kReal ? slab_width_default(L->precision) : slab_width_default_cplx(L->precision);
   int W = L->slab_w > 0 ? static_cast<int>(L->slab_w) : Wdef;
   int want_split = static_cast<int>(L->row_split), want_depth = static_cast<int>(L->depth);
-  if (L->autotune && L->slab_w == 0 && L->row_split == 0 && L->depth == 0 && n_sites > 0) {
+  // small real lattices: the whole recursion in shared memory, one launch
+  const int Wres = (mode == kReal && L->resident && L->slab_w == 0 && L->row_split == 0 && L->depth == 0 &&
+                    !L->autotune && !L->stall)
+                       ? plan_resident(L->precision, L->Lx, L->Ly, n_sites, M)
+                       : 0;
+  if (Wres) W = Wres;
+  if (!Wres && L->autotune && L->slab_w == 0 && L->row_split == 0 && L->depth == 0 && n_sites > 0) {
     TuneVal tv;
     cbdg_status ts = autotune(L, mode, n_sites, &tv);
     if (ts != CBDG_OK) return ts;
@@ -376,6 +408,38 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
   for (int c0 = 0; c0 < n_sites; c0 += chunk) {
     const int ncols = std::min(chunk, n_sites - c0);
     const int ld = ((ncols + W - 1) / W) * W;
+    if (Wres) {
+      const size_t vbytes = rows * ld * es;
+      CK(L->vec0.ensure(vbytes));
+      CK(L->vec1.ensure(vbytes));
+      CK(L->mu1.ensure(ld * sizeof(double)));
+      CK(L->dA.ensure(ld * sizeof(double2)));
+      CK(L->acc_n.ensure(ld * sizeof(double)));
+      CK(L->acc_d.ensure(ld * 4 * sizeof(double2)));
+      CK(cudaMemsetAsync(L->vec0.p, 0, vbytes, L->stream));
+      CK(cudaMemsetAsync(L->vec1.p, 0, vbytes, L->stream));
+      double *mee = mom_ee ? mom_ee + static_cast<size_t>(c0) * M : nullptr;
+      double2 *meh = mom_eh ? mom_eh + static_cast<size_t>(c0) * M * mom_stride : nullptr;
+      CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, W, sites + c0,
+                          L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
+                          L->scal.as<double>(), L->C.as<double>(), M, L->vec0.p, L->vec1.p,
+                          L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
+                          L->acc_d.as<double2>(), mee, meh, mom_stride, L->stream));
+      CK(launch_resident(L->precision, W, L->Lx, L->Ly, ld, ncols, M, (M + 1) / 2 - 1, L->vec0.p, L->vec1.p,
+                         L->params.p, L->C.as<double>(), L->mu1.as<double>(), L->dA.as<double2>(),
+                         L->acc_n.as<double>(), L->acc_d.as<double2>(), mee, meh, mom_stride,
+                         L->flags.as<unsigned int>(), tol, L->stream));
+      L->launches += 2;
+      if (finalize) {
+        CK(launch_finalize_onsite(ncols, sites + c0, L->coupling, L->acc_n.as<double>(),
+                                  L->acc_d.as<double2>(), L->dout.as<double2>(), L->nout.as<double>(),
+                                  L->stream));
+        L->launches += 1;
+      }
+      L->last_cfg = StepConfig{W, 0, 1, 256, 0};
+      L->last_temporal = 1;
+      continue;
+    }
     StepConfig cfg;
     const bool planned =
         mode == kReal ? plan_step_real(L->precision, L->Lx, L->Ly, ld, W, want_split, want_depth, &cfg)
@@ -703,6 +767,8 @@ cbdg_status cbdg_destroy(cbdg_lattice *L) {
                   &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b, &L->adj_ck, &L->adj_seg, &L->adj_lam, &L->adj_part, &L->adj_w, &L->adj_out};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
+  L->drop_graph();
+  if (L->capture_stream) cudaStreamDestroy(L->capture_stream);
   delete L;
   return CBDG_OK;
 }
@@ -894,11 +960,64 @@ cbdg_status cbdg_scf_step(cbdg_lattice *L, double T, int32_t M, double mix,
   cbdg_status st = begin(L);
   if (st != CBDG_OK) return st;
   if (!(mix > 0.0 && mix <= 1.0)) return fail(CBDG_ERR_INVALID_ARG, "mix must be in (0, 1]");
-  st = order_parameter_impl(L, T, CBDG_JACKSON, 0.0, M);
-  if (st != CBDG_OK) return st;
-  CK(launch_mix(L->nd, mix, L->dout.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
-                L->stream));
-  L->launches += 1;
+  // One iteration = coefficient tables, recursion and folds, mixing: a fixed
+  // sequence of launches for fixed (T, M, mix) and buffers.  The first call
+  // runs it directly (and sizes every buffer), the second captures it as a
+  // CUDA graph, later calls replay the graph.
+  const bool graphable = L->use_graph && !L->profile && !L->autotune && !L->fixed_a_pico && !L->stall;
+  const uint64_t gen = g_buffer_generation.load();
+  auto iteration = [&]() -> cbdg_status {
+    cbdg_status s2 = order_parameter_impl(L, T, CBDG_JACKSON, 0.0, M);
+    if (s2 != CBDG_OK) return s2;
+    CK(launch_mix(L->nd, mix, L->dout.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
+                  L->stream));
+    L->launches += 1;
+    return CBDG_OK;
+  };
+  if (graphable && L->graph_key.same(T, M, mix, gen)) {
+    CK(cudaGraphLaunch(L->graph_exec, L->stream));
+    L->launches += L->graph_launches;
+  } else if (graphable && L->warm_key.same(T, M, mix, gen)) {
+    L->drop_graph();
+    const int64_t l0 = L->launches;
+    // capture on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); nothing runs while capturing
+    if (!L->capture_stream) CK(cudaStreamCreateWithFlags(&L->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t user_stream = L->stream;
+    L->stream = L->capture_stream;
+    cudaError_t ce = cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeRelaxed);
+    if (ce != cudaSuccess) {
+      L->stream = user_stream;
+      return cuda_fail(ce, "starting the capture of the iteration");
+    }
+    st = iteration();
+    cudaGraph_t graph = nullptr;
+    ce = cudaStreamEndCapture(L->stream, &graph);
+    L->stream = user_stream;
+    if (st != CBDG_OK || ce != cudaSuccess || g_buffer_generation.load() != gen) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      if (st != CBDG_OK) return st;
+      if (ce != cudaSuccess) return cuda_fail(ce, "capturing the iteration");
+      // a buffer moved while capturing: run this iteration directly
+      L->launches = l0;
+      st = iteration();
+      if (st != CBDG_OK) return st;
+    } else {
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) return cuda_fail(ie, "instantiating the iteration graph");
+      L->graph_exec = exec;
+      L->graph_key = {T, mix, M, gen, true};
+      L->graph_launches = L->launches - l0;
+      CK(cudaGraphLaunch(L->graph_exec, L->stream));
+    }
+  } else {
+    st = iteration();
+    if (st != CBDG_OK) return st;
+    if (graphable) L->warm_key = {T, mix, M, g_buffer_generation.load(), true};
+  }
   double bits = 0.0;
   CK(cudaMemcpyAsync(&bits, L->scal.as<double>() + kScalMaxDiffBits, sizeof(double),
                      cudaMemcpyDeviceToHost, L->stream));
@@ -1109,6 +1228,7 @@ cbdg_status cbdg_get_rescale(cbdg_lattice *L, double *a) {
 
 cbdg_status cbdg_set_option(cbdg_lattice *L, int32_t option, int64_t value) {
   if (!L) return fail(CBDG_ERR_INVALID_ARG, "lattice is NULL");
+  L->drop_graph();  // any option may change the launch sequence
   switch (option) {
     case CBDG_OPT_QUADRATURE_NODES:
       if (value < 16 || value > (1 << 24)) return fail(CBDG_ERR_INVALID_ARG, "K out of range");
@@ -1160,6 +1280,14 @@ cbdg_status cbdg_set_option(cbdg_lattice *L, int32_t option, int64_t value) {
       if (value < 0 || value > 4) return fail(CBDG_ERR_INVALID_ARG, "temporal steps must be in [0, 4]");
       L->temporal = value;
       return CBDG_OK;
+    case CBDG_OPT_GRAPH:
+      if (value != 0 && value != 1) return fail(CBDG_ERR_INVALID_ARG, "graph option must be 0 or 1");
+      L->use_graph = value;
+      return CBDG_OK;
+    case CBDG_OPT_RESIDENT:
+      if (value != 0 && value != 1) return fail(CBDG_ERR_INVALID_ARG, "resident option must be 0 or 1");
+      L->resident = value;
+      return CBDG_OK;
   }
   return fail(CBDG_ERR_INVALID_ARG, "unknown option %d", option);
 }
@@ -1180,6 +1308,8 @@ cbdg_status cbdg_get_option(cbdg_lattice *L, int32_t option, int64_t *value) {
     case CBDG_OPT_TEST_STALL_COPY: *value = L->stall; return CBDG_OK;
     case CBDG_OPT_AUTOTUNE: *value = L->autotune; return CBDG_OK;
     case CBDG_OPT_TEMPORAL_STEPS: *value = L->temporal; return CBDG_OK;
+    case CBDG_OPT_GRAPH: *value = L->use_graph; return CBDG_OK;
+    case CBDG_OPT_RESIDENT: *value = L->resident; return CBDG_OK;
     case CBDG_INFO_LAST_TEMPORAL: *value = L->last_temporal; return CBDG_OK;
     case CBDG_INFO_LAST_TILE:
       *value = static_cast<int64_t>(L->last_cfg.slab_w) | (static_cast<int64_t>(L->last_cfg.depth) << 16) |

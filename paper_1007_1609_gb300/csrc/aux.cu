@@ -40,45 +40,63 @@ __global__ void set_rescale_kernel(double margin, double *scal) {
 }
 
 // f_k = tanh(a cos(th_k) / 2T), th_k = pi (k + 1/2) / K  (sign(x) at T = 0).
-__global__ void fermi_nodes_kernel(int K, double T, const double *scal, double *f) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const double a = scal[kScalA];
-  const double x = cospi((2.0 * k + 1.0) / (2.0 * K));
-  f[k] = (T > 0.0) ? tanh(a * x / (2.0 * T)) : (x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0));
-}
+// Coefficients of Eqs. 6-7 for the Fermi factor tanh(a x / 2T) (its
+// Chebyshev series has only odd terms) by a K-node Gauss-Chebyshev sum,
+//   c_n = (1/K) sum_k f_k T_n(x_k),  x_k = cos(pi (2k+1) / 2K),
+//   C_n = g_n (2 - delta_n0) c_n,
+// with T_n(x_k) from the three-term recurrence (one FMA per term; the FP64
+// rounding error grows like n * 2^-53).  One thread per node, n in chunks of
+// kCoefChunk: a warp-shuffle sum per n, the warps of a block summed in a fixed
+// order into part[block][n]; a second kernel sums the blocks.
+constexpr int kCoefThreads = 256, kCoefChunk = 128;
 
-// C_n = g_n (2 - delta_n0) c_n with the Gauss-Chebyshev sum
-// c_n = (1/K) sum_k f_k cos(n th_k).  cos(n th_k) = cospi(r / 2K) with the
-// exact integer reduction r = n (2k+1) mod 4K.  One block per n, fixed-order
-// reduction.
-__global__ void coefficient_kernel(int M, int K, int kernel, double lambda, const double *f,
-                                   double *C) {
-  const int n = blockIdx.x;
-  __shared__ double red[256];
-  const long long period = 4LL * K;
-  double s = 0.0;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const long long r = (static_cast<long long>(n) * (2LL * k + 1)) % period;
-    s += f[k] * cospi(static_cast<double>(r) / (2.0 * K));
+__global__ void __launch_bounds__(kCoefThreads) coef_partial_kernel(int M, int K, double T, const double *scal,
+                                                                    double *part) {
+  __shared__ double wsum[kCoefThreads / 32][kCoefChunk];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double a = scal[kScalA];
+  double x = 0.0, f = 0.0;
+  if (k < K) {
+    x = cospi((2.0 * k + 1.0) / (2.0 * K));
+    f = (T > 0.0) ? tanh(a * x / (2.0 * T)) : (x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0));
   }
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+  double tm1 = 0.0, tn = 1.0;  // T_{n-1}, T_n at x
+  for (int n0 = 0; n0 < M; n0 += kCoefChunk) {
+    const int nc = min(kCoefChunk, M - n0);
+    for (int j = 0; j < nc; ++j) {
+      double v = f * tn;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) wsum[warp][j] = v;
+      const double tp = (n0 + j == 0) ? x : fma(2.0 * x, tn, -tm1);
+      tm1 = tn;
+      tn = tp;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+      double v = 0.0;
+      for (int w = 0; w < kCoefThreads / 32; ++w) v += wsum[w][j];
+      part[static_cast<size_t>(blockIdx.x) * M + n0 + j] = v;
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const double c = red[0] / K;
-    double g;
-    if (kernel == 0) {  // Jackson
-      const double q = 1.0 / (M + 1.0);
-      g = ((M - n + 1) * cospi(n * q) + sinpi(n * q) * cospi(q) / sinpi(q)) / (M + 1.0);
-    } else {  // Lorentz, Eq. 16
-      g = sinh(lambda * (1.0 - static_cast<double>(n) / M)) / sinh(lambda);
-    }
-    C[n] = g * (n == 0 ? 1.0 : 2.0) * c;
+}
+
+__global__ void coef_final_kernel(int M, int K, int nblocks, int kernel, double lambda, const double *part,
+                                  double *C) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= M) return;
+  double c = 0.0;
+  for (int b = 0; b < nblocks; ++b) c += part[static_cast<size_t>(b) * M + n];
+  c /= K;
+  double g;
+  if (kernel == 0) {  // Jackson
+    const double q = 1.0 / (M + 1.0);
+    g = ((M - n + 1) * cospi(n * q) + sinpi(n * q) * cospi(q) / sinpi(q)) / (M + 1.0);
+  } else {  // Lorentz, Eq. 16
+    g = sinh(lambda * (1.0 - static_cast<double>(n) / M)) / sinh(lambda);
   }
+  C[n] = g * (n == 0 ? 1.0 : 2.0) * c;
 }
 
 template <typename S>
@@ -239,10 +257,15 @@ cudaError_t launch_gershgorin(int N, int n_dirs, int pairing, int, int, int, int
   return cudaGetLastError();
 }
 
+size_t coefficient_work(int M, int K) {
+  return static_cast<size_t>(blocks(K, kCoefThreads)) * static_cast<size_t>(M);
+}
+
 cudaError_t launch_coefficients(int M, int K, double T, int kernel, double lambda,
-                                const double *scal, double *f, double *C, cudaStream_t s) {
-  fermi_nodes_kernel<<<blocks(K, 256), 256, 0, s>>>(K, T, scal, f);
-  coefficient_kernel<<<M, 256, 0, s>>>(M, K, kernel, lambda, f, C);
+                                const double *scal, double *work, double *C, cudaStream_t s) {
+  const int nb = blocks(K, kCoefThreads);
+  coef_partial_kernel<<<nb, kCoefThreads, 0, s>>>(M, K, T, scal, work);
+  coef_final_kernel<<<blocks(M, 128), 128, 0, s>>>(M, K, nb, kernel, lambda, work, C);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,17 @@ bool plan_step_multi(int Lx, int Ly, int ld, int want_w, int want_k, int want_de
                      StepConfig *cfg, int *k_out);
 cudaError_t launch_step_multi(const StepArgs &a, const StepConfig &cfg, int K, cudaStream_t s);
 
+// Whole recursion in shared memory for small real on-site lattices
+// (resident.cu): plan_resident returns the slab width (1, 2 or 4) or 0 when
+// the lattice does not fit; launch_resident runs steps 1..steps with the
+// folds of fold_kernel on j_0, j_1 written by init_real at that width.
+int plan_resident(int precision, int Lx, int Ly, int ncols, int M);
+cudaError_t launch_resident(int precision, int W, int Lx, int Ly, int ld, int ncols, int M, int steps,
+                            const void *j0, const void *j1, const void *params, const double *C,
+                            const double *mu1, const double2 *dA, double *acc_n, double2 *acc_d,
+                            double *mu_ee, double2 *mu_eh, int mom_stride, unsigned int *flags, double tol,
+                            cudaStream_t s);
+
 // Recursion step for the general lattice (complex vectors; nnn: 8 hopping
 // directions; bond: nearest-neighbour pairing, which skips the column sums).
 // The partial sums, when formed, are [row_split][4][ld].
@@ -112,8 +123,11 @@ cudaError_t launch_finalize_bond(int N, int Lx, int Ly, int px, int py, double V
 cudaError_t launch_gershgorin(int N, int n_dirs, int pairing, int Lx, int Ly, int px, int py,
                               const double *eps, double mu, const double2 *hop,
                               const double2 *delta, double margin, double *scal, cudaStream_t s);
+// Coefficient table C[M] (Eqs. 6-7 with the kernel of Eq. 16 or Jackson);
+// work holds coefficient_work(M, K) doubles.
+size_t coefficient_work(int M, int K);
 cudaError_t launch_coefficients(int M, int K, double T, int kernel, double lambda,
-                                const double *scal, double *f, double *C, cudaStream_t s);
+                                const double *scal, double *work, double *C, cudaStream_t s);
 cudaError_t launch_params_real(int precision, int N, const double *eps, double mu,
                                const double2 *hop, const double2 *delta, const double *scal,
                                void *params, cudaStream_t s);

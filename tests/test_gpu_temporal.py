@@ -43,7 +43,7 @@ def test_moments_match_oracle(case, steps, depth, slab):
     Lx, Ly, M = case
     p = rect(Lx, Ly, M, seed=Lx * 31 + Ly, periodic=0)
     sites = np.arange(p.N, dtype=np.int32)
-    lat = gpu_lattice(p, "fp32", temporal_steps=steps, pipeline_depth=depth, slab_width=slab)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=steps, pipeline_depth=depth, slab_width=slab)
     (ee, eh), launches = recursion_launches(lat, sites, M)
     n_steps = (M + 1) // 2 - 1
     # the grouped launches ran: K steps per pass, then single steps for the rest
@@ -63,15 +63,15 @@ def test_same_as_one_step_per_pass(steps):
     equals the one-step-per-pass result to FP32 rounding of the sums."""
     p = rect(33, 17, 65, seed=5, periodic=0)
     sites = np.arange(p.N, dtype=np.int32)[::-1].copy()
-    one = gpu_lattice(p, "fp32", temporal_steps=1).moments(sites, p.M)
-    got = gpu_lattice(p, "fp32", temporal_steps=steps).moments(sites, p.M)
+    one = gpu_lattice(p, "fp32", resident=0, temporal_steps=1).moments(sites, p.M)
+    got = gpu_lattice(p, "fp32", resident=0, temporal_steps=steps).moments(sites, p.M)
     assert max_abs(got[0], one[0]) < 1e-6 and max_abs(got[1], one[1]) < 1e-6
 
 
 def test_periodic_y_falls_back_to_one_step():
     p = rect(6, 9, 40, seed=4, periodic=1)
     sites = np.arange(p.N, dtype=np.int32)
-    lat = gpu_lattice(p, "fp32", temporal_steps=4)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=4)
     (ee, eh), launches = recursion_launches(lat, sites, p.M)
     assert launches == (p.M + 1) // 2 - 1
     oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, p.M)
@@ -93,7 +93,7 @@ def test_full_size_disordered_128_sampled(steps, slab):
     """The 128x128 disordered workload at M = 1024, all 16384 start vectors:
     Delta_out and n at sampled sites vs the oracle."""
     p = wl.swave_disordered(128, 1024, seed=1001)
-    lat = gpu_lattice(p, "fp32", temporal_steps=steps, slab_width=slab, profile=1)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=steps, slab_width=slab, profile=1)
     d, n = lat.order_parameter(p.T, p.M)
     _, launches, _ = cbdg.cbdg_profile_read(lat.handle, reset=True)
     assert launches == 511 // steps + 511 % steps
