@@ -45,40 +45,58 @@ __global__ void set_rescale_kernel(double margin, double *scal) {
 //   c_n = (1/K) sum_k f_k T_n(x_k),  x_k = cos(pi (2k+1) / 2K),
 //   C_n = g_n (2 - delta_n0) c_n,
 // with T_n(x_k) from the three-term recurrence (one FMA per term; the FP64
-// rounding error grows like n * 2^-53).  One thread per node, n in chunks of
-// kCoefChunk: a warp-shuffle sum per n, the warps of a block summed in a fixed
-// order into part[block][n]; a second kernel sums the blocks.
-constexpr int kCoefThreads = 256, kCoefChunk = 128;
+// rounding error grows like (n - n0) * 2^-53 inside a chunk of kCoefChunk
+// moments started from directly evaluated T_{n0}, T_{n0-1}).  kCoefNodes
+// nodes per thread: per n a thread sums its nodes, a warp-shuffle sum follows,
+// the warps of a block are summed in a fixed order into part[node block][n];
+// a second kernel sums the node blocks.
+constexpr int kCoefThreads = 256, kCoefChunk = 128, kCoefNodes = 4;  // nodes per thread
 
+// cos(n pi (2k+1) / 2K) with the exact integer reduction of the argument.
+__device__ __forceinline__ double cheb_node_cos(long long n, int k, int K) {
+  const long long period = 4LL * K;
+  const long long r = (n % period) * (2LL * k + 1) % period;
+  return cospi(static_cast<double>(r) / (2.0 * K));
+}
+
+// Grid (node blocks, n chunks): block (b, c) sums nodes
+// [b * kCoefNodes * 256, (b + 1) * kCoefNodes * 256) for n in chunk c, starting
+// the recurrence from T_{n0} and T_{n0-1} evaluated directly.
 __global__ void __launch_bounds__(kCoefThreads) coef_partial_kernel(int M, int K, double T, const double *scal,
                                                                     double *part) {
   __shared__ double wsum[kCoefThreads / 32][kCoefChunk];
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.y * kCoefChunk, nc = min(kCoefChunk, M - n0);
   const double a = scal[kScalA];
-  double x = 0.0, f = 0.0;
-  if (k < K) {
-    x = cospi((2.0 * k + 1.0) / (2.0 * K));
-    f = (T > 0.0) ? tanh(a * x / (2.0 * T)) : (x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0));
+  double x[kCoefNodes], f[kCoefNodes], tm1[kCoefNodes], tn[kCoefNodes];
+#pragma unroll
+  for (int j = 0; j < kCoefNodes; ++j) {
+    const int k = (blockIdx.x * kCoefNodes + j) * kCoefThreads + threadIdx.x;
+    x[j] = f[j] = tm1[j] = tn[j] = 0.0;
+    if (k < K) {
+      x[j] = cospi((2.0 * k + 1.0) / (2.0 * K));
+      f[j] = (T > 0.0) ? tanh(a * x[j] / (2.0 * T)) : (x[j] > 0.0 ? 1.0 : (x[j] < 0.0 ? -1.0 : 0.0));
+      tn[j] = cheb_node_cos(n0, k, K);
+      tm1[j] = n0 > 0 ? cheb_node_cos(n0 - 1, k, K) : 0.0;
+    }
   }
-  double tm1 = 0.0, tn = 1.0;  // T_{n-1}, T_n at x
-  for (int n0 = 0; n0 < M; n0 += kCoefChunk) {
-    const int nc = min(kCoefChunk, M - n0);
-    for (int j = 0; j < nc; ++j) {
-      double v = f * tn;
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) wsum[warp][j] = v;
-      const double tp = (n0 + j == 0) ? x : fma(2.0 * x, tn, -tm1);
-      tm1 = tn;
-      tn = tp;
+  for (int i = 0; i < nc; ++i) {
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < kCoefNodes; ++j) {
+      v = fma(f[j], tn[j], v);
+      const double tp = (n0 + i == 0) ? x[j] : fma(2.0 * x[j], tn[j], -tm1[j]);
+      tm1[j] = tn[j];
+      tn[j] = tp;
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-      double v = 0.0;
-      for (int w = 0; w < kCoefThreads / 32; ++w) v += wsum[w][j];
-      part[static_cast<size_t>(blockIdx.x) * M + n0 + j] = v;
-    }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[warp][i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < kCoefThreads / 32; ++w) v += wsum[w][i];
+    part[static_cast<size_t>(blockIdx.x) * M + n0 + i] = v;
   }
 }
 
@@ -258,13 +276,13 @@ cudaError_t launch_gershgorin(int N, int n_dirs, int pairing, int, int, int, int
 }
 
 size_t coefficient_work(int M, int K) {
-  return static_cast<size_t>(blocks(K, kCoefThreads)) * static_cast<size_t>(M);
+  return static_cast<size_t>(blocks(K, kCoefThreads * kCoefNodes)) * static_cast<size_t>(M);
 }
 
 cudaError_t launch_coefficients(int M, int K, double T, int kernel, double lambda,
                                 const double *scal, double *work, double *C, cudaStream_t s) {
-  const int nb = blocks(K, kCoefThreads);
-  coef_partial_kernel<<<nb, kCoefThreads, 0, s>>>(M, K, T, scal, work);
+  const int nb = blocks(K, kCoefThreads * kCoefNodes);
+  coef_partial_kernel<<<dim3(nb, blocks(M, kCoefChunk)), kCoefThreads, 0, s>>>(M, K, T, scal, work);
   coef_final_kernel<<<blocks(M, 128), 128, 0, s>>>(M, K, nb, kernel, lambda, work, C);
   return cudaGetLastError();
 }

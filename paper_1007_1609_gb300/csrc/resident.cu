@@ -10,8 +10,15 @@
 // C = sum (u'v - v'u)) are reduced per step by warp shuffles and an FP64 sum
 // over warps, and folded in FP64 by one thread per column exactly as
 // fold_kernel does (moments 2n, 2n+1 of Eqs. 11 and 14, the Delta and n
-// accumulators, the |mu| <= 1 check).  No vector traffic reaches HBM; for the
-// 16 x 16 lattice a self-consistency iteration becomes one recursion launch.
+// accumulators, the |mu| <= 1 check).  In FP64 without moment output the
+// fold is linear in A, B, C, so each thread folds its own partial sums into
+// FP64 accumulators that are reduced once at the end (the constant terms are
+// added by the column's thread), and the full per-step reduction runs only
+// every kCheckEvery steps and at the last step for the |mu| <= 1 check (the
+// norm of j_n grows monotonically once a is too small); on GB300, where FP64
+// runs at 1/64 of the FP32 rate, the shuffle tree of every step would cost as
+// much as the stencil.  No vector traffic reaches HBM; for the 16 x 16
+// lattice a self-consistency iteration becomes one recursion launch.
 #include <algorithm>
 
 #include "internal.h"
@@ -21,6 +28,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kCheckEvery = 16;
 
 template <typename S, int VEC>
 struct alignas(sizeof(S) * VEC) Pack {
@@ -46,7 +54,7 @@ struct ResidentArgs {
   int Lx, Ly, M, steps, ncols;
 };
 
-template <typename S, int W>
+template <typename S, int W, bool LINEAR>
 __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
   constexpr int VEC = (W * sizeof(S) >= 16) ? 16 / static_cast<int>(sizeof(S)) : W;
   constexpr int QUADS = W / VEC, XS = kThreads / QUADS;
@@ -87,6 +95,9 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
     da = a.dA[col];
   }
   bool bad = false;
+  double ln[VEC], ld_[VEC];  // linear fold: this thread's share of acc_n and Re acc_d
+#pragma unroll
+  for (int l = 0; l < VEC; ++l) ln[l] = ld_[l] = 0.0;
   __syncthreads();
 
   S *prev = bp, *cur = bq;
@@ -128,25 +139,39 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
       *reinterpret_cast<P *>(prev + (rc + x + Lx) * W + off) = vn;
     }
     (void)hb;
-    // column sums: lanes with the same q hold the same columns
-    double *wr = wred + static_cast<size_t>(n & 1) * kWarps * 3 * W + static_cast<size_t>(warp) * 3 * W;
+    const int m0 = 2 * n, mo = 2 * n + 1;
+    if (LINEAR) {
 #pragma unroll
-    for (int l = 0; l < VEC; ++l) {
-      S xa = pa[l], xb = pb[l], xc = pc[l];
-#pragma unroll
-      for (int o = QUADS; o < 32; o <<= 1) {
-        xa += __shfl_xor_sync(0xffffffffu, xa, o);
-        xb += __shfl_xor_sync(0xffffffffu, xb, o);
-        xc += __shfl_xor_sync(0xffffffffu, xc, o);
+      for (int l = 0; l < VEC; ++l) {
+        if (m0 < M) ln[l] -= 2.0 * Cs[m0] * static_cast<double>(pa[l]);
+        if (mo < M) {
+          ln[l] -= 2.0 * Cs[mo] * static_cast<double>(pb[l]);
+          ld_[l] += 2.0 * ((n & 1) ? 1.0 : -1.0) * Cs[mo] * static_cast<double>(pc[l]);
+        }
       }
-      if (lane < QUADS) {
-        wr[0 * W + off + l] = static_cast<double>(xa);
-        wr[1 * W + off + l] = static_cast<double>(xb);
-        wr[2 * W + off + l] = static_cast<double>(xc);
+    }
+    const bool reduce = !LINEAR || n % kCheckEvery == 0 || n == a.steps;
+    if (reduce) {
+      // column sums: lanes with the same q hold the same columns
+      double *wr = wred + static_cast<size_t>(n & 1) * kWarps * 3 * W + static_cast<size_t>(warp) * 3 * W;
+#pragma unroll
+      for (int l = 0; l < VEC; ++l) {
+        S xa = pa[l], xb = pb[l], xc = pc[l];
+#pragma unroll
+        for (int o = QUADS; o < 32; o <<= 1) {
+          xa += __shfl_xor_sync(0xffffffffu, xa, o);
+          xb += __shfl_xor_sync(0xffffffffu, xb, o);
+          if (!LINEAR) xc += __shfl_xor_sync(0xffffffffu, xc, o);
+        }
+        if (lane < QUADS) {
+          wr[0 * W + off + l] = static_cast<double>(xa);
+          wr[1 * W + off + l] = static_cast<double>(xb);
+          wr[2 * W + off + l] = static_cast<double>(xc);
+        }
       }
     }
     __syncthreads();  // j_{n+1} complete; this step's warp sums visible
-    if (folder) {
+    if (folder && reduce) {
       const double *wb = wred + static_cast<size_t>(n & 1) * kWarps * 3 * W;
       double A = 0.0, B = 0.0, Cc = 0.0;
       for (int w = 0; w < kWarps; ++w) {
@@ -154,21 +179,22 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
         B += wb[(w * 3 + 1) * W + t];
         Cc += wb[(w * 3 + 2) * W + t];
       }
-      const int m0 = 2 * n, mo = 2 * n + 1;
       const double e0 = 2.0 * A - 1.0;
       const double e1 = 2.0 * B - m1;
       const double sgn = (n & 1) ? 1.0 : -1.0;  // (-1)^(n+1)
       const double2 h1 = make_double2(2.0 * sgn * Cc - da.x, -da.y);
       if (m0 < M) {
-        an -= Cs[m0] * e0;
+        if (!LINEAR) an -= Cs[m0] * e0;
         bad |= fabs(e0) > 1.0 + a.tol;
         if (a.mu_ee) a.mu_ee[static_cast<size_t>(col) * M + m0] = e0;
         if (a.mu_eh) a.mu_eh[(static_cast<size_t>(col) * M + m0) * a.mom_stride] = make_double2(0.0, 0.0);
       }
       if (mo < M) {
-        an -= Cs[mo] * e1;
-        ad.x += Cs[mo] * h1.x;
-        ad.y -= Cs[mo] * h1.y;
+        if (!LINEAR) {
+          an -= Cs[mo] * e1;
+          ad.x += Cs[mo] * h1.x;
+          ad.y -= Cs[mo] * h1.y;
+        }
         bad |= fabs(e1) > 1.0 + a.tol;
         if (a.mu_ee) a.mu_ee[static_cast<size_t>(col) * M + mo] = e1;
         if (a.mu_eh) a.mu_eh[(static_cast<size_t>(col) * M + mo) * a.mom_stride] = h1;
@@ -178,6 +204,41 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
     S *tmp = prev;
     prev = cur;
     cur = tmp;
+  }
+  if (LINEAR) {
+    __syncthreads();  // the last check's sums have been read before wred is reused
+    // per-column totals of the per-thread shares, then the constant terms:
+    //   acc_n += sum_{2n<M} C_2n + mu_1 sum_{2n+1<M} C_2n+1,
+    //   acc_d -= (Delta/a) sum_{2n+1<M} C_2n+1 (as in fold_kernel's h1)
+    double *wr = wred + static_cast<size_t>(warp) * 3 * W;
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) {
+      double xn = ln[l], xd = ld_[l];
+#pragma unroll
+      for (int o = QUADS; o < 32; o <<= 1) {
+        xn += __shfl_xor_sync(0xffffffffu, xn, o);
+        xd += __shfl_xor_sync(0xffffffffu, xd, o);
+      }
+      if (lane < QUADS) {
+        wr[0 * W + off + l] = xn;
+        wr[1 * W + off + l] = xd;
+      }
+    }
+    __syncthreads();
+    if (folder) {
+      double sn = 0.0, sd = 0.0, c_even = 0.0, c_odd = 0.0;
+      for (int w = 0; w < kWarps; ++w) {
+        sn += wred[(w * 3 + 0) * W + t];
+        sd += wred[(w * 3 + 1) * W + t];
+      }
+      for (int n = 1; n <= a.steps; ++n) {
+        if (2 * n < M) c_even += Cs[2 * n];
+        if (2 * n + 1 < M) c_odd += Cs[2 * n + 1];
+      }
+      an += sn + c_even + m1 * c_odd;
+      ad.x += sd - da.x * c_odd;
+      ad.y += da.y * c_odd;
+    }
   }
   if (folder) {
     a.acc_n[col] = an;
@@ -194,10 +255,10 @@ size_t smem_bytes(int N, int M) {
 
 constexpr size_t kMaxSmem = 227 * 1024 - 1024;
 
-template <typename S, int W>
-cudaError_t launch_w(const ResidentArgs &a, int ld, cudaStream_t s) {
+template <typename S, int W, bool LINEAR>
+cudaError_t launch_one(const ResidentArgs &a, int ld, cudaStream_t s) {
   const size_t smem = smem_bytes<S, W>(a.Lx * a.Ly, a.M);
-  auto k = resident_kernel<S, W>;
+  auto k = resident_kernel<S, W, LINEAR>;
   static int attr_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -208,6 +269,13 @@ cudaError_t launch_w(const ResidentArgs &a, int ld, cudaStream_t s) {
   }
   k<<<ld / W, kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// FP64 without moment output folds linearly (see above); everything else per step.
+template <typename S, int W>
+cudaError_t launch_w(const ResidentArgs &a, int ld, cudaStream_t s) {
+  if (sizeof(S) == 8 && !a.mu_ee && !a.mu_eh) return launch_one<S, W, true>(a, ld, s);
+  return launch_one<S, W, false>(a, ld, s);
 }
 
 size_t smem_for(int precision, int W, int N, int M) {
