@@ -27,6 +27,7 @@
 
 #include "../../include/cbdg.h"
 #include "internal.h"
+#include "multi_pass.cuh"
 
 using namespace cbdg;
 
@@ -59,6 +60,7 @@ struct EnsArgs {
   double *nout;                     // [total]
   unsigned *queue;                  // item counter
   unsigned *flags;
+  int multi;                        // 1: two steps per pass (mp::multi_pass) while two remain
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
@@ -189,7 +191,51 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_recursion_kernel(EnsA
 
     const int steps = (a.M + 1) / 2 - 1;
     float *cur = bufB, *prev = bufA;
-    for (int n = 1; n <= steps && !abort_flag; ++n) {
+    // fixed-order FP64 column sums of one step -> moments 2n, 2n+1 -> fold
+    auto reduce_fold = [&](int n, auto &sA, auto &sB, auto &sC) {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        red[0][xs][q * VEC + j] = sA[j].value();
+        red[1][xs][q * VEC + j] = sB[j].value();
+        red[2][xs][q * VEC + j] = sC[j].value();
+      }
+      __syncthreads();
+      if (t < cols) {
+        double A = 0.0, B = 0.0, Cs = 0.0;
+        for (int z = 0; z < XSLOTS; ++z) {
+          A += red[0][z][t];
+          B += red[1][z][t];
+          Cs += red[2][z][t];
+        }
+        const int m0 = 2 * n, m1 = 2 * n + 1;
+        const double e0 = 2.0 * A - 1.0, e1 = 2.0 * B - m1s[t];
+        const double sgn = (n & 1) ? 1.0 : -1.0;
+        const double h1 = 2.0 * sgn * Cs - dAs[t];
+        if (m0 < a.M) accn[t] -= C[m0] * e0;
+        if (m1 < a.M) {
+          accn[t] -= C[m1] * e1;
+          accd[t] += C[m1] * h1;
+        }
+        if (!(fabs(e0) <= 1.0 + 1e-4) || !(fabs(e1) <= 1.0 + 1e-4)) atomicOr(a.flags, kFlagSpectrum);
+      }
+      __syncthreads();
+    };
+    int n = 1;
+    if (a.multi && Ly >= 2) {
+      // two steps per pass over the item's vectors; (prev, cur) end as (j_{n+1}, j_{n+2})
+      for (; n + 1 <= steps && !abort_flag; n += 2) {
+        mp::Kahan pA[2][VEC], pB[2][VEC], pC[2][VEC];
+        if (!mp::multi_pass<W, 2, D, MAXX>(prev, cur, par, Lx, Ly, reinterpret_cast<float *>(smem_raw), bars, G,
+                                           kWaitNs, 0u, &abort_flag, pA, pB, pC))
+          break;
+        G += Ly;
+        // the new rows were stored by this thread; the next pass reads them through TMA
+        asm volatile("fence.proxy.async;\n" ::: "memory");
+        reduce_fold(n, pA[0], pB[0], pC[0]);
+        reduce_fold(n + 1, pA[1], pB[1], pC[1]);
+      }
+    }
+    for (; n <= steps && !abort_flag; ++n) {
       const int rows = Ly;
       const unsigned row_bytes = rowel * 4u, par_bytes = pel * 4u;
       auto issue = [&](int k) {
@@ -284,35 +330,9 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_recursion_kernel(EnsA
         break;
       }
       G += rows + 2;
-      // column sums -> moments 2n, 2n+1 -> fold (FP64, fixed order)
-#pragma unroll
-      for (int j = 0; j < VEC; ++j) {
-        red[0][xs][q * VEC + j] = accA[j].value();
-        red[1][xs][q * VEC + j] = accB[j].value();
-        red[2][xs][q * VEC + j] = accC[j].value();
-      }
       // the new vector is read by the next step through TMA (async proxy)
       asm volatile("fence.proxy.async;\n" ::: "memory");
-      __syncthreads();
-      if (t < cols) {
-        double A = 0.0, B = 0.0, Cs = 0.0;
-        for (int z = 0; z < XSLOTS; ++z) {
-          A += red[0][z][t];
-          B += red[1][z][t];
-          Cs += red[2][z][t];
-        }
-        const int m0 = 2 * n, m1 = 2 * n + 1;
-        const double e0 = 2.0 * A - 1.0, e1 = 2.0 * B - m1s[t];
-        const double sgn = (n & 1) ? 1.0 : -1.0;
-        const double h1 = 2.0 * sgn * Cs - dAs[t];
-        if (m0 < a.M) accn[t] -= C[m0] * e0;
-        if (m1 < a.M) {
-          accn[t] -= C[m1] * e1;
-          accd[t] += C[m1] * h1;
-        }
-        if (!(fabs(e0) <= 1.0 + 1e-4) || !(fabs(e1) <= 1.0 + 1e-4)) atomicOr(a.flags, kFlagSpectrum);
-      }
-      __syncthreads();
+      reduce_fold(n, accA, accB, accC);
       float *tmp = cur;
       cur = prev;
       prev = tmp;
@@ -473,6 +493,7 @@ struct cbdg_ensemble {
   int n_items = 0, grid = 0;
   long long scratch_per_buf = 0;
   size_t smem = 0;
+  int multi = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double g_T = -1, g_mix = -1, g_tol = -1;
@@ -503,6 +524,12 @@ size_t ens_smem(int Lmax) {
   const size_t rowel = static_cast<size_t>(2) * Lmax * kEnsW;
   return ((kEnsJS + kEnsOS) * rowel + kEnsJS * static_cast<size_t>(Lmax) * kParamStride) * sizeof(float);
 }
+// shared memory of the two-step pass (its barriers are the kEnsJS of the one-step march)
+size_t ens_multi_smem(int Lmax) {
+  static_assert(mp::PassShape<kEnsW, 2, kEnsD>::NB == kEnsJS, "the pass and the march share the barriers");
+  return mp::PassShape<kEnsW, 2, kEnsD>::smem_floats(Lmax) * sizeof(float);
+}
+constexpr size_t kEnsDynLimit = 200 * 1024;
 
 template <int MAXX>
 cudaError_t launch_ens(const EnsArgs &a, int grid, size_t smem, cudaStream_t s) {
@@ -571,6 +598,7 @@ cudaError_t enqueue_iteration(cbdg_ensemble *e, double T, int M, double mix, dou
   a.nout = static_cast<double *>(e->d_nout);
   a.queue = small;
   a.flags = small + 2;
+  a.multi = e->multi;
   const int maxx = (e->Lmax + 63) / 64;
   err = maxx == 1 ? launch_ens<1>(a, e->grid, e->smem, s) : launch_ens<2>(a, e->grid, e->smem, s);
   if (err != cudaSuccess) return err;
@@ -629,7 +657,9 @@ cbdg_status cbdg_build_ensemble(const cbdg_lattice_desc *descs, int32_t n, cbdg_
   };
   if (e->Lmax > 128) return bail(efail(CBDG_ERR_UNSUPPORTED, "ensemble lattices must have Lx <= 128"));
   e->smem = ens_smem(e->Lmax);
-  if (e->smem > 200 * 1024) return bail(efail(CBDG_ERR_UNSUPPORTED, "ensemble lattice rows too long"));
+  if (e->smem > kEnsDynLimit) return bail(efail(CBDG_ERR_UNSUPPORTED, "ensemble lattice rows too long"));
+  e->multi = ens_multi_smem(e->Lmax) <= kEnsDynLimit ? 1 : 0;
+  if (e->multi) e->smem = std::max(e->smem, ens_multi_smem(e->Lmax));
   // items: (sample, slab) ordered by sample size, largest first
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);

@@ -13,265 +13,43 @@
 // 4 vector streams per K steps instead of 3 per step.  Rows -1 and Ly do not
 // exist (open edges), which is what makes the single wavefront possible.
 //
-// Staging uses TMA bulk copies on mbarriers with bounded waits, as in step.cu.
-// Slab-blocked layout, electron rows then hole rows in each lattice row.
+// The pass itself (register windows, TMA staging, bounded waits) is
+// mp::multi_pass in multi_pass.cuh; this file launches it once per slab and
+// reduces each level's column sums across the CTA in FP64.
 #include <algorithm>
 
-#include "internal.h"
+#include "multi_pass.cuh"
 
 namespace cbdg {
 namespace {
 
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void bulk_load(unsigned dst, const void *src, unsigned bytes, unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit_ns) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  for (unsigned it = 0;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > limit_ns) return false;
-  }
-}
+using mp::Kahan;
+constexpr int kThreads = mp::kPassThreads;
 
-// Kahan accumulation of a1*b1 + a2*b2 with the products and the compensation
-// fused into two FMAs (the same arithmetic as the one-step kernel).
-struct Kahan {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add2(float a1, float b1, float a2, float b2) {
-    const float y = __fmaf_rn(a1, b1, __fmaf_rn(a2, b2, -c));
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
-__device__ __forceinline__ float fc(const float4 &v, int j) { return reinterpret_cast<const float *>(&v)[j]; }
-
-constexpr int kThreads = 256;
-
-__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-
-// Thread (x, column quad) is fixed for the whole sweep, so the rows a thread
-// needs from the level below at its own x (centre, above, below, and the row
-// two levels down) are the rows it computed itself: they stay in registers, in
-// a three-row window per level (levels 0 .. K-1), indexed by row mod 3.  Only
-// the x +- 1 neighbours come from shared memory, where each level keeps its
-// two most recent rows.  Level l at wavefront g computes row g - l + 1, whose
-// x-neighbour row of level l - 1 was written at wavefront g - 1, so one CTA
-// barrier per wavefront orders all shared-memory traffic.  The wavefront loop
-// is unrolled by three so that every window index is a compile-time constant.
 template <int W, int K, int D, int MAXX>
 __global__ void __launch_bounds__(kThreads, 1) step_multi_kernel(StepArgs a) {
-  constexpr int VEC = 4, QUADS = W / VEC, XSLOTS = kThreads / QUADS;
-  constexpr int RS = 3 + D;      // j_n / j_{n-1} staging ring: rows g-1 .. g+2+D
-  constexpr int AS = K + 2 + D;  // parameter ring: rows g-K+1 .. g+2+D
-  constexpr int NB = RS;         // one mbarrier per staged row
-  static_assert(W % VEC == 0 && kThreads % QUADS == 0 && K >= 2, "bad shape");
-
+  using Sh = mp::PassShape<W, K, D>;
+  constexpr int VEC = Sh::VEC, XSLOTS = Sh::XSLOTS, NB = Sh::NB;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bars[NB];
   __shared__ int abort_flag;
-  const int Lx = a.Lx, Ly = a.Ly;
-  const int rowel = 2 * Lx * W;
-  const int pel = Lx * kParamStride;
-  float *sq = reinterpret_cast<float *>(smem_raw);  // [RS][rowel]  j_n
-  float *sp = sq + RS * rowel;                       // [RS][rowel]  j_{n-1}
-  float *sl = sp + RS * rowel;                       // [K-1][2][rowel] levels 1..K-1
-  float *sa = sl + (K - 1) * 2 * rowel;              // [AS][pel]
-
   const int t = threadIdx.x;
-  const int q = t % QUADS, xs = t / QUADS;
-  const size_t slab = static_cast<size_t>(blockIdx.x) * (static_cast<size_t>(2) * Lx * Ly * W);
-  float *P = static_cast<float *>(a.prev) + slab;
-  float *Q = static_cast<float *>(const_cast<void *>(a.cur)) + slab;
-  const float *par = static_cast<const float *>(a.params);
-  const unsigned row_bytes = rowel * 4u, par_bytes = pel * 4u;
-  const unsigned long long wait_ns = a.wait_ns;
-
+  const int q = t % Sh::QUADS, xs = t / Sh::QUADS;
+  const size_t slab = static_cast<size_t>(blockIdx.x) * (static_cast<size_t>(2) * a.Lx * a.Ly * W);
   if (t == 0) {
     for (int k = 0; k < NB; ++k)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bars[k])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mp::smem_addr(&bars[k])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     abort_flag = 0;
   }
   __syncthreads();
-
-  // load l: rows l of j_n and j_{n-1} and the parameters of lattice row l
-  auto issue = [&](int l) {
-    const unsigned bar = smem_addr(&bars[l % NB]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
-                 "r"(2 * row_bytes + par_bytes + (l == 0 ? a.stall_tx : 0u))
-                 : "memory");
-    bulk_load(smem_addr(sq + (l % RS) * rowel), Q + static_cast<size_t>(l) * rowel, row_bytes, bar);
-    bulk_load(smem_addr(sp + (l % RS) * rowel), P + static_cast<size_t>(l) * rowel, row_bytes, bar);
-    bulk_load(smem_addr(sa + (l % AS) * pel), par + static_cast<size_t>(l) * pel, par_bytes, bar);
-  };
-  int issued = min(Ly, 2 + D);
-  if (t == 0)
-    for (int l = 0; l < issued; ++l) issue(l);
-
-  const int hb = Lx * W;
-  const int off = q * VEC;
-  float4 wu[K][3][MAXX], wv[K][3][MAXX];
-#pragma unroll
-  for (int l = 0; l < K; ++l)
-#pragma unroll
-    for (int s = 0; s < 3; ++s)
-#pragma unroll
-      for (int k = 0; k < MAXX; ++k) wu[l][s][k] = wv[l][s][k] = zero4();
   Kahan accA[K][VEC], accB[K][VEC], accC[K][VEC];
-
-  int waited = 0;
-  bool ok = mbar_wait(smem_addr(&bars[0]), 0u, wait_ns);
-  if (ok) {
-    waited = 1;
-#pragma unroll
-    for (int k = 0; k < MAXX; ++k) {
-      const int x = xs + k * XSLOTS;
-      if (x < Lx) {
-        wu[0][0][k] = lds4(sq + x * W + off);
-        wv[0][0][k] = lds4(sq + hb + x * W + off);
-      }
-    }
-  }
-  const int G = Ly + K - 1;
-  bool stop = false;
-  for (int g0 = 0; g0 < G && !stop; g0 += 3) {
-#pragma unroll
-    for (int ph = 0; ph < 3; ++ph) {
-      const int g = g0 + ph;
-      if (stop || g >= G) break;
-      // rows up to g + 1 must have landed
-      for (; ok && waited <= min(g + 1, Ly - 1); ++waited)
-        if (!mbar_wait(smem_addr(&bars[waited % NB]), static_cast<unsigned>((waited / NB) & 1), wait_ns))
-          ok = false;
-      if (!ok) abort_flag = 1;
-      __syncthreads();
-      if (abort_flag) {
-        stop = true;
-        break;
-      }
-      // the slot of row g - 1 is free: every read of it happened before the barrier
-      if (g + 2 + D < Ly) {
-        if (t == 0) issue(g + 2 + D);
-        issued = g + 3 + D;
-      }
-      // level 0 "computes" row g + 1: its centre enters the window
-#pragma unroll
-      for (int k = 0; k < MAXX; ++k) {
-        const int x = xs + k * XSLOTS;
-        float4 nu = zero4(), nv = zero4();
-        if (x < Lx && g + 1 < Ly) {
-          const float *src = sq + ((g + 1) % RS) * rowel;
-          nu = lds4(src + x * W + off);
-          nv = lds4(src + hb + x * W + off);
-        }
-        wu[0][(ph + 1) % 3][k] = nu;
-        wv[0][(ph + 1) % 3][k] = nv;
-      }
-#pragma unroll
-      for (int lv = 1; lv <= K; ++lv) {
-        const int r = g - lv + 1;
-        const int sm = (ph - lv + 6) % 3, sc = (ph - lv + 7) % 3, su = (ph - lv + 8) % 3;
-        if (r >= 0 && r < Ly) {
-          const float *nb = lv == 1 ? sq + (r % RS) * rowel : sl + ((lv - 2) * 2 + (r & 1)) * rowel;
-          const float *po = sp + (r % RS) * rowel;
-          const float *pc = sa + (r % AS) * pel;
-          float *dl = lv < K ? sl + ((lv - 1) * 2 + (r & 1)) * rowel : nullptr;
-#pragma unroll
-          for (int k = 0; k < MAXX; ++k) {
-            const int x = xs + k * XSLOTS;
-            if (x < Lx) {
-              const int xl = (x == 0) ? Lx - 1 : x - 1;
-              const int xr = (x == Lx - 1) ? 0 : x + 1;
-              const float4 u = wu[lv - 1][sc][k], v = wv[lv - 1][sc][k];
-              const float4 uu = wu[lv - 1][su][k], vu = wv[lv - 1][su][k];
-              const float4 ud = wu[lv - 1][sm][k], vd = wv[lv - 1][sm][k];
-              const float4 ur = lds4(nb + xr * W + off), vr = lds4(nb + hb + xr * W + off);
-              const float4 ul = lds4(nb + xl * W + off), vl = lds4(nb + hb + xl * W + off);
-              float4 uo, vo;
-              if (lv == 1) {
-                uo = lds4(po + x * W + off);
-                vo = lds4(po + hb + x * W + off);
-              } else {
-                uo = wu[lv >= 2 ? lv - 2 : 0][sc][k];
-                vo = wv[lv >= 2 ? lv - 2 : 0][sc][k];
-              }
-              const float4 pa = lds4(pc + x * kParamStride), pb = lds4(pc + x * kParamStride + 4);
-              const float e = pa.x, d = pa.y, t0 = pa.z, t1 = pa.w, t2 = pb.x, t3 = pb.y;
-              float4 un, vn;
-#pragma unroll
-              for (int j = 0; j < VEC; ++j) {
-                const float uj = fc(u, j), vj = fc(v, j);
-                const float unj = __fmaf_rn(e, uj, __fmaf_rn(d, vj, -__fmaf_rn(t3, fc(ud, j), __fmaf_rn(t2, fc(uu, j),
-                                      __fmaf_rn(t1, fc(ul, j), __fmaf_rn(t0, fc(ur, j), fc(uo, j)))))));
-                const float vnj = __fmaf_rn(d, uj, __fmaf_rn(-e, vj, __fmaf_rn(t3, fc(vd, j), __fmaf_rn(t2, fc(vu, j),
-                                      __fmaf_rn(t1, fc(vl, j), __fmaf_rn(t0, fc(vr, j), -fc(vo, j)))))));
-                reinterpret_cast<float *>(&un)[j] = unj;
-                reinterpret_cast<float *>(&vn)[j] = vnj;
-                accA[lv - 1][j].add2(uj, uj, vj, vj);
-                accB[lv - 1][j].add2(unj, uj, vnj, vj);
-                accC[lv - 1][j].add2(unj, vj, -vnj, uj);
-              }
-              if (lv < K) {
-                wu[lv < K ? lv : 0][sc][k] = un;
-                wv[lv < K ? lv : 0][sc][k] = vn;
-                *reinterpret_cast<float4 *>(dl + x * W + off) = un;
-                *reinterpret_cast<float4 *>(dl + hb + x * W + off) = vn;
-              }
-              // levels K-1 and K become the new (P, Q); their HBM rows are no longer read
-              if (lv == K - 1) {
-                float *o = P + static_cast<size_t>(r) * rowel;
-                __stcs(reinterpret_cast<float4 *>(o + x * W + off), un);
-                __stcs(reinterpret_cast<float4 *>(o + hb + x * W + off), vn);
-              } else if (lv == K) {
-                float *o = Q + static_cast<size_t>(r) * rowel;
-                __stcs(reinterpret_cast<float4 *>(o + x * W + off), un);
-                __stcs(reinterpret_cast<float4 *>(o + hb + x * W + off), vn);
-              }
-            }
-          }
-        } else if (lv < K) {
-          // rows outside [0, Ly) are zero (open edges)
-#pragma unroll
-          for (int k = 0; k < MAXX; ++k) {
-            wu[lv < K ? lv : 0][sc][k] = zero4();
-            wv[lv < K ? lv : 0][sc][k] = zero4();
-          }
-        }
-      }
-    }
-  }
-  if (abort_flag) {
-    if (t == 0) {
-      atomicOr(a.flags, kFlagTimeout);
-      for (int l = waited; l < issued; ++l)
-        if (!mbar_wait(smem_addr(&bars[l % NB]), static_cast<unsigned>((l / NB) & 1), wait_ns)) break;
-    }
+  const bool ok = mp::multi_pass<W, K, D, MAXX>(
+      static_cast<float *>(a.prev) + slab, static_cast<float *>(const_cast<void *>(a.cur)) + slab,
+      static_cast<const float *>(a.params), a.Lx, a.Ly, reinterpret_cast<float *>(smem_raw), bars, 0,
+      a.wait_ns, a.stall_tx, &abort_flag, accA, accB, accC);
+  if (!ok) {
+    if (t == 0) atomicOr(a.flags, kFlagTimeout);
     return;
   }
   __syncthreads();
@@ -300,9 +78,7 @@ constexpr int kMaxDynSmem = 227 * 1024 - 1024;
 
 template <int W, int K, int D>
 size_t smem_bytes(int Lx) {
-  const size_t rowel = static_cast<size_t>(2) * Lx * W;
-  const size_t pel = static_cast<size_t>(Lx) * kParamStride;
-  const size_t ring = (2 * (3 + D) + 2 * (K - 1)) * rowel + (K + 2 + D) * pel;
+  const size_t ring = mp::PassShape<W, K, D>::smem_floats(Lx);
   const size_t red = static_cast<size_t>(3) * (kThreads / (W / 4)) * W * sizeof(double) / sizeof(float);
   return std::max(ring, red) * sizeof(float);
 }
