@@ -39,15 +39,23 @@ L, M, SEED = 128, 1024, 1001
 FP64_FLOPS_PER_ELEMENT_STEP = 20.0  # stencil 12 + moment products 8 (FMA = 2 flops)
 
 
-def recorded_traffic(source="step.cu", pattern="step_real_kernel_fp32_*.md"):
+def kernel_source_digest(sources):
+    """First 16 hex digits of the SHA-256 of the kernel's source files, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for src in sources:
+        with open(os.path.join(ROOT, "paper_1007_1609_gb300/csrc", src), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(sources=("step.cu",), pattern="step_real_kernel_fp32_*.md"):
     """DRAM bytes per launch of a recursion kernel from the committed ncu
     summary, or None when the kernel source changed since those counters were
     taken."""
     import glob
-    import hashlib
     import re
-    with open(os.path.join(ROOT, "paper_1007_1609_gb300/csrc", source), "rb") as fh:
-        digest = hashlib.sha256(fh.read()).hexdigest()[:16]
+    digest = kernel_source_digest(sources)
     for path in glob.glob(os.path.join(ROOT, "profiles", pattern)):
         text = open(path).read()
         m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+kernel_source_sha256_16:\s*([0-9a-f]+)", text)
@@ -295,7 +303,7 @@ def run_gb300(args):
         hbm, peak_kind = peaks()
         achieved = (step_bytes / step_n) / (step_ms / step_n / 1e3) / 1e9 if step_n else None
         if k_used >= 2:
-            traffic, traffic_src = recorded_traffic("step_multi.cu", "step_multi_kernel_fp32_*.md")
+            traffic, traffic_src = recorded_traffic(("step_multi.cu", "multi_pass.cuh"), "step_multi_kernel_fp32_*.md")
             kernel = (f"step_multi_kernel: FP32, {k_used} recursion steps per pass over the vectors "
                       "(reads j_(n-1), j_n; writes the last two), moment products fused; the "
                       "leftover odd step of each iteration runs step_real_kernel")
