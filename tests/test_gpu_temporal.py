@@ -105,3 +105,21 @@ def test_full_size_disordered_128_sampled(steps, slab):
     assert max_abs(d[sample], od) < TOL_DELTA, max_abs(d[sample], od)
     assert max_abs(n[sample], on) < TOL_DELTA, max_abs(n[sample], on)
     assert np.all(np.abs(d) <= 0.5 * p.coupling + 1e-9)
+
+
+def test_lost_copy_times_out_in_the_two_step_kernel():
+    """Failure detection without a fault in the two-step pass: the stall hook
+    makes the first staged row of every CTA expect 16 bytes that never
+    arrive; the bounded wait runs out (20 ms), the call reports
+    CBDG_ERR_CUDA, and the same lattice then computes correct moments."""
+    p = rect(24, 16, 40, seed=51, periodic=0)
+    sites = np.arange(p.N, dtype=np.int32)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=2, wait_limit_ms=20, test_stall_copy=1)
+    with pytest.raises(cbdg.CbdgError) as ei:
+        lat.moments(sites, p.M)
+    assert ei.value.status == cbdg.CBDG_ERR_CUDA and "gave up waiting" in str(ei.value)
+    lat.set_option(cbdg.CBDG_OPT_TEST_STALL_COPY, 0)
+    (ee, eh), launches = recursion_launches(lat, sites, p.M)
+    assert launches == 19 // 2 + 19 % 2  # the two-step kernel ran
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, p.M)
+    assert max_abs(ee, oee) < TOL_MOM and max_abs(eh, oeh) < TOL_MOM
