@@ -188,7 +188,10 @@ cbdg_status cbdg_order_parameter_backward(cbdg_lattice *lat, double T, int32_t M
                                           const cbdg_complex *dL_ddelta_out, double *dL_deps,
                                           double *dL_dhop, double *dL_ddelta_in);
 
-/* Copies the lattice's current Delta ([N] or [N*4]) out, or replaces it. */
+/* Copies the lattice's current Delta ([N] or [N*4]) out, or replaces it.  A
+ * new bond Delta must be symmetric (Delta_{j,d^1} == Delta_{i,d}) and 0
+ * across open edges, like delta0 (the recursion reads each bond from one end);
+ * otherwise INVALID_ARG. */
 cbdg_status cbdg_get_delta(cbdg_lattice *lat, cbdg_complex *delta);
 cbdg_status cbdg_set_delta(cbdg_lattice *lat, const cbdg_complex *delta);
 

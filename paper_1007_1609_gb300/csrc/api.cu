@@ -1214,6 +1214,28 @@ cbdg_status cbdg_set_delta(cbdg_lattice *L, const cbdg_complex *delta) {
     if (!finite_c(z)) return fail(CBDG_ERR_INVALID_ARG, "delta is not finite");
     if (!L->cplx && z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex delta on a real lattice");
   }
+  if (L->pairing == CBDG_BOND_V) {
+    // the recursion reads each bond from one end only: Delta_ij must equal Delta_ji
+    cbdg_lattice_desc d{};
+    d.Lx = L->Lx;
+    d.Ly = L->Ly;
+    d.periodic_x = L->px;
+    d.periodic_y = L->py;
+    for (int i = 0; i < L->N; ++i)
+      for (int dir = 0; dir < 4; ++dir) {
+        const cbdg_complex v = h[static_cast<size_t>(i) * 4 + dir];
+        const int j = host_neighbour(&d, i, dir);
+        if (j < 0) {
+          if (v.re != 0.0 || v.im != 0.0)
+            return fail(CBDG_ERR_INVALID_ARG, "delta[%d][%d] crosses an open edge and must be 0", i, dir);
+          continue;
+        }
+        const cbdg_complex w = h[static_cast<size_t>(j) * 4 + (dir ^ 1)];
+        const double tol = 1e-12 * (1.0 + hypot(v.re, v.im));
+        if (fabs(w.re - v.re) > tol || fabs(w.im - v.im) > tol)
+          return fail(CBDG_ERR_INVALID_ARG, "bond pairing is not symmetric at site %d dir %d", i, dir);
+      }
+  }
   CK(cudaMemcpyAsync(L->delta.p, h.data(), static_cast<size_t>(L->nd) * sizeof(double2),
                      cudaMemcpyHostToDevice, L->stream));
   CK(cudaStreamSynchronize(L->stream));

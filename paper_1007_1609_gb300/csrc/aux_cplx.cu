@@ -44,14 +44,18 @@ __global__ void params_cplx_kernel(int N, int Lx, int n_dirs, int pairing, const
   if (pairing == 0) {
     f(kCpDelta, s2 * delta[i].x, s2 * delta[i].y);
   } else {
-    for (int d = 0; d < 4; ++d) {
-      const double2 b = delta[static_cast<size_t>(i) * 4 + d];
-      f(kCpBond + d, s2 * b.x, s2 * b.y);
-    }
+    // forward bonds +x (direction 0) and +y (direction 2)
+    const double2 bx = delta[static_cast<size_t>(i) * 4 + 0], by = delta[static_cast<size_t>(i) * 4 + 2];
+    f(kCpBond + 0, s2 * bx.x, s2 * bx.y);
+    f(kCpBond + 1, s2 * by.x, s2 * by.y);
   }
-  for (int d = 0; d < n_dirs; ++d) {
-    const double2 t = hop[static_cast<size_t>(i) * n_dirs + d];
-    f(kCpHop + d, s2 * t.x, s2 * t.y);
+  // forward hoppings +x, +y (directions 0, 2) and, with next-nearest
+  // neighbours, +x+y, -x+y (directions 4, 7)
+  const int fwd[4] = {0, 2, 4, 7};
+  for (int k = 0; k < 4; ++k) {
+    if (fwd[k] >= n_dirs) continue;
+    const double2 t = hop[static_cast<size_t>(i) * n_dirs + fwd[k]];
+    f(kCpHop + k, s2 * t.x, s2 * t.y);
   }
 }
 

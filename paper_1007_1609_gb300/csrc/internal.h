@@ -12,17 +12,20 @@ namespace cbdg {
 // application yields 2 H~ j:
 //   [0] 2 (eps - mu)/a   [1] 2 Delta/a   [2..5] 2 t_{s,d}/a (d = 0..3)   [6,7] 0
 constexpr int kParamStride = 8;
-// General (complex / next-nearest / bond) parameters: 14 complex fields per
+// General (complex / next-nearest / bond) parameters: 8 complex fields per
 // site, stored field-major inside each lattice row, field f of site (x, y)
 // (real, imaginary) at
 //   params[((y * kCplxFields + f) * Lx + x) * 2 + {0, 1}]
 // so that a lattice row is one contiguous block of kCplxParamStride * Lx
-// scalars and threads on consecutive x read consecutive pairs.  Fields:
-//   [0] (2(eps-mu)/a, 0)  [1] 2 Delta_i/a  [2+d] 2 t_{i,d}/a (d < 8)
-//   [10+d] 2 Delta_{i,d}/a (d < 4)
-constexpr int kCplxFields = 14;
+// scalars and threads on consecutive x read consecutive pairs.  Only the
+// forward half of the Hermitian hoppings and of the symmetric bond pairing is
+// stored (the backward half is the neighbour's, see step_cplx.cu).  Fields:
+//   [0] (2(eps-mu)/a, 0)  [1] 2 Delta_i/a
+//   [2..5] 2 t_{i,d}/a for d = +x, +y, +x+y, -x+y
+//   [6, 7] 2 Delta_{i,d}/a for d = +x, +y
+constexpr int kCplxFields = 8;
 constexpr int kCplxParamStride = 2 * kCplxFields;
-constexpr int kCpE = 0, kCpDelta = 1, kCpHop = 2, kCpBond = 10;
+constexpr int kCpE = 0, kCpDelta = 1, kCpHop = 2, kCpBond = 6;
 
 // Arguments of one recursion step j_{n+1} = 2 H~ j_n - j_{n-1} over a block
 // of ld start vectors.  Vectors use the slab-blocked layout: column slab

@@ -9,11 +9,18 @@
 //
 // Vectors are complex (float2 / double2) in the slab-blocked layout of the
 // real kernel (rows electron-then-hole inside each lattice row), staged by
-// TMA bulk copies on mbarriers with bounded waits.  Parameters (14 complex
-// fields per site, field-major inside each lattice row) stay resident in L2: the FP32
-// kernel stages each row with the j_{n-1} row, the FP64 kernel reads them
+// TMA bulk copies on mbarriers with bounded waits.  Parameters (8 complex
+// fields per site, field-major inside each lattice row) stay resident in L2:
+// the FP32 kernel stages each row with the j_n row of the same lattice row
+// (so rows y - 1 and y are on chip together), the FP64 kernel reads them
 // through the read-only cache; either way threads on consecutive x read
-// consecutive words.
+// consecutive pairs.  H is Hermitian and the bond pairing symmetric, so a
+// site stores only its forward hoppings (+x, +y, +x+y, -x+y) and bonds
+// (+x, +y); the backward ones are those of the left, lower and diagonal
+// neighbours, conjugated for the hoppings:
+//   t(i, -x) = conj t(i-x, +x),  t(i, -y) = conj t(i-y, +y),
+//   t(i, -x-y) = conj t(i-x-y, +x+y),  t(i, +x-y) = conj t(i+x-y, -x+y),
+//   D(i, -x) = D(i-x, +x),  D(i, -y) = D(i-y, +y).
 //
 // With on-site pairing the doubling identities apply and the kernel fuses
 // four column sums (|j_n|^2, Re<j_{n+1}|j_n>, and the complex symplectic sum
@@ -155,8 +162,8 @@ __device__ __forceinline__ Cx<S> pcx(const S *p, int k, int Lx) {
 
 template <typename S, int W, int NT, int MAXX, int D, bool NNN, bool BOND, bool SUMS>
 __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
-  // FP32: parameter rows ride the TMA pipeline with j_{n-1}; FP64 (bound by
-  // its arithmetic) reads them through the read-only cache.
+  // FP32: parameter rows ride the TMA pipeline with j_n; FP64 (bound by its
+  // arithmetic) reads them through the read-only cache.
   constexpr bool PSTAGE = sizeof(S) == 4;
   using V = typename CVec<S>::T;
   constexpr int VC = CVec<S>::N;       // complex elements per 16-byte vector
@@ -174,7 +181,7 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
   S *sj = reinterpret_cast<S *>(smem_raw);
   S *so = sj + JS * rowel;
   const int pel = Lx * kCplxParamStride;  // parameter scalars of one lattice row
-  S *sp = so + OS * rowel;                  // [OS][pel] when PSTAGE
+  S *sp = so + OS * rowel;                  // [JS][pel] when PSTAGE, slot as the j_n row
 
   const int t = threadIdx.x;
   const int q = t % QUADS;
@@ -202,14 +209,13 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
     const int r = k - 1;
     const bool with_old = (r >= 0 && r < rows);
     const unsigned bar = smem_addr(&bars[k % JS]);
-    mbar_expect_tx(bar, row_bytes + (with_old ? row_bytes + par_bytes : 0u) + (k == 0 ? a.stall_tx : 0u));
+    mbar_expect_tx(bar, row_bytes + par_bytes + (with_old ? row_bytes : 0u) + (k == 0 ? a.stall_tx : 0u));
     bulk_load(smem_addr(sj + (k % JS) * rowel), cur + static_cast<size_t>(y) * rowel, row_bytes, bar);
-    if (with_old) {
+    if (PSTAGE)
+      bulk_load(smem_addr(sp + (k % JS) * pel), par + static_cast<size_t>(y) * pel, par_bytes, bar);
+    if (with_old)
       bulk_load(smem_addr(so + (r % OS) * rowel), prev + static_cast<size_t>(y0 + r) * rowel,
                 row_bytes, bar);
-      if (PSTAGE)
-        bulk_load(smem_addr(sp + (r % OS) * pel), par + static_cast<size_t>(y0 + r) * pel, par_bytes, bar);
-    }
   };
   int issued = min(D + 2, rows + 2);
   if (t == 0)
@@ -246,9 +252,35 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
           auto ld = [&](const S *row, int xx, int part) {
             return *reinterpret_cast<const V *>(row + part * hb + xx * W * 2 + off);
           };
-          const S *pp = PSTAGE ? sp + (i % OS) * pel + 2 * x : par + static_cast<size_t>(y) * pel + 2 * x;
+          // parameter rows y (own, left neighbour) and y - 1 (lower neighbours)
+          const S *py0 = PSTAGE ? sp + ((i + 1) % JS) * pel : par + static_cast<size_t>(y) * pel;
+          const S *py1 = PSTAGE ? sp + (i % JS) * pel
+                                : par + static_cast<size_t>(y == 0 ? Ly - 1 : y - 1) * pel;
+          const S *pp = py0 + 2 * x;
           const S e = pcx<S, !PSTAGE>(pp, kCpE, Lx).re;
           const Cx<S> dl = pcx<S, !PSTAGE>(pp, kCpDelta, Lx);
+          auto conj_ = [](Cx<S> z) { return Cx<S>{z.re, -z.im}; };
+          // hopping of direction dd: forward from this site, backward from the neighbour
+          auto hop_of = [&](int dd) -> Cx<S> {
+            switch (dd) {
+              case 0: return pcx<S, !PSTAGE>(pp, kCpHop + 0, Lx);
+              case 1: return conj_(pcx<S, !PSTAGE>(py0 + 2 * xl, kCpHop + 0, Lx));
+              case 2: return pcx<S, !PSTAGE>(pp, kCpHop + 1, Lx);
+              case 3: return conj_(pcx<S, !PSTAGE>(py1 + 2 * x, kCpHop + 1, Lx));
+              case 4: return pcx<S, !PSTAGE>(pp, kCpHop + 2, Lx);
+              case 5: return conj_(pcx<S, !PSTAGE>(py1 + 2 * xl, kCpHop + 2, Lx));
+              case 6: return conj_(pcx<S, !PSTAGE>(py1 + 2 * xr, kCpHop + 3, Lx));
+              default: return pcx<S, !PSTAGE>(pp, kCpHop + 3, Lx);
+            }
+          };
+          auto bond_of = [&](int dd) -> Cx<S> {
+            switch (dd) {
+              case 0: return pcx<S, !PSTAGE>(pp, kCpBond + 0, Lx);
+              case 1: return pcx<S, !PSTAGE>(py0 + 2 * xl, kCpBond + 0, Lx);
+              case 2: return pcx<S, !PSTAGE>(pp, kCpBond + 1, Lx);
+              default: return pcx<S, !PSTAGE>(py1 + 2 * x, kCpBond + 1, Lx);
+            }
+          };
           // neighbour rows/columns per direction 0:+x 1:-x 2:+y 3:-y 4:+x+y 5:-x-y 6:+x-y 7:-x+y
           const S *nrow[8] = {rc, rc, rp, rm, rp, rm, rm, rp};
           const int ncol[8] = {xr, xl, x, x, xr, xl, xr, xl};
@@ -266,8 +298,8 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
 #pragma unroll
           for (int dd = 0; dd < (NNN ? 8 : 4); ++dd) {
             const V ud = ld(nrow[dd], ncol[dd], 0), vd = ld(nrow[dd], ncol[dd], 1);
-            const Cx<S> td = pcx<S, !PSTAGE>(pp, kCpHop + dd, Lx);
-            const Cx<S> bd = (BOND && dd < 4) ? pcx<S, !PSTAGE>(pp, kCpBond + dd, Lx) : Cx<S>{0, 0};
+            const Cx<S> td = hop_of(dd);
+            const Cx<S> bd = (BOND && dd < 4) ? bond_of(dd) : Cx<S>{0, 0};
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
               Cx<S> hu = cget<V, S>(un, j), hv = cget<V, S>(vn, j);
@@ -341,7 +373,7 @@ size_t smem_bytes(int Lx) {
   constexpr int XSLOTS = kThreads / QUADS;
   const size_t rowel = static_cast<size_t>(2) * Lx * W * 2;
   const size_t pel = sizeof(S) == 4 ? static_cast<size_t>(Lx) * kCplxParamStride : 0;
-  const size_t ring = (((3 + D) + (2 + D)) * rowel + (2 + D) * pel) * sizeof(S);
+  const size_t ring = (((3 + D) + (2 + D)) * rowel + (3 + D) * pel) * sizeof(S);
   const size_t red = static_cast<size_t>(4) * XSLOTS * W * sizeof(double);
   return std::max(ring, red);
 }
