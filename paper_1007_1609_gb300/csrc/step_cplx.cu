@@ -127,6 +127,22 @@ __device__ __forceinline__ Cx<S> csub(Cx<S> a, Cx<S> b) {
   return {a.re - b.re, a.im - b.im};
 }
 
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+// acc + a * b and acc + conj(a) * b, four FMAs each
+template <typename S>
+__device__ __forceinline__ Cx<S> cmac(Cx<S> acc, Cx<S> a, Cx<S> b) {
+  return {fma_rn(a.re, b.re, fma_rn(-a.im, b.im, acc.re)), fma_rn(a.re, b.im, fma_rn(a.im, b.re, acc.im))};
+}
+template <typename S>
+__device__ __forceinline__ Cx<S> cmacc(Cx<S> acc, Cx<S> a, Cx<S> b) {
+  return {fma_rn(a.re, b.re, fma_rn(a.im, b.im, acc.re)), fma_rn(a.re, b.im, fma_rn(-a.im, b.re, acc.im))};
+}
+template <typename S>
+__device__ __forceinline__ Cx<S> cneg(Cx<S> a) {
+  return {-a.re, -a.im};
+}
+
 template <typename V, typename S>
 __device__ __forceinline__ Cx<S> cget(const V &v, int j) {
   const S *p = reinterpret_cast<const S *>(&v);
@@ -287,27 +303,31 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
           const V u = ld(rc, x, 0), v = ld(rc, x, 1);
           const V uo = ld(ro, x, 0), vo = ld(ro, x, 1);
           V un, vn;
+          // start from -j_{n-1} and the on-site terms:
+          //   u' = e u + D v - u_old,  v' = conj(D) u - e v - v_old
 #pragma unroll
           for (int j = 0; j < VC; ++j) {
             const Cx<S> uj = cget<V, S>(u, j), vj = cget<V, S>(v, j);
-            Cx<S> hu = cadd(Cx<S>{e * uj.re, e * uj.im}, cmul(dl, vj));
-            Cx<S> hv = csub(cmulc(dl, uj), Cx<S>{e * vj.re, e * vj.im});
+            const Cx<S> uoj = cget<V, S>(uo, j), voj = cget<V, S>(vo, j);
+            const Cx<S> hu = cmac(Cx<S>{fma_rn(e, uj.re, -uoj.re), fma_rn(e, uj.im, -uoj.im)}, dl, vj);
+            const Cx<S> hv = cmacc(Cx<S>{fma_rn(-e, vj.re, -voj.re), fma_rn(-e, vj.im, -voj.im)}, dl, uj);
             cset<V, S>(un, j, hu);
             cset<V, S>(vn, j, hv);
           }
 #pragma unroll
           for (int dd = 0; dd < (NNN ? 8 : 4); ++dd) {
             const V ud = ld(nrow[dd], ncol[dd], 0), vd = ld(nrow[dd], ncol[dd], 1);
-            const Cx<S> td = hop_of(dd);
+            const Cx<S> td = hop_of(dd), ntd = cneg(td);
             const Cx<S> bd = (BOND && dd < 4) ? bond_of(dd) : Cx<S>{0, 0};
 #pragma unroll
             for (int j = 0; j < VC; ++j) {
               Cx<S> hu = cget<V, S>(un, j), hv = cget<V, S>(vn, j);
-              hu = csub(hu, cmul(td, cget<V, S>(ud, j)));
-              hv = cadd(hv, cmulc(td, cget<V, S>(vd, j)));
+              // u' -= t_d u_d, v' += conj(t_d) v_d; bond pairing: u' += B_d v_d, v' += conj(B_d) u_d
+              hu = cmac(hu, ntd, cget<V, S>(ud, j));
+              hv = cmacc(hv, td, cget<V, S>(vd, j));
               if (BOND && dd < 4) {
-                hu = cadd(hu, cmul(bd, cget<V, S>(vd, j)));
-                hv = cadd(hv, cmulc(bd, cget<V, S>(ud, j)));
+                hu = cmac(hu, bd, cget<V, S>(vd, j));
+                hv = cmacc(hv, bd, cget<V, S>(ud, j));
               }
               cset<V, S>(un, j, hu);
               cset<V, S>(vn, j, hv);
@@ -315,10 +335,8 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
           }
 #pragma unroll
           for (int j = 0; j < VC; ++j) {
-            const Cx<S> unj = csub(cget<V, S>(un, j), cget<V, S>(uo, j));
-            const Cx<S> vnj = csub(cget<V, S>(vn, j), cget<V, S>(vo, j));
-            cset<V, S>(un, j, unj);
-            cset<V, S>(vn, j, vnj);
+            const Cx<S> unj = cget<V, S>(un, j);
+            const Cx<S> vnj = cget<V, S>(vn, j);
             if (SUMS) {
               const Cx<S> uj = cget<V, S>(u, j), vj = cget<V, S>(v, j);
               accA[j].add(uj.re * uj.re + uj.im * uj.im + vj.re * vj.re + vj.im * vj.im);
