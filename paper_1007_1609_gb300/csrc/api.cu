@@ -262,7 +262,9 @@ struct TuneKey {
 };
 struct TuneVal {
   int W, D, split;
-  float ms;
+  float ms;      // per recursion step
+  int K = 1;     // recursion steps per pass (temporal blocking); 1: the one-step kernel
+  int Dm = 0;    // depth of the multi-step pass when K >= 2
 };
 std::mutex g_tune_mutex;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -342,6 +344,54 @@ cbdg_status autotune(cbdg_lattice *L, int mode, int n_sites, TuneVal *out) {
       }
     }
   }
+  // several steps per pass (real FP32, open y edges): compare the time per step
+  if (real && L->precision == CBDG_FP32_MIXED && !L->py) {
+    for (int W : {8, 16}) {
+      if (ld % W) continue;
+      for (int K = 2; K <= 4; ++K) {
+        for (int D = 1; D <= 2; ++D) {
+          StepConfig mcfg;
+          int Kt = 0;
+          if (!plan_step_multi(L->Lx, L->Ly, static_cast<int>(ld), W, K, D, &mcfg, &Kt) || mcfg.depth != D) continue;
+          // the one-step kernel takes any leftover step at the same slab width
+          StepConfig rcfg;
+          if (!plan_step_real(L->precision, L->Lx, L->Ly, static_cast<int>(ld), W, 0, 0, &rcfg) || rcfg.slab_w != W)
+            continue;
+          CK(L->partials.ensure(static_cast<size_t>(K) * 3 * ld * sizeof(double)));
+          StepArgs a;
+          a.cur = L->vec1.p;
+          a.prev = L->vec0.p;
+          a.params = L->params.p;
+          a.partials = L->partials.as<double>();
+          a.flags = L->flags.as<unsigned int>();
+          a.wait_ns = static_cast<unsigned long long>(L->wait_ms) * 1000000ull;
+          a.stall_tx = 0;
+          a.Lx = L->Lx;
+          a.Ly = L->Ly;
+          a.ld = static_cast<int>(ld);
+          a.rows_per_cta = L->Ly;
+          CK(launch_step_multi(a, mcfg, K, L->stream));
+          float t_best = 1e30f;
+          for (int r = 0; r < 3; ++r) {
+            CK(cudaEventRecord(e0, L->stream));
+            CK(launch_step_multi(a, mcfg, K, L->stream));
+            CK(cudaEventRecord(e1, L->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            t_best = std::min(t_best, ms);
+          }
+          L->launches += 4;
+          const float per_step = t_best / K;
+          if (per_step < best.ms) {
+            best = TuneVal{W, rcfg.depth, rcfg.row_split, per_step};
+            best.K = K;
+            best.Dm = D;
+          }
+        }
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best.W == 0) return fail(CBDG_ERR_UNSUPPORTED, "no tile fits this lattice");
@@ -372,6 +422,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
                        ? plan_resident(L->precision, L->Lx, L->Ly, n_sites, M)
                        : 0;
   if (Wres) W = Wres;
+  int tuned_k = 0, tuned_dm = 0;
   if (!Wres && L->autotune && L->slab_w == 0 && L->row_split == 0 && L->depth == 0 && n_sites > 0) {
     TuneVal tv;
     cbdg_status ts = autotune(L, mode, n_sites, &tv);
@@ -379,6 +430,8 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     W = tv.W;
     want_split = tv.split;
     want_depth = tv.D;
+    tuned_k = tv.K;
+    tuned_dm = tv.Dm;
     L->tuned_w = tv.W;
     L->tuned_d = tv.D;
     L->tuned_split = tv.split;
@@ -450,11 +503,12 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     // temporal blocking: K steps per HBM pass (real FP32, open y edges)
     StepConfig mcfg;
     int Kt = 1;
-    const int64_t want_k = L->temporal == 0 ? kDefaultTemporalSteps : L->temporal;
+    const int64_t want_k = L->temporal != 0 ? L->temporal : (tuned_k ? tuned_k : kDefaultTemporalSteps);
     // both kernels run on the same slab-blocked layout, so they share the slab width
     if (!(mode == kReal && L->precision == CBDG_FP32_MIXED && !L->py && want_k >= 2 &&
           (cfg.slab_w == 8 || cfg.slab_w == 16) &&
-          plan_step_multi(L->Lx, L->Ly, ld, cfg.slab_w, static_cast<int>(want_k), want_depth, &mcfg, &Kt)))
+          plan_step_multi(L->Lx, L->Ly, ld, cfg.slab_w, static_cast<int>(want_k), tuned_dm ? tuned_dm : want_depth,
+                          &mcfg, &Kt)))
       Kt = 1;
     L->last_temporal = Kt;
     const int nsum = mode == kReal ? 3 : 4;

@@ -257,3 +257,6 @@ def test_autotuned_tile(precision):
     again = lat.moments(sites, p.M)  # cached tile: bitwise repeatable
     assert lat.last_tile() == (W, D, split)
     assert np.array_equal(again[0], got[0])
+    # FP32 on open edges also weighs two to four steps per pass
+    k = cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL)
+    assert 1 <= k <= (4 if precision == "fp32" else 1)
