@@ -434,10 +434,10 @@ def leg_dwave(cbdg, wl, stream, hbm, columns=4096):
                          "unit": "GB/s", "frac": sb / (sms * 1e-3) / 1e9 / hbm}}
 
 
-def leg_ensemble(cbdg, wl, stream):
+def leg_ensemble(cbdg, wl, stream, samples=256):
     """256 disordered lattices (sides 32..96, M = 512): one graph-replayed
-    self-consistency iteration."""
-    probs = wl.ensemble()
+    self-consistency iteration (fewer samples for profiling runs)."""
+    probs = wl.ensemble()[:samples]
     ens = cbdg.Ensemble(probs, stream=stream)
     t0 = time.perf_counter()
     ens.scf(0.01, 512, 0.5, 0.0, 1)  # includes the graph capture
@@ -494,13 +494,13 @@ def leg_tiny(cbdg, wl, stream):
     return out
 
 
-def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096):
+def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=256):
     """Other hot-path stages at their workload sizes (not the headline)."""
     legs = {
         "tiny": lambda: leg_tiny(cbdg, wl, stream),
         "contraction": lambda: leg_contraction(cbdg, torch, stream),
         "dwave": lambda: leg_dwave(cbdg, wl, stream, hbm, columns),
-        "ensemble": lambda: leg_ensemble(cbdg, wl, stream),
+        "ensemble": lambda: leg_ensemble(cbdg, wl, stream, samples),
         "adjoint": lambda: leg_adjoint(cbdg, wl, stream),
     }
     return {name: fn() for name, fn in legs.items() if only is None or only == name}
@@ -557,6 +557,8 @@ def main():
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")
     ap.add_argument("--moments", type=int, default=M)
+    ap.add_argument("--samples", type=int, default=256,
+                    help="lattices of the ensemble stage (--stage ensemble)")
     ap.add_argument("--columns", type=int, default=4096,
                     help="start vectors of the d-wave stage (--stage dwave)")
     ap.add_argument("--temporal", type=int, default=None,
@@ -572,7 +574,8 @@ def main():
         from paper_1007_1609_gb300 import workloads as wl
         stream = torch.cuda.Stream()
         hbm, _ = peaks()
-        rec = extra_legs(cbdg, wl, torch, stream, hbm, only=args.stage, columns=args.columns)
+        rec = extra_legs(cbdg, wl, torch, stream, hbm, only=args.stage, columns=args.columns,
+                         samples=args.samples)
         print(json.dumps({"stage": args.stage, **rec}), flush=True)
         return 0
     return run_gb300(args)

@@ -111,15 +111,21 @@ __device__ __forceinline__ float fcomp(const float4 &v, int j) {
   return reinterpret_cast<const float *>(&v)[j];
 }
 
-template <int MAXX>
-__global__ void __launch_bounds__(kEnsThreads, 1) ensemble_recursion_kernel(EnsArgs a) {
-  constexpr int W = kEnsW, VEC = 4, QUADS = W / VEC, XSLOTS = kEnsThreads / QUADS;
+// NT threads (256): one or two lattice sites per thread, Lx <= 128.  (384
+// threads with one site each up to Lx = 96 measured slower on the 256-lattice
+// ensemble: 7.04 s against 6.79 s per iteration; the passes over its short
+// rows are bound by per-wavefront latency, not by the uneven site split.)
+template <int MAXX, int NT>
+__global__ void __launch_bounds__(NT, 1) ensemble_recursion_kernel(EnsArgs a) {
+  constexpr int W = kEnsW, VEC = 4, QUADS = W / VEC, XSLOTS = NT / QUADS;
   constexpr int JS = kEnsJS, OS = kEnsOS, D = kEnsD;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bars[JS];
   __shared__ int abort_flag;
   __shared__ int item_s;
-  __shared__ double red[3][XSLOTS][W];
+  // per-thread column sums, [3][XSLOTS][W], in the ring's space: written and
+  // read only between passes, when no staged row is live
+  auto red = reinterpret_cast<double (*)[XSLOTS][W]>(smem_raw);
   __shared__ double accn[W], accd[W], m1s[W], dAs[W];
 
   const int t = threadIdx.x;
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_recursion_kernel(EnsA
     float *sp = so_ + OS * rowel;
 
     // j_0 = e_i (bufA), j_1 = H~ e_i (bufB) for the item's columns
-    for (size_t k = t; k < vec_el; k += kEnsThreads) {
+    for (size_t k = t; k < vec_el; k += NT) {
       bufA[k] = 0.f;
       bufB[k] = 0.f;
     }
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(kEnsThreads, 1) ensemble_recursion_kernel(EnsA
       // two steps per pass over the item's vectors; (prev, cur) end as (j_{n+1}, j_{n+2})
       for (; n + 1 <= steps && !abort_flag; n += 2) {
         mp::Kahan pA[2][VEC], pB[2][VEC], pC[2][VEC];
-        if (!mp::multi_pass<W, 2, D, MAXX>(prev, cur, par, Lx, Ly, reinterpret_cast<float *>(smem_raw), bars, G,
+        if (!mp::multi_pass<W, 2, D, MAXX, NT>(prev, cur, par, Lx, Ly, reinterpret_cast<float *>(smem_raw), bars, G,
                                            kWaitNs, 0u, &abort_flag, pA, pB, pC))
           break;
         G += Ly;
@@ -529,17 +535,32 @@ size_t ens_multi_smem(int Lmax) {
   static_assert(mp::PassShape<kEnsW, 2, kEnsD>::NB == kEnsJS, "the pass and the march share the barriers");
   return mp::PassShape<kEnsW, 2, kEnsD>::smem_floats(Lmax) * sizeof(float);
 }
-constexpr size_t kEnsDynLimit = 200 * 1024;
+// the per-thread column sums [3][XSLOTS][W] doubles share the ring's space
+size_t ens_red_smem(int Lmax);
+constexpr size_t kEnsDynLimit = 220 * 1024;
 
-template <int MAXX>
+template <int MAXX, int NT>
 cudaError_t launch_ens(const EnsArgs &a, int grid, size_t smem, cudaStream_t s) {
-  ensemble_recursion_kernel<MAXX><<<grid, kEnsThreads, smem, s>>>(a);
+  ensemble_recursion_kernel<MAXX, NT><<<grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t set_ens_attr(int maxx, size_t smem) {
-  if (maxx == 1) return cudaFuncSetAttribute(ensemble_recursion_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  return cudaFuncSetAttribute(ensemble_recursion_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+// Kernel shape for the widest lattice.
+int ens_threads(int) { return kEnsThreads; }
+int ens_maxx(int Lmax) { return (Lmax + 63) / 64; }
+size_t ens_red_smem(int Lmax) {
+  return static_cast<size_t>(3) * (ens_threads(Lmax) / (kEnsW / 4)) * kEnsW * sizeof(double);
+}
+
+cudaError_t set_ens_attr(int Lmax, size_t smem) {
+  const int attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (ens_maxx(Lmax) == 1)
+    return cudaFuncSetAttribute(ensemble_recursion_kernel<1, kEnsThreads>, (cudaFuncAttribute)attr, static_cast<int>(smem));
+  return cudaFuncSetAttribute(ensemble_recursion_kernel<2, kEnsThreads>, (cudaFuncAttribute)attr, static_cast<int>(smem));
+}
+
+cudaError_t launch_ens_for(int Lmax, const EnsArgs &a, int grid, size_t smem, cudaStream_t s) {
+  return ens_maxx(Lmax) == 1 ? launch_ens<1, kEnsThreads>(a, grid, smem, s) : launch_ens<2, kEnsThreads>(a, grid, smem, s);
 }
 
 // Records the launch sequence of one self-consistency iteration on e->stream.
@@ -599,8 +620,7 @@ cudaError_t enqueue_iteration(cbdg_ensemble *e, double T, int M, double mix, dou
   a.queue = small;
   a.flags = small + 2;
   a.multi = e->multi;
-  const int maxx = (e->Lmax + 63) / 64;
-  err = maxx == 1 ? launch_ens<1>(a, e->grid, e->smem, s) : launch_ens<2>(a, e->grid, e->smem, s);
+  err = launch_ens_for(e->Lmax, a, e->grid, e->smem, s);
   if (err != cudaSuccess) return err;
   ens_mix_kernel<<<gs, 256, 0, s>>>(static_cast<int *>(e->d_Lx), static_cast<int *>(e->d_Ly),
                                     static_cast<long long *>(e->d_off), conv, mix,
@@ -656,7 +676,7 @@ cbdg_status cbdg_build_ensemble(const cbdg_lattice_desc *descs, int32_t n, cbdg_
     return st;
   };
   if (e->Lmax > 128) return bail(efail(CBDG_ERR_UNSUPPORTED, "ensemble lattices must have Lx <= 128"));
-  e->smem = ens_smem(e->Lmax);
+  e->smem = std::max(ens_smem(e->Lmax), ens_red_smem(e->Lmax));
   if (e->smem > kEnsDynLimit) return bail(efail(CBDG_ERR_UNSUPPORTED, "ensemble lattice rows too long"));
   e->multi = ens_multi_smem(e->Lmax) <= kEnsDynLimit ? 1 : 0;
   if (e->multi) e->smem = std::max(e->smem, ens_multi_smem(e->Lmax));
@@ -721,7 +741,7 @@ cbdg_status cbdg_build_ensemble(const cbdg_lattice_desc *descs, int32_t n, cbdg_
       (err = cudaMemset(e->d_iters, 0, n * sizeof(int))) != cudaSuccess ||
       (err = cudaMemset(e->d_last, 0, n * sizeof(double))) != cudaSuccess ||
       (err = cudaMemset(e->d_scal, 0, static_cast<size_t>(n) * kScalars * sizeof(double))) != cudaSuccess ||
-      (err = set_ens_attr((e->Lmax + 63) / 64, e->smem)) != cudaSuccess)
+      (err = set_ens_attr(e->Lmax, e->smem)) != cudaSuccess)
     return bail(efail(CBDG_ERR_CUDA, "ensemble setup: %s", cudaGetErrorString(err)));
   *out = e;
   return CBDG_OK;

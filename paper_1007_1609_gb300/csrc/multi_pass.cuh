@@ -87,9 +87,9 @@ __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cas
 
 constexpr int kPassThreads = 256;
 
-template <int W, int K, int D>
+template <int W, int K, int D, int NT = kPassThreads>
 struct PassShape {
-  static constexpr int VEC = 4, QUADS = W / VEC, XSLOTS = kPassThreads / QUADS;
+  static constexpr int VEC = 4, QUADS = W / VEC, XSLOTS = NT / QUADS;
   static constexpr int RS = 3 + D;      // j_n / j_{n-1} staging ring: rows g-1 .. g+2+D
   static constexpr int AS = K + 2 + D;  // parameter ring: rows g-K+1 .. g+2+D
   static constexpr int NB = RS;         // mbarriers (one per staged row in flight)
@@ -100,15 +100,15 @@ struct PassShape {
   }
 };
 
-template <int W, int K, int D, int MAXX>
+template <int W, int K, int D, int MAXX, int NT = kPassThreads>
 __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__restrict__ par, int Lx, int Ly,
                                            float *smem, unsigned long long *bars, long long base,
                                            unsigned long long wait_ns, unsigned stall_tx, int *abort_flag,
                                            Kahan (&accA)[K][4], Kahan (&accB)[K][4], Kahan (&accC)[K][4]) {
-  using Sh = PassShape<W, K, D>;
+  using Sh = PassShape<W, K, D, NT>;
   constexpr int VEC = Sh::VEC, QUADS = Sh::QUADS, XSLOTS = Sh::XSLOTS;
   constexpr int RS = Sh::RS, AS = Sh::AS, NB = Sh::NB;
-  static_assert(W % VEC == 0 && kPassThreads % QUADS == 0 && K >= 2, "bad shape");
+  static_assert(W % VEC == 0 && NT % QUADS == 0 && K >= 2, "bad shape");
   const int rowel = 2 * Lx * W;
   const int pel = Lx * kParamStride;
   float *sq = smem;                       // [RS][rowel]  j_n
