@@ -188,6 +188,25 @@ cbdg_status cbdg_order_parameter_backward(cbdg_lattice *lat, double T, int32_t M
                                           const cbdg_complex *dL_ddelta_out, double *dL_deps,
                                           double *dL_dhop, double *dL_ddelta_in);
 
+/* Gradient of a loss L(Delta*) on the self-consistent order parameter
+ * Delta* = F(Delta*; eps, t) (the fixed point of cbdg_scf_step, with a and the
+ * coefficients frozen as in cbdg_order_parameter_backward), through the fixed
+ * point rather than one map: by the implicit function theorem
+ *   dL/dtheta = lam^T dF/dtheta,  lam = dL/dDelta* + (dF/dDelta_in)^T lam,
+ * solved by the damped iteration lam <- (1 - mix) lam + mix (dL/dDelta* +
+ * (dF/dDelta_in)^T lam), each product one run of the adjoint of
+ * cbdg_order_parameter_backward, until max_i |d lam_i| < tol (at most
+ * max_iter runs; it converges when the mixed self-consistency loop does).
+ * The lattice's current Delta must be the converged Delta*.  dL_ddelta [N]
+ * (real part used); outputs dL_deps [N], dL_dhop [N*4] as in
+ * cbdg_order_parameter_backward (may be NULL); iterations may be NULL.
+ * Real on-site lattices only.  Errors: INVALID_ARG, UNSUPPORTED,
+ * NOT_CONVERGED (outputs hold the last lam's gradients), OOM, CUDA.  Not in
+ * the paper. */
+cbdg_status cbdg_fixed_point_backward(cbdg_lattice *lat, double T, int32_t M, double mix,
+                                      const cbdg_complex *dL_ddelta, double tol, int32_t max_iter,
+                                      double *dL_deps, double *dL_dhop, int32_t *iterations);
+
 /* Copies the lattice's current Delta ([N] or [N*4]) out, or replaces it.  A
  * new bond Delta must be symmetric (Delta_{j,d^1} == Delta_{i,d}) and 0
  * across open edges, like delta0 (the recursion reads each bond from one end);

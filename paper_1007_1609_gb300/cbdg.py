@@ -109,6 +109,7 @@ def load():
             "cbdg_split_tf32": [P, I32, I32, I32, P, P, P],
             "cbdg_contract_tf32x3_planes": [P, P, P, P, I32, P, I32, I32, I32, P],
             "cbdg_order_parameter_backward": [P, D, I32, P, P, P, P],
+            "cbdg_fixed_point_backward": [P, D, I32, D, P, D, I32, P, P, P],
             "cbdg_build_ensemble": [P, I32, P, P],
             "cbdg_ensemble_destroy": [P],
             "cbdg_ensemble_scf": [P, D, I32, D, D, I32, P, P],
@@ -257,6 +258,14 @@ def cbdg_split_tf32(src, ld, rows, k, hi, lo, stream=None):
 def cbdg_contract_tf32x3_planes(a_hi, a_lo, b_hi, b_lo, kp, D, ldd, m, n, stream=None):
     _check(load().cbdg_contract_tf32x3_planes(_ptr(a_hi), _ptr(a_lo), _ptr(b_hi), _ptr(b_lo), int(kp),
                                               _ptr(D), int(ldd), int(m), int(n), _stream_handle(stream)))
+
+
+def cbdg_fixed_point_backward(lat, T, M, mix, dL_ddelta, tol, max_iter, dL_deps, dL_dhop):
+    """Gradient through the self-consistent fixed point; returns the iteration count."""
+    it = ctypes.c_int32(0)
+    _check(load().cbdg_fixed_point_backward(lat, float(T), int(M), float(mix), _ptr(dL_ddelta), float(tol),
+                                            int(max_iter), _ptr(dL_deps), _ptr(dL_dhop), ctypes.byref(it)))
+    return it.value
 
 
 def cbdg_order_parameter_backward(lat, T, M, dL_ddelta_out, dL_deps, dL_dhop, dL_ddelta_in):
@@ -458,6 +467,14 @@ class Lattice:
     def freeze_rescale(self, a):
         """Use a fixed a (None: back to the Gershgorin rescale)."""
         cbdg_set_option(self.handle, CBDG_OPT_FIXED_RESCALE_PICO, 0 if a is None else int(round(a * 1e12)))
+
+    def fixed_point_backward(self, T, M, mix, dL_ddelta, tol=1e-12, max_iter=500):
+        """(dL/deps [N], dL/dhop [N, 4], iterations) through the converged Delta."""
+        g = np.ascontiguousarray(dL_ddelta, dtype=np.complex128).reshape(-1)
+        ge = np.zeros(self.N)
+        gh = np.zeros(self.N * 4)
+        it = cbdg_fixed_point_backward(self.handle, T, M, mix, g, tol, max_iter, ge, gh)
+        return ge, gh.reshape(self.N, 4), it
 
     def backward(self, T, M, dL_ddelta_out):
         """Gradients (eps [N], hop [N, 4], delta_in [N]) of one map (see the C ABI)."""

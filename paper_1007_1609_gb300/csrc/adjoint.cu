@@ -156,6 +156,22 @@ __global__ void __launch_bounds__(256) adjoint_accumulate_kernel(int Lx, int Ly,
   }
 }
 
+// One damped step of the fixed-point adjoint lam = g + J^T lam (J = dF/dDelta_in):
+//   lam <- (1 - mix) lam + mix (g + J^T lam),  J^T lam = gd from the last adjoint run;
+// w (the next run's weights) <- lam; max |lam_new - lam| into scal[kScalMaxDiffBits]
+// (non-negative doubles order like their bit patterns).
+__global__ void fixed_point_update_kernel(int N, double mix, const double *g, const double *gd, double *lam,
+                                          double *w, double *scal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double next = (1.0 - mix) * lam[i] + mix * (g[i] + gd[i]);
+  const double diff = fabs(next - lam[i]);
+  atomicMax(reinterpret_cast<unsigned long long *>(scal + kScalMaxDiffBits),
+            static_cast<unsigned long long>(__double_as_longlong(isfinite(diff) ? diff : 1e300)));
+  lam[i] = next;
+  w[i] = next;
+}
+
 // dL/deps_i = (G_ee - G_hh)/a, dL/dDelta_i = (G_eh + G_he)/a,
 // dL/dt_b = (-G_{e_i e_j} - G_{e_j e_i} + G_{h_i h_j} + G_{h_j h_i})/a for the
 // undirected bond b = (i, i+d), stored on both directed entries.
@@ -250,6 +266,12 @@ cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int
                                       double *part, cudaStream_t s) {
   return precision == 1 ? accumulate_s<float>(Lx, Ly, px, py, ld, W, groups, lam, j, f, part, s)
                         : accumulate_s<double>(Lx, Ly, px, py, ld, W, groups, lam, j, f, part, s);
+}
+
+cudaError_t launch_fixed_point_update(int N, double mix, const double *g, const double *gd, double *lam,
+                                      double *w, double *scal, cudaStream_t s) {
+  fixed_point_update_kernel<<<blocks(N, 256), 256, 0, s>>>(N, mix, g, gd, lam, w, scal);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_final(int Lx, int Ly, int px, int py, int groups, const double *part,

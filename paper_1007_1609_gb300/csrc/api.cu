@@ -117,7 +117,7 @@ struct cbdg_lattice {
   int nd = 0;  // number of Delta entries (N or 4N)
   DBuf eps, hop, delta, params, scal, flags, f, C, sites_all, sites_user;
   DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
-  DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out;
+  DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out, adj_fp;
   // options
   int K = 65536;
   int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0, fixed_a_pico = 0, wait_ms = 2000, stall = 0, autotune = 0, temporal = 0;
@@ -687,6 +687,155 @@ cbdg_status order_parameter_impl(cbdg_lattice *L, double T, int kernel, double l
   return run_columns(L, L->sites_all.as<int32_t>(), L->N, M, nullptr, nullptr, 1, true);
 }
 
+// One adjoint run of the self-consistency map with the weights w_i = dL/dDelta_out,i
+// already in L->adj_w (device): leaves dL/deps, dL/dDelta_in and dL/dt in
+// L->adj_out ([N] eps, [N] Delta, [N*4] hop).
+cbdg_status adjoint_run(cbdg_lattice *L, double T, int M) {
+  const int N = L->N;
+  cbdg_status st = prepare(L, T, CBDG_JACKSON, 0.0, M, true);
+  if (st != CBDG_OK) return st;
+  std::vector<double> hC(M);
+  CK(cudaMemcpyAsync(hC.data(), L->C.p, M * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+
+  const size_t es = elem_size(L);
+  const size_t rows = 2 * static_cast<size_t>(N);
+  const int W = slab_width_default(L->precision);
+  const int S = std::max(2, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(M)))));
+  const int nseg = (M + S - 1) / S;
+  // per column: 2 checkpoint vectors per segment, S segment vectors, 2 forward, 2 adjoint
+  const int64_t per_col = static_cast<int64_t>((2 * nseg + S + 4) * rows * es);
+  size_t cap;
+  if (L->ws_mb > 0) {
+    cap = static_cast<size_t>(L->ws_mb) << 20;
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    cap = static_cast<size_t>(0.5 * (fr + L->adj_ck.bytes + L->adj_seg.bytes + L->adj_lam.bytes +
+                                     L->vec0.bytes + L->vec1.bytes));
+  }
+  int64_t max_cols = (static_cast<int64_t>(cap) / per_col / W) * W;
+  if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
+  if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for the adjoint");
+  const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((N + W - 1) / W) * W));
+  const int groups = adjoint_groups(L->Ly, ((std::min(chunk, N) + W - 1) / W) * W, W);
+  CK(L->adj_part.ensure(static_cast<size_t>(groups) * N * 12 * sizeof(double)));
+  CK(cudaMemsetAsync(L->adj_part.p, 0, static_cast<size_t>(groups) * N * 12 * sizeof(double), L->stream));
+  const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
+  (void)tol;
+
+  for (int c0 = 0; c0 < N; c0 += chunk) {
+    const int ncols = std::min(chunk, N - c0);
+    const int ld = ((ncols + W - 1) / W) * W;
+    StepConfig cfg;
+    if (!plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
+                        static_cast<int>(L->depth), &cfg) || cfg.slab_w != W)
+      return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d for the adjoint", L->Lx);
+    const size_t vb = rows * ld * es;
+    CK(L->vec0.ensure(vb));
+    CK(L->vec1.ensure(vb));
+    CK(L->adj_ck.ensure(2 * nseg * vb));
+    CK(L->adj_seg.ensure(static_cast<size_t>(S) * vb));
+    CK(L->adj_lam.ensure(2 * vb));
+    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 3 * ld * sizeof(double)));
+    CK(L->mu1.ensure(ld * sizeof(double)));
+    CK(L->dA.ensure(ld * sizeof(double2)));
+    CK(L->acc_n.ensure(ld * sizeof(double)));
+    CK(L->acc_d.ensure(ld * 4 * sizeof(double2)));
+    const int32_t *sites = L->sites_all.as<int32_t>() + c0;
+    unsigned char *ck = L->adj_ck.as<unsigned char>();
+    unsigned char *seg = L->adj_seg.as<unsigned char>();
+    auto ckv = [&](int k, int which) { return ck + (2 * static_cast<size_t>(k) + which) * vb; };
+    auto segv = [&](int r) { return seg + static_cast<size_t>(r) * vb; };
+    StepArgs a;
+    a.params = L->params.p;
+    a.partials = L->partials.as<double>();
+    a.flags = L->flags.as<unsigned int>();
+    a.wait_ns = static_cast<unsigned long long>(L->wait_ms) * 1000000ull;
+    a.stall_tx = L->stall ? 16u : 0u;
+    a.Lx = L->Lx;
+    a.Ly = L->Ly;
+    a.ld = ld;
+    a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+    // j_{m} = 2 H~ j_{m-1} - j_{m-2} written over dst, which must hold j_{m-2}
+    auto step = [&](void *cur, void *prev_inout) -> cbdg_status {
+      a.cur = cur;
+      a.prev = prev_inout;
+      CK(launch_step_real(L->precision, a, cfg, L->stream));
+      L->launches += 1;
+      return CBDG_OK;
+    };
+    // ---- forward with checkpoints (j_{kS}, j_{kS+1})
+    CK(cudaMemsetAsync(L->vec0.p, 0, vb, L->stream));
+    CK(cudaMemsetAsync(L->vec1.p, 0, vb, L->stream));
+    CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, W, sites, L->eps.as<double>(),
+                        L->mu, L->hop.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
+                        L->C.as<double>(), M, L->vec0.p, L->vec1.p, L->mu1.as<double>(),
+                        L->dA.as<double2>(), L->acc_n.as<double>(), L->acc_d.as<double2>(), nullptr,
+                        nullptr, 1, L->stream));
+    L->launches += 1;
+    // checkpoint k holds j_{kS} (slot 0) and j_{kS+1} (slot 1, when kS+1 < M)
+    CK(cudaMemcpyAsync(ckv(0, 0), L->vec0.p, vb, cudaMemcpyDeviceToDevice, L->stream));
+    CK(cudaMemcpyAsync(ckv(0, 1), L->vec1.p, vb, cudaMemcpyDeviceToDevice, L->stream));
+    void *jm2 = L->vec0.p, *jm1 = L->vec1.p;  // j_{m-2}, j_{m-1} before step m
+    const int m_last = (nseg - 1) * S + 1;     // no later j is ever needed from the forward pass
+    for (int m = 2; m < M && m <= m_last; ++m) {
+      st = step(jm1, jm2);  // jm2 <- j_m
+      if (st != CBDG_OK) return st;
+      std::swap(jm1, jm2);  // jm1 = j_m
+      if (m % S == 0) CK(cudaMemcpyAsync(ckv(m / S, 0), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+      if ((m - 1) % S == 0 && m - 1 >= S)
+        CK(cudaMemcpyAsync(ckv((m - 1) / S, 1), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+    }
+    // ---- reverse: lam_m for m = M-1 .. 1, gradient f_m lam_m (x) j_{m-1}
+    void *lam1 = L->adj_lam.p;                                  // lam_{m+1}
+    void *lam2 = L->adj_lam.as<unsigned char>() + vb;          // lam_{m+2}
+    CK(cudaMemsetAsync(lam1, 0, vb, L->stream));
+    CK(cudaMemsetAsync(lam2, 0, vb, L->stream));
+    const double halfU = 0.5 * L->coupling;
+    bool first = true;
+    for (int k = nseg - 1; k >= 0; --k) {
+      // recompute j_{kS} .. j_{kS+S-1} (those below M) into the segment
+      const int r_end = std::min(S, M - k * S);
+      CK(cudaMemcpyAsync(segv(0), ckv(k, 0), vb, cudaMemcpyDeviceToDevice, L->stream));
+      if (r_end > 1) CK(cudaMemcpyAsync(segv(1), ckv(k, 1), vb, cudaMemcpyDeviceToDevice, L->stream));
+      for (int r = 2; r < r_end; ++r) {
+        // j_r = 2 H~ j_{r-1} - j_{r-2}, out of place (the segment keeps j_{r-2})
+        a.cur = segv(r - 1);
+        a.prev = segv(r - 2);
+        a.out = segv(r);
+        CK(launch_step_real(L->precision, a, cfg, L->stream));
+        a.out = nullptr;
+        L->launches += 1;
+      }
+      // m - 1 in [kS, kS + r_end - 1]  ->  m in [kS + 1, kS + r_end], m <= M - 1
+      const int m_hi = std::min(M - 1, k * S + r_end), m_lo = k * S + 1;
+      for (int m = m_hi; m >= m_lo; --m) {
+        if (first) {
+          // lam_{M-1} = y_{M-1}
+          first = false;
+        } else {
+          st = step(lam1, lam2);  // lam2 <- 2 H~ lam_{m+1} - lam_{m+2} = lam_m without source
+          if (st != CBDG_OK) return st;
+          std::swap(lam1, lam2);  // lam1 = lam_m, lam2 = lam_{m+1}
+        }
+        CK(launch_adjoint_source(L->precision, L->Lx, L->Ly, ncols, W, sites, L->adj_w.as<double>(),
+                                 halfU * hC[m], lam1, L->stream));
+        CK(launch_adjoint_accumulate(L->precision, L->Lx, L->Ly, L->px, L->py, ld, W, groups, lam1,
+                                     segv(m - 1 - k * S), m == 1 ? 1.0 : 2.0,
+                                     L->adj_part.as<double>(), L->stream));
+        L->launches += 2;
+      }
+    }
+  }
+  CK(L->adj_out.ensure(static_cast<size_t>(N) * 6 * sizeof(double)));
+  double *ge = L->adj_out.as<double>(), *gd = ge + N, *gh = ge + 2 * N;
+  CK(launch_adjoint_final(L->Lx, L->Ly, L->px, L->py, groups, L->adj_part.as<double>(),
+                          L->scal.as<double>(), ge, gh, gd, L->stream));
+  L->launches += 1;
+  return CBDG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -818,7 +967,7 @@ cbdg_status cbdg_destroy(cbdg_lattice *L) {
   DBuf *bufs[] = {&L->eps,     &L->hop,   &L->delta, &L->params,  &L->scal,  &L->flags,
                   &L->f,       &L->C,     &L->sites_all, &L->sites_user, &L->vec0, &L->vec1,
                   &L->partials, &L->mu1,  &L->dA,    &L->acc_n,   &L->acc_d, &L->dout,
-                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b, &L->adj_ck, &L->adj_seg, &L->adj_lam, &L->adj_part, &L->adj_w, &L->adj_out};
+                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b, &L->adj_ck, &L->adj_seg, &L->adj_lam, &L->adj_part, &L->adj_w, &L->adj_out, &L->adj_fp};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
   L->drop_graph();
@@ -1100,154 +1249,73 @@ cbdg_status cbdg_order_parameter_backward(cbdg_lattice *L, double T, int32_t M,
     if (!isfinite(hw[i].re)) return fail(CBDG_ERR_INVALID_ARG, "dL_ddelta_out is not finite");
     w[i] = hw[i].re;
   }
-  st = prepare(L, T, CBDG_JACKSON, 0.0, M, true);
-  if (st != CBDG_OK) return st;
   CK(L->adj_w.ensure(N * sizeof(double)));
   CK(cudaMemcpyAsync(L->adj_w.p, w.data(), N * sizeof(double), cudaMemcpyHostToDevice, L->stream));
-  std::vector<double> hC(M);
-  CK(cudaMemcpyAsync(hC.data(), L->C.p, M * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
-  CK(cudaStreamSynchronize(L->stream));
-
-  const size_t es = elem_size(L);
-  const size_t rows = 2 * static_cast<size_t>(N);
-  const int W = slab_width_default(L->precision);
-  const int S = std::max(2, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(M)))));
-  const int nseg = (M + S - 1) / S;
-  // per column: 2 checkpoint vectors per segment, S segment vectors, 2 forward, 2 adjoint
-  const int64_t per_col = static_cast<int64_t>((2 * nseg + S + 4) * rows * es);
-  size_t cap;
-  if (L->ws_mb > 0) {
-    cap = static_cast<size_t>(L->ws_mb) << 20;
-  } else {
-    size_t fr = 0, tot = 0;
-    CK(cudaMemGetInfo(&fr, &tot));
-    cap = static_cast<size_t>(0.5 * (fr + L->adj_ck.bytes + L->adj_seg.bytes + L->adj_lam.bytes +
-                                     L->vec0.bytes + L->vec1.bytes));
-  }
-  int64_t max_cols = (static_cast<int64_t>(cap) / per_col / W) * W;
-  if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
-  if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for the adjoint");
-  const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((N + W - 1) / W) * W));
-  const int groups = adjoint_groups(L->Ly, ((std::min(chunk, N) + W - 1) / W) * W, W);
-  CK(L->adj_part.ensure(static_cast<size_t>(groups) * N * 12 * sizeof(double)));
-  CK(cudaMemsetAsync(L->adj_part.p, 0, static_cast<size_t>(groups) * N * 12 * sizeof(double), L->stream));
-  const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
-  (void)tol;
-
-  for (int c0 = 0; c0 < N; c0 += chunk) {
-    const int ncols = std::min(chunk, N - c0);
-    const int ld = ((ncols + W - 1) / W) * W;
-    StepConfig cfg;
-    if (!plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
-                        static_cast<int>(L->depth), &cfg) || cfg.slab_w != W)
-      return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d for the adjoint", L->Lx);
-    const size_t vb = rows * ld * es;
-    CK(L->vec0.ensure(vb));
-    CK(L->vec1.ensure(vb));
-    CK(L->adj_ck.ensure(2 * nseg * vb));
-    CK(L->adj_seg.ensure(static_cast<size_t>(S) * vb));
-    CK(L->adj_lam.ensure(2 * vb));
-    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 3 * ld * sizeof(double)));
-    CK(L->mu1.ensure(ld * sizeof(double)));
-    CK(L->dA.ensure(ld * sizeof(double2)));
-    CK(L->acc_n.ensure(ld * sizeof(double)));
-    CK(L->acc_d.ensure(ld * 4 * sizeof(double2)));
-    const int32_t *sites = L->sites_all.as<int32_t>() + c0;
-    unsigned char *ck = L->adj_ck.as<unsigned char>();
-    unsigned char *seg = L->adj_seg.as<unsigned char>();
-    auto ckv = [&](int k, int which) { return ck + (2 * static_cast<size_t>(k) + which) * vb; };
-    auto segv = [&](int r) { return seg + static_cast<size_t>(r) * vb; };
-    StepArgs a;
-    a.params = L->params.p;
-    a.partials = L->partials.as<double>();
-    a.flags = L->flags.as<unsigned int>();
-    a.wait_ns = static_cast<unsigned long long>(L->wait_ms) * 1000000ull;
-    a.stall_tx = L->stall ? 16u : 0u;
-    a.Lx = L->Lx;
-    a.Ly = L->Ly;
-    a.ld = ld;
-    a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
-    // j_{m} = 2 H~ j_{m-1} - j_{m-2} written over dst, which must hold j_{m-2}
-    auto step = [&](void *cur, void *prev_inout) -> cbdg_status {
-      a.cur = cur;
-      a.prev = prev_inout;
-      CK(launch_step_real(L->precision, a, cfg, L->stream));
-      L->launches += 1;
-      return CBDG_OK;
-    };
-    // ---- forward with checkpoints (j_{kS}, j_{kS+1})
-    CK(cudaMemsetAsync(L->vec0.p, 0, vb, L->stream));
-    CK(cudaMemsetAsync(L->vec1.p, 0, vb, L->stream));
-    CK(launch_init_real(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, W, sites, L->eps.as<double>(),
-                        L->mu, L->hop.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
-                        L->C.as<double>(), M, L->vec0.p, L->vec1.p, L->mu1.as<double>(),
-                        L->dA.as<double2>(), L->acc_n.as<double>(), L->acc_d.as<double2>(), nullptr,
-                        nullptr, 1, L->stream));
-    L->launches += 1;
-    // checkpoint k holds j_{kS} (slot 0) and j_{kS+1} (slot 1, when kS+1 < M)
-    CK(cudaMemcpyAsync(ckv(0, 0), L->vec0.p, vb, cudaMemcpyDeviceToDevice, L->stream));
-    CK(cudaMemcpyAsync(ckv(0, 1), L->vec1.p, vb, cudaMemcpyDeviceToDevice, L->stream));
-    void *jm2 = L->vec0.p, *jm1 = L->vec1.p;  // j_{m-2}, j_{m-1} before step m
-    const int m_last = (nseg - 1) * S + 1;     // no later j is ever needed from the forward pass
-    for (int m = 2; m < M && m <= m_last; ++m) {
-      st = step(jm1, jm2);  // jm2 <- j_m
-      if (st != CBDG_OK) return st;
-      std::swap(jm1, jm2);  // jm1 = j_m
-      if (m % S == 0) CK(cudaMemcpyAsync(ckv(m / S, 0), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
-      if ((m - 1) % S == 0 && m - 1 >= S)
-        CK(cudaMemcpyAsync(ckv((m - 1) / S, 1), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
-    }
-    // ---- reverse: lam_m for m = M-1 .. 1, gradient f_m lam_m (x) j_{m-1}
-    void *lam1 = L->adj_lam.p;                                  // lam_{m+1}
-    void *lam2 = L->adj_lam.as<unsigned char>() + vb;          // lam_{m+2}
-    CK(cudaMemsetAsync(lam1, 0, vb, L->stream));
-    CK(cudaMemsetAsync(lam2, 0, vb, L->stream));
-    const double halfU = 0.5 * L->coupling;
-    bool first = true;
-    for (int k = nseg - 1; k >= 0; --k) {
-      // recompute j_{kS} .. j_{kS+S-1} (those below M) into the segment
-      const int r_end = std::min(S, M - k * S);
-      CK(cudaMemcpyAsync(segv(0), ckv(k, 0), vb, cudaMemcpyDeviceToDevice, L->stream));
-      if (r_end > 1) CK(cudaMemcpyAsync(segv(1), ckv(k, 1), vb, cudaMemcpyDeviceToDevice, L->stream));
-      for (int r = 2; r < r_end; ++r) {
-        // j_r = 2 H~ j_{r-1} - j_{r-2}, out of place (the segment keeps j_{r-2})
-        a.cur = segv(r - 1);
-        a.prev = segv(r - 2);
-        a.out = segv(r);
-        CK(launch_step_real(L->precision, a, cfg, L->stream));
-        a.out = nullptr;
-        L->launches += 1;
-      }
-      // m - 1 in [kS, kS + r_end - 1]  ->  m in [kS + 1, kS + r_end], m <= M - 1
-      const int m_hi = std::min(M - 1, k * S + r_end), m_lo = k * S + 1;
-      for (int m = m_hi; m >= m_lo; --m) {
-        if (first) {
-          // lam_{M-1} = y_{M-1}
-          first = false;
-        } else {
-          st = step(lam1, lam2);  // lam2 <- 2 H~ lam_{m+1} - lam_{m+2} = lam_m without source
-          if (st != CBDG_OK) return st;
-          std::swap(lam1, lam2);  // lam1 = lam_m, lam2 = lam_{m+1}
-        }
-        CK(launch_adjoint_source(L->precision, L->Lx, L->Ly, ncols, W, sites, L->adj_w.as<double>(),
-                                 halfU * hC[m], lam1, L->stream));
-        CK(launch_adjoint_accumulate(L->precision, L->Lx, L->Ly, L->px, L->py, ld, W, groups, lam1,
-                                     segv(m - 1 - k * S), m == 1 ? 1.0 : 2.0,
-                                     L->adj_part.as<double>(), L->stream));
-        L->launches += 2;
-      }
-    }
-  }
-  // gradients
-  CK(L->adj_out.ensure(static_cast<size_t>(N) * 6 * sizeof(double)));
+  st = adjoint_run(L, T, M);
+  if (st != CBDG_OK) return st;
   double *ge = L->adj_out.as<double>(), *gd = ge + N, *gh = ge + 2 * N;
-  CK(launch_adjoint_final(L->Lx, L->Ly, L->px, L->py, groups, L->adj_part.as<double>(),
-                          L->scal.as<double>(), ge, gh, gd, L->stream));
-  L->launches += 1;
   CK(deliver(L, dL_deps, ge, N * sizeof(double)));
   CK(deliver(L, dL_ddelta_in, gd, N * sizeof(double)));
   CK(deliver(L, dL_dhop, gh, static_cast<size_t>(N) * 4 * sizeof(double)));
   return finish(L);
+}
+
+cbdg_status cbdg_fixed_point_backward(cbdg_lattice *L, double T, int32_t M, double mix,
+                                      const cbdg_complex *dL_ddelta, double tol, int32_t max_iter,
+                                      double *dL_deps, double *dL_dhop, int32_t *iterations) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  if (mode_of(L) != kReal)
+    return fail(CBDG_ERR_UNSUPPORTED, "the adjoint handles real on-site pairing with 4 directions");
+  if (!(T >= 0.0) || !isfinite(T)) return fail(CBDG_ERR_INVALID_ARG, "T must be finite and >= 0");
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  if (!(mix > 0.0 && mix <= 1.0)) return fail(CBDG_ERR_INVALID_ARG, "mix must be in (0, 1]");
+  if (!(tol > 0.0) || max_iter < 1) return fail(CBDG_ERR_INVALID_ARG, "need tol > 0 and max_iter >= 1");
+  if (!dL_ddelta) return fail(CBDG_ERR_INVALID_ARG, "dL_ddelta is NULL");
+  const int N = L->N;
+  std::vector<cbdg_complex> hg;
+  cudaError_t e = host_copy(dL_ddelta, N, hg);
+  if (e != cudaSuccess) return cuda_fail(e, "reading dL_ddelta");
+  std::vector<double> g(N);
+  for (int i = 0; i < N; ++i) {
+    if (!isfinite(hg[i].re)) return fail(CBDG_ERR_INVALID_ARG, "dL_ddelta is not finite");
+    g[i] = hg[i].re;
+  }
+  // g, lam (device); the first adjoint run takes w = lam = g
+  CK(L->adj_fp.ensure(2 * static_cast<size_t>(N) * sizeof(double)));
+  CK(L->adj_w.ensure(N * sizeof(double)));
+  double *dg = L->adj_fp.as<double>(), *lam = dg + N;
+  CK(cudaMemcpyAsync(dg, g.data(), N * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  CK(cudaMemcpyAsync(lam, dg, N * sizeof(double), cudaMemcpyDeviceToDevice, L->stream));
+  CK(cudaMemcpyAsync(L->adj_w.p, dg, N * sizeof(double), cudaMemcpyDeviceToDevice, L->stream));
+  int it = 0;
+  bool converged = false;
+  double diff = 0.0;
+  while (it < max_iter && !converged) {
+    st = adjoint_run(L, T, M);  // adj_out + N = J^T lam
+    if (st != CBDG_OK) return st;
+    CK(cudaMemsetAsync(L->scal.as<double>() + kScalMaxDiffBits, 0, sizeof(double), L->stream));
+    CK(launch_fixed_point_update(N, mix, dg, L->adj_out.as<double>() + N, lam, L->adj_w.as<double>(),
+                                 L->scal.as<double>(), L->stream));
+    L->launches += 1;
+    CK(cudaMemcpyAsync(&diff, L->scal.as<double>() + kScalMaxDiffBits, sizeof(double), cudaMemcpyDeviceToHost,
+                       L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+    ++it;
+    converged = diff < tol;
+  }
+  // dL/dtheta = (dF/dtheta)^T lam with the final lam
+  st = adjoint_run(L, T, M);
+  if (st != CBDG_OK) return st;
+  double *ge = L->adj_out.as<double>(), *gh = ge + 2 * N;
+  CK(deliver(L, dL_deps, ge, N * sizeof(double)));
+  CK(deliver(L, dL_dhop, gh, static_cast<size_t>(N) * 4 * sizeof(double)));
+  if (iterations) *iterations = it;
+  st = finish(L);
+  if (st != CBDG_OK) return st;
+  if (!converged)
+    return fail(CBDG_ERR_NOT_CONVERGED, "fixed-point adjoint: max |d lam| = %g after %d iterations", diff, it);
+  return CBDG_OK;
 }
 
 cbdg_status cbdg_get_delta(cbdg_lattice *L, cbdg_complex *delta) {

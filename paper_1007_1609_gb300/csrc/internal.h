@@ -187,6 +187,8 @@ int adjoint_groups(int Ly, int ld, int W);
 cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int py, int ld, int W,
                                       int groups, const void *lam, const void *j, double f,
                                       double *part, cudaStream_t s);
+cudaError_t launch_fixed_point_update(int N, double mix, const double *g, const double *gd, double *lam,
+                                      double *w, double *scal, cudaStream_t s);
 cudaError_t launch_adjoint_final(int Lx, int Ly, int px, int py, int groups, const double *part,
                                  const double *scal, double *g_eps, double *g_hop, double *g_delta,
                                  cudaStream_t s);
