@@ -27,6 +27,9 @@
  *     Van Loan, the symmetric Jacobi method with a phase rotation for the
  *     complex off-diagonal), used only as an independent exact check.
  *   - reverse-mode gradient of one self-consistency map, storing every j_n.
+ *   - nonlocal moments <alpha_t|T_n|e_i> at chosen target sites, the
+ *     Green's function of gf1 built from them, and the bond currents of
+ *     Eq. 20 from the one-body density matrix f(H).
  *
  * OpenMP parallelises over start sites (the paper's "trivially parallel"
  * axis, paragraph after Eq. 20) and over coefficient indices.
@@ -463,6 +466,147 @@ int orc_ldos(const orc_lattice *L, double a, const int32_t *sites, int n_sites, 
   orc_ldos_from_moments(mu_ee, n_sites, M, a, kernel, lambda, energies, n_E, ldos);
   free(mu_ee);
   free(mu_eh);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nonlocal Green's functions (Eqs. 11-15, gf1) and bond currents (Eq. 20).   */
+/* ------------------------------------------------------------------------ */
+
+/* The direct recursion of Eq. 15 from the basis vector of row start_row:
+ * out[m*n_rows + r] = <row rows[r] | T_m(H/a) | start_row> for m < M, 0 for
+ * rows[r] < 0.  jprev, jcur are work vectors of H->n entries. */
+static void chebyshev_rows(const orc_csr *H, double a, int start_row, int M, const int *rows,
+                           int n_rows, cplx *out, cplx *jprev, cplx *jcur) {
+  memset(jprev, 0, sizeof(cplx) * H->n);
+  jprev[start_row] = 1.0;
+  for (int m = 0; m < M; ++m) {
+    cplx *jn;
+    if (m == 0) {
+      jn = jprev;
+    } else if (m == 1) {
+      csr_step(H, 1.0 / a, jprev, 0.0, jprev, jcur);
+      jn = jcur;
+    } else {
+      csr_step(H, 2.0 / a, jcur, -1.0, jprev, jprev);
+      cplx *t = jprev;
+      jprev = jcur;
+      jcur = t;
+      jn = jcur;
+    }
+    for (int r = 0; r < n_rows; ++r) out[(size_t)m * n_rows + r] = rows[r] >= 0 ? jn[rows[r]] : 0.0;
+  }
+}
+
+/* One direct recursion (Eq. 15) per start vector, j_0 = e_i (start_part 0,
+ * the |c^dagger_{i,up}> of Eq. 15) or j_0 = h_i (start_part 1), i = sites[c];
+ * every moment is read at every listed target site:
+ *   a_e[(c*M + n)*n_t + t] = <e_{targets[t]} | T_n(H/a) | j_0>
+ *   a_h[(c*M + n)*n_t + t] = <h_{targets[t]} | T_n(H/a) | j_0>
+ * With start_part 0 these are a^{11}_n(t, i) and a^{12}_n(t, i) of Eqs. 11
+ * and coeff2 times (1 + delta_n0): one recursion gives G^{1 alpha}_{t i} for
+ * all t and alpha (the paragraph after Eq. 15).  Either output may be NULL. */
+int orc_green_moments(const orc_lattice *L, double a, int start_part, const int32_t *sites,
+                      int n_sites, const int32_t *targets, int n_t, int M, cplx *a_e, cplx *a_h) {
+  orc_csr H = build_csr(L);
+  int *rows = (int *)malloc(sizeof(int) * 2 * (n_t > 0 ? n_t : 1));
+  for (int t = 0; t < n_t; ++t) {
+    rows[t] = 2 * targets[t];
+    rows[n_t + t] = 2 * targets[t] + 1;
+  }
+#pragma omp parallel
+  {
+    cplx *jprev = (cplx *)malloc(sizeof(cplx) * H.n);
+    cplx *jcur = (cplx *)malloc(sizeof(cplx) * H.n);
+    cplx *out = (cplx *)malloc(sizeof(cplx) * (size_t)M * 2 * (n_t > 0 ? n_t : 1));
+#pragma omp for schedule(dynamic, 1)
+    for (int c = 0; c < n_sites; ++c) {
+      chebyshev_rows(&H, a, 2 * sites[c] + start_part, M, rows, 2 * n_t, out, jprev, jcur);
+      for (int m = 0; m < M; ++m)
+        for (int t = 0; t < n_t; ++t) {
+          size_t o = ((size_t)c * M + m) * n_t + t;
+          if (a_e) a_e[o] = out[(size_t)m * 2 * n_t + t];
+          if (a_h) a_h[o] = out[(size_t)m * 2 * n_t + n_t + t];
+        }
+    }
+    free(jprev);
+    free(jcur);
+    free(out);
+  }
+  free(rows);
+  free_csr(&H);
+  return 0;
+}
+
+/* Retarded Green's function of gf1 from moments of the rescaled H~ = H/a:
+ *   G(E) = (1/a) (-2i / sqrt(1 - x^2)) sum_n g_n mom_n / (1 + delta_n0) exp(-i n arccos x),
+ * x = E/a, g_n the Jackson (kernel 0) or Lorentz (kernel 1, Eq. 16) kernel;
+ * its imaginary part is Eq. imag2 and its real part Eq. real1.  mom is laid
+ * out as orc_green_moments writes it, [(c*M + n)*n_t + t]; G is
+ * [(c*n_t + t)*n_E + e].  Energies must satisfy |E| < a. */
+int orc_green_function(const cplx *mom, int n_sites, int n_t, int M, double a, int kernel,
+                       double lambda, const double *energies, int n_E, cplx *G) {
+  double *g = (double *)malloc(sizeof(double) * M);
+  if (kernel == 0) orc_jackson(M, g);
+  else orc_lorentz(M, lambda, g);
+  for (int c = 0; c < n_sites; ++c)
+    for (int t = 0; t < n_t; ++t)
+      for (int e = 0; e < n_E; ++e) {
+        double x = energies[e] / a;
+        double th = acos(x);
+        cplx s = 0.0;
+        for (int m = 0; m < M; ++m) {
+          cplx am = mom[((size_t)c * M + m) * n_t + t] * g[m] / (m == 0 ? 2.0 : 1.0);
+          s += am * cexp(-I * (double)m * th);
+        }
+        G[((size_t)c * n_t + t) * n_E + e] = -2.0 * I * s / (sqrt(1.0 - x * x) * a);
+      }
+  free(g);
+  return 0;
+}
+
+/* Particle current along every bond with hopping (Eq. 20, read as the
+ * lattice continuity equation of the hopping term of Eq. 2 with e = hbar = 1):
+ *   J^s_{i->j} = 2 Im[ t_ij <c^dagger_{i s} c_{j s}> ],   j = i + d,
+ * the one-body density matrix taken from the damped series of
+ * f(E) = [1 - tanh(E/2T)]/2 in the Nambu basis (i != j):
+ *   spin up:   <c^dag_{i,up} c_{j,up}> = <e_j|f(H)|e_i> = -(1/2) sum_n C_n <e_j|T_n|e_i>
+ *   spin down: <c^dag_{i,dn} c_{j,dn}> = -<h_i|f(H)|h_j> = (1/2) conj(sum_n C_n <h_j|T_n|h_i>)
+ * spin selects the start vectors: 0 (up) starts from e_i, 1 (down) from h_i.
+ * J is [N*n_dirs]; J[i*n_dirs + d] is the current from i to i + d, 0 where
+ * an open edge cuts the bond. */
+int orc_bond_currents(const orc_lattice *L, double a, double T, int M, int K, int kernel,
+                      double lambda, int spin, double *J) {
+  int N = L->Lx * L->Ly, nd = L->n_dirs;
+  double *C = (double *)malloc(sizeof(double) * M);
+  orc_fold_coefficients(M, K, a, T, kernel, lambda, C);
+  orc_csr H = build_csr(L);
+#pragma omp parallel
+  {
+    cplx *jprev = (cplx *)malloc(sizeof(cplx) * H.n);
+    cplx *jcur = (cplx *)malloc(sizeof(cplx) * H.n);
+    cplx *out = (cplx *)malloc(sizeof(cplx) * (size_t)M * nd);
+    int rows[8];
+#pragma omp for schedule(dynamic, 1)
+    for (int i = 0; i < N; ++i) {
+      for (int d = 0; d < nd; ++d) {
+        int j = orc_neighbour(L, i, d);
+        rows[d] = j >= 0 ? 2 * j + spin : -1;
+      }
+      chebyshev_rows(&H, a, 2 * i + spin, M, rows, nd, out, jprev, jcur);
+      for (int d = 0; d < nd; ++d) {
+        cplx k = 0.0;
+        for (int m = 0; m < M; ++m) k += C[m] * out[(size_t)m * nd + d];
+        cplx rho = (spin == 0) ? -0.5 * k : 0.5 * conj(k);
+        J[(size_t)i * nd + d] = rows[d] >= 0 ? 2.0 * cimag(L->hop[(size_t)i * nd + d] * rho) : 0.0;
+      }
+    }
+    free(jprev);
+    free(jcur);
+    free(out);
+  }
+  free_csr(&H);
+  free(C);
   return 0;
 }
 

@@ -21,6 +21,11 @@ Functions and the passages of arXiv:1007.1609 they follow:
 * ``scf`` -- the self-consistency loop described after Eq. 20.
 * ``jacobi_eigh`` -- exact diagonalisation (cyclic Jacobi), an independent check.
 * ``scf_map_gradient`` -- reverse mode of one self-consistency map.
+* ``green_moments`` -- Eq. 15 read at arbitrary target sites (a^{11}, a^{12}
+  of Eqs. 11 and coeff2 for every target from one recursion).
+* ``green_function`` -- the full retarded G(E) of gf1 (imag2 + real1).
+* ``bond_currents`` -- Eq. 20 read as the continuity equation of the hopping
+  term, from the damped series of the Fermi function.
 """
 from __future__ import annotations
 
@@ -91,6 +96,9 @@ def _load():
             lib.orc_jacobi_eigh.argtypes = [I, P, P, P, D, I]
             lib.orc_scf_map_gradient.argtypes = [P, D, P, I, P, P, P, P]
             lib.orc_neighbour.argtypes = [P, I, I]
+            lib.orc_green_moments.argtypes = [P, D, I, P, I, P, I, I, P, P]
+            lib.orc_green_function.argtypes = [P, I, I, I, D, I, D, P, I, P]
+            lib.orc_bond_currents.argtypes = [P, D, D, I, I, I, D, I, P]
             lib.orc_num_threads.restype = I
             _lib = lib
     return _lib
@@ -298,6 +306,42 @@ def scf_map_gradient(lat: Lattice, a: float, C, w):
     _load().orc_scf_map_gradient(ctypes.byref(c), float(a), _ptr(C), C.size, _ptr(w),
                                  _ptr(g_eps), _ptr(g_hop), _ptr(g_delta))
     return g_eps, g_hop.reshape(lat.N, lat.n_dirs), g_delta
+
+
+def green_moments(lat: Lattice, a: float, sites, targets, M: int, start_part: int = 0):
+    """Returns (a_e, a_h), each [n_sites, M, n_targets] complex128:
+    a_e[c, n, t] = <e_t|T_n(H/a)|j_0>, a_h[c, n, t] = <h_t|T_n(H/a)|j_0>, with
+    j_0 = e_i (start_part 0) or h_i (start_part 1), i = sites[c]."""
+    sites = np.ascontiguousarray(sites, dtype=np.int32)
+    targets = np.ascontiguousarray(targets, dtype=np.int32)
+    a_e = np.zeros((sites.size, M, targets.size), dtype=np.complex128)
+    a_h = np.zeros_like(a_e)
+    c = lat._c()
+    _load().orc_green_moments(ctypes.byref(c), float(a), int(start_part), _ptr(sites), sites.size,
+                              _ptr(targets), targets.size, M, _ptr(a_e), _ptr(a_h))
+    return a_e, a_h
+
+
+def green_function(mom, a: float, energies, kernel: int = 0, lam: float = 0.0):
+    """G(E) of gf1 from moments [n_sites, M, n_t]; returns [n_sites, n_t, n_E] complex."""
+    mom = np.ascontiguousarray(mom, dtype=np.complex128)
+    energies = np.ascontiguousarray(energies, dtype=np.float64)
+    ns, M, nt = mom.shape
+    G = np.zeros((ns, nt, energies.size), dtype=np.complex128)
+    _load().orc_green_function(_ptr(mom), ns, nt, M, float(a), int(kernel), float(lam),
+                               _ptr(energies), energies.size, _ptr(G))
+    return G
+
+
+def bond_currents(lat: Lattice, a: float, T: float, M: int, K: int, kernel: int = 0, lam: float = 0.0,
+                  spin: int = 0):
+    """Per-spin particle current J[i, d] from site i to i + d (Eq. 20);
+    spin 0 from the electron start vectors, 1 from the hole start vectors."""
+    J = np.zeros(lat.N * lat.n_dirs)
+    c = lat._c()
+    _load().orc_bond_currents(ctypes.byref(c), float(a), float(T), M, K, int(kernel), float(lam),
+                              int(spin), _ptr(J))
+    return J.reshape(lat.N, lat.n_dirs)
 
 
 def num_threads() -> int:
