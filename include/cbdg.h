@@ -127,6 +127,52 @@ cbdg_status cbdg_ldos(cbdg_lattice *lat, const int32_t *sites, int32_t n_sites, 
                       int32_t kernel, double lambda, const double *energies, int32_t n_E,
                       float *ldos);
 
+/* Nonlocal Chebyshev moments: one direct recursion (Eq. 15) per start site
+ * i = sites[c], j_0 = e_i (the |c^dagger_{i,up}> of Eq. 15), read at every
+ * target site t = targets[k] (the paragraph after Eq. 15: one recursion gives
+ * G^{1 alpha}_{t i} for all t and alpha):
+ *   a11[(c*M + n)*n_targets + k] = <e_t | T_n(H~) | e_i>   (a^{11}_n(t, i) (1 + delta_n0), Eq. 11)
+ *   a12[(c*M + n)*n_targets + k] = <h_t | T_n(H~) | e_i>   (a^{12}_n(t, i) (1 + delta_n0), Eq. coeff2)
+ * for n < M.  Any lattice kind (the recursion runs on complex vectors; a
+ * real lattice gets complex copies of its parameters).  Arrays host or
+ * device; sites and targets may repeat; either output may be NULL.  M >= 2.
+ * Errors: INVALID_ARG (also an index outside 0..N-1), SPECTRUM (a moment
+ * above 1 in magnitude), OOM, CUDA. */
+cbdg_status cbdg_green_moments(cbdg_lattice *lat, const int32_t *sites, int32_t n_sites,
+                               const int32_t *targets, int32_t n_targets, int32_t M,
+                               cbdg_complex *a11, cbdg_complex *a12);
+
+/* Retarded Green's functions of Eq. gf1 (imaginary part Eq. imag2, real part
+ * Eq. real1) at absolute energies E (|E| < a) from the moments of
+ * cbdg_green_moments:
+ *   G11[(c*n_targets + k)*n_E + e] = (1/a) (-2i / sqrt(1 - x^2))
+ *                                    sum_n g_n a11_n / (1 + delta_n0) exp(-i n arccos x),  x = E_e/a,
+ * and G12 likewise from a12, g_n the Jackson kernel or the Lorentz kernel of
+ * Eq. 16 (lambda; broadening lambda/M in arccos x).  G11 at t = i is
+ * -pi times the LDOS of Eq. 17 in its imaginary part.  The sum over n is a
+ * complex FP64 contraction [M] x [M x n_E] per (site, target).  Arrays host
+ * or device; either output may be NULL.  Errors: INVALID_ARG (also for
+ * |E| >= a), SPECTRUM, OOM, CUDA. */
+cbdg_status cbdg_green_function(cbdg_lattice *lat, const int32_t *sites, int32_t n_sites,
+                                const int32_t *targets, int32_t n_targets, int32_t M, int32_t kernel,
+                                double lambda, const double *energies, int32_t n_E, cbdg_complex *G11,
+                                cbdg_complex *G12);
+
+/* Bond currents of Eq. 20, read as the continuity equation of the hopping
+ * term of Eq. 2 (particle current, e = hbar = 1), summed over both spins:
+ *   J[i*n_dirs + d] = sum_s 2 Im[t_{i,d} <c^dagger_{i,s} c_{j,s}>],  j = i + d,
+ * with the density matrix of the kernel-damped series of the Fermi function
+ * f(E) = [1 - tanh(E/2T)]/2 (the C_n of cbdg_order_parameter):
+ *   <c^dagger_{i,up} c_{j,up}> = -(1/2) sum_n C_n <e_j|T_n(H~)|e_i>   (i != j)
+ * and the equal spin-down term (particle-hole symmetry of Eq. 2).  J is the
+ * current from i to its neighbour along d (directions as in hop), 0 across an
+ * open edge; J_{i->j} = -J_{j->i}.  All N sites are start vectors (M - 2
+ * recursion steps each).  J host or device, [N*n_dirs].  Any lattice kind (a
+ * real lattice, with real t and Delta, carries none up to round-off).
+ * Errors: INVALID_ARG, SPECTRUM, OOM, CUDA. */
+cbdg_status cbdg_bond_currents(cbdg_lattice *lat, double T, int32_t M, int32_t kernel, double lambda,
+                               double *J);
+
 /* Dense contraction behind cbdg_ldos, on the tensor cores (tcgen05,
  * kind::tf32) with each operand split into TF32 head and tail (3 products,
  * about 21 significant bits; FP32 accumulation, re-based every 256 terms of

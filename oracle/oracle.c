@@ -573,11 +573,13 @@ int orc_green_function(const cplx *mom, int n_sites, int n_t, int M, double a, i
  *   spin up:   <c^dag_{i,up} c_{j,up}> = <e_j|f(H)|e_i> = -(1/2) sum_n C_n <e_j|T_n|e_i>
  *   spin down: <c^dag_{i,dn} c_{j,dn}> = -<h_i|f(H)|h_j> = (1/2) conj(sum_n C_n <h_j|T_n|h_i>)
  * spin selects the start vectors: 0 (up) starts from e_i, 1 (down) from h_i.
- * J is [N*n_dirs]; J[i*n_dirs + d] is the current from i to i + d, 0 where
- * an open edge cuts the bond. */
+ * The start sites are sites[0..n_sites), or all N in order when sites is
+ * NULL.  J is [n_sites*n_dirs]; J[c*n_dirs + d] is the current from
+ * i = sites[c] to i + d, 0 where an open edge cuts the bond. */
 int orc_bond_currents(const orc_lattice *L, double a, double T, int M, int K, int kernel,
-                      double lambda, int spin, double *J) {
-  int N = L->Lx * L->Ly, nd = L->n_dirs;
+                      double lambda, int spin, const int32_t *sites, int n_sites, double *J) {
+  int nd = L->n_dirs;
+  if (!sites) n_sites = L->Lx * L->Ly;
   double *C = (double *)malloc(sizeof(double) * M);
   orc_fold_coefficients(M, K, a, T, kernel, lambda, C);
   orc_csr H = build_csr(L);
@@ -588,7 +590,8 @@ int orc_bond_currents(const orc_lattice *L, double a, double T, int M, int K, in
     cplx *out = (cplx *)malloc(sizeof(cplx) * (size_t)M * nd);
     int rows[8];
 #pragma omp for schedule(dynamic, 1)
-    for (int i = 0; i < N; ++i) {
+    for (int c = 0; c < n_sites; ++c) {
+      int i = sites ? sites[c] : c;
       for (int d = 0; d < nd; ++d) {
         int j = orc_neighbour(L, i, d);
         rows[d] = j >= 0 ? 2 * j + spin : -1;
@@ -598,7 +601,7 @@ int orc_bond_currents(const orc_lattice *L, double a, double T, int M, int K, in
         cplx k = 0.0;
         for (int m = 0; m < M; ++m) k += C[m] * out[(size_t)m * nd + d];
         cplx rho = (spin == 0) ? -0.5 * k : 0.5 * conj(k);
-        J[(size_t)i * nd + d] = rows[d] >= 0 ? 2.0 * cimag(L->hop[(size_t)i * nd + d] * rho) : 0.0;
+        J[(size_t)c * nd + d] = rows[d] >= 0 ? 2.0 * cimag(L->hop[(size_t)i * nd + d] * rho) : 0.0;
       }
     }
     free(jprev);

@@ -98,7 +98,7 @@ def _load():
             lib.orc_neighbour.argtypes = [P, I, I]
             lib.orc_green_moments.argtypes = [P, D, I, P, I, P, I, I, P, P]
             lib.orc_green_function.argtypes = [P, I, I, I, D, I, D, P, I, P]
-            lib.orc_bond_currents.argtypes = [P, D, D, I, I, I, D, I, P]
+            lib.orc_bond_currents.argtypes = [P, D, D, I, I, I, D, I, P, I, P]
             lib.orc_num_threads.restype = I
             _lib = lib
     return _lib
@@ -334,14 +334,21 @@ def green_function(mom, a: float, energies, kernel: int = 0, lam: float = 0.0):
 
 
 def bond_currents(lat: Lattice, a: float, T: float, M: int, K: int, kernel: int = 0, lam: float = 0.0,
-                  spin: int = 0):
-    """Per-spin particle current J[i, d] from site i to i + d (Eq. 20);
-    spin 0 from the electron start vectors, 1 from the hole start vectors."""
-    J = np.zeros(lat.N * lat.n_dirs)
+                  spin: int = 0, sites=None):
+    """Per-spin particle current J[c, d] from site i = sites[c] (all sites in
+    order by default) to i + d (Eq. 20); spin 0 from the electron start
+    vectors, 1 from the hole start vectors."""
     c = lat._c()
+    if sites is None:
+        J = np.zeros(lat.N * lat.n_dirs)
+        _load().orc_bond_currents(ctypes.byref(c), float(a), float(T), M, K, int(kernel), float(lam),
+                                  int(spin), None, 0, _ptr(J))
+        return J.reshape(lat.N, lat.n_dirs)
+    sites = np.ascontiguousarray(sites, dtype=np.int32)
+    J = np.zeros(sites.size * lat.n_dirs)
     _load().orc_bond_currents(ctypes.byref(c), float(a), float(T), M, K, int(kernel), float(lam),
-                              int(spin), _ptr(J))
-    return J.reshape(lat.N, lat.n_dirs)
+                              int(spin), _ptr(sites), sites.size, _ptr(J))
+    return J.reshape(sites.size, lat.n_dirs)
 
 
 def num_threads() -> int:

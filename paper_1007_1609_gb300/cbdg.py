@@ -95,6 +95,9 @@ def load():
             "cbdg_moments": [P, P, I32, I32, P, P],
             "cbdg_order_parameter": [P, D, I32, D, I32, P, P],
             "cbdg_ldos": [P, P, I32, I32, I32, D, P, I32, P],
+            "cbdg_green_moments": [P, P, I32, P, I32, I32, P, P],
+            "cbdg_green_function": [P, P, I32, P, I32, I32, I32, D, P, I32, P, P],
+            "cbdg_bond_currents": [P, D, I32, I32, D, P],
             "cbdg_scf_step": [P, D, I32, D, P],
             "cbdg_get_delta": [P, P],
             "cbdg_set_delta": [P, P],
@@ -190,6 +193,20 @@ def cbdg_order_parameter(lat, T, kernel, lam, M, delta_out, n_out):
 def cbdg_ldos(lat, sites, n_sites, M, kernel, lam, energies, n_E, ldos):
     _check(load().cbdg_ldos(lat, _ptr(sites), int(n_sites), int(M), int(kernel), float(lam),
                             _ptr(energies), int(n_E), _ptr(ldos)))
+
+
+def cbdg_green_moments(lat, sites, n_sites, targets, n_targets, M, a11, a12):
+    _check(load().cbdg_green_moments(lat, _ptr(sites), int(n_sites), _ptr(targets), int(n_targets), int(M),
+                                     _ptr(a11), _ptr(a12)))
+
+
+def cbdg_green_function(lat, sites, n_sites, targets, n_targets, M, kernel, lam, energies, n_E, G11, G12):
+    _check(load().cbdg_green_function(lat, _ptr(sites), int(n_sites), _ptr(targets), int(n_targets), int(M),
+                                      int(kernel), float(lam), _ptr(energies), int(n_E), _ptr(G11), _ptr(G12)))
+
+
+def cbdg_bond_currents(lat, T, M, kernel, lam, J):
+    _check(load().cbdg_bond_currents(lat, float(T), int(M), int(kernel), float(lam), _ptr(J)))
 
 
 def cbdg_scf_step(lat, T, M, mix):
@@ -397,6 +414,7 @@ class Lattice:
         d.eps = _ptr(self._eps)
         d.mu = float(p.mu)
         d.n_dirs = int(self._hop.shape[-1]) if self._hop.ndim == 2 else int(self._hop.size // self.N)
+        self.n_dirs = int(d.n_dirs)
         d.hop = _ptr(self._hop)
         d.pairing = self.pairing
         d.coupling = float(p.coupling)
@@ -446,6 +464,32 @@ class Lattice:
         out = np.zeros((sites.size, energies.size), dtype=np.float32)
         cbdg_ldos(self.handle, sites, sites.size, M, KERNELS[kernel], lam, energies, energies.size, out)
         return out
+
+    def green_moments(self, sites, targets, M):
+        """(a11, a12), each [n_sites, M, n_targets] complex128: <e_t|T_n|e_i>, <h_t|T_n|e_i>."""
+        sites = np.ascontiguousarray(sites, dtype=np.int32)
+        targets = np.ascontiguousarray(targets, dtype=np.int32)
+        a11 = np.zeros((sites.size, M, targets.size), dtype=np.complex128)
+        a12 = np.zeros_like(a11)
+        cbdg_green_moments(self.handle, sites, sites.size, targets, targets.size, M, a11, a12)
+        return a11, a12
+
+    def green_function(self, sites, targets, M, energies, kernel="jackson", lam=0.0):
+        """(G11, G12), each [n_sites, n_targets, n_E] complex128 (Eq. gf1)."""
+        sites = np.ascontiguousarray(sites, dtype=np.int32)
+        targets = np.ascontiguousarray(targets, dtype=np.int32)
+        energies = np.ascontiguousarray(energies, dtype=np.float64)
+        G11 = np.zeros((sites.size, targets.size, energies.size), dtype=np.complex128)
+        G12 = np.zeros_like(G11)
+        cbdg_green_function(self.handle, sites, sites.size, targets, targets.size, M, KERNELS[kernel], lam,
+                            energies, energies.size, G11, G12)
+        return G11, G12
+
+    def bond_currents(self, T, M, kernel="jackson", lam=0.0):
+        """J [N, n_dirs]: current from site i to its neighbour along d, both spins (Eq. 20)."""
+        J = np.zeros((self.N, self.n_dirs))
+        cbdg_bond_currents(self.handle, T, M, KERNELS[kernel], lam, J)
+        return J
 
     def scf_step(self, T, M, mix):
         return cbdg_scf_step(self.handle, T, M, mix)

@@ -118,6 +118,7 @@ struct cbdg_lattice {
   DBuf eps, hop, delta, params, scal, flags, f, C, sites_all, sites_user;
   DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
   DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out, adj_fp;
+  DBuf params_c, g_acc, g_tgt, g_mom, g_w, g_out;  // nonlocal readout (green.cu)
   // options
   int K = 65536;
   int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0, fixed_a_pico = 0, wait_ms = 2000, stall = 0, autotune = 0, temporal = 0;
@@ -673,6 +674,105 @@ cbdg_status finish(cbdg_lattice *L) {
   return CBDG_OK;
 }
 
+// Direct recursion (Eq. 15) from e_i for the n_sites start sites of the
+// device list, every moment m < M read at n_t targets (device list, or NULL
+// for the neighbours of each start site along directions 0..n_t-1):
+//   acc[c*n_t + t] += C_m <e_t|j_m>               (when acc != NULL)
+//   a_e / a_h[(c*M + m)*n_t + t] = <e_t|j_m> / <h_t|j_m>   (when != NULL)
+// Runs on every lattice kind with the general complex kernel (bond fields
+// are zero for on-site pairing; a real lattice gets complex parameters of
+// its own).  prepare() must have run for the current Delta.
+cbdg_status run_targets(cbdg_lattice *L, const int32_t *sites, int n_sites, int M, const int32_t *targets,
+                        int n_t, double2 *acc, double2 *a_e, double2 *a_h) {
+  const void *params = L->params.p;
+  if (mode_of(L) == kReal) {
+    CK(L->params_c.ensure(static_cast<size_t>(L->N) * kCplxParamStride * elem_size(L)));
+    CK(launch_params_cplx(L->precision, L->N, L->Lx, L->n_dirs, L->pairing, L->eps.as<double>(), L->mu,
+                          L->hop.as<double2>(), L->delta.as<double2>(), L->scal.as<double>(),
+                          L->params_c.p, L->stream));
+    L->launches += 1;
+    params = L->params_c.p;
+  }
+  const size_t es = 2 * elem_size(L);
+  const size_t rows = 2 * static_cast<size_t>(L->N);
+  const int Wdef = slab_width_default_cplx(L->precision);
+  const bool w_ok = L->precision == CBDG_FP32_MIXED ? (L->slab_w == 2 || L->slab_w == 4 || L->slab_w == 8)
+                                                     : (L->slab_w == 1 || L->slab_w == 2 || L->slab_w == 4);
+  const int W = w_ok ? static_cast<int>(L->slab_w) : Wdef;
+  size_t cap;
+  if (L->ws_mb > 0) {
+    cap = static_cast<size_t>(L->ws_mb) << 20;
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    cap = static_cast<size_t>(0.6 * (fr + L->vec0.bytes + L->vec1.bytes));
+  }
+  int64_t max_cols = static_cast<int64_t>(cap) / static_cast<int64_t>(2 * rows * es);
+  max_cols = (max_cols / W) * W;
+  if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
+  if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for one column slab");
+  const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((n_sites + W - 1) / W) * W));
+  const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
+  for (int c0 = 0; c0 < n_sites; c0 += chunk) {
+    const int ncols = std::min(chunk, n_sites - c0);
+    const int ld = ((ncols + W - 1) / W) * W;
+    StepConfig cfg;
+    if (!plan_step_cplx(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
+                        static_cast<int>(L->depth), &cfg))
+      return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d with %d columns", L->Lx, ld);
+    L->last_cfg = cfg;
+    L->last_temporal = 1;
+    const size_t vbytes = rows * ld * es;
+    CK(L->vec0.ensure(vbytes));
+    CK(L->vec1.ensure(vbytes));
+    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 4 * ld * sizeof(double)));
+    CK(L->mu1.ensure(ld * sizeof(double)));
+    CK(L->dA.ensure(ld * sizeof(double2)));
+    CK(L->acc_n.ensure(ld * sizeof(double)));
+    CK(L->acc_d.ensure(ld * 4 * sizeof(double2)));
+    CK(cudaMemsetAsync(L->vec0.p, 0, vbytes, L->stream));
+    CK(cudaMemsetAsync(L->vec1.p, 0, vbytes, L->stream));
+    CK(launch_init_cplx(L->precision, L->Lx, L->Ly, L->px, L->py, L->n_dirs, L->pairing, ncols, W, sites + c0,
+                        L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
+                        L->scal.as<double>(), L->C.as<double>(), M, L->vec0.p, L->vec1.p, L->mu1.as<double>(),
+                        L->dA.as<double2>(), L->acc_n.as<double>(), L->acc_d.as<double2>(), nullptr, nullptr,
+                        1, L->stream));
+    L->launches += 1;
+    double2 *acc_c = acc ? acc + static_cast<size_t>(c0) * n_t : nullptr;
+    double2 *ae_c = a_e ? a_e + static_cast<size_t>(c0) * M * n_t : nullptr;
+    double2 *ah_c = a_h ? a_h + static_cast<size_t>(c0) * M * n_t : nullptr;
+    for (int m = 0; m < 2 && m < M; ++m) {
+      CK(launch_target_gather(L->precision, m, M, L->Lx, L->Ly, L->px, L->py, ncols, W, sites + c0, n_t, targets,
+                              m == 0 ? L->vec0.p : L->vec1.p, L->C.as<double>(), acc_c, ae_c, ah_c,
+                              L->flags.as<unsigned int>(), tol, L->stream));
+      L->launches += 1;
+    }
+    StepArgs a;
+    a.params = params;
+    a.partials = L->partials.as<double>();
+    a.flags = L->flags.as<unsigned int>();
+    a.wait_ns = static_cast<unsigned long long>(L->wait_ms) * 1000000ull;
+    a.stall_tx = L->stall ? 16u : 0u;
+    a.Lx = L->Lx;
+    a.Ly = L->Ly;
+    a.ld = ld;
+    a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+    void *cur = L->vec1.p, *prev = L->vec0.p;
+    // step n turns (j_{n-1}, j_n) into j_{n+1}, written over j_{n-1}
+    for (int n = 1; n + 1 < M; ++n) {
+      a.cur = cur;
+      a.prev = prev;
+      CK(launch_step_cplx(L->precision, L->n_dirs == 8, 1, a, cfg, L->stream));
+      CK(launch_target_gather(L->precision, n + 1, M, L->Lx, L->Ly, L->px, L->py, ncols, W, sites + c0, n_t,
+                              targets, prev, L->C.as<double>(), acc_c, ae_c, ah_c, L->flags.as<unsigned int>(),
+                              tol, L->stream));
+      L->launches += 2;
+      std::swap(cur, prev);
+    }
+  }
+  return CBDG_OK;
+}
+
 cbdg_status order_parameter_impl(cbdg_lattice *L, double T, int kernel, double lambda, int M) {
   if (!(T >= 0.0) || !isfinite(T)) return fail(CBDG_ERR_INVALID_ARG, "T must be finite and >= 0");
   if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
@@ -967,7 +1067,8 @@ cbdg_status cbdg_destroy(cbdg_lattice *L) {
   DBuf *bufs[] = {&L->eps,     &L->hop,   &L->delta, &L->params,  &L->scal,  &L->flags,
                   &L->f,       &L->C,     &L->sites_all, &L->sites_user, &L->vec0, &L->vec1,
                   &L->partials, &L->mu1,  &L->dA,    &L->acc_n,   &L->acc_d, &L->dout,
-                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b, &L->adj_ck, &L->adj_seg, &L->adj_lam, &L->adj_part, &L->adj_w, &L->adj_out, &L->adj_fp};
+                  &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b, &L->adj_ck, &L->adj_seg, &L->adj_lam, &L->adj_part, &L->adj_w, &L->adj_out, &L->adj_fp,
+                  &L->params_c, &L->g_acc, &L->g_tgt, &L->g_mom, &L->g_w, &L->g_out};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
   L->drop_graph();
@@ -1089,6 +1190,144 @@ cbdg_status cbdg_ldos(cbdg_lattice *L, const int32_t *sites, int32_t n_sites, in
                             L->flags.as<unsigned int>(), L->stream));
   L->launches += 3;
   if (dst != ldos) CK(deliver(L, ldos, dD, d_bytes));
+  return finish(L);
+}
+
+namespace {
+cbdg_status check_kernel(int32_t kernel, double lambda) {
+  if (kernel != CBDG_JACKSON && kernel != CBDG_LORENTZ)
+    return fail(CBDG_ERR_INVALID_ARG, "unknown kernel %d", kernel);
+  if (kernel == CBDG_LORENTZ && !(lambda > 0.0 && isfinite(lambda)))
+    return fail(CBDG_ERR_INVALID_ARG, "Lorentz kernel needs lambda > 0");
+  return CBDG_OK;
+}
+
+// Validated device copies of a start-site list and a target list.
+cbdg_status upload_pairs(cbdg_lattice *L, const int32_t *sites, int32_t n_sites, const int32_t *targets,
+                         int32_t n_t) {
+  std::vector<int32_t> hs, ht;
+  cudaError_t e = host_copy(sites, n_sites, hs);
+  if (e != cudaSuccess) return cuda_fail(e, "reading sites");
+  e = host_copy(targets, n_t, ht);
+  if (e != cudaSuccess) return cuda_fail(e, "reading targets");
+  for (int c = 0; c < n_sites; ++c)
+    if (hs[c] < 0 || hs[c] >= L->N) return fail(CBDG_ERR_INVALID_ARG, "site %d out of range", hs[c]);
+  for (int t = 0; t < n_t; ++t)
+    if (ht[t] < 0 || ht[t] >= L->N) return fail(CBDG_ERR_INVALID_ARG, "target %d out of range", ht[t]);
+  CK(L->sites_user.ensure(n_sites * sizeof(int32_t)));
+  CK(L->g_tgt.ensure(n_t * sizeof(int32_t)));
+  CK(cudaMemcpyAsync(L->sites_user.p, hs.data(), n_sites * sizeof(int32_t), cudaMemcpyHostToDevice, L->stream));
+  CK(cudaMemcpyAsync(L->g_tgt.p, ht.data(), n_t * sizeof(int32_t), cudaMemcpyHostToDevice, L->stream));
+  CK(cudaStreamSynchronize(L->stream));  // hs, ht live on this stack frame
+  return CBDG_OK;
+}
+}  // namespace
+
+cbdg_status cbdg_bond_currents(cbdg_lattice *L, double T, int32_t M, int32_t kernel, double lambda, double *J) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  if (!(T >= 0.0) || !isfinite(T)) return fail(CBDG_ERR_INVALID_ARG, "T must be finite and >= 0");
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  if ((st = check_kernel(kernel, lambda)) != CBDG_OK) return st;
+  if (!J) return fail(CBDG_ERR_INVALID_ARG, "J is NULL");
+  if ((st = prepare(L, T, kernel, lambda, M, true)) != CBDG_OK) return st;
+  const size_t nj = static_cast<size_t>(L->N) * L->n_dirs;
+  CK(L->g_acc.ensure(nj * sizeof(double2)));
+  CK(cudaMemsetAsync(L->g_acc.p, 0, nj * sizeof(double2), L->stream));
+  st = run_targets(L, L->sites_all.as<int32_t>(), L->N, M, nullptr, L->n_dirs, L->g_acc.as<double2>(), nullptr,
+                   nullptr);
+  if (st != CBDG_OK) return st;
+  double *dst = J;
+  if (!is_device_ptr(J)) {
+    CK(L->g_out.ensure(nj * sizeof(double)));
+    dst = L->g_out.as<double>();
+  }
+  CK(launch_bond_currents(L->N, L->n_dirs, L->Lx, L->Ly, L->px, L->py, L->hop.as<double2>(),
+                          L->g_acc.as<double2>(), dst, L->stream));
+  L->launches += 1;
+  if (dst != J) CK(deliver(L, J, dst, nj * sizeof(double)));
+  return finish(L);
+}
+
+cbdg_status cbdg_green_moments(cbdg_lattice *L, const int32_t *sites, int32_t n_sites, const int32_t *targets,
+                               int32_t n_targets, int32_t M, cbdg_complex *a11, cbdg_complex *a12) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  if (n_sites < 0 || n_targets < 0 || (n_sites > 0 && !sites) || (n_targets > 0 && !targets))
+    return fail(CBDG_ERR_INVALID_ARG, "bad site or target list");
+  if (n_sites == 0 || n_targets == 0 || (!a11 && !a12)) return CBDG_OK;
+  if ((st = upload_pairs(L, sites, n_sites, targets, n_targets)) != CBDG_OK) return st;
+  if ((st = prepare(L, 0.0, CBDG_JACKSON, 0.0, M, false)) != CBDG_OK) return st;
+  const size_t n = static_cast<size_t>(n_sites) * M * n_targets;
+  double2 *de = a11 && is_device_ptr(a11) ? reinterpret_cast<double2 *>(a11) : nullptr;
+  double2 *dh = a12 && is_device_ptr(a12) ? reinterpret_cast<double2 *>(a12) : nullptr;
+  const bool stage_e = a11 && !de, stage_h = a12 && !dh;
+  if (stage_e || stage_h) {
+    CK(L->g_mom.ensure((stage_e + stage_h) * n * sizeof(double2)));
+    if (stage_e) de = L->g_mom.as<double2>();
+    if (stage_h) dh = L->g_mom.as<double2>() + (stage_e ? n : 0);
+  }
+  st = run_targets(L, L->sites_user.as<int32_t>(), n_sites, M, L->g_tgt.as<int32_t>(), n_targets, nullptr, de, dh);
+  if (st != CBDG_OK) return st;
+  if (stage_e) CK(deliver(L, a11, de, n * sizeof(double2)));
+  if (stage_h) CK(deliver(L, a12, dh, n * sizeof(double2)));
+  return finish(L);
+}
+
+cbdg_status cbdg_green_function(cbdg_lattice *L, const int32_t *sites, int32_t n_sites, const int32_t *targets,
+                                int32_t n_targets, int32_t M, int32_t kernel, double lambda,
+                                const double *energies, int32_t n_E, cbdg_complex *G11, cbdg_complex *G12) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  if ((st = check_kernel(kernel, lambda)) != CBDG_OK) return st;
+  if (n_sites < 0 || n_targets < 0 || n_E < 0 || (n_sites > 0 && !sites) || (n_targets > 0 && !targets) ||
+      (n_E > 0 && !energies))
+    return fail(CBDG_ERR_INVALID_ARG, "bad site, target or energy list");
+  if (n_sites == 0 || n_targets == 0 || n_E == 0 || (!G11 && !G12)) return CBDG_OK;
+  std::vector<double> he;
+  cudaError_t e = host_copy(energies, n_E, he);
+  if (e != cudaSuccess) return cuda_fail(e, "reading energies");
+  if ((st = upload_pairs(L, sites, n_sites, targets, n_targets)) != CBDG_OK) return st;
+  if ((st = prepare(L, 0.0, CBDG_JACKSON, 0.0, M, false)) != CBDG_OK) return st;
+  double a = 0.0;
+  CK(cudaMemcpyAsync(&a, L->scal.as<double>() + kScalA, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  for (int k = 0; k < n_E; ++k)
+    if (!(fabs(he[k]) < a))
+      return fail(CBDG_ERR_INVALID_ARG, "energy %g outside the rescaled band (-a, a), a = %g", he[k], a);
+  const size_t nm = static_cast<size_t>(n_sites) * M * n_targets;
+  const size_t ng = static_cast<size_t>(n_sites) * n_targets * n_E;
+  const int parts = (G11 ? 1 : 0) + (G12 ? 1 : 0);
+  CK(L->g_mom.ensure(parts * nm * sizeof(double2)));
+  double2 *me = G11 ? L->g_mom.as<double2>() : nullptr;
+  double2 *mh = G12 ? L->g_mom.as<double2>() + (G11 ? nm : 0) : nullptr;
+  st = run_targets(L, L->sites_user.as<int32_t>(), n_sites, M, L->g_tgt.as<int32_t>(), n_targets, nullptr, me, mh);
+  if (st != CBDG_OK) return st;
+  auto r256 = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+  const size_t w_bytes = static_cast<size_t>(n_E) * M * sizeof(double2);
+  const size_t e_bytes = static_cast<size_t>(n_E) * sizeof(double);
+  const size_t g_bytes = ng * sizeof(double2);
+  CK(L->g_w.ensure(r256(w_bytes) + r256(e_bytes) + 2 * r256(g_bytes)));
+  unsigned char *wb = L->g_w.as<unsigned char>();
+  double2 *W = reinterpret_cast<double2 *>(wb);
+  double *dE = reinterpret_cast<double *>(wb + r256(w_bytes));
+  double2 *gbuf[2] = {reinterpret_cast<double2 *>(wb + r256(w_bytes) + r256(e_bytes)),
+                      reinterpret_cast<double2 *>(wb + r256(w_bytes) + r256(e_bytes) + r256(g_bytes))};
+  CK(cudaMemcpyAsync(dE, he.data(), e_bytes, cudaMemcpyHostToDevice, L->stream));
+  CK(launch_green_weights(n_E, M, kernel, lambda, dE, L->scal.as<double>(), W, L->stream));
+  L->launches += 1;
+  cbdg_complex *outs[2] = {G11, G12};
+  const double2 *moms[2] = {me, mh};
+  for (int p = 0; p < 2; ++p) {
+    if (!outs[p]) continue;
+    double2 *dst = is_device_ptr(outs[p]) ? reinterpret_cast<double2 *>(outs[p]) : gbuf[p];
+    CK(launch_green_contract(n_sites, n_targets, M, n_E, moms[p], W, dst, L->stream));
+    L->launches += 1;
+    if (dst != reinterpret_cast<double2 *>(outs[p])) CK(deliver(L, outs[p], dst, g_bytes));
+  }
+  CK(cudaStreamSynchronize(L->stream));  // he is read by the copy above
   return finish(L);
 }
 

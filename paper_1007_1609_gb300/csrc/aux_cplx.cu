@@ -10,22 +10,11 @@ namespace {
 
 inline int blocks(long long n, int t) { return static_cast<int>((n + t - 1) / t); }
 
-__device__ __forceinline__ int nbr(int Lx, int Ly, int px, int py, int s, int d) {
-  const int DX[8] = {1, -1, 0, 0, 1, -1, 1, -1}, DY[8] = {0, 0, 1, -1, 1, -1, -1, 1};
-  int x = s % Lx + DX[d], y = s / Lx + DY[d];
-  if (x < 0 || x >= Lx) {
-    if (!px) return -1;
-    x = (x + Lx) % Lx;
-  }
-  if (y < 0 || y >= Ly) {
-    if (!py) return -1;
-    y = (y + Ly) % Ly;
-  }
-  return x + Lx * y;
-}
-
-// [0] 2(eps-mu)/a  [2,3] 2 Delta_i/a  [4+2d, 5+2d] 2 t_{i,d}/a (d < 8)
-// [20+2d, 21+2d] 2 Delta_{i,d}/a (d < 4, bond pairing); the rest 0.
+// Field-major parameters: complex field k of site (x, y) at
+// ((y * kCplxFields + k) * Lx + x) * 2:  kCpE 2(eps - mu)/a, kCpDelta 2 Delta_i/a
+// (on-site pairing), kCpHop + k 2 t_{i,d}/a for the forward directions
+// d = 0, 2, 4, 7, kCpBond + k 2 Delta_{i,d}/a for d = 0, 2 (bond pairing);
+// the rest 0.
 template <typename S>
 __global__ void params_cplx_kernel(int N, int Lx, int n_dirs, int pairing, const double *eps, double mu,
                                    const double2 *hop, const double2 *delta, const double *scal,
@@ -93,7 +82,7 @@ __global__ void init_cplx_kernel(int Lx, int Ly, int px, int py, int n_dirs, int
     put(j1, rows, W, Lx, i, 1, b, dl.x / a, -dl.y / a);
   }
   for (int d = 0; d < n_dirs; ++d) {
-    const int j = nbr(Lx, Ly, px, py, i, d);
+    const int j = neighbour_site(Lx, Ly, px, py, i, d);
     if (j < 0) continue;
     const double2 t = hop[static_cast<size_t>(i) * n_dirs + d];
     put(j1, rows, W, Lx, j, 0, b, -t.x / a, t.y / a);
@@ -185,7 +174,7 @@ __global__ void gather_kernel(int m, int M, int Lx, int Ly, int px, int py, int 
   if (mu_ee) mu_ee[static_cast<size_t>(b) * M + m] = ee.x;
   if (mu_eh) mu_eh[(static_cast<size_t>(b) * M + m) * 5] = hh;
   for (int d = 0; d < 4; ++d) {
-    const int jn = nbr(Lx, Ly, px, py, i, d);
+    const int jn = neighbour_site(Lx, Ly, px, py, i, d);
     const double2 h = jn >= 0 ? get(jn, 1) : make_double2(0.0, 0.0);
     double2 ab = acc_b[static_cast<size_t>(b) * 4 + d];
     ab.x += cm * h.x;
@@ -204,7 +193,7 @@ __global__ void finalize_bond_kernel(int N, int Lx, int Ly, int px, int py, doub
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   for (int d = 0; d < 4; ++d) {
-    const int j = nbr(Lx, Ly, px, py, i, d);
+    const int j = neighbour_site(Lx, Ly, px, py, i, d);
     double2 r = make_double2(0.0, 0.0);
     if (j >= 0) {
       const double2 f = acc_b[static_cast<size_t>(i) * 4 + d];

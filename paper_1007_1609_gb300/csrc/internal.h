@@ -65,6 +65,23 @@ __host__ __device__ inline size_t blocked_index(size_t r, size_t b, size_t rows,
   return (b / W) * rows * W + r * W + (b % W);
 }
 
+// Neighbour of site s = x + Lx*y along direction d (0:+x 1:-x 2:+y 3:-y
+// 4:+x+y 5:-x-y 6:+x-y 7:-x+y), or -1 where an open edge cuts the bond.
+__host__ __device__ inline int neighbour_site(int Lx, int Ly, int px, int py, int s, int d) {
+  const int dx = (d == 0 || d == 4 || d == 6) ? 1 : (d == 1 || d == 5 || d == 7) ? -1 : 0;
+  const int dy = (d == 2 || d == 4 || d == 7) ? 1 : (d == 3 || d == 5 || d == 6) ? -1 : 0;
+  int x = s % Lx + dx, y = s / Lx + dy;
+  if (x < 0 || x >= Lx) {
+    if (!px) return -1;
+    x = (x + Lx) % Lx;
+  }
+  if (y < 0 || y >= Ly) {
+    if (!py) return -1;
+    y = (y + Ly) % Ly;
+  }
+  return x + Lx * y;
+}
+
 // Recursion step for real on-site (s-wave) lattices with nearest-neighbour
 // hopping.  precision 0: double, 1: float.
 cudaError_t launch_step_real(int precision, const StepArgs &a, const StepConfig &cfg,
@@ -121,6 +138,20 @@ cudaError_t launch_gather(int precision, int m, int M, int Lx, int Ly, int px, i
 cudaError_t launch_finalize_bond(int N, int Lx, int Ly, int px, int py, double V,
                                  const double *acc_n, const double2 *acc_b, double2 *dout,
                                  double *nout, cudaStream_t s);
+
+// ---- nonlocal readout, bond currents, Green's function (green.cu) -----------
+// Moment m at every (column, target) of j_m; targets == NULL: the neighbours
+// of each column's start site along directions 0..n_t-1.  Any output may be NULL.
+cudaError_t launch_target_gather(int precision, int m, int M, int Lx, int Ly, int px, int py, int ncols,
+                                 int W, const int32_t *sites, int n_t, const int32_t *targets,
+                                 const void *j, const double *C, double2 *acc, double2 *a_e,
+                                 double2 *a_h, unsigned int *flags, double tol, cudaStream_t s);
+cudaError_t launch_bond_currents(int N, int n_dirs, int Lx, int Ly, int px, int py, const double2 *hop,
+                                 const double2 *K, double *J, cudaStream_t s);
+cudaError_t launch_green_weights(int n_E, int M, int kernel, double lambda, const double *energies,
+                                 const double *scal, double2 *W, cudaStream_t s);
+cudaError_t launch_green_contract(int n_sites, int n_t, int M, int n_E, const double2 *mom,
+                                  const double2 *W, double2 *G, cudaStream_t s);
 
 // ---- auxiliary kernels (aux.cu) -------------------------------------------
 cudaError_t launch_gershgorin(int N, int n_dirs, int pairing, int Lx, int Ly, int px, int py,

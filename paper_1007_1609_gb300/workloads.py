@@ -149,6 +149,33 @@ def dwave_vortex(L=256, M=2048, flux_quanta=2.0, n_energies=512):
                     extra={"energy_frac": np.linspace(-0.9, 0.9, n_energies)})
 
 
+def currents_dwave(L=128, M=512, flux_quanta=2.0, xi=3.0):
+    """Bond-current workload: the d-wave vortex lattice (periodic L x L, t=1,
+    t'=-0.3, mu=-1, V=1.5, T=0.005, uniform field of ``flux_quanta`` h/2e)
+    with ``flux_quanta`` vortices imprinted on the initial bonds: vortex k at
+    r_k on a diagonal, each bond Delta_{ij} = +-0.5 (x / y bonds) times
+    prod_k tanh(|r_m - r_k| / xi) exp(i arg(r_m - r_k)) at the bond midpoint
+    r_m (the neighbour taken unwrapped across the seam)."""
+    N = L * L
+    hop = square_hops(L, L, 1, 1, t=1.0, tp=-0.3, flux_quanta=flux_quanta)
+    nv = max(1, int(round(flux_quanta)))
+    cores = [((k + 0.5) * L / nv + 0.25, (k + 0.5) * L / nv + 0.25) for k in range(nv)]
+    d0 = np.zeros((N, 4), dtype=np.complex128)
+    for s in range(N):
+        x, y = s % L, s // L
+        for d in (0, 2):
+            mx, my = x + 0.5 * DX[d], y + 0.5 * DY[d]
+            z = 0.5 if d == 0 else -0.5
+            for cx, cy in cores:
+                r = np.hypot(mx - cx, my - cy)
+                z *= np.tanh(r / xi) * np.exp(1j * np.arctan2(my - cy, mx - cx))
+            j = ((x + DX[d]) % L) + L * ((y + DY[d]) % L)
+            d0[s, d] = z
+            d0[j, d ^ 1] = z
+    return _problem(f"currents_dwave_{L}x{L}_M{M}", L, 1, np.zeros(N), -1.0, hop, BOND, 1.5, d0,
+                    0.005, M, mix=0.5, tol=1e-6, max_iter=100)
+
+
 def ensemble(n_samples=256, sides=(32, 48, 64, 80, 96), M=512, seed_sizes=1003, seed_eps=1004):
     """Ensemble of independent disordered s-wave lattices: sides drawn
     uniformly from ``sides`` and W ~ U[0.5, 2] per sample (seed_sizes),
