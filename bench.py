@@ -494,6 +494,37 @@ def leg_tiny(cbdg, wl, stream):
     return out
 
 
+def leg_currents(cbdg, wl, torch, stream, hbm):
+    """Bond currents (Eq. 20) on the vortex-imprinted d-wave lattice, 128x128,
+    M = 512, FP32 complex vectors: all 16384 sites as start vectors, 510
+    direct recursion steps each plus the nearest-bond readout.  Event-timed
+    whole call and per-step kernel time (CBDG_OPT_PROFILE)."""
+    p = wl.currents_dwave(128, 512)
+    lat = cbdg.Lattice(p, precision="fp32", stream=stream)
+    lat.bond_currents(p.T, 8)  # buffers and tables
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
+    cbdg.cbdg_profile_read(lat.handle, reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    J = lat.bond_currents(p.T, p.M)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sms, sn, sb = cbdg.cbdg_profile_read(lat.handle)
+    tile = lat.last_tile()
+    lat.close()
+    units = p.N * (p.M - 2)
+    return {"lattice": "128x128 periodic, t'=-0.3, 2 h/2e flux, 2 imprinted vortices, bond pairing, complex64",
+            "M": p.M, "call_ms": ms, "vector_steps_per_s": units / (ms * 1e-3),
+            "step_launches": sn, "avg_step_ms": sms / max(sn, 1), "step_share_of_call": sms / ms,
+            "tile": list(tile), "max_abs_J": float(abs(J).max()),
+            "roofline": {"bound": "hbm", "achieved": sb / (sms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": sb / (sms * 1e-3) / 1e9 / hbm,
+                         "note": "step_cplx_kernel (direct mode), 3 vector streams of 2N x N x 8 B per step"}}
+
+
 def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=256):
     """Other hot-path stages at their workload sizes (not the headline)."""
     legs = {
@@ -502,6 +533,7 @@ def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=25
         "dwave": lambda: leg_dwave(cbdg, wl, stream, hbm, columns),
         "ensemble": lambda: leg_ensemble(cbdg, wl, stream, samples),
         "adjoint": lambda: leg_adjoint(cbdg, wl, stream),
+        "currents": lambda: leg_currents(cbdg, wl, torch, stream, hbm),
     }
     return {name: fn() for name, fn in legs.items() if only is None or only == name}
 
@@ -552,7 +584,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint"],
+    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint", "currents"],
                     help="measure only this stage and print its record (profiling runs)")
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")

@@ -758,16 +758,36 @@ cbdg_status run_targets(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     a.ld = ld;
     a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
     void *cur = L->vec1.p, *prev = L->vec0.p;
+    const int steps = M - 2;
+    if (L->profile && static_cast<int>(L->events.size()) < 2 * steps) {
+      for (int k = static_cast<int>(L->events.size()); k < 2 * steps; ++k) {
+        cudaEvent_t ev;
+        CK(cudaEventCreate(&ev));
+        L->events.push_back(ev);
+      }
+    }
     // step n turns (j_{n-1}, j_n) into j_{n+1}, written over j_{n-1}
     for (int n = 1; n + 1 < M; ++n) {
       a.cur = cur;
       a.prev = prev;
+      if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1)], L->stream));
       CK(launch_step_cplx(L->precision, L->n_dirs == 8, 1, a, cfg, L->stream));
+      if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1) + 1], L->stream));
       CK(launch_target_gather(L->precision, n + 1, M, L->Lx, L->Ly, L->px, L->py, ncols, W, sites + c0, n_t,
                               targets, prev, L->C.as<double>(), acc_c, ae_c, ah_c, L->flags.as<unsigned int>(),
                               tol, L->stream));
       L->launches += 2;
       std::swap(cur, prev);
+    }
+    if (L->profile && steps > 0) {
+      CK(cudaStreamSynchronize(L->stream));
+      for (int k = 0; k < steps; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, L->events[2 * k], L->events[2 * k + 1]));
+        L->prof_ms += ms;
+        L->prof_bytes += 3.0 * static_cast<double>(vbytes);
+      }
+      L->prof_launches += steps;
     }
   }
   return CBDG_OK;

@@ -102,7 +102,7 @@ def test_bond_currents_match_oracle(case, precision):
         assert np.abs(ref).max() > 1e-3
 
 
-@pytest.mark.parametrize("opts", [{"chunk": 40}, {"chunk": 24, "slab_w": 2}, {"depth": 1}])
+@pytest.mark.parametrize("opts", [{"column_chunk": 40}, {"column_chunk": 24, "slab_width": 2}, {"pipeline_depth": 1}])
 def test_currents_with_column_chunks_and_tiles(opts):
     """Several column chunks (ragged last chunk) and other tiles give the same
     currents (the accumulators are indexed by start site)."""
@@ -206,7 +206,7 @@ def test_normal_state_currents_conserved_64():
     p.delta0 = np.zeros(p.N, dtype=np.complex128)
     lat = gpu_lattice(p, "fp64")
     J = lat.bond_currents(p.T, M)
-    assert np.abs(J).max() > 1e-3
+    assert np.abs(J).max() > 1e-5          # a weak field: 4 h/2e through 4096 plaquettes
     assert np.abs(J.sum(1)).max() < 1e-11
     Lx = p.Lx
     x, y = np.arange(p.N) % Lx, np.arange(p.N) // Lx
