@@ -58,7 +58,14 @@ typedef struct {
   int32_t pairing;     /* 0: on-site Delta_i; 1: nearest-neighbour Delta_ij  */
   double coupling;     /* U (on-site) or V (bond)                            */
   const cplx *delta;   /* [N] (on-site) or [N*4] (bond)                      */
+  const double *coupling_site; /* NULL, or a coupling per Delta entry ([N] U_i
+                                  or [N*4] V_{i,d}) that replaces `coupling`  */
 } orc_lattice;
+
+/* The coupling of Delta entry k (site i, or bond (i, d) at k = 4i + d). */
+static double coupling_of(const orc_lattice *L, size_t k) {
+  return L->coupling_site ? L->coupling_site[k] : L->coupling;
+}
 
 /* Direction d -> lattice offset.  0:+x 1:-x 2:+y 3:-y 4:+x+y 5:-x-y 6:+x-y
  * 7:-x+y.  Opposite directions are d and d^1. */
@@ -330,7 +337,7 @@ int orc_order_parameter(const orc_lattice *L, double a, double T, int M, int K, 
     if (L->pairing == 0) {
       cplx s = 0.0;
       for (int m = 0; m < M; ++m) s += C[m] * conj(mu_eh[(size_t)i * M + m]);
-      delta_out[i] = 0.5 * L->coupling * s;
+      delta_out[i] = 0.5 * coupling_of(L, i) * s;
     } else {
       for (int d = 0; d < 4; ++d) {
         int j = orc_neighbour(L, i, d);
@@ -345,7 +352,7 @@ int orc_order_parameter(const orc_lattice *L, double a, double T, int M, int K, 
           cplx bwd = mu_eh[((size_t)j * M + m) * 5 + 1 + dback]; /* <h_i|T_n|e_j> */
           s += C[m] * conj(fwd + bwd);
         }
-        delta_out[(size_t)i * 4 + d] = 0.125 * L->coupling * s;
+        delta_out[(size_t)i * 4 + d] = 0.125 * coupling_of(L, (size_t)i * 4 + d) * s;
       }
     }
   }
@@ -377,7 +384,7 @@ int orc_order_parameter_sites(const orc_lattice *L, double a, double T, int M, i
       s += C[m] * conj(mu_eh[(size_t)c * M + m]);
     }
     if (n_out) n_out[c] = nn;
-    delta_out[c] = 0.5 * L->coupling * s;
+    delta_out[c] = 0.5 * coupling_of(L, sites[c]) * s;
   }
   free(C);
   free(mu_ee);
@@ -423,7 +430,7 @@ int orc_order_parameter_bonds(const orc_lattice *L, double a, double T, int M, i
         cplx bwd = mu_eh[((size_t)(5 * c + 1 + d) * M + m) * 5 + 1 + (d ^ 1)];
         s += C[m] * conj(fwd + bwd);
       }
-      delta_out[(size_t)c * 4 + d] = 0.125 * L->coupling * s;
+      delta_out[(size_t)c * 4 + d] = 0.125 * coupling_of(L, (size_t)sites[c] * 4 + d) * s;
     }
   }
   free(C);
@@ -771,7 +778,7 @@ int orc_scf_map_gradient(const orc_lattice *L, double a, const double *C, int M,
         }
       }
       /* output s_i = sum_m y_m . j_m with y_m = w_i (U/2) C_m h_i */
-      double wi = w[i] * 0.5 * L->coupling;
+      double wi = w[i] * 0.5 * coupling_of(L, i);
       memset(lam, 0, sizeof(double) * (size_t)n * (M + 2));
       for (int m = M - 1; m >= 1; --m) {
         double *lm = lam + (size_t)m * n, *l1 = lam + (size_t)(m + 1) * n, *l2 = lam + (size_t)(m + 2) * n;

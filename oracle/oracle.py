@@ -68,6 +68,7 @@ class _Lat(ctypes.Structure):
         ("pairing", ctypes.c_int32),
         ("coupling", ctypes.c_double),
         ("delta", ctypes.c_void_p),
+        ("coupling_site", ctypes.c_void_p),
     ]
 
 
@@ -113,10 +114,13 @@ class Lattice:
 
     hop is [N, n_dirs] complex (t_ij of the bond from site i along direction d;
     directions 0:+x 1:-x 2:+y 3:-y 4:+x+y 5:-x-y 6:+x-y 7:-x+y).  delta is [N]
-    (on-site pairing) or [N, 4] (bond pairing, directions 0..3).
+    (on-site pairing) or [N, 4] (bond pairing, directions 0..3).  coupling_site,
+    when given, holds one coupling per Delta entry (U_i, or V_{i,d}) in place of
+    the scalar coupling.
     """
 
-    def __init__(self, Lx, Ly, periodic_x, periodic_y, eps, mu, hop, pairing, coupling, delta):
+    def __init__(self, Lx, Ly, periodic_x, periodic_y, eps, mu, hop, pairing, coupling, delta,
+                 coupling_site=None):
         self.Lx, self.Ly = int(Lx), int(Ly)
         self.periodic_x, self.periodic_y = int(periodic_x), int(periodic_y)
         self.eps = np.ascontiguousarray(eps, dtype=np.float64).reshape(-1)
@@ -127,6 +131,8 @@ class Lattice:
         self.pairing = int(pairing)
         self.coupling = float(coupling)
         self.delta = np.ascontiguousarray(delta, dtype=np.complex128).reshape(-1).copy()
+        self.coupling_site = None if coupling_site is None else \
+            np.ascontiguousarray(coupling_site, dtype=np.float64).reshape(-1).copy()
 
     @property
     def N(self):
@@ -143,11 +149,13 @@ class Lattice:
         s.pairing = self.pairing
         s.coupling = self.coupling
         s.delta = _ptr(self.delta)
+        s.coupling_site = None if self.coupling_site is None else _ptr(self.coupling_site)
         return s
 
     def with_delta(self, delta):
         return Lattice(self.Lx, self.Ly, self.periodic_x, self.periodic_y, self.eps, self.mu,
-                       self.hop.reshape(self.N, self.n_dirs), self.pairing, self.coupling, delta)
+                       self.hop.reshape(self.N, self.n_dirs), self.pairing, self.coupling, delta,
+                       self.coupling_site)
 
 
 def neighbour(lat: Lattice, s: int, d: int) -> int:

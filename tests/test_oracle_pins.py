@@ -528,3 +528,95 @@ def test_scf_map_gradient_vs_finite_differences():
         fd = (loss(hop=h1) - loss(hop=h2)) / (2 * h)
         assert g_hop[i, d] == pytest.approx(fd, rel=1e-6, abs=1e-9)
         assert g_hop[j, d ^ 1] == pytest.approx(g_hop[i, d], rel=1e-12)
+
+
+# ---------------------------------------------------------------- site-dependent coupling
+
+
+def _site_lattice(p, cpl):
+    return orc.Lattice(p.Lx, p.Ly, p.periodic_x, p.periodic_y, p.eps, p.mu, p.hop, p.pairing,
+                       p.coupling, p.delta0, coupling_site=cpl)
+
+
+def test_site_coupling_onsite_matches_ed():
+    """U_i per site (zero on a normal strip, as in an S/N junction):
+    Delta_i = (U_i/2) sum_k u_k(i) conj(v_k(i)) F_M(E_k/a), exactly zero where
+    U_i = 0, and n_i unaffected; the sampled-site routine agrees."""
+    M, K = 96, 1 << 13
+    p = wl.random_swave(5, M, seed=91, periodic=1, complex_delta=True, flux_quanta=2.0, T=0.05)
+    U = np.random.default_rng(4).uniform(1.0, 3.0, p.N)
+    U[(np.arange(p.N) % p.Lx) >= 3] = 0.0
+    lat = _site_lattice(p, U)
+    a = orc.rescale(lat)
+    d, nn = orc.order_parameter(lat, a, p.T, M, K)
+    C = orc.fold_coefficients(M, K, a, p.T)
+    w, V = np.linalg.eigh(orc.dense_hamiltonian(lat))
+    F = sum(C[n] * cheb_T(n, w / a) for n in range(M))
+    u, v = V[0::2], V[1::2]
+    assert np.allclose(d, 0.5 * U * (u * np.conj(v) * F).sum(1), atol=1e-12)
+    assert np.all(d[U == 0.0] == 0.0)
+    _, n_scalar = orc.order_parameter(as_oracle(p), a, p.T, M, K)
+    assert np.array_equal(nn, n_scalar)
+    sites = np.array([0, 7, 4, 0])
+    ds, _ = orc.order_parameter_sites(lat, a, p.T, M, K, sites)
+    assert np.array_equal(ds, d[sites])
+
+
+def test_site_coupling_bond_matches_ed():
+    """V_{i,d} per bond (symmetric): each bond's Delta scales by its own V."""
+    M, K = 64, 1 << 13
+    p = wl.random_dwave(4, M, seed=92, flux_quanta=2.0)
+    lat0 = as_oracle(p)
+    rng = np.random.default_rng(5)
+    Vb = np.zeros((p.N, 4))
+    for i in range(p.N):
+        for dd in (0, 2):
+            j = orc.neighbour(lat0, i, dd)
+            Vb[i, dd] = Vb[j, dd ^ 1] = rng.uniform(0.5, 2.0)
+    lat = _site_lattice(p, Vb)
+    a = orc.rescale(lat)
+    d, _ = orc.order_parameter(lat, a, p.T, M, K)
+    d0, _ = orc.order_parameter(lat0, a, p.T, M, K)
+    assert np.allclose(d, d0 * Vb / p.coupling, atol=1e-13)
+    C = orc.fold_coefficients(M, K, a, p.T)
+    w, V = np.linalg.eigh(orc.dense_hamiltonian(lat))
+    F = sum(C[n] * cheb_T(n, w / a) for n in range(M))
+    i, dd = 5, 2
+    j = orc.neighbour(lat, i, dd)
+    ref = Vb[i, dd] / 8 * ((V[2 * i] * np.conj(V[2 * j + 1]) + V[2 * j] * np.conj(V[2 * i + 1])) * F).sum()
+    assert d[i, dd] == pytest.approx(ref, abs=1e-12)
+    ds, _ = orc.order_parameter_bonds(lat, a, p.T, M, K, np.array([i, 0]))
+    assert np.allclose(ds, d[[i, 0]], atol=1e-15)
+
+
+def test_site_coupling_uniform_equals_scalar_and_gradient():
+    """A uniform coupling array reproduces the scalar bit for bit; the
+    reverse-mode gradient with U_i matches central differences."""
+    M, K = 48, 1 << 12
+    p = wl.random_swave(4, M, seed=93, T=0.05)
+    a = orc.rescale(as_oracle(p))
+    d_s, n_s = orc.order_parameter(as_oracle(p), a, p.T, M, K)
+    d_u, n_u = orc.order_parameter(_site_lattice(p, np.full(p.N, p.coupling)), a, p.T, M, K)
+    assert np.array_equal(d_s, d_u) and np.array_equal(n_s, n_u)
+    U = np.where(np.arange(p.N) % 2 == 0, 2.5, 0.0)
+    lat = _site_lattice(p, U)
+    C = orc.fold_coefficients(M, K, a, p.T)
+    w = np.random.default_rng(6).normal(size=p.N)
+    g_eps, _, g_delta = orc.scf_map_gradient(lat, a, C, w)
+
+    def loss(eps=None, delta=None):
+        l2 = orc.Lattice(p.Lx, p.Ly, 0, 0, p.eps if eps is None else eps, p.mu, p.hop, 0, p.coupling,
+                         p.delta0 if delta is None else delta, coupling_site=U)
+        d, _ = orc.order_parameter(l2, a, p.T, M, K)
+        return float((w * d.real).sum())
+
+    h = 1e-6
+    for i in (0, 3, 6, 9):
+        e1, e2 = p.eps.copy(), p.eps.copy()
+        e1[i] += h
+        e2[i] -= h
+        assert g_eps[i] == pytest.approx((loss(eps=e1) - loss(eps=e2)) / (2 * h), rel=1e-6, abs=1e-9)
+        d1, d2 = p.delta0.copy(), p.delta0.copy()
+        d1[i] += h
+        d2[i] -= h
+        assert g_delta[i] == pytest.approx((loss(delta=d1) - loss(delta=d2)) / (2 * h), rel=1e-6, abs=1e-9)
