@@ -525,6 +525,35 @@ def leg_currents(cbdg, wl, torch, stream, hbm):
                          "note": "step_cplx_kernel (direct mode), 3 vector streams of 2N x N x 8 B per step"}}
 
 
+def leg_junction(cbdg, wl, torch, stream, hbm):
+    """The S/N slab after the paper's first example (64 x 320, U = 0 on the
+    top 20 rows, M = 2048, FP32): one self-consistency iteration (second call,
+    graph replay) and the surface LDOS (64 sites x 201 energies) with the
+    Lorentz kernel at a broadening of 0.001 t."""
+    import numpy as np
+    p = wl.sn_slab()
+    lat = cbdg.Lattice(p, precision="fp32", stream=stream)
+    lat.set_coupling(p.extra["coupling_site"])
+    lat.scf_step(p.T, p.M, p.mix)
+    t0 = time.perf_counter()
+    diff = lat.scf_step(p.T, p.M, p.mix)
+    t1 = time.perf_counter()
+    lam = lat.lorentz_lambda(p.extra["broadening"], p.M)
+    E = p.extra["energy_frac"] * lat.rescale
+    sites = p.extra["surface_sites"]
+    lat.ldos(sites, p.M, E, kernel="lorentz", lam=lam)
+    t2 = time.perf_counter()
+    rho = lat.ldos(sites, p.M, E, kernel="lorentz", lam=lam)
+    t3 = time.perf_counter()
+    d = lat.delta
+    lat.close()
+    units = p.N * ((p.M + 1) // 2)
+    return {"lattice": "64x320, periodic x, open y, S rows 0-299 (U = 1.41), N rows 300-319 (U = 0)",
+            "M": p.M, "scf_iteration_s": t1 - t0, "vector_steps_per_s": units / (t1 - t0),
+            "max_abs_ddelta": diff, "delta_bulk": float(abs(d[64 * 150])), "delta_interface": float(abs(d[64 * 299])),
+            "surface_ldos_s": t3 - t2, "lorentz_lambda": lam, "surface_ldos_at_0": float(rho[:, 100].mean())}
+
+
 def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=256):
     """Other hot-path stages at their workload sizes (not the headline)."""
     legs = {
@@ -534,6 +563,7 @@ def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=25
         "ensemble": lambda: leg_ensemble(cbdg, wl, stream, samples),
         "adjoint": lambda: leg_adjoint(cbdg, wl, stream),
         "currents": lambda: leg_currents(cbdg, wl, torch, stream, hbm),
+        "junction": lambda: leg_junction(cbdg, wl, torch, stream, hbm),
     }
     return {name: fn() for name, fn in legs.items() if only is None or only == name}
 
@@ -584,7 +614,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint", "currents"],
+    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint", "currents", "junction"],
                     help="measure only this stage and print its record (profiling runs)")
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")

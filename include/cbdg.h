@@ -260,6 +260,17 @@ cbdg_status cbdg_fixed_point_backward(cbdg_lattice *lat, double T, int32_t M, do
 cbdg_status cbdg_get_delta(cbdg_lattice *lat, cbdg_complex *delta);
 cbdg_status cbdg_set_delta(cbdg_lattice *lat, const cbdg_complex *delta);
 
+/* Replaces the scalar coupling of the descriptor by one coupling per Delta
+ * entry: coupling[i] = U_i for on-site pairing ([N]), coupling[4i + d] =
+ * V_{i,d} for bond pairing ([N*4], symmetric: V_{j,d^1} == V_{i,d}; entries
+ * across an open edge are ignored).  Eq. 19 then reads Delta_i = (U_i/2) ...
+ * (and Delta_{i,d} = (V_{i,d}/8) ...) in cbdg_order_parameter, cbdg_scf_step
+ * and the gradients; U_i = 0 marks a normal-metal site (the S/N and S/N/S
+ * junctions of the paper's examples).  NULL restores the scalar.  Host or
+ * device array, read during the call.  Errors: INVALID_ARG (not finite, not
+ * symmetric), OOM, CUDA.  Not in the ensemble API. */
+cbdg_status cbdg_set_coupling(cbdg_lattice *lat, const double *coupling);
+
 /* The rescale factor a used by the most recent compute call (0 before any). */
 cbdg_status cbdg_get_rescale(cbdg_lattice *lat, double *a);
 

@@ -98,6 +98,7 @@ def load():
             "cbdg_green_moments": [P, P, I32, P, I32, I32, P, P],
             "cbdg_green_function": [P, P, I32, P, I32, I32, I32, D, P, I32, P, P],
             "cbdg_bond_currents": [P, D, I32, I32, D, P],
+            "cbdg_set_coupling": [P, P],
             "cbdg_scf_step": [P, D, I32, D, P],
             "cbdg_get_delta": [P, P],
             "cbdg_set_delta": [P, P],
@@ -207,6 +208,10 @@ def cbdg_green_function(lat, sites, n_sites, targets, n_targets, M, kernel, lam,
 
 def cbdg_bond_currents(lat, T, M, kernel, lam, J):
     _check(load().cbdg_bond_currents(lat, float(T), int(M), int(kernel), float(lam), _ptr(J)))
+
+
+def cbdg_set_coupling(lat, coupling):
+    _check(load().cbdg_set_coupling(lat, _ptr(coupling)))
 
 
 def cbdg_scf_step(lat, T, M, mix):
@@ -484,6 +489,22 @@ class Lattice:
         cbdg_green_function(self.handle, sites, sites.size, targets, targets.size, M, KERNELS[kernel], lam,
                             energies, energies.size, G11, G12)
         return G11, G12
+
+    def set_coupling(self, coupling):
+        """One coupling per Delta entry (U_i [N] or V_{i,d} [N, 4]); None restores the scalar."""
+        if coupling is None:
+            cbdg_set_coupling(self.handle, None)
+            return
+        self._cpl = np.ascontiguousarray(coupling, dtype=np.float64).reshape(-1)
+        cbdg_set_coupling(self.handle, self._cpl)
+
+    def lorentz_lambda(self, broadening, M):
+        """lambda of the Lorentz kernel (Eq. 16) for an energy broadening eps at
+        the band centre: eps = a lambda / M with the current rescale a."""
+        a = self.rescale
+        if not a > 0.0:
+            raise RuntimeError("no rescale yet: run a compute call first")
+        return float(broadening) * M / a
 
     def bond_currents(self, T, M, kernel="jackson", lam=0.0):
         """J [N, n_dirs]: current from site i to its neighbour along d, both spins (Eq. 20)."""

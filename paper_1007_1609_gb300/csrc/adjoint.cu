@@ -33,13 +33,14 @@ inline int blocks(long long n, int t) { return static_cast<int>((n + t - 1) / t)
 
 template <typename S>
 __global__ void adjoint_source_kernel(int Lx, int Ly, int ncols, int W, const int32_t *sites,
-                                      const double *w, double scale_m, S *lam) {
+                                      const double *w, const double *U_site, double scale_m, S *lam) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= ncols) return;
   const int i = sites[b];
   const size_t rows = 2 * static_cast<size_t>(Lx) * Ly;
   const size_t k = blocked_index(vector_row(Lx, i, 1), b, rows, W);
-  lam[k] = static_cast<S>(static_cast<double>(lam[k]) + w[i] * scale_m);
+  const double wi = U_site ? w[i] * U_site[i] : w[i];
+  lam[k] = static_cast<S>(static_cast<double>(lam[k]) + wi * scale_m);
 }
 
 template <typename S>
@@ -216,15 +217,15 @@ __global__ void adjoint_final_kernel(int Lx, int Ly, int px, int py, int groups,
 }  // namespace
 
 cudaError_t launch_adjoint_source(int precision, int Lx, int Ly, int ncols, int W,
-                                  const int32_t *sites, const double *w, double scale_m, void *lam,
-                                  cudaStream_t s) {
+                                  const int32_t *sites, const double *w, const double *U_site,
+                                  double scale_m, void *lam, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
   if (precision == 1)
-    adjoint_source_kernel<float><<<blocks(ncols, 128), 128, 0, s>>>(Lx, Ly, ncols, W, sites, w, scale_m,
-                                                                    static_cast<float *>(lam));
+    adjoint_source_kernel<float><<<blocks(ncols, 128), 128, 0, s>>>(Lx, Ly, ncols, W, sites, w, U_site,
+                                                                    scale_m, static_cast<float *>(lam));
   else
-    adjoint_source_kernel<double><<<blocks(ncols, 128), 128, 0, s>>>(Lx, Ly, ncols, W, sites, w, scale_m,
-                                                                     static_cast<double *>(lam));
+    adjoint_source_kernel<double><<<blocks(ncols, 128), 128, 0, s>>>(Lx, Ly, ncols, W, sites, w, U_site,
+                                                                     scale_m, static_cast<double *>(lam));
   return cudaGetLastError();
 }
 

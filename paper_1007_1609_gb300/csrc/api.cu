@@ -119,6 +119,9 @@ struct cbdg_lattice {
   DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
   DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out, adj_fp;
   DBuf params_c, g_acc, g_tgt, g_mom, g_w, g_out;  // nonlocal readout (green.cu)
+  DBuf cpl;              // coupling per Delta entry (cbdg_set_coupling)
+  int site_cpl = 0;      // 1 while cpl replaces the scalar coupling
+  const double *coupling_site() const { return site_cpl ? static_cast<const double *>(cpl.p) : nullptr; }
   // options
   int K = 65536;
   int64_t chunk = 0, slab_w = 0, row_split = 0, ws_mb = 0, margin_milli = 1100, depth = 0, fixed_a_pico = 0, wait_ms = 2000, stall = 0, autotune = 0, temporal = 0;
@@ -485,7 +488,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
                          L->flags.as<unsigned int>(), tol, L->stream));
       L->launches += 2;
       if (finalize) {
-        CK(launch_finalize_onsite(ncols, sites + c0, L->coupling, L->acc_n.as<double>(),
+        CK(launch_finalize_onsite(ncols, sites + c0, L->coupling, L->coupling_site(), L->acc_n.as<double>(),
                                   L->acc_d.as<double2>(), L->dout.as<double2>(), L->nout.as<double>(),
                                   L->stream));
         L->launches += 1;
@@ -627,7 +630,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
       ++n;
     }
     if (finalize && mode != kDirect) {
-      CK(launch_finalize_onsite(ncols, sites + c0, L->coupling, L->acc_n.as<double>(),
+      CK(launch_finalize_onsite(ncols, sites + c0, L->coupling, L->coupling_site(), L->acc_n.as<double>(),
                                 L->acc_d.as<double2>(), L->dout.as<double2>(), L->nout.as<double>(),
                                 L->stream));
       L->launches += 1;
@@ -644,7 +647,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     }
   }
   if (finalize && mode == kDirect) {
-    CK(launch_finalize_bond(L->N, L->Lx, L->Ly, L->px, L->py, L->coupling,
+    CK(launch_finalize_bond(L->N, L->Lx, L->Ly, L->px, L->py, L->coupling, L->coupling_site(),
                             L->acc_site_n.as<double>(), L->acc_site_b.as<double2>(),
                             L->dout.as<double2>(), L->nout.as<double>(), L->stream));
     L->launches += 1;
@@ -912,7 +915,7 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M) {
     void *lam2 = L->adj_lam.as<unsigned char>() + vb;          // lam_{m+2}
     CK(cudaMemsetAsync(lam1, 0, vb, L->stream));
     CK(cudaMemsetAsync(lam2, 0, vb, L->stream));
-    const double halfU = 0.5 * L->coupling;
+    const double halfU = L->site_cpl ? 0.5 : 0.5 * L->coupling;
     bool first = true;
     for (int k = nseg - 1; k >= 0; --k) {
       // recompute j_{kS} .. j_{kS+S-1} (those below M) into the segment
@@ -940,7 +943,7 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M) {
           std::swap(lam1, lam2);  // lam1 = lam_m, lam2 = lam_{m+1}
         }
         CK(launch_adjoint_source(L->precision, L->Lx, L->Ly, ncols, W, sites, L->adj_w.as<double>(),
-                                 halfU * hC[m], lam1, L->stream));
+                                 L->coupling_site(), halfU * hC[m], lam1, L->stream));
         CK(launch_adjoint_accumulate(L->precision, L->Lx, L->Ly, L->px, L->py, ld, W, groups, lam1,
                                      segv(m - 1 - k * S), m == 1 ? 1.0 : 2.0,
                                      L->adj_part.as<double>(), L->stream));
@@ -1088,7 +1091,7 @@ cbdg_status cbdg_destroy(cbdg_lattice *L) {
                   &L->f,       &L->C,     &L->sites_all, &L->sites_user, &L->vec0, &L->vec1,
                   &L->partials, &L->mu1,  &L->dA,    &L->acc_n,   &L->acc_d, &L->dout,
                   &L->nout,    &L->mom_ee, &L->mom_eh, &L->stage, &L->acc_site_n, &L->acc_site_b, &L->adj_ck, &L->adj_seg, &L->adj_lam, &L->adj_part, &L->adj_w, &L->adj_out, &L->adj_fp,
-                  &L->params_c, &L->g_acc, &L->g_tgt, &L->g_mom, &L->g_w, &L->g_out};
+                  &L->params_c, &L->g_acc, &L->g_tgt, &L->g_mom, &L->g_w, &L->g_out, &L->cpl};
   for (DBuf *b : bufs) b->release();
   for (cudaEvent_t ev : L->events) cudaEventDestroy(ev);
   L->drop_graph();
@@ -1620,6 +1623,40 @@ cbdg_status cbdg_set_delta(cbdg_lattice *L, const cbdg_complex *delta) {
   CK(cudaMemcpyAsync(L->delta.p, h.data(), static_cast<size_t>(L->nd) * sizeof(double2),
                      cudaMemcpyHostToDevice, L->stream));
   CK(cudaStreamSynchronize(L->stream));
+  return CBDG_OK;
+}
+
+cbdg_status cbdg_set_coupling(cbdg_lattice *L, const double *coupling) {
+  if (!L) return fail(CBDG_ERR_INVALID_ARG, "lattice is NULL");
+  CK(cudaSetDevice(L->device));
+  L->drop_graph();
+  if (!coupling) {
+    L->site_cpl = 0;
+    return CBDG_OK;
+  }
+  std::vector<double> h;
+  cudaError_t e = host_copy(coupling, L->nd, h);
+  if (e != cudaSuccess) return cuda_fail(e, "reading coupling");
+  for (int k = 0; k < L->nd; ++k)
+    if (!isfinite(h[k])) return fail(CBDG_ERR_INVALID_ARG, "coupling[%d] is not finite", k);
+  if (L->pairing == CBDG_BOND_V) {
+    cbdg_lattice_desc d{};
+    d.Lx = L->Lx;
+    d.Ly = L->Ly;
+    d.periodic_x = L->px;
+    d.periodic_y = L->py;
+    for (int i = 0; i < L->N; ++i)
+      for (int dir = 0; dir < 4; ++dir) {
+        const int j = host_neighbour(&d, i, dir);
+        if (j >= 0 && h[static_cast<size_t>(i) * 4 + dir] != h[static_cast<size_t>(j) * 4 + (dir ^ 1)])
+          return fail(CBDG_ERR_INVALID_ARG, "bond coupling is not symmetric at site %d dir %d", i, dir);
+      }
+  }
+  CK(L->cpl.ensure(static_cast<size_t>(L->nd) * sizeof(double)));
+  CK(cudaMemcpyAsync(L->cpl.p, h.data(), static_cast<size_t>(L->nd) * sizeof(double), cudaMemcpyHostToDevice,
+                     L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  L->site_cpl = 1;
   return CBDG_OK;
 }
 

@@ -238,13 +238,15 @@ __global__ void fold_kernel(int n, int M, int ncols, int ld, int row_split,
   if (bad) atomicOr(flags, kFlagSpectrum);
 }
 
-// Delta_i = (U/2) acc_d, n_i = 1 + acc_n for the column's start site.
-__global__ void finalize_onsite_kernel(int ncols, const int32_t *sites, double U,
+// Delta_i = (U_i/2) acc_d, n_i = 1 + acc_n for the column's start site
+// (U_i = U_site[i], or the lattice's U when U_site is NULL).
+__global__ void finalize_onsite_kernel(int ncols, const int32_t *sites, double U_all, const double *U_site,
                                        const double *acc_n, const double2 *acc_d, double2 *dout,
                                        double *nout) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= ncols) return;
   const int i = sites[b];
+  const double U = U_site ? U_site[i] : U_all;
   const double2 ad = acc_d[b];
   if (dout) dout[i] = make_double2(0.5 * U * ad.x, 0.5 * U * ad.y);
   if (nout) nout[i] = 1.0 + acc_n[b];
@@ -329,11 +331,12 @@ cudaError_t launch_fold(int n, int M, int ncols, int ld, int row_split, const do
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_onsite(int ncols, const int32_t *sites, double U,
+cudaError_t launch_finalize_onsite(int ncols, const int32_t *sites, double U, const double *U_site,
                                    const double *acc_n, const double2 *acc_d, double2 *dout,
                                    double *nout, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
-  finalize_onsite_kernel<<<blocks(ncols, 256), 256, 0, s>>>(ncols, sites, U, acc_n, acc_d, dout, nout);
+  finalize_onsite_kernel<<<blocks(ncols, 256), 256, 0, s>>>(ncols, sites, U, U_site, acc_n, acc_d, dout,
+                                                            nout);
   return cudaGetLastError();
 }
 

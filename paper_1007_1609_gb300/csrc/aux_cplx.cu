@@ -185,17 +185,19 @@ __global__ void gather_kernel(int m, int M, int Lx, int Ly, int px, int py, int 
   if (!(fabs(ee.x) <= 1.0 + tol)) atomicOr(flags, kFlagSpectrum);
 }
 
-// Delta_{i,d} = (V/8) (acc_b[i][d] + acc_b[i+d][d^1]),  n_i = 1 + acc_n[i]
-// (accumulators indexed by site; every site was a start vector).
-__global__ void finalize_bond_kernel(int N, int Lx, int Ly, int px, int py, double V,
-                                     const double *acc_n, const double2 *acc_b, double2 *dout,
-                                     double *nout) {
+// Delta_{i,d} = (V_{i,d}/8) (acc_b[i][d] + acc_b[i+d][d^1]),  n_i = 1 + acc_n[i]
+// (accumulators indexed by site; every site was a start vector; V_{i,d} =
+// V_site[4i + d], or the lattice's V when V_site is NULL).
+__global__ void finalize_bond_kernel(int N, int Lx, int Ly, int px, int py, double V_all,
+                                     const double *V_site, const double *acc_n, const double2 *acc_b,
+                                     double2 *dout, double *nout) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   for (int d = 0; d < 4; ++d) {
     const int j = neighbour_site(Lx, Ly, px, py, i, d);
     double2 r = make_double2(0.0, 0.0);
     if (j >= 0) {
+      const double V = V_site ? V_site[static_cast<size_t>(i) * 4 + d] : V_all;
       const double2 f = acc_b[static_cast<size_t>(i) * 4 + d];
       const double2 g = acc_b[static_cast<size_t>(j) * 4 + (d ^ 1)];
       r = make_double2(0.125 * V * (f.x + g.x), 0.125 * V * (f.y + g.y));
@@ -266,10 +268,11 @@ cudaError_t launch_gather(int precision, int m, int M, int Lx, int Ly, int px, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_bond(int N, int Lx, int Ly, int px, int py, double V,
+cudaError_t launch_finalize_bond(int N, int Lx, int Ly, int px, int py, double V, const double *V_site,
                                  const double *acc_n, const double2 *acc_b, double2 *dout,
                                  double *nout, cudaStream_t s) {
-  finalize_bond_kernel<<<blocks(N, 256), 256, 0, s>>>(N, Lx, Ly, px, py, V, acc_n, acc_b, dout, nout);
+  finalize_bond_kernel<<<blocks(N, 256), 256, 0, s>>>(N, Lx, Ly, px, py, V, V_site, acc_n, acc_b, dout,
+                                                      nout);
   return cudaGetLastError();
 }
 

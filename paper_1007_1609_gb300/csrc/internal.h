@@ -135,7 +135,8 @@ cudaError_t launch_gather(int precision, int m, int M, int Lx, int Ly, int px, i
                           int W, const int32_t *sites, const void *j, const double *C,
                           double *acc_n, double2 *acc_b, double *mu_ee, double2 *mu_eh,
                           unsigned int *flags, double tol, cudaStream_t s);
-cudaError_t launch_finalize_bond(int N, int Lx, int Ly, int px, int py, double V,
+// V_site (may be NULL): a coupling per bond [N*4] in place of V.
+cudaError_t launch_finalize_bond(int N, int Lx, int Ly, int px, int py, double V, const double *V_site,
                                  const double *acc_n, const double2 *acc_b, double2 *dout,
                                  double *nout, cudaStream_t s);
 
@@ -175,7 +176,8 @@ cudaError_t launch_fold(int n, int M, int ncols, int ld, int row_split, const do
                         const double *C, const double *mu1, const double2 *dA, double *acc_n,
                         double2 *acc_d, double *mu_ee, double2 *mu_eh, int mom_stride,
                         unsigned int *flags, double tol, cudaStream_t s);
-cudaError_t launch_finalize_onsite(int ncols, const int32_t *sites, double U,
+// U_site (may be NULL): a coupling per site [N] in place of U.
+cudaError_t launch_finalize_onsite(int ncols, const int32_t *sites, double U, const double *U_site,
                                    const double *acc_n, const double2 *acc_d, double2 *dout,
                                    double *nout, cudaStream_t s);
 cudaError_t launch_mix(int n, double mix, const double2 *dout, double2 *delta, double *scal,
@@ -210,9 +212,10 @@ cudaError_t launch_split_tf32_f64(const double *src, size_t ld, int rows, int k,
 cudaError_t launch_contract_planes(const float *a_hi, const float *a_lo, const float *b_hi, const float *b_lo,
                                    int kp, float *D, int ldd, int m, int n, unsigned *flags, cudaStream_t s);
 // Adjoint of one self-consistency map (adjoint.cu).
+// lam(h_i) += w_i u_i scale_m, u_i = U_site[i] (or 1 when U_site is NULL).
 cudaError_t launch_adjoint_source(int precision, int Lx, int Ly, int ncols, int W,
-                                  const int32_t *sites, const double *w, double scale_m, void *lam,
-                                  cudaStream_t s);
+                                  const int32_t *sites, const double *w, const double *U_site,
+                                  double scale_m, void *lam, cudaStream_t s);
 // Column groups of the accumulation for ld columns at slab width W on Ly rows.
 int adjoint_groups(int Ly, int ld, int W);
 cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int py, int ld, int W,

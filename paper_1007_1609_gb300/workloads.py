@@ -176,6 +176,56 @@ def currents_dwave(L=128, M=512, flux_quanta=2.0, xi=3.0):
                     0.005, M, mix=0.5, tol=1e-6, max_iter=100)
 
 
+def sn_slab(Lx=64, L_S=300, L_N=20, M=2048, U=1.41, mu=-0.5, T=0.005, broadening=0.001):
+    """Planar S/N system after the paper's first example: superconductor (U)
+    for rows y < L_S, normal metal (U = 0) for the L_N rows above it, open
+    along y (the slab normal) and periodic along x (the plane, Lx sites).
+    t = 1, no disorder; U = 1.41 at mu = -0.5 gives a bulk gap of about
+    0.1 t (coherence length about 7 sites).  Initial Delta 0.1 in S, 0 in N.
+    LDOS at the N surface (row y = L_S + L_N - 1) with the Lorentz kernel,
+    energy broadening ``broadening`` (in units of t).  Per-site couplings in
+    extra['coupling_site']."""
+    Ly = L_S + L_N
+    N = Lx * Ly
+    y = np.arange(N) // Lx
+    U_site = np.where(y < L_S, U, 0.0)
+    d0 = np.where(y < L_S, 0.1, 0.0).astype(np.complex128)
+    surface = np.arange((Ly - 1) * Lx, Ly * Lx, dtype=np.int32)
+    p = Problem(name=f"sn_slab_{Lx}x{Ly}_M{M}", Lx=Lx, Ly=Ly, periodic_x=1, periodic_y=0, eps=np.zeros(N),
+                mu=mu, hop=np.ascontiguousarray(square_hops(Lx, Ly, 1, 0), dtype=np.complex128),
+                pairing=ONSITE, coupling=U, delta0=d0, T=T, M=M, mix=0.5, tol=1e-6, max_iter=200,
+                extra={"coupling_site": U_site, "surface_sites": surface, "broadening": broadening,
+                       "energy_frac": np.linspace(-0.05, 0.05, 201)})
+    return p
+
+
+def sns_junction(L_S=50, L_N=50, W=100, M=2048, U=1.41, mu=-0.5, T=0.005, impurity=2.0, r0=(50, 60),
+                 phase=0.0, broadening=0.001):
+    """S/N/S junction with a Gaussian impurity after the paper's second
+    example: along y, L_S superconducting rows, L_N normal rows (U = 0) and
+    L_S superconducting rows; W sites across (x); open edges.  On-site
+    potential eps_i = impurity * exp(-|r_i - r0|^2) (lattice constant 1) at
+    r0 = (x, y) in the normal layer.  Initial Delta 0.1 in the lower S layer
+    and 0.1 exp(i phase) in the upper one (phase != 0 drives a Josephson
+    current; the lattice is then complex).  Per-site couplings in
+    extra['coupling_site']; LDOS sites around the impurity in
+    extra['ldos_sites']."""
+    Ly = 2 * L_S + L_N
+    N = W * Ly
+    x, y = np.arange(N) % W, np.arange(N) // W
+    in_s = (y < L_S) | (y >= L_S + L_N)
+    U_site = np.where(in_s, U, 0.0)
+    eps = impurity * np.exp(-((x - r0[0]) ** 2 + (y - r0[1]) ** 2))
+    d0 = np.where(y < L_S, 0.1, 0.0) + np.where(y >= L_S + L_N, 0.1 * np.exp(1j * phase), 0.0)
+    near = np.array([(r0[0] + dx) + W * r0[1] for dx in range(-5, 6)], dtype=np.int32)
+    return Problem(name=f"sns_junction_{W}x{Ly}_M{M}", Lx=W, Ly=Ly, periodic_x=0, periodic_y=0, eps=eps,
+                   mu=mu, hop=np.ascontiguousarray(square_hops(W, Ly, 0, 0), dtype=np.complex128),
+                   pairing=ONSITE, coupling=U, delta0=np.ascontiguousarray(d0, dtype=np.complex128), T=T, M=M,
+                   mix=0.5, tol=1e-6, max_iter=200,
+                   extra={"coupling_site": U_site, "ldos_sites": near, "broadening": broadening,
+                          "energy_frac": np.linspace(-0.05, 0.05, 201)})
+
+
 def ensemble(n_samples=256, sides=(32, 48, 64, 80, 96), M=512, seed_sizes=1003, seed_eps=1004):
     """Ensemble of independent disordered s-wave lattices: sides drawn
     uniformly from ``sides`` and W ~ U[0.5, 2] per sample (seed_sizes),
