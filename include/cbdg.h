@@ -305,7 +305,8 @@ enum {
                                     blocking), 1..4, for real on-site FP32 lattices with open
                                     y edges: one pass reads j_(n-1), j_n and writes
                                     j_(n+K-1), j_(n+K); 1 = one step per pass; 0 (default) =
-                                    2.  Shapes the multi-step kernel does not serve run one
+                                    3 where each thread holds one lattice site (Lx <= 256 /
+                                    (W / 4)), else 2.  Shapes the multi-step kernel does not serve run one
                                     step per pass: periodic y, FP64, complex fields, slab
                                     widths other than 8 and 16, Lx above 64 (K = 2: 128) at
                                     slab width 16 or above 128 (K = 2: 256) at slab width 8,
