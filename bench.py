@@ -546,12 +546,75 @@ def leg_junction(cbdg, wl, torch, stream, hbm):
     rho = lat.ldos(sites, p.M, E, kernel="lorentz", lam=lam)
     t3 = time.perf_counter()
     d = lat.delta
+    # recursion kernels alone (profiled iteration: direct launches, no graph)
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
+    cbdg.cbdg_profile_read(lat.handle, reset=True)
+    lat.order_parameter(p.T, p.M)
+    sms, sn, sb = cbdg.cbdg_profile_read(lat.handle)
+    k = cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL)
     lat.close()
     units = p.N * ((p.M + 1) // 2)
     return {"lattice": "64x320, periodic x, open y, S rows 0-299 (U = 1.41), N rows 300-319 (U = 0)",
             "M": p.M, "scf_iteration_s": t1 - t0, "vector_steps_per_s": units / (t1 - t0),
             "max_abs_ddelta": diff, "delta_bulk": float(abs(d[64 * 150])), "delta_interface": float(abs(d[64 * 299])),
-            "surface_ldos_s": t3 - t2, "lorentz_lambda": lam, "surface_ldos_at_0": float(rho[:, 100].mean())}
+            "surface_ldos_s": t3 - t2, "lorentz_lambda": lam, "surface_ldos_at_0": float(rho[:, 100].mean()),
+            "steps_per_pass": k, "recursion_launches": sn, "recursion_ms": sms,
+            "roofline": {"bound": "hbm", "achieved": sb / (sms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": sb / (sms * 1e-3) / 1e9 / hbm,
+                         "note": "step_multi_kernel, 4 vector streams per pass of K steps (algorithmic bytes)"}}
+
+
+def leg_green(cbdg, wl, torch, stream):
+    """Nonlocal Green's functions (gf1) around a vortex core of the 128x128
+    d-wave lattice, M = 1024: 16 start sites (a 4x4 block at the core) x 256
+    targets (a 16x16 block) x 512 energies in [-0.5a, 0.5a], device outputs.
+    The recursion (16 columns, 1022 steps) is timed by cbdg_green_moments;
+    the FP64 contraction is the difference to cbdg_green_function (weights
+    and two [M] x [M x 512] complex contractions per (site, target))."""
+    import numpy as np
+    p = wl.currents_dwave(128, 1024)
+    L, M, n_E = 128, p.M, 512
+    lat = cbdg.Lattice(p, precision="fp32", stream=stream)
+    xs, ys = np.meshgrid(np.arange(30, 34), np.arange(30, 34))
+    sites = (xs + L * ys).ravel().astype(np.int32)
+    xt, yt = np.meshgrid(np.arange(24, 40), np.arange(24, 40))
+    targets = (xt + L * yt).ravel().astype(np.int32)
+    ns, nt = sites.size, targets.size
+    lat.green_moments(sites[:1], targets[:1], 8)   # buffers; sets the rescale
+    E = np.linspace(-0.5, 0.5, n_E) * lat.rescale
+    a11 = torch.empty((ns, M, nt), dtype=torch.complex128, device="cuda")
+    a12 = torch.empty_like(a11)
+    G11 = torch.empty((ns, nt, n_E), dtype=torch.complex128, device="cuda")
+    G12 = torch.empty_like(G11)
+    dE = torch.from_numpy(E).cuda()
+
+    def moments():
+        cbdg.cbdg_green_moments(lat.handle, sites, ns, targets, nt, M, a11, a12)
+
+    def green():
+        cbdg.cbdg_green_function(lat.handle, sites, ns, targets, nt, M, 0, 0.0, dE, n_E, G11, G12)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    t_mom = timed(moments)
+    t_all = timed(green)
+    lat.close()
+    flops = 2 * 8.0 * ns * nt * M * n_E
+    t_con = max(t_all - t_mom, 1e-9)
+    tf = flops / t_con / 1e12
+    return {"lattice": "128x128 d-wave vortex lattice, complex64 recursion", "M": M, "sites": ns, "targets": nt,
+            "energies": n_E, "moments_s": t_mom, "green_function_s": t_all, "contraction_s": t_con,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": 1.25, "unit": "TFLOP/s", "frac": tf / 1.25,
+                         "peak_kind": "nominal FP64 rate of the profiling recipe's table",
+                         "note": "green_contract_kernel, FP64 complex multiply-adds (8 flops each), from the call "
+                                 "time difference"}}
 
 
 def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=256):
@@ -564,6 +627,7 @@ def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=25
         "adjoint": lambda: leg_adjoint(cbdg, wl, stream),
         "currents": lambda: leg_currents(cbdg, wl, torch, stream, hbm),
         "junction": lambda: leg_junction(cbdg, wl, torch, stream, hbm),
+        "green": lambda: leg_green(cbdg, wl, torch, stream),
     }
     return {name: fn() for name, fn in legs.items() if only is None or only == name}
 
@@ -614,7 +678,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint", "currents", "junction"],
+    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint", "currents", "junction", "green"],
                     help="measure only this stage and print its record (profiling runs)")
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")
