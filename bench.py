@@ -454,20 +454,51 @@ def leg_ensemble(cbdg, wl, stream, samples=256):
             "algorithmic_bytes": algo_bytes}
 
 
-def leg_adjoint(cbdg, wl, stream):
-    """Gradient of one self-consistency map, 64x64, M = 512 (FP64 and FP32)."""
+def adjoint_streams(M):
+    """Vector streams (reads + writes of one 2N x B vector) of one adjoint run
+    as the library schedules it: forward with checkpoints every S = ceil(sqrt M)
+    steps, per segment the checkpoint copies and the recomputation, the
+    reverse recursion (3 streams per step) and the gradient accumulation
+    (lambda_m and j_(m-1): 2 streams per moment)."""
+    import math
+    S = max(2, math.ceil(math.sqrt(M)))
+    nseg = (M + S - 1) // S
+    m_last = (nseg - 1) * S + 1
+    # steps m = 2 .. min(M - 1, m_last); copies (2 streams each) of j_0, j_1 and of j_kS, j_kS+1
+    fwd = 3 * max(0, min(M - 1, m_last) - 1) + 2 * 2
+    fwd += 2 * sum(1 for k in range(1, nseg) if k * S <= min(M - 1, m_last))
+    fwd += 2 * sum(1 for k in range(1, nseg) if k * S + 1 <= min(M - 1, m_last))
+    rec = 0
+    for k in range(nseg):
+        r_end = min(S, M - k * S)
+        rec += 2 + (2 if r_end > 1 else 0) + 3 * max(0, r_end - 2)
+    rev = 3 * (M - 2) + 2 * (M - 1)
+    return fwd + rec + rev
+
+
+def leg_adjoint(cbdg, wl, stream, hbm):
+    """Gradient of one self-consistency map, 64x64, M = 512 (FP64 and FP32),
+    with the algorithmic bytes of the implemented schedule (adjoint_streams)."""
     import numpy as np
     pg = wl.gradient_case()
     out = {}
-    for prec in ("fp64", "fp32"):
+    for prec, es in (("fp64", 8), ("fp32", 4)):
         lg = cbdg.Lattice(pg, precision=prec, stream=stream)
         d, _ = lg.order_parameter(pg.T, pg.M)
         w = (2.0 * (d.real - pg.extra["target"])).astype(np.complex128)
         lg.backward(pg.T, pg.M, w)
         t0 = time.perf_counter()
         lg.backward(pg.T, pg.M, w)
-        out[f"{prec}_s"] = time.perf_counter() - t0
+        dt = time.perf_counter() - t0
+        out[f"{prec}_s"] = dt
         lg.close()
+        if prec == "fp32":
+            vb = 2 * pg.N * pg.N * es
+            gbs = adjoint_streams(pg.M) * vb / dt / 1e9
+            out["fp32_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                    "frac": gbs / hbm, "streams": adjoint_streams(pg.M), "vector_bytes": vb,
+                                    "note": "whole backward call (forward with checkpoints, recomputation, "
+                                            "reverse recursion, accumulation) over its algorithmic bytes"}
     return out
 
 
@@ -624,7 +655,7 @@ def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=25
         "contraction": lambda: leg_contraction(cbdg, torch, stream),
         "dwave": lambda: leg_dwave(cbdg, wl, stream, hbm, columns),
         "ensemble": lambda: leg_ensemble(cbdg, wl, stream, samples),
-        "adjoint": lambda: leg_adjoint(cbdg, wl, stream),
+        "adjoint": lambda: leg_adjoint(cbdg, wl, stream, hbm),
         "currents": lambda: leg_currents(cbdg, wl, torch, stream, hbm),
         "junction": lambda: leg_junction(cbdg, wl, torch, stream, hbm),
         "green": lambda: leg_green(cbdg, wl, torch, stream),
