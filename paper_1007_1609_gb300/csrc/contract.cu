@@ -8,7 +8,7 @@
 // is done once per operand element, into hi / lo planes [rows][kp] in HBM
 // (kp = k rounded up to 32, zero padded), by an HBM-bound pass.
 //
-// Pipeline (one CTA per 128 x 256 tile of D, 10 warps):
+// Pipeline (persistent: one CTA per SM walks the 128 x 256 tiles of D, 10 warps):
 //   warp 0   TMA producer: per K-block of 16 (64-byte rows) four 2-D tensor
 //            copies (A_hi, A_lo 128 rows; B_hi, B_lo 256 rows) with 64-byte
 //            swizzle into a 4-stage ring (48 KB per stage), on full[s];
@@ -23,8 +23,10 @@
 //            running sum held in its registers and releases the accumulator,
 //            while the tensor cores already fill the other one; after the last
 //            group the running sums go to D.
-// CTAs are ordered N-tile fastest, so the CTAs that share an A tile run
-// together and the second read of it hits L2.
+// Tiles are numbered N-tile fastest and CTA c takes tiles c, c + gridDim.x,
+// ..., so the CTAs that share an A tile run together and the second read of
+// it hits L2; a CTA's copies and MMAs for its next tile start while its
+// drain warps still write the previous tile out.
 // Every wait is bounded and also gives up when another role has given up;
 // on expiry the CTA records an error bit, waits (bounded) for the copies and
 // tensor-core work it issued, frees its tensor memory and returns.
@@ -162,7 +164,7 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float *v) {
 __global__ void __launch_bounds__(kThreads, 1)
     contract_kernel(const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
                     const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo,
-                    float *__restrict__ D, int ldd, int m, int n, int kblocks, unsigned *flags) {
+                    float *__restrict__ D, int ldd, int m, int n, int kblocks, int tiles, unsigned *flags) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -174,7 +176,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int t = threadIdx.x;
   const int warp = t >> 5, lane = t & 31;
   const int n_tiles = (n + kBN - 1) / kBN;
-  const int m0 = static_cast<int>(blockIdx.x / n_tiles) * kBM, n0 = static_cast<int>(blockIdx.x % n_tiles) * kBN;
   const int groups = (kblocks + kGroupBlocks - 1) / kGroupBlocks;
 
   if (warp == 1) {
@@ -201,119 +202,133 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = tmem_slot;
-  int issued = 0;         // producer: K-blocks whose copies were issued
+  // The CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the
+  // K-blocks of all its tiles form one stream through the stage ring (it)
+  // and the accumulation groups one alternation of the two accumulators
+  // (gg), so the next tile's copies and MMAs start while the drain warps
+  // still write the previous tile out.
+  long long issued = 0;   // producer: K-blocks whose copies were issued
   bool mma_issued = false;
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < kblocks && !abort_flag; ++kb) {
-        const int s = kb % kStages;
-        const unsigned u = static_cast<unsigned>(kb / kStages);
-        // stage s is free once the MMAs of its previous use completed
-        if (!mbar_wait(smem_addr(&empty_bar[s]), (u & 1u) ^ 1u, &abort_flag)) {
-          abort_flag = 1;
-          break;
+      long long it = 0;
+      for (int tile = blockIdx.x; tile < tiles && !abort_flag; tile += gridDim.x) {
+        const int m0 = (tile / n_tiles) * kBM, n0 = (tile % n_tiles) * kBN;
+        for (int kb = 0; kb < kblocks && !abort_flag; ++kb, ++it) {
+          const int s = static_cast<int>(it % kStages);
+          const unsigned u = static_cast<unsigned>(it / kStages);
+          // stage s is free once the MMAs of its previous use completed
+          if (!mbar_wait(smem_addr(&empty_bar[s]), (u & 1u) ^ 1u, &abort_flag)) {
+            abort_flag = 1;
+            break;
+          }
+          const unsigned bar = smem_addr(&full_bar[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(kStageBytes)
+                       : "memory");
+          const unsigned st = smem_addr(base + s * kStageBytes);
+          const int x = kb * kBK;
+          tma_load_2d(st, &tm_ahi, x, m0, bar);
+          tma_load_2d(st + kATile, &tm_alo, x, m0, bar);
+          tma_load_2d(st + 2 * kATile, &tm_bhi, x, n0, bar);
+          tma_load_2d(st + 2 * kATile + kBTile, &tm_blo, x, n0, bar);
+          issued = it + 1;
         }
-        const unsigned bar = smem_addr(&full_bar[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(kStageBytes)
-                     : "memory");
-        const unsigned st = smem_addr(base + s * kStageBytes);
-        const int x = kb * kBK;
-        tma_load_2d(st, &tm_ahi, x, m0, bar);
-        tma_load_2d(st + kATile, &tm_alo, x, m0, bar);
-        tma_load_2d(st + 2 * kATile, &tm_bhi, x, n0, bar);
-        tma_load_2d(st + 2 * kATile + kBTile, &tm_blo, x, n0, bar);
-        issued = kb + 1;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      int kb = 0;
-      for (int g = 0; g < groups && !abort_flag; ++g) {
-        // accumulator b = g % 2; the drain of group g - 2 must have read it
-        const int b = g & 1;
-        const unsigned acc = tmem + static_cast<unsigned>(b * kBN);
-        if (g >= 2 &&
-            !mbar_wait(smem_addr(&acce_bar[b]), static_cast<unsigned>(((g >> 1) - 1) & 1), &abort_flag)) {
-          abort_flag = 1;
-          break;
-        }
-        tc_fence_after();
-        const int kend = min(kblocks, (g + 1) * kGroupBlocks);
-        bool ok = true;
-        for (; kb < kend; ++kb) {
-          const int s = kb % kStages;
-          const unsigned u = static_cast<unsigned>(kb / kStages);
-          if (!mbar_wait(smem_addr(&full_bar[s]), u & 1u, &abort_flag)) {
+      long long it = 0, gg = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < tiles && ok && !abort_flag; tile += gridDim.x) {
+        int kb = 0;
+        for (int g = 0; g < groups && !abort_flag; ++g, ++gg) {
+          // accumulator b = gg % 2; the drain of group gg - 2 must have read it
+          const int b = static_cast<int>(gg & 1);
+          const unsigned acc = tmem + static_cast<unsigned>(b * kBN);
+          if (gg >= 2 &&
+              !mbar_wait(smem_addr(&acce_bar[b]), static_cast<unsigned>(((gg >> 1) - 1) & 1), &abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const unsigned st = smem_addr(base + s * kStageBytes);
-          const unsigned ah = st, al = st + kATile, bh = st + 2 * kATile, bl = bh + kBTile;
+          const int kend = min(kblocks, (g + 1) * kGroupBlocks);
+          for (; kb < kend; ++kb, ++it) {
+            const int s = static_cast<int>(it % kStages);
+            const unsigned u = static_cast<unsigned>(it / kStages);
+            if (!mbar_wait(smem_addr(&full_bar[s]), u & 1u, &abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const unsigned st = smem_addr(base + s * kStageBytes);
+            const unsigned ah = st, al = st + kATile, bh = st + 2 * kATile, bl = bh + kBTile;
 #pragma unroll
-          for (int ks = 0; ks < kBK / 8; ++ks) {
-            // K = 8 FP32 = 32 bytes per MMA: advance the start address inside the 64-byte row
-            const unsigned off = ks * 32;
-            const unsigned long long dah = smem_desc(ah + off), dal = smem_desc(al + off);
-            const unsigned long long dbh = smem_desc(bh + off), dbl = smem_desc(bl + off);
-            mma_tf32(acc, dah, dbh, (kb > g * kGroupBlocks || ks > 0) ? 1u : 0u);
-            mma_tf32(acc, dah, dbl, 1u);
-            mma_tf32(acc, dal, dbh, 1u);
+            for (int ks = 0; ks < kBK / 8; ++ks) {
+              // K = 8 FP32 = 32 bytes per MMA: advance the start address inside the 64-byte row
+              const unsigned off = ks * 32;
+              const unsigned long long dah = smem_desc(ah + off), dal = smem_desc(al + off);
+              const unsigned long long dbh = smem_desc(bh + off), dbl = smem_desc(bl + off);
+              mma_tf32(acc, dah, dbh, (kb > g * kGroupBlocks || ks > 0) ? 1u : 0u);
+              mma_tf32(acc, dah, dbl, 1u);
+              mma_tf32(acc, dal, dbh, 1u);
+            }
+            mma_issued = true;
+            tc_commit(smem_addr(&empty_bar[s]));
           }
-          mma_issued = true;
-          tc_commit(smem_addr(&empty_bar[s]));
+          if (!ok) break;
+          tc_commit(smem_addr(&accf_bar[b]));
         }
-        if (!ok) {
-          abort_flag = 1;
-          break;
-        }
-        tc_commit(smem_addr(&accf_bar[b]));
       }
+      if (!ok) abort_flag = 1;
     }
   } else {
     // drain: tensor-memory lanes 32 * (warp % 4) ..., columns [128 h, 128 h + 128)
     const int q = warp & 3, h = (warp - 2) >> 2;
     const unsigned lanes = static_cast<unsigned>(q * 32) << 16;
-    const int row = m0 + q * 32 + lane;
-    float sum[128];
-#pragma unroll
-    for (int j = 0; j < 128; ++j) sum[j] = 0.f;
+    const bool vec_ok = ((ldd & 3) == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
+    long long gg = 0;
     bool ok = true;
-    for (int g = 0; g < groups; ++g) {
-      const int b = g & 1;
-      // warp-uniform outcome: the tensor-memory loads below are warp-collective
-      ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&accf_bar[b]), static_cast<unsigned>((g >> 1) & 1),
-                                             &abort_flag));
-      if (!ok) {
-        abort_flag = 1;
-        break;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+      const int m0 = (tile / n_tiles) * kBM, n0 = (tile % n_tiles) * kBN;
+      const int row = m0 + q * 32 + lane;
+      float sum[128];
+#pragma unroll
+      for (int j = 0; j < 128; ++j) sum[j] = 0.f;
+      for (int g = 0; g < groups; ++g, ++gg) {
+        const int b = static_cast<int>(gg & 1);
+        // warp-uniform outcome: the tensor-memory loads below are warp-collective
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&accf_bar[b]), static_cast<unsigned>((gg >> 1) & 1),
+                                               &abort_flag));
+        if (!ok) {
+          abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const unsigned src = tmem + lanes + static_cast<unsigned>(b * kBN + h * 128);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float v[32];
+          tmem_ld32(src + c * 32, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sum[c * 32 + j] = __fadd_rn(sum[c * 32 + j], v[j]);
+        }
+        tc_fence_before();
+        mbar_arrive(smem_addr(&acce_bar[b]));
       }
-      tc_fence_after();
-      const unsigned src = tmem + lanes + static_cast<unsigned>(b * kBN + h * 128);
+      if (ok && row < m) {
+        float *drow = D + static_cast<size_t>(row) * ldd;
+        const int col0 = n0 + h * 128;
+        if (vec_ok && col0 + 128 <= n) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float v[32];
-        tmem_ld32(src + c * 32, v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          for (int j = 0; j < 128; j += 4)
+            *reinterpret_cast<float4 *>(drow + col0 + j) = make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sum[c * 32 + j] = __fadd_rn(sum[c * 32 + j], v[j]);
-      }
-      tc_fence_before();
-      mbar_arrive(smem_addr(&acce_bar[b]));
-    }
-    if (ok && row < m) {
-      float *drow = D + static_cast<size_t>(row) * ldd;
-      const int col0 = n0 + h * 128;
-      const bool vec_ok = ((ldd & 3) == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
-      if (vec_ok && col0 + 128 <= n) {
-#pragma unroll
-        for (int j = 0; j < 128; j += 4)
-          *reinterpret_cast<float4 *>(drow + col0 + j) = make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 128; ++j)
-          if (col0 + j < n) drow[col0 + j] = sum[j];
+          for (int j = 0; j < 128; ++j)
+            if (col0 + j < n) drow[col0 + j] = sum[j];
+        }
       }
     }
   }
@@ -325,8 +340,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < kStages && s < issued; ++s) {
-      const int last_kb = s + ((issued - 1 - s) / kStages) * kStages;
-      mbar_wait_drain(smem_addr(&full_bar[s]), static_cast<unsigned>((last_kb / kStages) & 1));
+      const long long last_it = s + ((issued - 1 - s) / kStages) * kStages;
+      mbar_wait_drain(smem_addr(&full_bar[s]), static_cast<unsigned>((last_it / kStages) & 1));
     }
   }
   tc_fence_before();
@@ -501,7 +516,17 @@ cudaError_t launch_contract_planes(const float *a_hi, const float *a_lo, const f
     return cudaErrorInvalidValue;
   const long long tiles = static_cast<long long>((n + kBN - 1) / kBN) * ((m + kBM - 1) / kBM);
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  contract_kernel<<<static_cast<unsigned>(tiles), kThreads, kSmem, s>>>(ahi, alo, bhi, blo, D, ldd, m, n, kp / kBK, flags);
+  // persistent: one CTA per SM (the stage ring fills the shared memory), each walking every
+  // gridDim-th tile
+  static int sms_dev = -1, sms = 0;
+  if (sms_dev != dev) {
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    sms_dev = dev;
+  }
+  const unsigned grid = static_cast<unsigned>(std::min<long long>(tiles, std::max(1, sms)));
+  contract_kernel<<<grid, kThreads, kSmem, s>>>(ahi, alo, bhi, blo, D, ldd, m, n, kp / kBK, static_cast<int>(tiles),
+                                                flags);
   return cudaGetLastError();
 }
 

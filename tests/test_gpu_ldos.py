@@ -34,7 +34,9 @@ def contract(A, B):
 
 
 @pytest.mark.parametrize("m,n,k", [(128, 256, 32), (1, 1, 1), (300, 300, 100), (129, 257, 33),
-                                   (640, 512, 2048), (200, 520, 600)])
+                                   (640, 512, 2048), (200, 520, 600),
+                                   # more tiles than SMs: each persistent CTA walks several tiles
+                                   (25600, 520, 40), (20000, 300, 700)])
 def test_contraction_matches_fp64_product(m, n, k):
     rng = np.random.default_rng(m * 7 + n + k)
     A = rng.standard_normal((m, k)).astype(np.float32).astype(np.float64)
