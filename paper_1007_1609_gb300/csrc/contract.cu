@@ -43,10 +43,12 @@ namespace {
 
 constexpr int kBM = 128;          // rows of A per tile = tensor-memory lanes
 constexpr int kBN = 256;          // rows of B per tile = accumulator columns
-constexpr int kBK = 16;           // FP32 elements per 64-byte K-block row (= the swizzle span)
+constexpr int kBK = 16;           // FP32 elements per K-block row (= the swizzle span: 16 -> 64 B, 8 -> 32 B)
 constexpr int kRowBytes = kBK * 4;
-constexpr int kStages = 4;
-constexpr int kGroupBlocks = 16;  // K-blocks per FP32 accumulation group (256 terms)
+constexpr int kStages = kBK == 16 ? 4 : 9;   // as many stages as the shared memory holds
+constexpr int kGroupBlocks = 256 / kBK;      // K-blocks per FP32 accumulation group (256 terms)
+constexpr unsigned kSwizzleMode = kBK == 16 ? 4u : 6u;  // descriptor layout: 64-byte or 32-byte swizzle
+static_assert(kBK == 16 || kBK == 8, "K-block rows of 64 or 32 bytes");
 constexpr int kThreads = 320;
 constexpr int kDrainThreads = 256;
 constexpr unsigned kTmemCols = 512;  // two 256-column accumulators
@@ -111,20 +113,20 @@ __device__ __forceinline__ void tc_commit(unsigned bar) {
                : "memory");
 }
 
-// Shared-memory matrix descriptor of a K-major, 64-byte-swizzled operand
-// tile as TMA writes it (rows of 64 bytes, 8-row swizzle atoms of 512 bytes):
+// Shared-memory matrix descriptor of a K-major, swizzled operand tile as TMA
+// writes it (rows of kRowBytes, 8-row swizzle atoms of 8 * kRowBytes):
 // start address >> 4 (bits 0-13), leading-dimension byte offset >> 4
 // (bits 16-29; unused by swizzled K-major layouts, set to 1), stride byte
-// offset >> 4 between 8-row groups (bits 32-45, 512 bytes), descriptor
-// version 1 (bits 46-47), base offset 0, swizzle mode 4 = 64 bytes
-// (bits 61-63).
+// offset >> 4 between 8-row groups (bits 32-45), descriptor version 1
+// (bits 46-47), base offset 0, swizzle mode in bits 61-63 (4 = 64 bytes,
+// 6 = 32 bytes).
 __device__ __forceinline__ unsigned long long smem_desc(unsigned addr) {
   unsigned long long d = 0;
   d |= static_cast<unsigned long long>((addr & 0x3FFFFu) >> 4);
   d |= static_cast<unsigned long long>(1u) << 16;
   d |= static_cast<unsigned long long>((8u * kRowBytes) >> 4) << 32;
   d |= static_cast<unsigned long long>(1u) << 46;
-  d |= static_cast<unsigned long long>(4u) << 61;
+  d |= static_cast<unsigned long long>(kSwizzleMode) << 61;
   return d;
 }
 
@@ -439,7 +441,8 @@ bool plane_map(CUtensorMap *map, const float *plane, int rows, int kp, int box_r
   const cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(plane), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, kBK == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
