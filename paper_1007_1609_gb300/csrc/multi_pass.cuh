@@ -79,6 +79,18 @@ struct Kahan {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Plain FP32 accumulation of a1*b1 + a2*b2 (two FMAs): the LEAN pass keeps
+// these to fit three levels into the registers.  A thread sums one site's
+// Ly rows (128 on the bench lattice), so the relative error stays below
+// Ly * 2^-24 before the FP64 reduction across the CTA.
+struct PlainSum {
+  float s = 0.f;
+  __device__ __forceinline__ void add2(float a1, float b1, float a2, float b2) {
+    s = __fmaf_rn(a1, b1, __fmaf_rn(a2, b2, s));
+  }
+  __device__ __forceinline__ double value() const { return (double)s; }
+};
+
 __device__ __forceinline__ float fc(const float4 &v, int j) { return reinterpret_cast<const float *>(&v)[j]; }
 
 
@@ -87,34 +99,41 @@ __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cas
 
 constexpr int kPassThreads = 256;
 
-template <int W, int K, int D, int NT = kPassThreads>
+// LEAN: level 0 (j_n) stays in its shared-memory ring instead of a register
+// window, one slot longer (RQ = 4 + D: rows g-2 .. g+2+D), and the stencil
+// parameters come through the read-only cache instead of a ring.  That frees
+// 16 registers per site and row, which is what a third level needs at two
+// sites per thread, and the shared memory the third level's rows need.
+template <int W, int K, int D, int NT = kPassThreads, bool LEAN = false>
 struct PassShape {
   static constexpr int VEC = 4, QUADS = W / VEC, XSLOTS = NT / QUADS;
-  static constexpr int RS = 3 + D;      // j_n / j_{n-1} staging ring: rows g-1 .. g+2+D
-  static constexpr int AS = K + 2 + D;  // parameter ring: rows g-K+1 .. g+2+D
-  static constexpr int NB = RS;         // mbarriers (one per staged row in flight)
+  static constexpr int RQ = LEAN ? 4 + D : 3 + D;  // j_n ring: rows g-1 (g-2 lean) .. g+2+D
+  static constexpr int RP = 3 + D;                 // j_{n-1} ring: rows g-1 .. g+2+D
+  static constexpr int RS = RQ;
+  static constexpr int AS = LEAN ? 0 : K + 2 + D;  // parameter ring: rows g-K+1 .. g+2+D
+  static constexpr int NB = RQ;                    // mbarriers (one per staged row in flight)
   // floats of shared memory the pass uses
   static __host__ __device__ size_t smem_floats(int Lx) {
     const size_t rowel = static_cast<size_t>(2) * Lx * W, pel = static_cast<size_t>(Lx) * kParamStride;
-    return (2 * RS + 2 * (K - 1)) * rowel + AS * pel;
+    return (RQ + RP + 2 * (K - 1)) * rowel + AS * pel;
   }
 };
 
-template <int W, int K, int D, int MAXX, int NT = kPassThreads>
+template <int W, int K, int D, int MAXX, int NT = kPassThreads, bool LEAN = false, typename Acc = Kahan>
 __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__restrict__ par, int Lx, int Ly,
                                            float *smem, unsigned long long *bars, long long base,
                                            unsigned long long wait_ns, unsigned stall_tx, int *abort_flag,
-                                           Kahan (&accA)[K][4], Kahan (&accB)[K][4], Kahan (&accC)[K][4]) {
-  using Sh = PassShape<W, K, D, NT>;
+                                           Acc (&accA)[K][4], Acc (&accB)[K][4], Acc (&accC)[K][4]) {
+  using Sh = PassShape<W, K, D, NT, LEAN>;
   constexpr int VEC = Sh::VEC, QUADS = Sh::QUADS, XSLOTS = Sh::XSLOTS;
-  constexpr int RS = Sh::RS, AS = Sh::AS, NB = Sh::NB;
+  constexpr int RQ = Sh::RQ, RP = Sh::RP, AS = Sh::AS, NB = Sh::NB;
   static_assert(W % VEC == 0 && NT % QUADS == 0 && K >= 2, "bad shape");
   const int rowel = 2 * Lx * W;
   const int pel = Lx * kParamStride;
-  float *sq = smem;                       // [RS][rowel]  j_n
-  float *sp = sq + RS * rowel;            // [RS][rowel]  j_{n-1}
-  float *sl = sp + RS * rowel;            // [K-1][2][rowel] levels 1..K-1
-  float *sa = sl + (K - 1) * 2 * rowel;   // [AS][pel]
+  float *sq = smem;                       // [RQ][rowel]  j_n
+  float *sp = sq + RQ * rowel;            // [RP][rowel]  j_{n-1}
+  float *sl = sp + RP * rowel;            // [K-1][2][rowel] levels 1..K-1
+  float *sa = sl + (K - 1) * 2 * rowel;   // [AS][pel] (not LEAN)
   const int t = threadIdx.x;
   const int q = t % QUADS, xs = t / QUADS;
   const unsigned row_bytes = rowel * 4u, par_bytes = pel * 4u;
@@ -125,11 +144,12 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
   auto issue = [&](int l) {
     const unsigned bar = bar_of(l);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
-                 "r"(2 * row_bytes + par_bytes + (l == 0 ? stall_tx : 0u))
+                 "r"(2 * row_bytes + (LEAN ? 0u : par_bytes) + (l == 0 ? stall_tx : 0u))
                  : "memory");
-    bulk_load(smem_addr(sq + (l % RS) * rowel), Q + static_cast<size_t>(l) * rowel, row_bytes, bar);
-    bulk_load(smem_addr(sp + (l % RS) * rowel), P + static_cast<size_t>(l) * rowel, row_bytes, bar);
-    bulk_load(smem_addr(sa + (l % AS) * pel), par + static_cast<size_t>(l) * pel, par_bytes, bar);
+    bulk_load(smem_addr(sq + (l % RQ) * rowel), Q + static_cast<size_t>(l) * rowel, row_bytes, bar);
+    bulk_load(smem_addr(sp + (l % RP) * rowel), P + static_cast<size_t>(l) * rowel, row_bytes, bar);
+    if constexpr (!LEAN)
+      bulk_load(smem_addr(sa + (l % AS) * pel), par + static_cast<size_t>(l) * pel, par_bytes, bar);
   };
   int issued = min(Ly, 2 + D);
   if (t == 0)
@@ -146,15 +166,18 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
       for (int k = 0; k < MAXX; ++k) wu[l][s][k] = wv[l][s][k] = zero4();
 
   int waited = 0;
-  bool ok = mbar_wait(bar_of(0), par_of(0), wait_ns);
-  if (ok) {
-    waited = 1;
+  bool ok = true;
+  if constexpr (!LEAN) {
+    ok = mbar_wait(bar_of(0), par_of(0), wait_ns);
+    if (ok) {
+      waited = 1;
 #pragma unroll
-    for (int k = 0; k < MAXX; ++k) {
-      const int x = xs + k * XSLOTS;
-      if (x < Lx) {
-        wu[0][0][k] = lds4(sq + x * W + off);
-        wv[0][0][k] = lds4(sq + hb + x * W + off);
+      for (int k = 0; k < MAXX; ++k) {
+        const int x = xs + k * XSLOTS;
+        if (x < Lx) {
+          wu[0][0][k] = lds4(sq + x * W + off);
+          wv[0][0][k] = lds4(sq + hb + x * W + off);
+        }
       }
     }
   }
@@ -175,32 +198,35 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
         stop = true;
         break;
       }
-      // the slot of row g - 1 is free: every read of it happened before the barrier
+      // the slots of rows g - 1 (j_{n-1}) and g - 1 (j_n; LEAN: g - 2) are free:
+      // every read of them happened before the barrier
       if (g + 2 + D < Ly) {
         if (t == 0) issue(g + 2 + D);
         issued = g + 3 + D;
       }
       // level 0 "computes" row g + 1: its centre enters the window
+      if constexpr (!LEAN) {
 #pragma unroll
-      for (int k = 0; k < MAXX; ++k) {
-        const int x = xs + k * XSLOTS;
-        float4 nu = zero4(), nv = zero4();
-        if (x < Lx && g + 1 < Ly) {
-          const float *src = sq + ((g + 1) % RS) * rowel;
-          nu = lds4(src + x * W + off);
-          nv = lds4(src + hb + x * W + off);
+        for (int k = 0; k < MAXX; ++k) {
+          const int x = xs + k * XSLOTS;
+          float4 nu = zero4(), nv = zero4();
+          if (x < Lx && g + 1 < Ly) {
+            const float *src = sq + ((g + 1) % RQ) * rowel;
+            nu = lds4(src + x * W + off);
+            nv = lds4(src + hb + x * W + off);
+          }
+          wu[0][(ph + 1) % 3][k] = nu;
+          wv[0][(ph + 1) % 3][k] = nv;
         }
-        wu[0][(ph + 1) % 3][k] = nu;
-        wv[0][(ph + 1) % 3][k] = nv;
       }
 #pragma unroll
       for (int lv = 1; lv <= K; ++lv) {
         const int r = g - lv + 1;
         const int sm = (ph - lv + 6) % 3, sc = (ph - lv + 7) % 3, su = (ph - lv + 8) % 3;
         if (r >= 0 && r < Ly) {
-          const float *nb = lv == 1 ? sq + (r % RS) * rowel : sl + ((lv - 2) * 2 + (r & 1)) * rowel;
-          const float *po = sp + (r % RS) * rowel;
-          const float *pc = sa + (r % AS) * pel;
+          const float *nb = lv == 1 ? sq + (r % RQ) * rowel : sl + ((lv - 2) * 2 + (r & 1)) * rowel;
+          const float *po = sp + (r % RP) * rowel;
+          const float *pc = LEAN ? par + static_cast<size_t>(r) * pel : sa + (r % AS) * pel;
           float *dl = lv < K ? sl + ((lv - 1) * 2 + (r & 1)) * rowel : nullptr;
 #pragma unroll
           for (int k = 0; k < MAXX; ++k) {
@@ -208,20 +234,51 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
             if (x < Lx) {
               const int xl = (x == 0) ? Lx - 1 : x - 1;
               const int xr = (x == Lx - 1) ? 0 : x + 1;
-              const float4 u = wu[lv - 1][sc][k], v = wv[lv - 1][sc][k];
-              const float4 uu = wu[lv - 1][su][k], vu = wv[lv - 1][su][k];
-              const float4 ud = wu[lv - 1][sm][k], vd = wv[lv - 1][sm][k];
+              float4 u, v, uu, vu, ud, vd;
+              if (LEAN && lv == 1) {
+                // level 0 rows r - 1, r, r + 1 at this x from the j_n ring (zero beyond the edges)
+                const float *rc = sq + (r % RQ) * rowel;
+                u = lds4(rc + x * W + off);
+                v = lds4(rc + hb + x * W + off);
+                uu = vu = ud = vd = zero4();
+                if (r + 1 < Ly) {
+                  const float *rp = sq + ((r + 1) % RQ) * rowel;
+                  uu = lds4(rp + x * W + off);
+                  vu = lds4(rp + hb + x * W + off);
+                }
+                if (r >= 1) {
+                  const float *rm = sq + ((r - 1) % RQ) * rowel;
+                  ud = lds4(rm + x * W + off);
+                  vd = lds4(rm + hb + x * W + off);
+                }
+              } else {
+                u = wu[lv - 1][sc][k], v = wv[lv - 1][sc][k];
+                uu = wu[lv - 1][su][k], vu = wv[lv - 1][su][k];
+                ud = wu[lv - 1][sm][k], vd = wv[lv - 1][sm][k];
+              }
               const float4 ur = lds4(nb + xr * W + off), vr = lds4(nb + hb + xr * W + off);
               const float4 ul = lds4(nb + xl * W + off), vl = lds4(nb + hb + xl * W + off);
               float4 uo, vo;
               if (lv == 1) {
                 uo = lds4(po + x * W + off);
                 vo = lds4(po + hb + x * W + off);
+              } else if (LEAN && lv == 2) {
+                // level 0 row r from the j_n ring
+                const float *rc = sq + (r % RQ) * rowel;
+                uo = lds4(rc + x * W + off);
+                vo = lds4(rc + hb + x * W + off);
               } else {
                 uo = wu[lv >= 2 ? lv - 2 : 0][sc][k];
                 vo = wv[lv >= 2 ? lv - 2 : 0][sc][k];
               }
-              const float4 pa = lds4(pc + x * kParamStride), pb = lds4(pc + x * kParamStride + 4);
+              float4 pa, pb;
+              if constexpr (LEAN) {
+                pa = __ldg(reinterpret_cast<const float4 *>(pc + x * kParamStride));
+                pb = __ldg(reinterpret_cast<const float4 *>(pc + x * kParamStride + 4));
+              } else {
+                pa = lds4(pc + x * kParamStride);
+                pb = lds4(pc + x * kParamStride + 4);
+              }
               const float e = pa.x, d = pa.y, t0 = pa.z, t1 = pa.w, t2 = pb.x, t3 = pb.y;
               float4 un, vn;
 #pragma unroll

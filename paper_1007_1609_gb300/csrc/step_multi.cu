@@ -17,6 +17,7 @@
 // mp::multi_pass in multi_pass.cuh; this file launches it once per slab and
 // reduces each level's column sums across the CTA in FP64.
 #include <algorithm>
+#include <type_traits>
 
 #include "multi_pass.cuh"
 
@@ -26,9 +27,9 @@ namespace {
 using mp::Kahan;
 constexpr int kThreads = mp::kPassThreads;
 
-template <int W, int K, int D, int MAXX>
+template <int W, int K, int D, int MAXX, bool LEAN>
 __global__ void __launch_bounds__(kThreads, 1) step_multi_kernel(StepArgs a) {
-  using Sh = mp::PassShape<W, K, D>;
+  using Sh = mp::PassShape<W, K, D, kThreads, LEAN>;
   constexpr int VEC = Sh::VEC, XSLOTS = Sh::XSLOTS, NB = Sh::NB;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bars[NB];
@@ -43,8 +44,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_multi_kernel(StepArgs a) {
     abort_flag = 0;
   }
   __syncthreads();
-  Kahan accA[K][VEC], accB[K][VEC], accC[K][VEC];
-  const bool ok = mp::multi_pass<W, K, D, MAXX>(
+  using Acc = typename std::conditional<LEAN, mp::PlainSum, Kahan>::type;
+  Acc accA[K][VEC], accB[K][VEC], accC[K][VEC];
+  const bool ok = mp::multi_pass<W, K, D, MAXX, kThreads, LEAN, Acc>(
       static_cast<float *>(a.prev) + slab, static_cast<float *>(const_cast<void *>(a.cur)) + slab,
       static_cast<const float *>(a.params), a.Lx, a.Ly, reinterpret_cast<float *>(smem_raw), bars, 0,
       a.wait_ns, a.stall_tx, &abort_flag, accA, accB, accC);
@@ -76,16 +78,16 @@ __global__ void __launch_bounds__(kThreads, 1) step_multi_kernel(StepArgs a) {
 
 constexpr int kMaxDynSmem = 227 * 1024 - 1024;
 
-template <int W, int K, int D>
+template <int W, int K, int D, bool LEAN = false>
 size_t smem_bytes(int Lx) {
-  const size_t ring = mp::PassShape<W, K, D>::smem_floats(Lx);
+  const size_t ring = mp::PassShape<W, K, D, kThreads, LEAN>::smem_floats(Lx);
   const size_t red = static_cast<size_t>(3) * (kThreads / (W / 4)) * W * sizeof(double) / sizeof(float);
   return std::max(ring, red) * sizeof(float);
 }
 
-template <int W, int K, int D, int MAXX>
+template <int W, int K, int D, int MAXX, bool LEAN = false>
 cudaError_t launch_one(const StepArgs &a, size_t smem, cudaStream_t s) {
-  auto k = step_multi_kernel<W, K, D, MAXX>;
+  auto k = step_multi_kernel<W, K, D, MAXX, LEAN>;
   static int attr_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -100,8 +102,12 @@ cudaError_t launch_one(const StepArgs &a, size_t smem, cudaStream_t s) {
 
 // Register windows take 24 x K x MAXX registers and the column sums 24 x K,
 // so only these shapes are built: one lattice site per thread for K = 2 .. 4,
-// two sites per thread for K = 2 (K = 4 spills a few bytes, the rest none).
+// two sites per thread for K = 2 (K = 4 spills a few bytes, the rest none),
+// and two sites per thread for K = 3 in the LEAN pass (level 0 read from its
+// shared-memory ring, parameters through the read-only cache), at depth 1
+// and slab width 16 (its rings fill the shared memory at Lx = 128).
 constexpr int max_sites_per_thread(int K) { return K == 2 ? 2 : 1; }
+constexpr int kLeanK = 3, kLeanW = 16, kLeanD = 1;
 
 template <int W, int K, int D>
 cudaError_t dispatch(const StepArgs &a, cudaStream_t s) {
@@ -112,6 +118,13 @@ cudaError_t dispatch(const StepArgs &a, cudaStream_t s) {
     if (a.Lx <= 2 * xsl) return launch_one<W, K, D, 2>(a, smem, s);
   }
   return cudaErrorInvalidValue;
+}
+
+// K = 3 at two sites per thread: the LEAN pass
+cudaError_t dispatch_lean(const StepArgs &a, cudaStream_t s) {
+  constexpr int xsl = kThreads / (kLeanW / 4);
+  if (a.Lx <= xsl || a.Lx > 2 * xsl) return cudaErrorInvalidValue;
+  return launch_one<kLeanW, kLeanK, kLeanD, 2, true>(a, smem_bytes<kLeanW, kLeanK, kLeanD, true>(a.Lx), s);
 }
 
 template <int W, int K>
@@ -139,6 +152,18 @@ bool plan_step_multi(int Lx, int Ly, int ld, int want_w, int want_k, int want_de
   int W = want_w > 0 ? want_w : 16;
   int K = want_k > 0 ? want_k : 2;
   int D = want_depth > 0 ? std::min(want_depth, 2) : 2;
+  if (W == kLeanW && K == kLeanK && Ly >= 2 && ld % W == 0 && Lx > kThreads / (W / 4) &&
+      Lx <= 2 * (kThreads / (W / 4)) && (want_depth <= 0 || want_depth == kLeanD)) {
+    const size_t b = smem_bytes<kLeanW, kLeanK, kLeanD, true>(Lx);
+    if (b > static_cast<size_t>(kMaxDynSmem)) return false;
+    cfg->slab_w = W;
+    cfg->depth = kLeanD;
+    cfg->row_split = 1;
+    cfg->threads = kThreads;
+    cfg->smem = b;
+    *k_out = K;
+    return true;
+  }
   if ((W != 8 && W != 16) || K < 2 || K > 4 || Ly < 2 || ld % W != 0 ||
       Lx > max_sites_per_thread(K) * (kThreads / (W / 4)))
     return false;
@@ -155,6 +180,8 @@ bool plan_step_multi(int Lx, int Ly, int ld, int want_w, int want_k, int want_de
 }
 
 cudaError_t launch_step_multi(const StepArgs &a, const StepConfig &cfg, int K, cudaStream_t s) {
+  if (cfg.slab_w == kLeanW && K == kLeanK && cfg.depth == kLeanD && a.Lx > kThreads / (kLeanW / 4))
+    return dispatch_lean(a, s);
 #define CBDG_MULTI_CASE(w, k, d) \
   if (cfg.slab_w == w && K == k && cfg.depth == d) return dispatch<w, k, d>(a, s);
   CBDG_MULTI_CASE(8, 2, 1)

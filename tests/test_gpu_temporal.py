@@ -20,11 +20,14 @@ pytestmark = [pytest.mark.gpu,
 TOL_MOM, TOL_DELTA = 1e-5, 1e-4
 
 
-def grouped(Lx, steps, slab):
+def grouped(Lx, steps, slab, depth=0):
     """Shapes the multi-step kernel serves: one lattice site per thread (256
-    threads, slab/4 threads per site) for any K, two sites per thread for K = 2."""
+    threads, slab/4 threads per site) for any K, two sites per thread for K = 2,
+    and two sites per thread for K = 3 in the lean pass (slab 16, depth 1)."""
     per_thread = 2 if steps == 2 else 1
-    return Lx <= per_thread * 256 // (slab // 4)
+    if Lx <= per_thread * 256 // (slab // 4):
+        return True
+    return steps == 3 and slab == 16 and depth in (0, 1) and Lx <= 128
 
 
 def recursion_launches(lat, sites, M):
@@ -47,7 +50,7 @@ def test_moments_match_oracle(case, steps, depth, slab):
     (ee, eh), launches = recursion_launches(lat, sites, M)
     n_steps = (M + 1) // 2 - 1
     # the grouped launches ran: K steps per pass, then single steps for the rest
-    if grouped(Lx, steps, slab):
+    if grouped(Lx, steps, slab, depth):
         assert launches == n_steps // steps + n_steps % steps
     else:
         assert launches == n_steps
@@ -88,7 +91,45 @@ def test_option_range():
     assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_OPT_TEMPORAL_STEPS) == 3
 
 
-@pytest.mark.parametrize("steps,slab", [(2, 16), (3, 8), (4, 8)])
+@pytest.mark.parametrize("case", [(65, 7, 40), (100, 23, 33), (128, 2, 64), (128, 31, 129), (97, 64, 24)])
+def test_lean_three_steps_match_oracle(case):
+    """Three steps per pass at two sites per thread (64 < Lx <= 128, slab 16):
+    level 0 read from its shared-memory ring, parameters through the
+    read-only cache, plain FP32 column sums.  Moments vs the oracle, and vs
+    one step per pass."""
+    Lx, Ly, M = case
+    p = rect(Lx, Ly, M, seed=Lx * 7 + Ly, periodic=0)
+    sites = np.arange(p.N, dtype=np.int32)[::-1].copy()
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3)
+    (ee, eh), launches = recursion_launches(lat, sites, M)
+    n_steps = (M + 1) // 2 - 1
+    assert launches == n_steps // 3 + n_steps % 3
+    assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL) == 3
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, M)
+    assert max_abs(ee, oee) < TOL_MOM, max_abs(ee, oee)
+    assert max_abs(eh, oeh) < TOL_MOM, max_abs(eh, oeh)
+    one = gpu_lattice(p, "fp32", resident=0, temporal_steps=1).moments(sites, M)
+    assert max_abs(ee, one[0]) < 5e-6 and max_abs(eh, one[1]) < 5e-6
+
+
+def test_lost_copy_times_out_in_the_lean_pass():
+    """The bounded waits of the lean three-step pass: a copy that never
+    arrives makes the call report CBDG_ERR_CUDA, and the lattice then
+    computes correct moments."""
+    p = rect(100, 12, 40, seed=52, periodic=0)
+    sites = np.arange(p.N, dtype=np.int32)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3, wait_limit_ms=20, test_stall_copy=1)
+    with pytest.raises(cbdg.CbdgError) as ei:
+        lat.moments(sites, p.M)
+    assert ei.value.status == cbdg.CBDG_ERR_CUDA and "gave up waiting" in str(ei.value)
+    lat.set_option(cbdg.CBDG_OPT_TEST_STALL_COPY, 0)
+    (ee, eh), launches = recursion_launches(lat, sites, p.M)
+    assert launches == 19 // 3 + 19 % 3
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, p.M)
+    assert max_abs(ee, oee) < TOL_MOM and max_abs(eh, oeh) < TOL_MOM
+
+
+@pytest.mark.parametrize("steps,slab", [(2, 16), (3, 8), (4, 8), (3, 16)])
 def test_full_size_disordered_128_sampled(steps, slab):
     """The 128x128 disordered workload at M = 1024, all 16384 start vectors:
     Delta_out and n at sampled sites vs the oracle."""
