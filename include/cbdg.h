@@ -306,11 +306,12 @@ enum {
                                     y edges: one pass reads j_(n-1), j_n and writes
                                     j_(n+K-1), j_(n+K); 1 = one step per pass; 0 (default) =
                                     3 where each thread holds one lattice site (Lx <= 256 /
-                                    (W / 4)), else 2.  Shapes the multi-step kernel does not serve run one
-                                    step per pass: periodic y, FP64, complex fields, slab
-                                    widths other than 8 and 16, Lx above 64 (K = 2: 128) at
-                                    slab width 16 or above 128 (K = 2: 256) at slab width 8,
-                                    and rings that do not fit in shared memory */
+                                    (W / 4)), else 2.  Shapes the multi-step kernel does not
+                                    serve run one step per pass: periodic y, FP64, complex
+                                    fields, slab widths other than 8 and 16, Lx above 64 at
+                                    slab width 16 (128 for K = 2, and for K = 3 at pipeline
+                                    depth 1, the lean pass), above 128 at slab width 8 (256
+                                    for K = 2), and rings that do not fit in shared memory */
   CBDG_OPT_GRAPH = 13,           /* 1 (default): cbdg_scf_step captures its iteration as a
                                     CUDA graph on the second call with the same (T, M, mix)
                                     and replays it afterwards (not while profiling,
