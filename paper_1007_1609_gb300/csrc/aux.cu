@@ -4,6 +4,8 @@
 // scatter and the self-consistency mix.  All in FP64.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace cbdg {
@@ -40,44 +42,53 @@ __global__ void set_rescale_kernel(double margin, double *scal) {
 }
 
 // f_k = tanh(a cos(th_k) / 2T), th_k = pi (k + 1/2) / K  (sign(x) at T = 0).
-// Coefficients of Eqs. 6-7 for the Fermi factor tanh(a x / 2T) (its
-// Chebyshev series has only odd terms) by a K-node Gauss-Chebyshev sum,
+// Coefficients of Eqs. 6-7 for the Fermi factor tanh(a x / 2T) by a K-node
+// Gauss-Chebyshev sum,
 //   c_n = (1/K) sum_k f_k T_n(x_k),  x_k = cos(pi (2k+1) / 2K),
-//   C_n = g_n (2 - delta_n0) c_n,
-// with T_n(x_k) from the three-term recurrence (one FMA per term; the FP64
-// rounding error grows like (n - n0) * 2^-53 inside a chunk of kCoefChunk
-// moments started from directly evaluated T_{n0}, T_{n0-1}).  kCoefNodes
-// nodes per thread: per n a thread sums its nodes, a warp-shuffle sum follows,
-// the warps of a block are summed in a fixed order into part[node block][n];
-// a second kernel sums the node blocks.
+//   C_n = g_n (2 - delta_n0) c_n.
+// tanh is odd and the nodes are symmetric (x_{K-1-k} = -x_k, T_n(-x) =
+// (-1)^n T_n(x)), so c_n = 0 for even n and, for odd n,
+//   c_n = (2/K) sum_{k < K/2} f_k T_n(x_k)
+// (for odd K the middle node x = 0 has f = 0).  Odd T_n come from the
+// two-step recurrence T_{n+2} = 2 T_2(x) T_n - T_{n-2} (one FMA per term; the
+// FP64 rounding error grows like the number of terms inside a chunk of
+// kCoefChunk odd moments started from directly evaluated T_{n0}, T_{n0-2}).
+// kCoefNodes nodes per thread: per n a thread sums its nodes, a warp-shuffle
+// sum follows, the warps of a block are summed in a fixed order into
+// part[node block][i] (n = 2i + 1); a second kernel sums the node blocks.
 constexpr int kCoefThreads = 256, kCoefChunk = 128, kCoefNodes = 4;  // nodes per thread
 
 // cos(n pi (2k+1) / 2K) with the exact integer reduction of the argument.
 __device__ __forceinline__ double cheb_node_cos(long long n, int k, int K) {
   const long long period = 4LL * K;
-  const long long r = (n % period) * (2LL * k + 1) % period;
+  const long long r = (((n % period) + period) % period) * (2LL * k + 1) % period;
   return cospi(static_cast<double>(r) / (2.0 * K));
 }
 
-// Grid (node blocks, n chunks): block (b, c) sums nodes
-// [b * kCoefNodes * 256, (b + 1) * kCoefNodes * 256) for n in chunk c, starting
-// the recurrence from T_{n0} and T_{n0-1} evaluated directly.
+// Grid (node blocks over k < K/2, chunks of odd n): block (b, c) sums nodes
+// [b * kCoefNodes * 256, (b + 1) * kCoefNodes * 256) for the odd n = 2i + 1,
+// i in chunk c, starting the recurrence from T_{n0} and T_{n0-2} evaluated
+// directly.
 __global__ void __launch_bounds__(kCoefThreads) coef_partial_kernel(int M, int K, double T, const double *scal,
                                                                     double *part) {
   __shared__ double wsum[kCoefThreads / 32][kCoefChunk];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.y * kCoefChunk, nc = min(kCoefChunk, M - n0);
+  const int n_odd = M / 2;  // odd n < M
+  const int i0 = blockIdx.y * kCoefChunk, nc = min(kCoefChunk, n_odd - i0);
+  const int n0 = 2 * i0 + 1;
+  const int half = K / 2;
   const double a = scal[kScalA];
-  double x[kCoefNodes], f[kCoefNodes], tm1[kCoefNodes], tn[kCoefNodes];
+  double t2[kCoefNodes], f[kCoefNodes], tm2[kCoefNodes], tn[kCoefNodes];
 #pragma unroll
   for (int j = 0; j < kCoefNodes; ++j) {
     const int k = (blockIdx.x * kCoefNodes + j) * kCoefThreads + threadIdx.x;
-    x[j] = f[j] = tm1[j] = tn[j] = 0.0;
-    if (k < K) {
-      x[j] = cospi((2.0 * k + 1.0) / (2.0 * K));
-      f[j] = (T > 0.0) ? tanh(a * x[j] / (2.0 * T)) : (x[j] > 0.0 ? 1.0 : (x[j] < 0.0 ? -1.0 : 0.0));
+    t2[j] = f[j] = tm2[j] = tn[j] = 0.0;
+    if (k < half) {
+      const double x = cospi((2.0 * k + 1.0) / (2.0 * K));
+      f[j] = (T > 0.0) ? tanh(a * x / (2.0 * T)) : (x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0));
+      t2[j] = 2.0 * cheb_node_cos(2, k, K);
       tn[j] = cheb_node_cos(n0, k, K);
-      tm1[j] = n0 > 0 ? cheb_node_cos(n0 - 1, k, K) : 0.0;
+      tm2[j] = cheb_node_cos(n0 - 2, k, K);
     }
   }
   for (int i = 0; i < nc; ++i) {
@@ -85,8 +96,8 @@ __global__ void __launch_bounds__(kCoefThreads) coef_partial_kernel(int M, int K
 #pragma unroll
     for (int j = 0; j < kCoefNodes; ++j) {
       v = fma(f[j], tn[j], v);
-      const double tp = (n0 + i == 0) ? x[j] : fma(2.0 * x[j], tn[j], -tm1[j]);
-      tm1[j] = tn[j];
+      const double tp = fma(t2[j], tn[j], -tm2[j]);
+      tm2[j] = tn[j];
       tn[j] = tp;
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -96,7 +107,7 @@ __global__ void __launch_bounds__(kCoefThreads) coef_partial_kernel(int M, int K
   for (int i = threadIdx.x; i < nc; i += blockDim.x) {
     double v = 0.0;
     for (int w = 0; w < kCoefThreads / 32; ++w) v += wsum[w][i];
-    part[static_cast<size_t>(blockIdx.x) * M + n0 + i] = v;
+    part[static_cast<size_t>(blockIdx.x) * n_odd + i0 + i] = v;
   }
 }
 
@@ -104,9 +115,12 @@ __global__ void coef_final_kernel(int M, int K, int nblocks, int kernel, double 
                                   double *C) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= M) return;
+  const int n_odd = M / 2;
   double c = 0.0;
-  for (int b = 0; b < nblocks; ++b) c += part[static_cast<size_t>(b) * M + n];
-  c /= K;
+  if (n & 1) {
+    for (int b = 0; b < nblocks; ++b) c += part[static_cast<size_t>(b) * n_odd + (n - 1) / 2];
+    c = 2.0 * c / K;
+  }
   double g;
   if (kernel == 0) {  // Jackson
     const double q = 1.0 / (M + 1.0);
@@ -278,14 +292,16 @@ cudaError_t launch_gershgorin(int N, int n_dirs, int pairing, int, int, int, int
 }
 
 size_t coefficient_work(int M, int K) {
-  return static_cast<size_t>(blocks(K, kCoefThreads * kCoefNodes)) * static_cast<size_t>(M);
+  return static_cast<size_t>(std::max(1, blocks(K / 2, kCoefThreads * kCoefNodes))) *
+         static_cast<size_t>(std::max(1, M / 2));
 }
 
 cudaError_t launch_coefficients(int M, int K, double T, int kernel, double lambda,
                                 const double *scal, double *work, double *C, cudaStream_t s) {
-  const int nb = blocks(K, kCoefThreads * kCoefNodes);
-  coef_partial_kernel<<<dim3(nb, blocks(M, kCoefChunk)), kCoefThreads, 0, s>>>(M, K, T, scal, work);
-  coef_final_kernel<<<blocks(M, 128), 128, 0, s>>>(M, K, nb, kernel, lambda, work, C);
+  const int nb = blocks(K / 2, kCoefThreads * kCoefNodes);
+  if (nb > 0 && M / 2 > 0)
+    coef_partial_kernel<<<dim3(nb, blocks(M / 2, kCoefChunk)), kCoefThreads, 0, s>>>(M, K, T, scal, work);
+  coef_final_kernel<<<blocks(M, 128), 128, 0, s>>>(M, K, M / 2 > 0 ? nb : 0, kernel, lambda, work, C);
   return cudaGetLastError();
 }
 

@@ -376,50 +376,58 @@ __global__ void ens_rescale_kernel(int n, double margin, const int *converged, d
   scal[s * kScalars + kScalA] = margin * b;
 }
 
-// Block partials of c_n = (1/K) sum_k f_k T_n(x_k), x_k = cos(pi (k+1/2)/K),
-// with T_n(x_k) by the Chebyshev recurrence (FP64) for each node.
-// grid (node blocks, sample); part[s][block][n].
+// Block partials of the odd c_n = (2/K) sum_{k < K/2} f_k T_n(x_k),
+// x_k = cos(pi (k+1/2)/K) (tanh is odd and the nodes symmetric, so the even
+// c_n vanish and the other half of the nodes repeats the first), with the odd
+// T_n(x_k) from the two-step recurrence T_{n+2} = 2 T_2 T_n - T_{n-2} (FP64)
+// for each node.  grid (node blocks, sample); part[s][block][i], n = 2i + 1.
 __global__ void ens_coef_partial_kernel(int M, int K, double T, const int *converged,
                                         const double *scal, double *part) {
   const int s = blockIdx.y;
   if (converged[s]) return;
-  extern __shared__ double wsum[];  // [warps][M]
+  extern __shared__ double wsum[];  // [warps][M / 2]
+  const int n_odd = M / 2;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double a = scal[s * kScalars + kScalA];
   double x = 0.0, f = 0.0;
-  if (k < K) {
+  if (k < K / 2) {
     x = cospi((2.0 * k + 1.0) / (2.0 * K));
     f = (T > 0.0) ? tanh(a * x / (2.0 * T)) : (x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0));
   }
-  double tm1 = 0.0, tn = 1.0;
-  for (int n = 0; n < M; ++n) {
+  const double t2 = 2.0 * (2.0 * x * x - 1.0);
+  double tm2 = x, tn = x;  // T_{-1} = T_1 = x
+  for (int i = 0; i < n_odd; ++i) {
     double v = f * tn;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) wsum[warp * M + n] = v;
-    const double tp = (n == 0) ? x : 2.0 * x * tn - tm1;
-    tm1 = tn;
+    if (lane == 0) wsum[warp * n_odd + i] = v;
+    const double tp = fma(t2, tn, -tm2);
+    tm2 = tn;
     tn = tp;
   }
   __syncthreads();
   const int warps = blockDim.x >> 5;
-  for (int n = threadIdx.x; n < M; n += blockDim.x) {
+  for (int i = threadIdx.x; i < n_odd; i += blockDim.x) {
     double v = 0.0;
-    for (int w = 0; w < warps; ++w) v += wsum[w * M + n];
-    part[(static_cast<size_t>(s) * gridDim.x + blockIdx.x) * M + n] = v;
+    for (int w = 0; w < warps; ++w) v += wsum[w * n_odd + i];
+    part[(static_cast<size_t>(s) * gridDim.x + blockIdx.x) * n_odd + i] = v;
   }
 }
 
-// C[s][n] = g_n (2 - delta_n0) (1/K) sum_blocks part (Jackson g_n).
+// C[s][n] = g_n (2 - delta_n0) c_n, c_n = (2/K) sum_blocks part for odd n, 0
+// for even n (Jackson g_n).
 __global__ void ens_coef_final_kernel(int n_samples, int M, int K, int nblocks,
                                       const int *converged, const double *part, double *C) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= static_cast<long long>(n_samples) * M) return;
   const int s = static_cast<int>(idx / M), n = static_cast<int>(idx % M);
   if (converged[s]) return;
+  const int n_odd = M / 2;
   double c = 0.0;
-  for (int b = 0; b < nblocks; ++b) c += part[(static_cast<size_t>(s) * nblocks + b) * M + n];
-  c /= K;
+  if (n & 1) {
+    for (int b = 0; b < nblocks; ++b) c += part[(static_cast<size_t>(s) * nblocks + b) * n_odd + (n - 1) / 2];
+    c = 2.0 * c / K;
+  }
   const double q = 1.0 / (M + 1.0);
   const double g = ((M - n + 1) * cospi(n * q) + sinpi(n * q) * cospi(q) / sinpi(q)) / (M + 1.0);
   C[idx] = g * (n == 0 ? 1.0 : 2.0) * c;
@@ -578,9 +586,9 @@ cudaError_t enqueue_iteration(cbdg_ensemble *e, double T, int M, double mix, dou
                                            static_cast<double2 *>(e->d_hop),
                                            static_cast<double2 *>(e->d_delta), scal);
   ens_rescale_kernel<<<blocks(e->n, 128), 128, 0, s>>>(e->n, 1.1, conv, scal);
-  const int nb = blocks(e->K, kCoefThreads);
+  const int nb = std::max(1, blocks(e->K / 2, kCoefThreads));
   dim3 gc(nb, e->n);
-  ens_coef_partial_kernel<<<gc, kCoefThreads, (kCoefThreads / 32) * M * sizeof(double), s>>>(
+  ens_coef_partial_kernel<<<gc, kCoefThreads, (kCoefThreads / 32) * std::max(1, M / 2) * sizeof(double), s>>>(
       M, e->K, T, conv, scal, static_cast<double *>(e->d_part));
   ens_coef_final_kernel<<<blocks(static_cast<long long>(e->n) * M, 256), 256, 0, s>>>(
       e->n, M, e->K, nb, conv, static_cast<double *>(e->d_part), static_cast<double *>(e->d_C));
