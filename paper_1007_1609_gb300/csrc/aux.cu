@@ -56,7 +56,7 @@ __global__ void set_rescale_kernel(double margin, double *scal) {
 // kCoefNodes nodes per thread: per n a thread sums its nodes, a warp-shuffle
 // sum follows, the warps of a block are summed in a fixed order into
 // part[node block][i] (n = 2i + 1); a second kernel sums the node blocks.
-constexpr int kCoefThreads = 256, kCoefChunk = 128, kCoefNodes = 4;  // nodes per thread
+constexpr int kCoefThreads = 256, kCoefChunk = 128, kCoefNodes = 1;  // nodes per thread (more blocks: FP64-bound)
 
 // cos(n pi (2k+1) / 2K) with the exact integer reduction of the argument.
 __device__ __forceinline__ double cheb_node_cos(long long n, int k, int K) {

@@ -17,7 +17,10 @@
 // every kCheckEvery steps and at the last step for the |mu| <= 1 check (the
 // norm of j_n grows monotonically once a is too small); on GB300, where FP64
 // runs at 1/64 of the FP32 rate, the shuffle tree of every step would cost as
-// much as the stencil.  No vector traffic reaches HBM; for the 16 x 16
+// much as the stencil.  FP32 without moment output folds linearly too, its
+// per-thread shares in compensated FP32 (the coefficients' FP32 copy times
+// the FP32 partial sums), so that no single folding thread sits on the
+// critical path of every step.  No vector traffic reaches HBM; for the 16 x 16
 // lattice a self-consistency iteration becomes one recursion launch.
 #include <algorithm>
 
@@ -33,6 +36,25 @@ constexpr int kCheckEvery = 16;
 template <typename S, int VEC>
 struct alignas(sizeof(S) * VEC) Pack {
   S v[VEC];
+};
+
+// Per-thread share of a linear fold: plain FP64, or compensated FP32.
+template <typename S>
+struct LinAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct LinAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -68,6 +90,7 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
   S *bp = reinterpret_cast<S *>(wred + 2 * kWarps * 3 * W);                // j_{n-1} -> j_{n+1}
   S *bq = bp + slab_el;                                                    // j_n
   S *par = bq + slab_el;                                                   // [N][kParamStride]
+  S *Cf = par + static_cast<size_t>(N) * kParamStride;                     // [M] C in S precision
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int q = t % QUADS, ts = t / QUADS;
@@ -81,7 +104,10 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
     }
     const S *gp = static_cast<const S *>(a.params);
     for (size_t k = t; k < static_cast<size_t>(N) * kParamStride; k += kThreads) par[k] = gp[k];
-    for (int k = t; k < M; k += kThreads) Cs[k] = a.C[k];
+    for (int k = t; k < M; k += kThreads) {
+      Cs[k] = a.C[k];
+      Cf[k] = static_cast<S>(a.C[k]);
+    }
   }
   // the fold state of column t (threads t < W)
   const int col = static_cast<int>(c0) + t;
@@ -95,9 +121,7 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
     da = a.dA[col];
   }
   bool bad = false;
-  double ln[VEC], ld_[VEC];  // linear fold: this thread's share of acc_n and Re acc_d
-#pragma unroll
-  for (int l = 0; l < VEC; ++l) ln[l] = ld_[l] = 0.0;
+  LinAcc<S> ln[VEC], ld_[VEC];  // linear fold: this thread's share of acc_n and Re acc_d
   __syncthreads();
 
   S *prev = bp, *cur = bq;
@@ -143,10 +167,10 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
     if (LINEAR) {
 #pragma unroll
       for (int l = 0; l < VEC; ++l) {
-        if (m0 < M) ln[l] -= 2.0 * Cs[m0] * static_cast<double>(pa[l]);
+        if (m0 < M) ln[l].add(S(-2) * Cf[m0] * pa[l]);
         if (mo < M) {
-          ln[l] -= 2.0 * Cs[mo] * static_cast<double>(pb[l]);
-          ld_[l] += 2.0 * ((n & 1) ? 1.0 : -1.0) * Cs[mo] * static_cast<double>(pc[l]);
+          ln[l].add(S(-2) * Cf[mo] * pb[l]);
+          ld_[l].add(((n & 1) ? S(2) : S(-2)) * Cf[mo] * pc[l]);
         }
       }
     }
@@ -213,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
     double *wr = wred + static_cast<size_t>(warp) * 3 * W;
 #pragma unroll
     for (int l = 0; l < VEC; ++l) {
-      double xn = ln[l], xd = ld_[l];
+      double xn = ln[l].value(), xd = ld_[l].value();
 #pragma unroll
       for (int o = QUADS; o < 32; o <<= 1) {
         xn += __shfl_xor_sync(0xffffffffu, xn, o);
@@ -250,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) resident_kernel(ResidentArgs a) {
 template <typename S, int W>
 size_t smem_bytes(int N, int M) {
   return static_cast<size_t>(M) * 8 + static_cast<size_t>(2) * kWarps * 3 * W * 8 +
-         (static_cast<size_t>(4) * N * W + static_cast<size_t>(N) * kParamStride) * sizeof(S);
+         (static_cast<size_t>(4) * N * W + static_cast<size_t>(N) * kParamStride + M) * sizeof(S);
 }
 
 constexpr size_t kMaxSmem = 227 * 1024 - 1024;
@@ -271,10 +295,10 @@ cudaError_t launch_one(const ResidentArgs &a, int ld, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// FP64 without moment output folds linearly (see above); everything else per step.
+// Without moment output the fold is linear (see above); with it, per step.
 template <typename S, int W>
 cudaError_t launch_w(const ResidentArgs &a, int ld, cudaStream_t s) {
-  if (sizeof(S) == 8 && !a.mu_ee && !a.mu_eh) return launch_one<S, W, true>(a, ld, s);
+  if (!a.mu_ee && !a.mu_eh) return launch_one<S, W, true>(a, ld, s);
   return launch_one<S, W, false>(a, ld, s);
 }
 
