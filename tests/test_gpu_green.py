@@ -236,3 +236,36 @@ def test_full_size_dwave_vortex_128_sampled(precision):
     for d in range(p.n_dirs):
         j = (x + wl.DX[d]) % Lx + Lx * ((y + wl.DY[d]) % p.Ly)
         assert np.abs(J[:, d] + J[j, d ^ 1]).max() < TOL_J[precision]
+
+
+def test_device_buffers_match_host_buffers():
+    """Device (torch) outputs and inputs give the same bits as host arrays for
+    the nonlocal moments, the Green's function and the currents."""
+    import torch
+    M = 40
+    p = CASES["nnn_field_10"](M)
+    lat = gpu_lattice(p, "fp64")
+    sites = np.array([3, 3, 57, 99], dtype=np.int32)
+    targets = np.array([3, 4, 13, 3, 98], dtype=np.int32)   # repeats, and the start sites themselves
+    h11, h12 = lat.green_moments(sites, targets, M)
+    d11 = torch.empty((sites.size, M, targets.size), dtype=torch.complex128, device="cuda")
+    d12 = torch.empty_like(d11)
+    cbdg.cbdg_green_moments(lat.handle, torch.from_numpy(sites).cuda(), sites.size,
+                            torch.from_numpy(targets).cuda(), targets.size, M, d11, d12)
+    assert np.array_equal(d11.cpu().numpy(), h11) and np.array_equal(d12.cpu().numpy(), h12)
+    a = orc.rescale(as_oracle(p))
+    E = np.linspace(-0.7 * a, 0.7 * a, 19)
+    g11, g12 = lat.green_function(sites, targets, M, E, kernel="lorentz", lam=2.0)
+    G11 = torch.empty((sites.size, targets.size, E.size), dtype=torch.complex128, device="cuda")
+    G12 = torch.empty_like(G11)
+    cbdg.cbdg_green_function(lat.handle, sites, sites.size, targets, targets.size, M, 1, 2.0,
+                             torch.from_numpy(E).cuda(), E.size, G11, G12)
+    assert np.array_equal(G11.cpu().numpy(), g11) and np.array_equal(G12.cpu().numpy(), g12)
+    J = lat.bond_currents(p.T, M)
+    Jd = torch.empty((p.N, 8), dtype=torch.float64, device="cuda")
+    cbdg.cbdg_bond_currents(lat.handle, p.T, M, 0, 0.0, Jd)
+    assert np.array_equal(Jd.cpu().numpy(), J)
+    # only one of the two outputs
+    o11 = np.zeros_like(h11)
+    cbdg.cbdg_green_moments(lat.handle, sites, sites.size, targets, targets.size, M, o11, None)
+    assert np.array_equal(o11, h11)
