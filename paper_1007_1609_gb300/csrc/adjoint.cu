@@ -207,7 +207,8 @@ __global__ void adjoint_final_kernel(int Lx, int Ly, int px, int py, int groups,
       double v = 0.0;
       if (ok) {
         const int jn = nx + Lx * ny, db = d ^ 1;
-        v = (-G(i, 4 + d) - G(jn, 4 + db) + G(i, 8 + d) + G(jn, 8 + db)) / a;
+        // pairwise sums are commutative, so both directed entries get the same bits
+        v = ((G(i, 8 + d) + G(jn, 8 + db)) - (G(i, 4 + d) + G(jn, 4 + db))) / a;
       }
       g_hop[static_cast<size_t>(i) * 4 + d] = v;
     }
