@@ -306,7 +306,10 @@ def run_gb300(args):
             traffic, traffic_src = recorded_traffic(("step_multi.cu", "multi_pass.cuh"), "step_multi_kernel_fp32_*.md")
             kernel = (f"step_multi_kernel: FP32, {k_used} recursion steps per pass over the vectors "
                       "(reads j_(n-1), j_n; writes the last two), moment products fused; the "
-                      "leftover odd step of each iteration runs step_real_kernel")
+                      "leftover step of each iteration runs step_real_kernel")
+            if k_used == 3 and p.Lx > 64:
+                kernel += ("; lean pass: level 0 read from its shared-memory ring, parameters in a ring "
+                           "of their own, FP32 column sums")
         else:
             traffic, traffic_src = recorded_traffic()
             kernel = "step_real_kernel: FP32 recursion step with fused moment products"
@@ -320,6 +323,10 @@ def run_gb300(args):
                     "peak_kind": f"{peak_kind} (copy bandwidth)",
                     "algorithmic_bytes_per_launch": (4 if k_used >= 2 else 3) * vec_bytes,
                     "recursion_launches_per_step": step_n / args.steps if args.steps else None,
+                    # the same time against the roofline of one step per pass (3 streams per step):
+                    # what several steps per pass buy over the unfused recursion
+                    "one_step_roofline_frac": ((3.0 * vec_bytes * k_used) / (step_ms / step_n / 1e3) / 1e9 / hbm
+                                               if step_n and k_used >= 2 else None),
                     "avg_launch_ms": step_ms / step_n if step_n else None,
                     "share_of_step": step_ms / ms if ms else None}
         extra = {}

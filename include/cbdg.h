@@ -306,7 +306,8 @@ enum {
                                     y edges: one pass reads j_(n-1), j_n and writes
                                     j_(n+K-1), j_(n+K); 1 = one step per pass; 0 (default) =
                                     3 where each thread holds one lattice site (Lx <= 256 /
-                                    (W / 4)), else 2.  Shapes the multi-step kernel does not
+                                    (W / 4)) and at slab width 16 up to Lx = 128 (the lean
+                                    pass), else 2.  Shapes the multi-step kernel does not
                                     serve run one step per pass: periodic y, FP64, complex
                                     fields, slab widths other than 8 and 16, Lx above 64 at
                                     slab width 16 (128 for K = 2, and for K = 3 at pipeline

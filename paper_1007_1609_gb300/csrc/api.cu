@@ -196,11 +196,15 @@ int host_neighbour(const cbdg_lattice_desc *d, int s, int dir) {
 bool finite_c(const cbdg_complex &z) { return isfinite(z.re) && isfinite(z.im); }
 
 // Recursion steps per HBM pass used when CBDG_OPT_TEMPORAL_STEPS is 0: two
-// steps per pass read and write 4 vectors where two single steps move 6.  A
-// third step pays when each thread holds one lattice site (Lx <= 64 at slab
-// width 16): measured 10-15% faster than two on 32..64-wide lattices, while
-// two sites per thread leave no registers for a third level.
-int64_t default_temporal_steps(int Lx, int W) { return Lx <= 256 / (W / 4) ? 3 : 2; }
+// steps per pass read and write 4 vectors where two single steps move 6, three
+// steps move 4 where three single steps move 9.  Three steps run where each
+// thread holds one lattice site (Lx <= 64 at slab width 16, 10-15% faster than
+// two on 32..64-wide lattices) and, at slab width 16, in the lean pass up to
+// Lx = 128 (two sites per thread; 0.594 against 0.685 ms per step on the
+// 128 x 128 lattice); elsewhere two.
+int64_t default_temporal_steps(int Lx, int W) {
+  return (Lx <= 256 / (W / 4) || (W == 16 && Lx <= 128)) ? 3 : 2;
+}
 
 // Recursion kernel family for the lattice:
 //   kReal:   real on-site pairing, nearest neighbours (step.cu), doubling;

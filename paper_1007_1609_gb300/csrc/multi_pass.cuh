@@ -101,9 +101,10 @@ constexpr int kPassThreads = 256;
 
 // LEAN: level 0 (j_n) stays in its shared-memory ring instead of a register
 // window, one slot longer (RQ = 4 + D: rows g-2 .. g+2+D), and the stencil
-// parameters come through the read-only cache instead of a ring.  That frees
-// 16 registers per site and row, which is what a third level needs at two
-// sites per thread, and the shared memory the third level's rows need.
+// parameters have a short ring of their own (AR = K + 1 rows: g-K+1 .. g+1,
+// row g+1 copied during wavefront g on its own barriers).  That frees 16
+// registers per site and row, which is what a third level needs at two sites
+// per thread, and the shared memory the third level's rows need.
 template <int W, int K, int D, int NT = kPassThreads, bool LEAN = false>
 struct PassShape {
   static constexpr int VEC = 4, QUADS = W / VEC, XSLOTS = NT / QUADS;
@@ -111,11 +112,12 @@ struct PassShape {
   static constexpr int RP = 3 + D;                 // j_{n-1} ring: rows g-1 .. g+2+D
   static constexpr int RS = RQ;
   static constexpr int AS = LEAN ? 0 : K + 2 + D;  // parameter ring: rows g-K+1 .. g+2+D
-  static constexpr int NB = RQ;                    // mbarriers (one per staged row in flight)
+  static constexpr int AR = LEAN ? K + 1 : 0;      // LEAN parameter ring: rows g-K+1 .. g+1
+  static constexpr int NB = RQ + AR;               // mbarriers (one per staged row in flight)
   // floats of shared memory the pass uses
   static __host__ __device__ size_t smem_floats(int Lx) {
     const size_t rowel = static_cast<size_t>(2) * Lx * W, pel = static_cast<size_t>(Lx) * kParamStride;
-    return (RQ + RP + 2 * (K - 1)) * rowel + AS * pel;
+    return (RQ + RP + 2 * (K - 1)) * rowel + (AS + AR) * pel;
   }
 };
 
@@ -126,19 +128,22 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
                                            Acc (&accA)[K][4], Acc (&accB)[K][4], Acc (&accC)[K][4]) {
   using Sh = PassShape<W, K, D, NT, LEAN>;
   constexpr int VEC = Sh::VEC, QUADS = Sh::QUADS, XSLOTS = Sh::XSLOTS;
-  constexpr int RQ = Sh::RQ, RP = Sh::RP, AS = Sh::AS, NB = Sh::NB;
+  constexpr int RQ = Sh::RQ, RP = Sh::RP, AS = Sh::AS, AR = Sh::AR;
   static_assert(W % VEC == 0 && NT % QUADS == 0 && K >= 2, "bad shape");
   const int rowel = 2 * Lx * W;
   const int pel = Lx * kParamStride;
   float *sq = smem;                       // [RQ][rowel]  j_n
   float *sp = sq + RQ * rowel;            // [RP][rowel]  j_{n-1}
   float *sl = sp + RP * rowel;            // [K-1][2][rowel] levels 1..K-1
-  float *sa = sl + (K - 1) * 2 * rowel;   // [AS][pel] (not LEAN)
+  float *sa = sl + (K - 1) * 2 * rowel;   // [AS][pel], LEAN: [AR][pel]
   const int t = threadIdx.x;
   const int q = t % QUADS, xs = t / QUADS;
   const unsigned row_bytes = rowel * 4u, par_bytes = pel * 4u;
-  auto bar_of = [&](int l) { return smem_addr(&bars[(base + l) % NB]); };
-  auto par_of = [&](int l) { return static_cast<unsigned>(((base + l) / NB) & 1); };
+  auto bar_of = [&](int l) { return smem_addr(&bars[(base + l) % RQ]); };
+  auto par_of = [&](int l) { return static_cast<unsigned>(((base + l) / RQ) & 1); };
+  // LEAN parameter row l: slot and barrier (base + l) % AR, after the RQ row barriers
+  auto pbar_of = [&](int l) { return smem_addr(&bars[RQ + (AR > 0 ? (base + l) % AR : 0)]); };
+  auto ppar_of = [&](int l) { return static_cast<unsigned>(AR > 0 ? ((base + l) / AR) & 1 : 0); };
 
   // load l: rows l of j_n and j_{n-1} and the parameters of lattice row l
   auto issue = [&](int l) {
@@ -151,9 +156,19 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
     if constexpr (!LEAN)
       bulk_load(smem_addr(sa + (l % AS) * pel), par + static_cast<size_t>(l) * pel, par_bytes, bar);
   };
+  // LEAN: parameter row l, copied into its own ring slot
+  auto issue_par = [&](int l) {
+    const unsigned bar = pbar_of(l);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(par_bytes) : "memory");
+    bulk_load(smem_addr(sa + (AR > 0 ? (base + l) % AR : 0) * pel), par + static_cast<size_t>(l) * pel, par_bytes,
+              bar);
+  };
   int issued = min(Ly, 2 + D);
-  if (t == 0)
+  int pissued = LEAN ? min(Ly, 2) : 0;  // rows 0, 1 before the first wavefront
+  if (t == 0) {
     for (int l = 0; l < issued; ++l) issue(l);
+    for (int l = 0; l < pissued; ++l) issue_par(l);
+  }
 
   const int hb = Lx * W;
   const int off = q * VEC;
@@ -165,7 +180,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
 #pragma unroll
       for (int k = 0; k < MAXX; ++k) wu[l][s][k] = wv[l][s][k] = zero4();
 
-  int waited = 0;
+  int waited = 0, pwaited = 0;
   bool ok = true;
   if constexpr (!LEAN) {
     ok = mbar_wait(bar_of(0), par_of(0), wait_ns);
@@ -188,10 +203,14 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
     for (int ph = 0; ph < 3; ++ph) {
       const int g = g0 + ph;
       if (stop || g >= G) break;
-      // rows up to g + 1 must have landed
+      // rows up to g + 1 must have landed (LEAN: parameter rows up to g)
       for (; ok && waited <= min(g + 1, Ly - 1); ++waited)
         if (!mbar_wait(bar_of(waited), par_of(waited), wait_ns))
           ok = false;
+      if constexpr (LEAN)
+        for (; ok && pwaited <= min(g, Ly - 1); ++pwaited)
+          if (!mbar_wait(pbar_of(pwaited), ppar_of(pwaited), wait_ns))
+            ok = false;
       if (!ok) *abort_flag = 1;
       __syncthreads();
       if (*abort_flag) {
@@ -203,6 +222,14 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
       if (g + 2 + D < Ly) {
         if (t == 0) issue(g + 2 + D);
         issued = g + 3 + D;
+      }
+      // LEAN: the parameter slot of row g - K is free (its last reader, level K,
+      // ran at wavefront g - 1): parameter row g + 1 goes there
+      if constexpr (LEAN) {
+        if (g + 1 < Ly && g + 1 >= pissued) {
+          if (t == 0) issue_par(g + 1);
+          pissued = g + 2;
+        }
       }
       // level 0 "computes" row g + 1: its centre enters the window
       if constexpr (!LEAN) {
@@ -226,7 +253,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
         if (r >= 0 && r < Ly) {
           const float *nb = lv == 1 ? sq + (r % RQ) * rowel : sl + ((lv - 2) * 2 + (r & 1)) * rowel;
           const float *po = sp + (r % RP) * rowel;
-          const float *pc = LEAN ? par + static_cast<size_t>(r) * pel : sa + (r % AS) * pel;
+          const float *pc = LEAN ? sa + ((base + r) % (AR > 0 ? AR : 1)) * pel : sa + (r % (AS > 0 ? AS : 1)) * pel;
           float *dl = lv < K ? sl + ((lv - 1) * 2 + (r & 1)) * rowel : nullptr;
 #pragma unroll
           for (int k = 0; k < MAXX; ++k) {
@@ -271,14 +298,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
                 uo = wu[lv >= 2 ? lv - 2 : 0][sc][k];
                 vo = wv[lv >= 2 ? lv - 2 : 0][sc][k];
               }
-              float4 pa, pb;
-              if constexpr (LEAN) {
-                pa = __ldg(reinterpret_cast<const float4 *>(pc + x * kParamStride));
-                pb = __ldg(reinterpret_cast<const float4 *>(pc + x * kParamStride + 4));
-              } else {
-                pa = lds4(pc + x * kParamStride);
-                pb = lds4(pc + x * kParamStride + 4);
-              }
+              const float4 pa = lds4(pc + x * kParamStride), pb = lds4(pc + x * kParamStride + 4);
               const float e = pa.x, d = pa.y, t0 = pa.z, t1 = pa.w, t2 = pb.x, t3 = pb.y;
               float4 un, vn;
 #pragma unroll
@@ -324,9 +344,12 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
     }
   }
   if (*abort_flag) {
-    if (t == 0)
+    if (t == 0) {
       for (int l = waited; l < issued; ++l)
         if (!mbar_wait(bar_of(l), par_of(l), wait_ns)) break;
+      for (int l = pwaited; l < pissued; ++l)
+        if (!mbar_wait(pbar_of(l), ppar_of(l), wait_ns)) break;
+    }
     return false;
   }
   return true;
