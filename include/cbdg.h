@@ -45,7 +45,7 @@ enum {
   CBDG_ERR_OOM = 3,           /* device allocation failed */
   CBDG_ERR_SPECTRUM = 4,      /* a moment exceeded 1 in magnitude: a too small */
   CBDG_ERR_NOT_CONVERGED = 5, /* self-consistency did not reach its tolerance */
-  CBDG_ERR_UNSUPPORTED = 6    /* valid input that this build does not handle */
+  CBDG_ERR_UNSUPPORTED = 6    /* valid input that the library has no kernel for */
 };
 
 enum { CBDG_ONSITE_U = 0, CBDG_BOND_V = 1 };        /* pairing channel */
@@ -80,7 +80,7 @@ typedef struct {
  * into library-owned device memory (Eq. 2).  All descriptor arrays are read
  * during the call only.  *out receives an opaque handle; release it with
  * cbdg_destroy.  Errors: INVALID_ARG for any violated constraint above,
- * UNSUPPORTED for combinations this build has no kernel for, OOM, CUDA. */
+ * UNSUPPORTED for combinations the library has no kernel for, OOM, CUDA. */
 cbdg_status cbdg_build_lattice(const cbdg_lattice_desc *desc, cbdg_stream stream,
                                cbdg_lattice **out);
 
