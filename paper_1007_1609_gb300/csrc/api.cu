@@ -600,13 +600,11 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
         CK(launch_step_multi(a, mcfg, Kt, L->stream));
         if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx + 1], L->stream));
         L->launches += 1;
-        for (int lv = 0; lv < Kt; ++lv) {
-          CK(launch_fold(n + lv, M, ncols, ld, 1, L->partials.as<double>() + static_cast<size_t>(lv) * 3 * ld,
-                         L->C.as<double>(), L->mu1.as<double>(), L->dA.as<double2>(),
-                         L->acc_n.as<double>(), L->acc_d.as<double2>(), mee, meh, mom_stride,
-                         L->flags.as<unsigned int>(), tol, L->stream));
-          L->launches += 1;
-        }
+        // the Kt levels' sums in one fold launch, in step order
+        CK(launch_fold(n, M, ncols, ld, 1, L->partials.as<double>(), L->C.as<double>(), L->mu1.as<double>(),
+                       L->dA.as<double2>(), L->acc_n.as<double>(), L->acc_d.as<double2>(), mee, meh, mom_stride,
+                       L->flags.as<unsigned int>(), tol, L->stream, Kt));
+        L->launches += 1;
         a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
         launch_bytes.push_back(4.0 * static_cast<double>(vbytes));
         ++launch_idx;

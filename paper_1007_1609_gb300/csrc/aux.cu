@@ -211,17 +211,26 @@ __global__ void init_real_kernel(int Lx, int Ly, int px, int py, int ncols, int 
 //   mu^eh_2n   = 0
 //   mu^eh_2n+1 = 2 (-1)^(n+1) sum_s (u'_s v_s - v'_s u_s) - conj(Delta_i)/a
 // then the fold acc_n -= C_m mu_m, acc_d += C_m conj(mu^eh_m).
-__global__ void fold_kernel(int n, int M, int ncols, int ld, int row_split,
+// Steps n .. n + levels - 1 in order (a multi-step pass leaves one [3][ld]
+// block of sums per level, row_split = 1); the same arithmetic, in the same
+// order, as one launch per step.
+__global__ void fold_kernel(int n0, int levels, int M, int ncols, int ld, int row_split,
                             const double *partials, const double *C, const double *mu1,
                             const double2 *dA, double *acc_n, double2 *acc_d, double *mu_ee,
                             double2 *mu_eh, int mom_stride, unsigned int *flags, double tol) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= ncols) return;
+  double an = acc_n[b];
+  double2 ad = acc_d[b];
+  bool bad = false;
+  for (int lv = 0; lv < levels; ++lv) {
+  const int n = n0 + lv;
+  const double *part = partials + static_cast<size_t>(lv) * row_split * 3 * ld;
   double A = 0.0, B = 0.0, Cs = 0.0;
   for (int s = 0; s < row_split; ++s) {
-    A += partials[(static_cast<size_t>(s) * 3 + 0) * ld + b];
-    B += partials[(static_cast<size_t>(s) * 3 + 1) * ld + b];
-    Cs += partials[(static_cast<size_t>(s) * 3 + 2) * ld + b];
+    A += part[(static_cast<size_t>(s) * 3 + 0) * ld + b];
+    B += part[(static_cast<size_t>(s) * 3 + 1) * ld + b];
+    Cs += part[(static_cast<size_t>(s) * 3 + 2) * ld + b];
   }
   const int m0 = 2 * n, m1 = 2 * n + 1;
   const double e0 = 2.0 * A - 1.0;
@@ -229,9 +238,6 @@ __global__ void fold_kernel(int n, int M, int ncols, int ld, int row_split,
   const double sgn = (n & 1) ? 1.0 : -1.0;  // (-1)^(n+1)
   const double2 da = dA[b];
   const double2 h1 = make_double2(2.0 * sgn * Cs - da.x, -da.y);
-  double an = acc_n[b];
-  double2 ad = acc_d[b];
-  bool bad = false;
   if (m0 < M) {
     an -= C[m0] * e0;
     bad |= fabs(e0) > 1.0 + tol;
@@ -247,6 +253,7 @@ __global__ void fold_kernel(int n, int M, int ncols, int ld, int row_split,
     if (mu_eh) mu_eh[(static_cast<size_t>(b) * M + m1) * mom_stride] = h1;
   }
   if (!(fabs(e0) < 1e300) || !(fabs(e1) < 1e300)) bad = true;  // NaN / inf
+  }
   acc_n[b] = an;
   acc_d[b] = ad;
   if (bad) atomicOr(flags, kFlagSpectrum);
@@ -340,9 +347,9 @@ cudaError_t launch_init_real(int precision, int Lx, int Ly, int px, int py, int 
 cudaError_t launch_fold(int n, int M, int ncols, int ld, int row_split, const double *partials,
                         const double *C, const double *mu1, const double2 *dA, double *acc_n,
                         double2 *acc_d, double *mu_ee, double2 *mu_eh, int mom_stride,
-                        unsigned int *flags, double tol, cudaStream_t s) {
+                        unsigned int *flags, double tol, cudaStream_t s, int levels) {
   if (ncols <= 0) return cudaSuccess;
-  fold_kernel<<<blocks(ncols, 256), 256, 0, s>>>(n, M, ncols, ld, row_split, partials, C, mu1, dA,
+  fold_kernel<<<blocks(ncols, 256), 256, 0, s>>>(n, levels, M, ncols, ld, row_split, partials, C, mu1, dA,
                                                  acc_n, acc_d, mu_ee, mu_eh, mom_stride, flags, tol);
   return cudaGetLastError();
 }

@@ -172,10 +172,11 @@ cudaError_t launch_init_real(int precision, int Lx, int Ly, int px, int py, int 
                              const double *C, int M, void *j0, void *j1, double *mu1,
                              double2 *dA, double *acc_n, double2 *acc_d, double *mu_ee,
                              double2 *mu_eh, int mom_stride, cudaStream_t s);
+// levels > 1: steps n .. n + levels - 1 of a multi-step pass, partials [levels][3][ld].
 cudaError_t launch_fold(int n, int M, int ncols, int ld, int row_split, const double *partials,
                         const double *C, const double *mu1, const double2 *dA, double *acc_n,
                         double2 *acc_d, double *mu_ee, double2 *mu_eh, int mom_stride,
-                        unsigned int *flags, double tol, cudaStream_t s);
+                        unsigned int *flags, double tol, cudaStream_t s, int levels = 1);
 // U_site (may be NULL): a coupling per site [N] in place of U.
 cudaError_t launch_finalize_onsite(int ncols, const int32_t *sites, double U, const double *U_site,
                                    const double *acc_n, const double2 *acc_d, double2 *dout,
