@@ -620,3 +620,19 @@ def test_site_coupling_uniform_equals_scalar_and_gradient():
         d1[i] += h
         d2[i] -= h
         assert g_delta[i] == pytest.approx((loss(delta=d1) - loss(delta=d2)) / (2 * h), rel=1e-6, abs=1e-9)
+
+
+def test_tanh_coefficients_odd_and_half_node_identity():
+    """tanh is odd and the Gauss-Chebyshev nodes are symmetric: the even c_n
+    vanish (to round-off) and the odd c_n equal twice the sum over the first
+    K/2 nodes, the identity the coefficient kernels use; also at T = 0."""
+    M, K, a = 200, 4096, 6.3
+    for T in (0.02, 0.0):
+        c = orc.tanh_coefficients(M, K, a, T)
+        assert np.abs(c[0::2]).max() < 1e-15
+        k = np.arange(K // 2)
+        x = np.cos(np.pi * (k + 0.5) / K)
+        f = np.tanh(a * x / (2 * T)) if T > 0 else np.sign(x)
+        n = np.arange(1, M, 2)
+        half = 2.0 / K * (f[None, :] * np.cos(n[:, None] * np.pi * (k[None, :] + 0.5) / K)).sum(1)
+        assert np.allclose(c[1::2], half, atol=1e-15, rtol=0)
