@@ -26,7 +26,8 @@
  *   - a cyclic Jacobi eigensolver for dense Hermitian matrices (Golub and
  *     Van Loan, the symmetric Jacobi method with a phase rotation for the
  *     complex off-diagonal), used only as an independent exact check.
- *   - reverse-mode gradient of one self-consistency map, storing every j_n.
+ *   - reverse-mode gradients, storing every j_n: of one self-consistency
+ *     map (a loss on Delta_out) and of a loss on the LDOS, a frozen.
  *   - nonlocal moments <alpha_t|T_n|e_i> at chosen target sites, the
  *     Green's function of gf1 built from them, and the bond currents of
  *     Eq. 20 from the one-body density matrix f(H).
@@ -725,27 +726,112 @@ int orc_jacobi_eigh(int n, cplx *A, double *w, cplx *V, double tol, int max_swee
 /* Reverse-mode gradient of one self-consistency map (a and C_n frozen).     */
 /* ------------------------------------------------------------------------ */
 
-/* Real on-site s-wave lattices only (real eps, real hoppings, real Delta).
- * Forward: Dout_i = (U/2) sum_{n<M} C_n <h_i|T_n(H/a)|e_i> for every site.
- * Given w_i = dL/dDout_i, returns
- *   g_eps[i]        = dL/d eps_i
+/* Reverse mode of the direct recursion for ONE start column e_i (real
+ * lattice): stores j_0 .. j_{M-1} in J [M*n], runs the adjoint recursion
+ *   lam_m = src[m] u + (2/a) H lam_{m+1} - lam_{m+2}   (m = M-1 .. 1),
+ * where u is the basis vector of row src_row, for the output
+ * sum_{m>=1} src[m] <u|j_m>, and adds the matrix gradient
+ * dOut/dH~_{rs} = sum_{m>=1} f_m lam_m(r) j_{m-1}(s) (f_1 = 1, f_m = 2) at
+ * every CSR position of H into Gl.  lam is [(M+2)*n], tmp [n]. */
+static void column_reverse_mode(const orc_csr *H, int n, int i, int M, double a, int src_row,
+                                const double *src, double *J, double *lam, double *tmp, double *Gl) {
+  /* forward, storing every j_m (real) */
+  memset(J, 0, sizeof(double) * n);
+  J[2 * i] = 1.0;
+  for (int m = 1; m < M; ++m) {
+    double *jm = J + (size_t)m * n, *j1 = J + (size_t)(m - 1) * n;
+    double *j2 = (m >= 2) ? J + (size_t)(m - 2) * n : NULL;
+    double s = (m == 1) ? 1.0 / a : 2.0 / a;
+    for (int r = 0; r < n; ++r) {
+      double acc = 0.0;
+      for (int k = H->rowptr[r]; k < H->rowptr[r + 1]; ++k) acc += creal(H->val[k]) * j1[H->col[k]];
+      jm[r] = s * acc - (j2 ? j2[r] : 0.0);
+    }
+  }
+  memset(lam, 0, sizeof(double) * (size_t)n * (M + 2));
+  for (int m = M - 1; m >= 1; --m) {
+    double *lm = lam + (size_t)m * n, *l1 = lam + (size_t)(m + 1) * n, *l2 = lam + (size_t)(m + 2) * n;
+    /* lam_m = y_m + (2/a) H l1 - l2, where the step producing j_{m+1} is
+     * j_{m+1} = (2/a)H j_m - j_{m-1} for m >= 1 (and j_1 = (1/a) H j_0). */
+    for (int r = 0; r < n; ++r) {
+      double acc = 0.0;
+      for (int k = H->rowptr[r]; k < H->rowptr[r + 1]; ++k) acc += creal(H->val[k]) * l1[H->col[k]];
+      tmp[r] = (m + 1 < M ? (2.0 / a) * acc : 0.0) - (m + 2 < M ? l2[r] : 0.0);
+    }
+    for (int r = 0; r < n; ++r) lm[r] = tmp[r];
+    lm[src_row] += src[m];
+  }
+  /* dL/dH~ contributions: step m (m>=2): j_m = 2 H~ j_{m-1} - j_{m-2}
+   *   -> 2 lam_m (x) j_{m-1};  step 1: j_1 = H~ j_0 -> lam_1 (x) j_0.
+   * Stored per CSR entry (r,s): sum lam(r) j(s). */
+  for (int m = 1; m < M; ++m) {
+    double f = (m == 1) ? 1.0 : 2.0;
+    double *lm = lam + (size_t)m * n, *jp = J + (size_t)(m - 1) * n;
+    for (int r = 0; r < n; ++r) {
+      double lr = f * lm[r];
+      if (lr == 0.0) continue;
+      for (int k = H->rowptr[r]; k < H->rowptr[r + 1]; ++k) Gl[k] += lr * jp[H->col[k]];
+    }
+  }
+}
+
+/* Contracts the matrix gradient G = dL/dH~ (per CSR position of H) with
+ * dH~/dparameter (H~ = H/a, Eq. 2):
+ *   g_eps[i]        = dL/d eps_i          (H_{e_i e_i} = eps - mu, H_{h_i h_i} = -(eps - mu))
  *   g_hop[i*nd + d] = dL/d t_{i,d}, treating t_{i,d} and its mirror
- *                     t_{i+d,d^1} as ONE real parameter (the undirected bond);
- *                     the value is stored on both directed entries
- *   g_delta[i]      = dL/d Delta_in,i
- * For every column the full sequence j_0..j_{M-1} is stored and the adjoint
- * recursion lam_n = y_n + 2 H~ lam_{n+1} - lam_{n+2} runs backwards; the
- * matrix gradient dL/dH~_{rs} = sum_n (2 lam_{n+1}(r) j_n(s)) (factor 1 on
- * the first step j_1 = H~ j_0) is contracted with dH~/dparam. */
-int orc_scf_map_gradient(const orc_lattice *L, double a, const double *C, int M,
-                         const double *w, double *g_eps, double *g_hop, double *g_delta) {
+ *                     t_{i+d,d^1} as ONE real parameter (the undirected bond;
+ *                     H_{e_i e_j} = -t, H_{h_i h_j} = +t for both directed
+ *                     copies); the value is stored on both directed entries
+ *   g_delta[i]      = dL/d Delta_i        (H_{e_i h_i} = H_{h_i e_i} = Delta_i). */
+static void matrix_gradient_to_params(const orc_lattice *L, const orc_csr *H, const double *G, double a,
+                                      double *g_eps, double *g_hop, double *g_delta) {
+  int N = L->Lx * L->Ly;
+  int nd = L->n_dirs;
+  for (int i = 0; i < N; ++i) {
+    double ge = 0.0, gd = 0.0;
+    for (int part = 0; part < 2; ++part) {
+      int r = 2 * i + part;
+      for (int k = H->rowptr[r]; k < H->rowptr[r + 1]; ++k) {
+        int c = H->col[k];
+        if (c == 2 * i && part == 0) ge += G[k];          /* H_{e_i e_i} = eps - mu */
+        if (c == 2 * i + 1 && part == 1) ge -= G[k];      /* H_{h_i h_i} = -(eps - mu) */
+        if (c == 2 * i + 1 && part == 0) gd += G[k];      /* H_{e_i h_i} = Delta_i */
+        if (c == 2 * i && part == 1) gd += G[k];          /* H_{h_i e_i} = Delta_i */
+      }
+    }
+    g_eps[i] = ge / a;
+    g_delta[i] = gd / a;
+  }
+  for (int i = 0; i < N; ++i) {
+    for (int d = 0; d < nd; ++d) {
+      int j = orc_neighbour(L, i, d);
+      double g = 0.0;
+      if (j >= 0) {
+        for (int part = 0; part < 2; ++part) {
+          for (int side = 0; side < 2; ++side) {
+            int r = side == 0 ? 2 * i + part : 2 * j + part;
+            int cc = side == 0 ? 2 * j + part : 2 * i + part;
+            for (int k = H->rowptr[r]; k < H->rowptr[r + 1]; ++k)
+              if (H->col[k] == cc) g += (part == 0 ? -1.0 : 1.0) * G[k];
+          }
+        }
+      }
+      g_hop[(size_t)i * nd + d] = g / a;
+    }
+  }
+}
+
+/* Reverse mode over the listed start columns: column c (start site
+ * sites[c]) contributes sum_{m>=1} src[c*M + m] <row(c)|j_m>, row(c) =
+ * 2 sites[c] + src_part (0: electron row e_i, 1: hole row h_i).  The matrix
+ * gradient is summed over columns (per-thread copies, added in thread order)
+ * and contracted with dH/dparam. */
+static void reverse_mode(const orc_lattice *L, double a, const int32_t *sites, int n_cols, int M, int src_part,
+                         const double *src, double *g_eps, double *g_hop, double *g_delta) {
   int N = L->Lx * L->Ly;
   int n = 2 * N;
-  int nd = L->n_dirs;
   orc_csr H = build_csr(L);
   int nnz = H.rowptr[n];
-  /* G[k] accumulates dL/dH~ at CSR position k (real arithmetic; the matrix
-   * is real here). */
   double *G = (double *)calloc(nnz, sizeof(double));
   int nthreads = 1;
 #ifdef _OPENMP
@@ -763,49 +849,8 @@ int orc_scf_map_gradient(const orc_lattice *L, double a, const double *C, int M,
     double *lam = (double *)malloc(sizeof(double) * (size_t)n * (M + 2));
     double *tmp = (double *)malloc(sizeof(double) * n);
 #pragma omp for schedule(dynamic, 1)
-    for (int i = 0; i < N; ++i) {
-      /* forward, storing every j_m (real) */
-      memset(J, 0, sizeof(double) * n);
-      J[2 * i] = 1.0;
-      for (int m = 1; m < M; ++m) {
-        double *jm = J + (size_t)m * n, *j1 = J + (size_t)(m - 1) * n;
-        double *j2 = (m >= 2) ? J + (size_t)(m - 2) * n : NULL;
-        double s = (m == 1) ? 1.0 / a : 2.0 / a;
-        for (int r = 0; r < n; ++r) {
-          double acc = 0.0;
-          for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k) acc += creal(H.val[k]) * j1[H.col[k]];
-          jm[r] = s * acc - (j2 ? j2[r] : 0.0);
-        }
-      }
-      /* output s_i = sum_m y_m . j_m with y_m = w_i (U/2) C_m h_i */
-      double wi = w[i] * 0.5 * coupling_of(L, i);
-      memset(lam, 0, sizeof(double) * (size_t)n * (M + 2));
-      for (int m = M - 1; m >= 1; --m) {
-        double *lm = lam + (size_t)m * n, *l1 = lam + (size_t)(m + 1) * n, *l2 = lam + (size_t)(m + 2) * n;
-        /* lam_m = y_m + (2/a) H l1 - l2, where the step producing j_{m+1} is
-         * j_{m+1} = (2/a)H j_m - j_{m-1} for m >= 1 (and j_1 = (1/a) H j_0). */
-        for (int r = 0; r < n; ++r) {
-          double acc = 0.0;
-          for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k) acc += creal(H.val[k]) * l1[H.col[k]];
-          tmp[r] = (m + 1 < M ? (2.0 / a) * acc : 0.0) - (m + 2 < M ? l2[r] : 0.0);
-        }
-        for (int r = 0; r < n; ++r) lm[r] = tmp[r];
-        lm[2 * i + 1] += wi * C[m];
-      }
-      /* dL/dH~ contributions: step m (m>=2): j_m = 2 H~ j_{m-1} - j_{m-2}
-       *   -> 2 lam_m (x) j_{m-1};  step 1: j_1 = H~ j_0 -> lam_1 (x) j_0.
-       * Stored per CSR entry (r,s): sum lam(r) j(s). Converted from H~ to H
-       * (divide by a) at the end. */
-      for (int m = 1; m < M; ++m) {
-        double f = (m == 1) ? 1.0 : 2.0;
-        double *lm = lam + (size_t)m * n, *jp = J + (size_t)(m - 1) * n;
-        for (int r = 0; r < n; ++r) {
-          double lr = f * lm[r];
-          if (lr == 0.0) continue;
-          for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k) Gl[k] += lr * jp[H.col[k]];
-        }
-      }
-    }
+    for (int c = 0; c < n_cols; ++c)
+      column_reverse_mode(&H, n, sites[c], M, a, 2 * sites[c] + src_part, src + (size_t)c * M, J, lam, tmp, Gl);
     free(J);
     free(lam);
     free(tmp);
@@ -813,42 +858,66 @@ int orc_scf_map_gradient(const orc_lattice *L, double a, const double *C, int M,
   for (int t = 0; t < nthreads; ++t)
     for (int k = 0; k < nnz; ++k) G[k] += Gt[(size_t)nnz * t + k];
   free(Gt);
-  /* contract with dH/dparam (H~ = H/a) */
-  for (int i = 0; i < N; ++i) {
-    double ge = 0.0, gd = 0.0;
-    for (int part = 0; part < 2; ++part) {
-      int r = 2 * i + part;
-      for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k) {
-        int c = H.col[k];
-        if (c == 2 * i && part == 0) ge += G[k];          /* H_{e_i e_i} = eps - mu */
-        if (c == 2 * i + 1 && part == 1) ge -= G[k];      /* H_{h_i h_i} = -(eps - mu) */
-        if (c == 2 * i + 1 && part == 0) gd += G[k];      /* H_{e_i h_i} = Delta_i */
-        if (c == 2 * i && part == 1) gd += G[k];          /* H_{h_i e_i} = Delta_i */
-      }
-    }
-    g_eps[i] = ge / a;
-    g_delta[i] = gd / a;
-  }
-  /* bonds: H_{e_i e_j} = -t, H_{h_i h_j} = +t, for both directed copies */
-  for (int i = 0; i < N; ++i) {
-    for (int d = 0; d < nd; ++d) {
-      int j = orc_neighbour(L, i, d);
-      double g = 0.0;
-      if (j >= 0) {
-        for (int part = 0; part < 2; ++part) {
-          for (int side = 0; side < 2; ++side) {
-            int r = side == 0 ? 2 * i + part : 2 * j + part;
-            int cc = side == 0 ? 2 * j + part : 2 * i + part;
-            for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k)
-              if (H.col[k] == cc) g += (part == 0 ? -1.0 : 1.0) * G[k];
-          }
-        }
-      }
-      g_hop[(size_t)i * nd + d] = g / a;
-    }
-  }
+  matrix_gradient_to_params(L, &H, G, a, g_eps, g_hop, g_delta);
   free(G);
   free_csr(&H);
+}
+
+/* Real on-site s-wave lattices only (real eps, real hoppings, real Delta).
+ * Forward: Dout_i = (U/2) sum_{n<M} C_n <h_i|T_n(H/a)|e_i> for every site.
+ * Given w_i = dL/dDout_i, returns g_eps, g_hop, g_delta as described at
+ * matrix_gradient_to_params (g_delta = dL/d Delta_in).  For every column
+ * the full sequence j_0..j_{M-1} is stored and the adjoint recursion
+ * lam_n = y_n + 2 H~ lam_{n+1} - lam_{n+2}, y_n = w_i (U_i/2) C_n h_i, runs
+ * backwards (column_reverse_mode). */
+int orc_scf_map_gradient(const orc_lattice *L, double a, const double *C, int M,
+                         const double *w, double *g_eps, double *g_hop, double *g_delta) {
+  int N = L->Lx * L->Ly;
+  int32_t *sites = (int32_t *)malloc(sizeof(int32_t) * N);
+  double *src = (double *)malloc(sizeof(double) * (size_t)N * M);
+  for (int i = 0; i < N; ++i) {
+    sites[i] = i;
+    double wi = w[i] * 0.5 * coupling_of(L, i);
+    for (int m = 0; m < M; ++m) src[(size_t)i * M + m] = wi * C[m];
+  }
+  reverse_mode(L, a, sites, N, M, 1, src, g_eps, g_hop, g_delta);
+  free(sites);
+  free(src);
+  return 0;
+}
+
+/* Reverse-mode gradient of a loss on the up-spin LDOS of Eq. 17 (with the
+ * expansion of Eq. 10) at the listed start sites, a frozen.  Real on-site
+ * s-wave lattices only.  The forward map is orc_ldos:
+ *   N(E_e, i_c) = sum_m w_m(E_e) mu_m(i_c),  mu_m(i) = <e_i|T_m(H/a)|e_i>,
+ *   w_m(E) = (2 - delta_m0) g_m T_m(E/a) / (pi a sqrt(1 - (E/a)^2)),
+ * so with G[c*n_E + e] = dL/dN(E_e, i_c) the output is
+ * sum_c sum_{m>=1} s_{c,m} <e_{i_c}|j_m> with s_{c,m} = sum_e G[c,e] w_m(E_e)
+ * (mu_0 = 1 carries no parameter), and the gradient follows by reverse
+ * mode exactly as for the self-consistency map, with the source on the
+ * electron row.  Returns g_eps, g_hop, g_delta as described at
+ * matrix_gradient_to_params. */
+int orc_ldos_gradient(const orc_lattice *L, double a, const int32_t *sites, int n_sites, int M, int kernel,
+                      double lambda, const double *energies, int n_E, const double *dL_dldos, double *g_eps,
+                      double *g_hop, double *g_delta) {
+  double *g = (double *)malloc(sizeof(double) * M);
+  if (kernel == 0) orc_jackson(M, g);
+  else orc_lorentz(M, lambda, g);
+  double *src = (double *)calloc((size_t)n_sites * M, sizeof(double));
+  for (int c = 0; c < n_sites; ++c) {
+    for (int m = 1; m < M; ++m) {
+      double s = 0.0;
+      for (int e = 0; e < n_E; ++e) {
+        double x = energies[e] / a;
+        double w = 2.0 * g[m] * cos(m * acos(x)) / (M_PI * a * sqrt(1.0 - x * x));
+        s += dL_dldos[(size_t)c * n_E + e] * w;
+      }
+      src[(size_t)c * M + m] = s;
+    }
+  }
+  reverse_mode(L, a, sites, n_sites, M, 0, src, g_eps, g_hop, g_delta);
+  free(g);
+  free(src);
   return 0;
 }
 

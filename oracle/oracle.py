@@ -44,16 +44,34 @@ _lock = threading.Lock()
 _lib = None
 
 
+def _stamp(cmd) -> str:
+    """SHA-256 of the source, the compile command and the machine type."""
+    import hashlib
+    import platform
+    h = hashlib.sha256()
+    with open(_SRC, "rb") as fh:
+        h.update(fh.read())
+    h.update(repr(cmd).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile oracle.c into a shared library (gcc, FP64, OpenMP)."""
+    """Compile oracle.c into a shared library (gcc, FP64, OpenMP); rebuilt
+    whenever the stamp of source, command and machine changes."""
     os.makedirs(_BUILD, exist_ok=True)
-    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
-    if force or stale:
+    flags = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-D_GNU_SOURCE"]
+    want = _stamp(flags)
+    stamp_path = _LIB + ".stamp"
+    fresh = (os.path.exists(_LIB) and os.path.exists(stamp_path)
+             and open(stamp_path).read().strip() == want)
+    if force or not fresh:
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-D_GNU_SOURCE",
-               "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        subprocess.run(flags + ["-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB)
+        with open(stamp_path + ".tmp", "w") as fh:
+            fh.write(want + "\n")
+        os.replace(stamp_path + ".tmp", stamp_path)
     return _LIB
 
 
@@ -96,6 +114,7 @@ def _load():
             lib.orc_scf.argtypes = [P, D, I, I, D, D, I, P, P, P]
             lib.orc_jacobi_eigh.argtypes = [I, P, P, P, D, I]
             lib.orc_scf_map_gradient.argtypes = [P, D, P, I, P, P, P, P]
+            lib.orc_ldos_gradient.argtypes = [P, D, P, I, I, I, D, P, I, P, P, P, P]
             lib.orc_neighbour.argtypes = [P, I, I]
             lib.orc_green_moments.argtypes = [P, D, I, P, I, P, I, I, P, P]
             lib.orc_green_function.argtypes = [P, I, I, I, D, I, D, P, I, P]
@@ -313,6 +332,24 @@ def scf_map_gradient(lat: Lattice, a: float, C, w):
     c = lat._c()
     _load().orc_scf_map_gradient(ctypes.byref(c), float(a), _ptr(C), C.size, _ptr(w),
                                  _ptr(g_eps), _ptr(g_hop), _ptr(g_delta))
+    return g_eps, g_hop.reshape(lat.N, lat.n_dirs), g_delta
+
+
+def ldos_gradient(lat: Lattice, a: float, sites, M: int, energies, dL_dldos, kernel: int = 0,
+                  lam: float = 0.0):
+    """Reverse-mode gradient of a loss on the LDOS of Eq. 17 at the listed
+    sites, given dL/dLDOS [n_sites, n_E], a frozen (real s-wave lattices only).
+
+    Returns (g_eps [N], g_hop [N, n_dirs], g_delta [N])."""
+    sites = np.ascontiguousarray(sites, dtype=np.int32)
+    energies = np.ascontiguousarray(energies, dtype=np.float64)
+    G = np.ascontiguousarray(dL_dldos, dtype=np.float64).reshape(sites.size, energies.size)
+    g_eps = np.zeros(lat.N)
+    g_hop = np.zeros(lat.N * lat.n_dirs)
+    g_delta = np.zeros(lat.N)
+    c = lat._c()
+    _load().orc_ldos_gradient(ctypes.byref(c), float(a), _ptr(sites), sites.size, M, int(kernel), float(lam),
+                              _ptr(energies), energies.size, _ptr(G), _ptr(g_eps), _ptr(g_hop), _ptr(g_delta))
     return g_eps, g_hop.reshape(lat.N, lat.n_dirs), g_delta
 
 

@@ -530,6 +530,82 @@ def test_scf_map_gradient_vs_finite_differences():
         assert g_hop[j, d ^ 1] == pytest.approx(g_hop[i, d], rel=1e-12)
 
 
+def _ldos_loss_lattice(seed):
+    M = 40
+    p = wl.random_swave(4, M, seed=seed, T=0.05)
+    return p, as_oracle(p), M
+
+
+@pytest.mark.parametrize("kernel,lam", [(0, 0.0), (1, 3.0)])
+def test_ldos_gradient_vs_finite_differences(kernel, lam):
+    """Reverse-mode gradient of L = sum_{c,e} G[c,e] LDOS(E_e, i_c) (Eq. 17
+    with Eq. 10, Jackson or Lorentz damping) vs central differences (h = 1e-6)
+    of the oracle's LDOS, a frozen; a repeated start site counts twice."""
+    p, lat, M = _ldos_loss_lattice(82)
+    a = orc.rescale(lat)
+    sites = np.array([0, 5, 10, 15, 6, 5], dtype=np.int32)
+    E = np.linspace(-0.85, 0.8, 9) * a
+    G = np.random.default_rng(4).normal(size=(sites.size, E.size))
+    g_eps, g_hop, g_delta = orc.ldos_gradient(lat, a, sites, M, E, G, kernel, lam)
+
+    def loss(eps=None, hop=None, delta=None):
+        l2 = orc.Lattice(p.Lx, p.Ly, 0, 0, p.eps if eps is None else eps, p.mu,
+                         p.hop if hop is None else hop, 0, p.coupling,
+                         p.delta0 if delta is None else delta)
+        return float((G * orc.ldos(l2, a, sites, M, E, kernel, lam)).sum())
+
+    h = 1e-6
+    for i in (0, 5, 9, 15):
+        e1, e2 = p.eps.copy(), p.eps.copy()
+        e1[i] += h
+        e2[i] -= h
+        assert g_eps[i] == pytest.approx((loss(eps=e1) - loss(eps=e2)) / (2 * h), rel=1e-6, abs=1e-9)
+        d1, d2 = p.delta0.copy(), p.delta0.copy()
+        d1[i] += h
+        d2[i] -= h
+        assert g_delta[i] == pytest.approx((loss(delta=d1) - loss(delta=d2)) / (2 * h), rel=1e-6, abs=1e-9)
+    for (i, d) in ((0, 0), (5, 2), (6, 1), (14, 3)):
+        j = orc.neighbour(lat, i, d)
+        h1, h2 = p.hop.copy(), p.hop.copy()
+        h1[i, d] += h
+        h1[j, d ^ 1] += h
+        h2[i, d] -= h
+        h2[j, d ^ 1] -= h
+        assert g_hop[i, d] == pytest.approx((loss(hop=h1) - loss(hop=h2)) / (2 * h), rel=1e-6, abs=1e-9)
+        assert g_hop[j, d ^ 1] == pytest.approx(g_hop[i, d], rel=1e-12)
+    assert np.abs(g_eps).max() > 1e-3 and np.abs(g_hop).max() > 1e-3 and np.abs(g_delta).max() > 1e-3
+
+
+@pytest.mark.parametrize("kernel,lam", [(0, 0.0), (1, 2.0)])
+def test_ldos_gradient_of_quadrature_moments(kernel, lam):
+    """Closed forms: with K-node Gauss-Chebyshev weights, sum_k w_k LDOS(E_k)
+    is the exact integral of the truncated series, i.e. g_0 mu_0 = 1 for every
+    lattice, so its gradient vanishes; and sum_k w_k E_k LDOS(E_k) = a g_1 mu_1
+    = g_1 (eps_i - mu) (mu_1 = <e_i|H~|e_i>), so its gradient is g_1 on eps_i
+    of each listed site and zero for every hopping and Delta."""
+    p, lat, M = _ldos_loss_lattice(83)
+    a = orc.rescale(lat)
+    K = 64  # 2K > M + 1: both identities are exact
+    th = np.pi * (np.arange(K) + 0.5) / K
+    x = np.cos(th)
+    E = a * x
+    w = np.pi * a / K * np.sqrt(1.0 - x * x)
+    sites = np.array([1, 7, 12, 7], dtype=np.int32)
+    G0 = np.tile(w, (sites.size, 1))
+    g_eps, g_hop, g_delta = orc.ldos_gradient(lat, a, sites, M, E, G0, kernel, lam)
+    assert np.abs(g_eps).max() < 1e-12 and np.abs(g_hop).max() < 1e-12 and np.abs(g_delta).max() < 1e-12
+    # the integral itself is 1 at every listed site
+    rho = orc.ldos(lat, a, sites, M, E, kernel, lam)
+    assert np.allclose((rho * w).sum(1), 1.0, atol=1e-12)
+    g1 = (orc.jackson(M) if kernel == 0 else orc.lorentz(M, lam))[1]
+    g_eps, g_hop, g_delta = orc.ldos_gradient(lat, a, sites, M, E, G0 * E, kernel, lam)
+    want = np.zeros(p.N)
+    for i in sites:
+        want[i] += g1
+    assert np.allclose(g_eps, want, atol=1e-12)
+    assert np.abs(g_hop).max() < 1e-12 and np.abs(g_delta).max() < 1e-12
+
+
 # ---------------------------------------------------------------- site-dependent coupling
 
 
