@@ -255,8 +255,7 @@ def run_gb300(args):
         lat.set_option(cbdg.CBDG_OPT_TEMPORAL_STEPS, args.temporal)
     for _ in range(args.warmup):
         lat.scf_step(p.T, p.M, p.mix)
-    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
-    cbdg.cbdg_profile_read(lat.handle, reset=True)
+    # the production path: every iteration after the second is a CUDA-graph replay
     cbdg.cbdg_launch_count(lat.handle, reset=True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -269,11 +268,25 @@ def run_gb300(args):
     barrier()
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world, dev)
-    step_ms, step_n, step_bytes = cbdg.cbdg_profile_read(lat.handle)
     launches = cbdg.cbdg_launch_count(lat.handle)
+    value = world * units_per_step * args.steps / (ms_max / 1e3)
+    # a separate profiled pass (direct launches, a CUDA event pair around every
+    # recursion launch on the lattice's stream) gives the kernel's average
+    # launch time for the roofline
+    prof_iters = max(1, min(2, args.steps))
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 1)
+    cbdg.cbdg_profile_read(lat.handle, reset=True)
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(prof_iters):
+        lat.scf_step(p.T, p.M, p.mix)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = pe0.elapsed_time(pe1)
+    step_ms, step_n, step_bytes = cbdg.cbdg_profile_read(lat.handle)
     k_used = cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL)
     cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_PROFILE, 0)
-    value = world * units_per_step * args.steps / (ms_max / 1e3)
 
     # ---------------- end to end through the C ABI with host buffers
     host_delta = torch.from_numpy(np.ascontiguousarray(p.delta0)).pin_memory()
@@ -322,17 +335,23 @@ def run_gb300(args):
                     "kernel": kernel, "steps_per_pass": int(k_used),
                     "peak_kind": f"{peak_kind} (copy bandwidth)",
                     "algorithmic_bytes_per_launch": (4 if k_used >= 2 else 3) * vec_bytes,
-                    "recursion_launches_per_step": step_n / args.steps if args.steps else None,
+                    "recursion_launches_per_step": step_n / prof_iters,
                     # the same time against the roofline of one step per pass (3 streams per step):
                     # what several steps per pass buy over the unfused recursion
                     "one_step_roofline_frac": ((3.0 * vec_bytes * k_used) / (step_ms / step_n / 1e3) / 1e9 / hbm
                                                if step_n and k_used >= 2 else None),
                     "avg_launch_ms": step_ms / step_n if step_n else None,
-                    "share_of_step": step_ms / ms if ms else None}
+                    "avg_launch_source": (f"separate profiled pass of {prof_iters} iteration(s) after the timed "
+                                          "region: CUDA events around every recursion launch on its stream"),
+                    "share_of_step": step_ms / prof_ms if prof_ms else None}
         extra = {}
+        ap = arith_peaks(cbdg, torch, stream, local)
+        extra["arith_peaks"] = ap
         if not args.no_fp64:
-            extra["fp64"] = fp64_leg(p, stream, cbdg, torch, units_per_step)
+            extra["fp64"] = fp64_leg(p, stream, cbdg, torch, units_per_step, fp64_peak=ap["fp64_fma"]["tflops"])
             extra["fp32_vs_fp64"] = {"speedup": value / world / extra["fp64"]["value"]}
+        if not args.no_converge and args.lattice == L and args.moments == M:
+            extra["converge"] = leg_converge(cbdg, wl, torch, stream, from_scratch=False)
         if not args.no_extras:
             extra["other_stages"] = extra_legs(cbdg, wl, torch, stream, hbm)
         cpu = None
@@ -371,6 +390,13 @@ def run_gb300(args):
             "scf_max_abs_ddelta": diffs[-1],
         }
         line.update(extra)
+        # short copies of the FP64 comparison inside config (kept by line parsers that keep only
+        # the contract's keys)
+        if "fp64" in extra:
+            line["config"]["fp64_vector_steps_per_s"] = extra["fp64"]["value"]
+            line["config"]["fp32_vs_fp64_speedup"] = extra["fp32_vs_fp64"]["speedup"]
+        if "converge" in extra:
+            line["config"]["converged_max_abs_delta_fp32_vs_fp64"] = extra["converge"]["max_abs_delta_fp32_vs_fp64"]
         print(json.dumps(line), flush=True)
     lat.close()
     if world > 1:
@@ -380,7 +406,7 @@ def run_gb300(args):
     return 0
 
 
-def leg_contraction(cbdg, torch, stream, shape=(65536, 2048, 512)):
+def leg_contraction(cbdg, torch, stream, shape=(65536, 2048, 512), tf32_peak=None):
     """LDOS contraction on the tensor cores at the vortex-lattice shape:
     [65536 sites x 2048 moments] . [2048 x 512 energies], 3xTF32.  Times the
     tcgen05 kernel on pre-split operand planes (the roofline) and the whole
@@ -412,13 +438,19 @@ def leg_contraction(cbdg, torch, stream, shape=(65536, 2048, 512)):
     ms_kernel = timed(lambda: cbdg.cbdg_contract_tf32x3_planes(ahi, alo, bhi, blo, kp, D, n, m, n, stream))
     ms_call = timed(lambda: cbdg.cbdg_contract_tf32x3(A, k, B, k, D, n, m, n, k, stream))
     tflops = flops / (ms_kernel * 1e-3) / 1e12
-    peak = bf16_peak() * 0.5
+    if tf32_peak:
+        peak, peak_kind = tf32_peak, "measured (cbdg_measure_peak, tcgen05 kind::tf32 at the kernel's MMA shape)"
+    else:
+        peak, peak_kind = bf16_peak() * 0.5, "measured bf16 dense burst x 0.5 (nominal tf32/bf16 ratio)"
+    useful = 2.0 * m * n * k
     return {"shape": [m, k, n], "ms": ms_kernel, "tflops": tflops,
+            "useful_tflops": useful / (ms_kernel * 1e-3) / 1e12,
             "call_ms_with_split": ms_call, "call_tflops_with_split": flops / (ms_call * 1e-3) / 1e12,
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-                         "frac": tflops / peak,
-                         "peak_kind": "measured bf16 dense burst x 0.5 (nominal tf32/bf16 ratio)",
-                         "note": "contract_kernel alone; 3 TF32 products per term (hi*hi + hi*lo + lo*hi)"}}
+                         "frac": tflops / peak, "peak_kind": peak_kind,
+                         "note": "contract_kernel alone; achieved counts the 3 TF32 products per term "
+                                 "(hi*hi + hi*lo + lo*hi) the tensor cores execute; useful_tflops counts "
+                                 "the method's 2 m n k"}}
 
 
 def leg_dwave(cbdg, wl, stream, hbm, columns=4096):
@@ -602,7 +634,7 @@ def leg_junction(cbdg, wl, torch, stream, hbm):
                          "note": "step_multi_kernel, 4 vector streams per pass of K steps (algorithmic bytes)"}}
 
 
-def leg_green(cbdg, wl, torch, stream):
+def leg_green(cbdg, wl, torch, stream, fp64_peak=None):
     """Nonlocal Green's functions (gf1) around a vortex core of the 128x128
     d-wave lattice, M = 1024: 16 start sites (a 4x4 block at the core) x 256
     targets (a 16x16 block) x 512 energies in [-0.5a, 0.5a], device outputs.
@@ -649,25 +681,138 @@ def leg_green(cbdg, wl, torch, stream):
     tf = flops / t_con / 1e12
     return {"lattice": "128x128 d-wave vortex lattice, complex64 recursion", "M": M, "sites": ns, "targets": nt,
             "energies": n_E, "moments_s": t_mom, "green_function_s": t_all, "contraction_s": t_con,
-            "roofline": {"bound": "alu", "achieved": tf, "peak": 1.25, "unit": "TFLOP/s", "frac": tf / 1.25,
-                         "peak_kind": "nominal FP64 rate of the profiling recipe's table",
+            "roofline": {"bound": "alu", "achieved": tf, "peak": fp64_peak or 1.25, "unit": "TFLOP/s",
+                         "frac": tf / (fp64_peak or 1.25),
+                         "peak_kind": ("measured (cbdg_measure_peak, FP64 FMA)" if fp64_peak
+                                       else "nominal FP64 rate of the profiling recipe's table"),
                          "note": "green_contract_kernel, FP64 complex multiply-adds (8 flops each), from the call "
                                  "time difference"}}
 
 
+def scf_to(lat, p, tol, max_iter, torch, err_tol=None):
+    """Self-consistency iterations (linear mixing p.mix) until max|Delta_out -
+    Delta| < tol or, with err_tol, until the estimated distance of the mixed
+    Delta to the fixed point is below err_tol: near the fixed point the
+    mixed iteration contracts by rho = r_k / r_(k-1) per step and leaves
+    Delta_(k+1) - Delta* = rho (Delta_k - Delta*) with |Delta_k - Delta*| =
+    r_k / (1 - F') = mix r_k / (1 - rho), i.e. an error of
+    rho mix r_k / (1 - rho).  Returns (iterations, seconds, last max|dDelta|,
+    last error estimate or None)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it, diff, prev, est = 0, float("inf"), None, None
+    while it < max_iter:
+        diff = lat.scf_step(p.T, p.M, p.mix)
+        it += 1
+        if err_tol is not None and prev is not None and 0.0 < diff < prev:
+            rho = diff / prev
+            est = rho * p.mix * diff / (1.0 - rho)
+            if est < err_tol:
+                break
+        elif err_tol is None and diff < tol:
+            break
+        prev = diff
+    torch.cuda.synchronize()
+    return it, time.perf_counter() - t0, diff, est
+
+
+def leg_converge(cbdg, wl, torch, stream, from_scratch=True, tol32=1e-4, tol64=1e-6, max_iter=400,
+                 margin=0.5):
+    """The 128x128 disordered workload to self-consistency in both forms: the
+    FP32 recursion (FP64 folds and mixing) from Delta = 0.5, stopped once the
+    estimated distance to the fixed point is below margin x 1e-4 (scf_to), and the
+    plain FP64 form to max|dDelta| < 1e-6, from Delta = 0.5 (time to
+    solution) or, when from_scratch is False, from the FP32 solution.
+    Reports iterations, times and max_i |Delta_FP32 - Delta_FP64| over all
+    sites; with from_scratch also the FP32 result at the update tolerance
+    max|dDelta| < 1e-4 alone."""
+    import numpy as np
+    p = wl.swave_disordered(L, M, seed=SEED)
+    out = {"sites": int(p.N)}
+    d32_upd = None
+    if from_scratch:
+        lat = cbdg.Lattice(p, precision="fp32", stream=stream)
+        n, t, r, _ = scf_to(lat, p, tol32, max_iter, torch)
+        d32_upd = lat.delta
+        lat.close()
+        out["fp32_update_tol"] = {"iterations": n, "seconds": t, "last_max_abs_ddelta": r, "tol": tol32}
+    lat32 = cbdg.Lattice(p, precision="fp32", stream=stream)
+    n32, t32, r32, e32 = scf_to(lat32, p, None, max_iter, torch, err_tol=margin * tol32)
+    d32 = lat32.delta
+    lat32.close()
+    out["fp32"] = {"iterations": n32, "seconds": t32, "last_max_abs_ddelta": r32, "estimated_error": e32,
+                   "stop": f"estimated |Delta - Delta*| < {margin * tol32:g} (target {tol32:g})"}
+    lat64 = cbdg.Lattice(p, precision="fp64", stream=stream)
+    if not from_scratch:
+        lat64.delta = d32
+    n64, t64, r64, _ = scf_to(lat64, p, tol64, max_iter, torch)
+    d64 = lat64.delta
+    lat64.close()
+    key = "fp64" if from_scratch else "fp64_from_fp32_solution"
+    out[key] = {"iterations": n64, "seconds": t64, "last_max_abs_ddelta": r64, "tol": tol64}
+    err = np.abs(d32 - d64)
+    out["max_abs_delta_fp32_vs_fp64"] = float(err.max())
+    out["mean_abs_delta_fp32_vs_fp64"] = float(err.mean())
+    if d32_upd is not None:
+        out["fp32_update_tol"]["max_abs_delta_vs_fp64"] = float(np.abs(d32_upd - d64).max())
+    out["delta_fp64_range"] = [float(np.abs(d64).min()), float(np.abs(d64).max())]
+    if from_scratch:
+        out["time_to_solution_speedup"] = t64 / t32
+    return out
+
+
 def extra_legs(cbdg, wl, torch, stream, hbm, only=None, columns=4096, samples=256):
     """Other hot-path stages at their workload sizes (not the headline)."""
+    ap = arith_peaks(cbdg, torch, stream)
     legs = {
         "tiny": lambda: leg_tiny(cbdg, wl, stream),
-        "contraction": lambda: leg_contraction(cbdg, torch, stream),
+        "contraction": lambda: leg_contraction(cbdg, torch, stream, tf32_peak=ap["tf32_mma"]["tflops"]),
         "dwave": lambda: leg_dwave(cbdg, wl, stream, hbm, columns),
         "ensemble": lambda: leg_ensemble(cbdg, wl, stream, samples),
         "adjoint": lambda: leg_adjoint(cbdg, wl, stream, hbm),
         "currents": lambda: leg_currents(cbdg, wl, torch, stream, hbm),
         "junction": lambda: leg_junction(cbdg, wl, torch, stream, hbm),
-        "green": lambda: leg_green(cbdg, wl, torch, stream),
+        "green": lambda: leg_green(cbdg, wl, torch, stream, fp64_peak=ap["fp64_fma"]["tflops"]),
     }
+    if only == "peaks":
+        return {"peaks": ap}
+    if only == "converge":
+        return {"converge": leg_converge(cbdg, wl, torch, stream)}
     return {name: fn() for name, fn in legs.items() if only is None or only == name}
+
+
+_ARITH = {}
+
+
+def arith_peaks(cbdg, torch, stream, local=0):
+    """FP64 / FP32 FMA and tcgen05 kind::tf32 MMA peaks of this GPU from the
+    library's own probes (cbdg_measure_peak): one warm-up and one CUDA-event
+    timed launch each (about 0.1 s), SM clocks sampled meanwhile.  Cached per
+    process.  TFLOP/s."""
+    if _ARITH:
+        return _ARITH
+    specs = (("fp64_fma", cbdg.CBDG_PEAK_FP64_FMA, 24000),
+             ("fp32_fma", cbdg.CBDG_PEAK_FP32_FMA, 1500000),
+             ("tf32_mma", cbdg.CBDG_PEAK_TF32_MMA, 1 << 20))
+    out = {}
+    with ClockSampler(local) as clk:
+        for name, kind, work in specs:
+            cbdg.cbdg_measure_peak(kind, max(1, work // 16), stream)
+            cbdg.cbdg_peak_status(stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flops = cbdg.cbdg_measure_peak(kind, work, stream)
+            e1.record(stream)
+            cbdg.cbdg_peak_status(stream)
+            ms = e0.elapsed_time(e1)
+            out[name] = {"tflops": flops / (ms * 1e-3) / 1e12, "ms": ms, "flops": flops}
+    out["clocks"] = clk.summary()
+    out["how"] = ("cbdg_measure_peak: FP64/FP32 -- 8 independent FMA chains per thread, 8 CTAs x 256 threads "
+                  "per SM; TF32 -- tcgen05.mma kind::tf32 M=128 N=256 K=8 from shared memory into tensor "
+                  "memory, one CTA per SM; one CUDA-event timed launch each after a warm-up")
+    _ARITH.update(out)
+    return _ARITH
 
 
 def bf16_peak():
@@ -678,7 +823,7 @@ def bf16_peak():
         return 1900.0
 
 
-def fp64_leg(p, stream, cbdg, torch, units_per_step):
+def fp64_leg(p, stream, cbdg, torch, units_per_step, fp64_peak=None):
     """The plain FP64 form on the same GPU: one warm-up and one timed iteration."""
     lat = cbdg.Lattice(p, precision="fp64", stream=stream)
     lat.scf_step(p.T, p.M, p.mix)
@@ -700,9 +845,10 @@ def fp64_leg(p, stream, cbdg, torch, units_per_step):
     return {"value": units_per_step / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "dtype": "f64",
             "roofline": {"bound": "alu", "achieved": flops / (step_ms / 1e3) / 1e12,
-                         "peak": 1.25, "unit": "TFLOP/s",
-                         "frac": flops / (step_ms / 1e3) / 1e12 / 1.25,
-                         "peak_kind": "nominal FP64 rate of the profiling recipe's table",
+                         "peak": fp64_peak or 1.25, "unit": "TFLOP/s",
+                         "frac": flops / (step_ms / 1e3) / 1e12 / (fp64_peak or 1.25),
+                         "peak_kind": ("measured (cbdg_measure_peak, FP64 FMA)" if fp64_peak
+                                       else "nominal FP64 rate of the profiling recipe's table"),
                          "hbm_gbs": step_bytes / (step_ms / 1e3) / 1e9}}
 
 
@@ -716,7 +862,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint", "currents", "junction", "green"],
+    ap.add_argument("--no-converge", action="store_true",
+                    help="skip the FP32-vs-FP64 self-consistency comparison (about 90 s)")
+    ap.add_argument("--stage", default=None, choices=["tiny", "contraction", "dwave", "ensemble", "adjoint", "currents", "junction", "green",
+                             "converge", "peaks"],
                     help="measure only this stage and print its record (profiling runs)")
     ap.add_argument("--lattice", type=int, default=L,
                     help="lattice side (profiling of smaller cases; the metric is quoted at 128)")

@@ -234,6 +234,27 @@ cbdg_status cbdg_order_parameter_backward(cbdg_lattice *lat, double T, int32_t M
                                           const cbdg_complex *dL_ddelta_out, double *dL_deps,
                                           double *dL_dhop, double *dL_ddelta_in);
 
+/* Reverse-mode gradient of a loss on the up-spin LDOS of Eq. 17 (the
+ * expansion of Eq. 10, as cbdg_ldos computes it) at the listed sites, for
+ * real on-site pairing with 4 directions, with the rescale a frozen at its
+ * value for the current Delta.  With G[c*n_E + e] = dL/dLDOS(E_e, sites[c])
+ * (dL_dldos, [n_sites*n_E] doubles, host or device), the derivative of L
+ * with respect to the moment mu_m(i_c) = <e_i|T_m(H~)|e_i> is
+ *   s_{c,m} = sum_e G[c,e] g_m (2 - delta_m0) T_m(E_e/a) / (pi a sqrt(1 - (E_e/a)^2))
+ * (formed in FP64 on the GPU), and the reverse recursion of
+ * cbdg_order_parameter_backward runs over the listed start sites with the
+ * source y_m = s_{c,m} e_i on the electron row.  Outputs (any may be NULL),
+ * as in cbdg_order_parameter_backward:
+ *   dL_deps [N], dL_dhop [N*4] (undirected bonds, stored on both directed
+ *   entries), dL_ddelta [N] (dL/dDelta_i).
+ * sites [n_sites] and energies [n_E] (|E| < a) are host or device arrays;
+ * kernel / lambda as for cbdg_ldos.  Errors: INVALID_ARG (bad lists, energy
+ * outside the band, non-finite host dL_dldos), UNSUPPORTED (complex or bond
+ * lattices), OOM, CUDA.  Not in the paper (it has no derivatives). */
+cbdg_status cbdg_ldos_backward(cbdg_lattice *lat, const int32_t *sites, int32_t n_sites, int32_t M,
+                               int32_t kernel, double lambda, const double *energies, int32_t n_E,
+                               const double *dL_dldos, double *dL_deps, double *dL_dhop, double *dL_ddelta);
+
 /* Gradient of a loss L(Delta*) on the self-consistent order parameter
  * Delta* = F(Delta*; eps, t) (the fixed point of cbdg_scf_step, with a and the
  * coefficients frozen as in cbdg_order_parameter_backward), through the fixed
@@ -271,8 +292,27 @@ cbdg_status cbdg_set_delta(cbdg_lattice *lat, const cbdg_complex *delta);
  * symmetric), OOM, CUDA.  Not in the ensemble API. */
 cbdg_status cbdg_set_coupling(cbdg_lattice *lat, const double *coupling);
 
+/* Replaces the on-site energies eps [N] and/or the hoppings hop [N*n_dirs]
+ * (Eq. 2; the same layout and rules as in the descriptor: zero across open
+ * edges, Hermitian pairs, real unless complex_field) of an existing lattice;
+ * NULL keeps the current array.  Host or device arrays, read during the
+ * call; an invalid array changes nothing.  Lets a caller that iterates on
+ * parameters (an optimiser, an autograd loop) reuse one lattice and its
+ * buffers.  Errors: INVALID_ARG, CUDA. */
+cbdg_status cbdg_set_hamiltonian(cbdg_lattice *lat, const double *eps, const cbdg_complex *hop);
+
 /* The rescale factor a used by the most recent compute call (0 before any). */
 cbdg_status cbdg_get_rescale(cbdg_lattice *lat, double *a);
+
+/* lambda of the Lorentz kernel (Eq. 16, g_n = sinh(lambda (1 - n/M)) /
+ * sinh(lambda)) that broadens every level by `broadening` (an energy, in the
+ * units of t) at the band centre: the kernel's width is lambda / M in the
+ * rescaled energy (the paragraph after Eq. 16), so lambda = broadening * M / a
+ * with the rescale a that the next compute call will use for the current
+ * Delta (1.1 x the Gershgorin bound, or the fixed rescale option), computed
+ * on the GPU by this call.  *lambda is a host double.  Errors: INVALID_ARG
+ * (broadening <= 0 or not finite, M < 2), SPECTRUM (a <= 0), CUDA. */
+cbdg_status cbdg_lorentz_lambda(cbdg_lattice *lat, double broadening, int32_t M, double *lambda);
 
 /* Tuning and instrumentation options (cbdg_set_option / cbdg_get_option). */
 enum {
@@ -370,30 +410,56 @@ cbdg_status cbdg_ensemble_set_option(cbdg_ensemble *ens, int32_t option, int64_t
 cbdg_status cbdg_launch_count(cbdg_lattice *lat, int64_t *launches, int32_t reset);
 
 /* Moments of cbdg_moments (same definitions, outputs and tolerances) for
- * callers that cannot allocate device memory -- for example code being
- * recorded into a CUDA graph, or a host program that works inside a fixed,
- * pre-planned memory budget -- and so cannot build a lattice handle.  The
- * paper has no counterpart; this is a deployment variant.
+ * callers that cannot allocate device memory while they run -- for example a
+ * host program that works inside a fixed, pre-planned memory budget, or a
+ * plug-in inside another framework whose allocator owns the GPU's memory --
+ * and so cannot build a lattice handle (which allocates).  The paper has no
+ * counterpart; this is a deployment variant.
  *   desc:    as for cbdg_build_lattice, but eps, hop and delta0 must be
  *            DEVICE pointers; inputs are not checked for finiteness or
  *            Hermiticity (invalid values give meaningless moments, or
  *            CBDG_ERR_SPECTRUM).  Real on-site pairing with n_dirs = 4 only.
- *   sites:   device array of n_sites start sites; mu_ee [n_sites*M] and
- *            mu_eh [n_sites*M] (n_eh = 1) device outputs, either may be NULL.
+ *   sites:   device array of n_sites start sites; a site outside [0, N) is
+ *            detected on the GPU, never indexed, and makes the call return
+ *            CBDG_ERR_INVALID_ARG (the outputs are then not valid).
+ *            mu_ee [n_sites*M] and mu_eh [n_sites*M] (n_eh = 1) are device
+ *            outputs, either may be NULL.
  *   stream:  the stream all work is queued on; the call returns after it
  *            has finished.
  * Every intermediate lives in one fixed 64 MiB device array reserved when
  * the library is loaded (on each GPU that loads it, until the process
  * exits); nothing is allocated.  Lattices whose single column slab does not
  * fit are rejected with CBDG_ERR_INVALID_ARG; more start sites are handled
- * in chunks.  The first call on a device looks up the array's device
- * address (once per device, with that device current): make that first
- * call before any stream capture.  All calls share the array and a call
+ * in chunks.  The recursion runs one CTA per column slab with no row split,
+ * so few start sites use few SMs: the call trades throughput for its fixed
+ * footprint.  The first call on a device looks up the array's device
+ * address (once per device, with that device current) and caches it: make
+ * that first call before any stream capture, and do not call again after a
+ * cudaDeviceReset in the same process.  All calls share the array and a call
  * resets what it needs, but calls whose GPU work overlaps (other streams or
  * threads) race on it: serialise them. */
 cbdg_status cbdg_moments_noalloc(const cbdg_lattice_desc *desc, const int32_t *sites,
                                  int32_t n_sites, int32_t M, double *mu_ee, cbdg_complex *mu_eh,
                                  cbdg_stream stream);
+
+/* Arithmetic peaks of the current GPU, measured by the library's own
+ * microbenchmarks: the denominators of the rooflines of the arithmetic-bound
+ * kernels (the FP64 recursion, the FP64 Green's-function contraction, the
+ * 3xTF32 LDOS contraction).  Not in the paper (it reports no timings).
+ *   kind: CBDG_PEAK_FP64_FMA / CBDG_PEAK_FP32_FMA -- 8 independent FMA
+ *         chains per thread, 8 CTAs of 256 threads per SM, `work` FMAs per
+ *         chain; CBDG_PEAK_TF32_MMA -- one CTA per SM issuing `work`
+ *         tcgen05.mma kind::tf32 of M = 128, N = 256, K = 8 (the LDOS
+ *         contraction's instruction) from shared memory into tensor memory.
+ *   work: 1 .. 2^40.  *flops (host) receives the flops of the launch
+ *         (2 per FMA, 2 M N K per MMA).
+ * Queues one launch on `stream` and returns without waiting: the caller
+ * times it (CUDA events).  cbdg_peak_status waits for the stream and
+ * reports CBDG_ERR_CUDA if the tensor-core probe's bounded final wait ran
+ * out.  Errors: INVALID_ARG, CUDA. */
+enum { CBDG_PEAK_FP64_FMA = 0, CBDG_PEAK_FP32_FMA = 1, CBDG_PEAK_TF32_MMA = 2 };
+cbdg_status cbdg_measure_peak(int32_t kind, int64_t work, cbdg_stream stream, double *flops);
+cbdg_status cbdg_peak_status(cbdg_stream stream);
 
 /* Per-thread description of the last error; never NULL. */
 const char *cbdg_last_error(void);

@@ -2,13 +2,18 @@
 
 Each .cu translation unit is compiled in parallel into an object file, then
 the objects are linked into ``paper_1007_1609_gb300/_lib/libcbdg.so``.  The
-build is skipped when the library is newer than every source and header.
+library is stamped with a SHA-256 of every source and header, the compiler
+flags, the nvcc version and the host machine type (``libcbdg.stamp`` beside
+it); the build is skipped only when the stamp matches, so a copied tree with
+stale objects or a library built on another machine is rebuilt.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 
@@ -17,6 +22,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcbdg.so")
+STAMP = os.path.join(OUT_DIR, "libcbdg.stamp")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
@@ -38,15 +44,34 @@ def _inputs():
         glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def _nvcc_version(nvcc: str) -> str:
+    r = subprocess.run([nvcc, "--version"], capture_output=True, text=True)
+    return r.stdout.strip().splitlines()[-1] if r.returncode == 0 and r.stdout.strip() else "?"
+
+
+def stamp(extra_flags=()) -> str:
+    """SHA-256 of the inputs (paths and contents), flags, nvcc version and machine."""
+    h = hashlib.sha256()
+    for path in sorted(set(_inputs())):
+        h.update(os.path.relpath(path, ROOT).encode())
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    h.update(repr((ARCH, NVCC_FLAGS, list(extra_flags))).encode())
+    h.update(_nvcc_version(_nvcc()).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
+def is_stale(extra_flags=()) -> bool:
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(p) > t for p in _inputs())
+    with open(STAMP) as fh:
+        return fh.read().strip() != stamp(extra_flags)
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and not is_stale():
+    want = stamp(extra_flags)
+    if not force and os.path.exists(LIB) and os.path.exists(STAMP) and open(STAMP).read().strip() == want:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
@@ -70,6 +95,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     tmp = LIB + ".tmp.%d" % os.getpid()
     run([nvcc, "-shared", "-o", tmp] + objs + ARCH)
     os.replace(tmp, LIB)
+    with open(STAMP + ".tmp", "w") as fh:
+        fh.write(want + "\n")
+    os.replace(STAMP + ".tmp", STAMP)
     return LIB
 
 

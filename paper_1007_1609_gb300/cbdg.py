@@ -102,17 +102,22 @@ def load():
             "cbdg_scf_step": [P, D, I32, D, P],
             "cbdg_get_delta": [P, P],
             "cbdg_set_delta": [P, P],
+            "cbdg_set_hamiltonian": [P, P, P],
             "cbdg_get_rescale": [P, P],
+            "cbdg_lorentz_lambda": [P, D, I32, P],
             "cbdg_set_option": [P, I32, I64],
             "cbdg_get_option": [P, I32, P],
             "cbdg_profile_read": [P, P, P, P, I32],
             "cbdg_launch_count": [P, P, I32],
             "cbdg_moments_noalloc": [P, P, I32, I32, P, P, P],
+            "cbdg_measure_peak": [I32, I64, P, P],
+            "cbdg_peak_status": [P],
             "cbdg_contract_tf32x3": [P, I32, P, I32, P, I32, I32, I32, I32, P],
             "cbdg_contract_kp": [I32],
             "cbdg_split_tf32": [P, I32, I32, I32, P, P, P],
             "cbdg_contract_tf32x3_planes": [P, P, P, P, I32, P, I32, I32, I32, P],
             "cbdg_order_parameter_backward": [P, D, I32, P, P, P, P],
+            "cbdg_ldos_backward": [P, P, I32, I32, I32, D, P, I32, P, P, P, P],
             "cbdg_fixed_point_backward": [P, D, I32, D, P, D, I32, P, P, P],
             "cbdg_build_ensemble": [P, I32, P, P],
             "cbdg_ensemble_destroy": [P],
@@ -228,9 +233,19 @@ def cbdg_set_delta(lat, delta):
     _check(load().cbdg_set_delta(lat, _ptr(delta)))
 
 
+def cbdg_set_hamiltonian(lat, eps, hop):
+    _check(load().cbdg_set_hamiltonian(lat, _ptr(eps), _ptr(hop)))
+
+
 def cbdg_get_rescale(lat):
     out = ctypes.c_double(0.0)
     _check(load().cbdg_get_rescale(lat, ctypes.byref(out)))
+    return out.value
+
+
+def cbdg_lorentz_lambda(lat, broadening, M):
+    out = ctypes.c_double()
+    _check(load().cbdg_lorentz_lambda(lat, float(broadening), int(M), ctypes.byref(out)))
     return out.value
 
 
@@ -263,6 +278,20 @@ def cbdg_moments_noalloc(desc, sites, n_sites, M, mu_ee, mu_eh, stream=None):
                                        _ptr(mu_ee), _ptr(mu_eh), _stream_handle(stream)))
 
 
+CBDG_PEAK_FP64_FMA, CBDG_PEAK_FP32_FMA, CBDG_PEAK_TF32_MMA = 0, 1, 2
+
+
+def cbdg_measure_peak(kind, work, stream=None):
+    """Queues one peak-probe launch on `stream`; returns its flops."""
+    out = ctypes.c_double()
+    _check(load().cbdg_measure_peak(int(kind), int(work), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def cbdg_peak_status(stream=None):
+    _check(load().cbdg_peak_status(_stream_handle(stream)))
+
+
 def cbdg_contract_tf32x3(A, lda, B, ldb, D, ldd, m, n, k, stream=None):
     _check(load().cbdg_contract_tf32x3(_ptr(A), int(lda), _ptr(B), int(ldb), _ptr(D), int(ldd),
                                        int(m), int(n), int(k), _stream_handle(stream)))
@@ -293,6 +322,13 @@ def cbdg_fixed_point_backward(lat, T, M, mix, dL_ddelta, tol, max_iter, dL_deps,
 def cbdg_order_parameter_backward(lat, T, M, dL_ddelta_out, dL_deps, dL_dhop, dL_ddelta_in):
     _check(load().cbdg_order_parameter_backward(lat, float(T), int(M), _ptr(dL_ddelta_out),
                                                 _ptr(dL_deps), _ptr(dL_dhop), _ptr(dL_ddelta_in)))
+
+
+def cbdg_ldos_backward(lat, sites, n_sites, M, kernel, lam, energies, n_E, dL_dldos, dL_deps, dL_dhop,
+                       dL_ddelta):
+    _check(load().cbdg_ldos_backward(lat, _ptr(sites), int(n_sites), int(M), int(kernel), float(lam),
+                                     _ptr(energies), int(n_E), _ptr(dL_dldos), _ptr(dL_deps), _ptr(dL_dhop),
+                                     _ptr(dL_ddelta)))
 
 
 def cbdg_build_ensemble(descs, stream=None):
@@ -499,12 +535,9 @@ class Lattice:
         cbdg_set_coupling(self.handle, self._cpl)
 
     def lorentz_lambda(self, broadening, M):
-        """lambda of the Lorentz kernel (Eq. 16) for an energy broadening eps at
-        the band centre: eps = a lambda / M with the current rescale a."""
-        a = self.rescale
-        if not a > 0.0:
-            raise RuntimeError("no rescale yet: run a compute call first")
-        return float(broadening) * M / a
+        """lambda of the Lorentz kernel (Eq. 16) for an energy broadening at the
+        band centre, with the rescale of the current Delta (cbdg_lorentz_lambda)."""
+        return cbdg_lorentz_lambda(self.handle, broadening, M)
 
     def bond_currents(self, T, M, kernel="jackson", lam=0.0):
         """J [N, n_dirs]: current from site i to its neighbour along d, both spins (Eq. 20)."""
@@ -540,6 +573,18 @@ class Lattice:
         gh = np.zeros(self.N * 4)
         it = cbdg_fixed_point_backward(self.handle, T, M, mix, g, tol, max_iter, ge, gh)
         return ge, gh.reshape(self.N, 4), it
+
+    def ldos_backward(self, sites, M, energies, dL_dldos, kernel="jackson", lam=0.0):
+        """(dL/deps [N], dL/dhop [N, 4], dL/dDelta [N]) of a loss on the LDOS at
+        (sites, energies), given dL/dLDOS [n_sites, n_E] (a frozen)."""
+        sites = np.ascontiguousarray(sites, dtype=np.int32)
+        energies = np.ascontiguousarray(energies, dtype=np.float64)
+        g = np.ascontiguousarray(dL_dldos, dtype=np.float64).reshape(sites.size, energies.size)
+        ge, gd = np.zeros(self.N), np.zeros(self.N)
+        gh = np.zeros(self.N * 4)
+        cbdg_ldos_backward(self.handle, sites, sites.size, M, KERNELS[kernel], lam, energies, energies.size, g,
+                           ge, gh, gd)
+        return ge, gh.reshape(self.N, 4), gd
 
     def backward(self, T, M, dL_ddelta_out):
         """Gradients (eps [N], hop [N, 4], delta_in [N]) of one map (see the C ABI)."""

@@ -1,6 +1,8 @@
 // adjoint.cu -- reverse-mode gradient of one self-consistency map
 // Delta_out(eps, t, Delta_in) (Eq. 19 through Eq. 15), with a and the
-// coefficients C_n frozen, for real on-site (s-wave) lattices.
+// coefficients C_n frozen, for real on-site (s-wave) lattices; and of a loss
+// on the LDOS (Eq. 17), whose source sits on the electron row instead:
+//     y_m = S[c][m] e_i,  S[c][m] = dL/dmu_m(i) (ldos.cu).
 //
 // For a start site i the forward recursion j_m = 2 H~ j_{m-1} - j_{m-2}
 // (j_1 = H~ j_0, j_0 = e_i) feeds Phi = sum_i w_i (U/2) sum_m C_m <h_i|j_m>,
@@ -41,6 +43,18 @@ __global__ void adjoint_source_kernel(int Lx, int Ly, int ncols, int W, const in
   const size_t k = blocked_index(vector_row(Lx, i, 1), b, rows, W);
   const double wi = U_site ? w[i] * U_site[i] : w[i];
   lam[k] = static_cast<S>(static_cast<double>(lam[k]) + wi * scale_m);
+}
+
+// LDOS loss: lam(e_i) += src[b * M + m] for column b (start site i)
+template <typename S>
+__global__ void adjoint_source_table_kernel(int Lx, int Ly, int ncols, int W, const int32_t *sites,
+                                            const double *src, int M, int m, S *lam) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= ncols) return;
+  const int i = sites[b];
+  const size_t rows = 2 * static_cast<size_t>(Lx) * Ly;
+  const size_t k = blocked_index(vector_row(Lx, i, 0), b, rows, W);
+  lam[k] = static_cast<S>(static_cast<double>(lam[k]) + src[static_cast<size_t>(b) * M + m]);
 }
 
 template <typename S>
@@ -227,6 +241,18 @@ cudaError_t launch_adjoint_source(int precision, int Lx, int Ly, int ncols, int 
   else
     adjoint_source_kernel<double><<<blocks(ncols, 128), 128, 0, s>>>(Lx, Ly, ncols, W, sites, w, U_site,
                                                                      scale_m, static_cast<double *>(lam));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_source_table(int precision, int Lx, int Ly, int ncols, int W, const int32_t *sites,
+                                        const double *src, int M, int m, void *lam, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  if (precision == 1)
+    adjoint_source_table_kernel<float><<<blocks(ncols, 128), 128, 0, s>>>(Lx, Ly, ncols, W, sites, src, M, m,
+                                                                          static_cast<float *>(lam));
+  else
+    adjoint_source_table_kernel<double><<<blocks(ncols, 128), 128, 0, s>>>(Lx, Ly, ncols, W, sites, src, M, m,
+                                                                           static_cast<double *>(lam));
   return cudaGetLastError();
 }
 

@@ -819,9 +819,20 @@ cbdg_status order_parameter_impl(cbdg_lattice *L, double T, int kernel, double l
 // One adjoint run of the self-consistency map with the weights w_i = dL/dDelta_out,i
 // already in L->adj_w (device): leaves dL/deps, dL/dDelta_in and dL/dt in
 // L->adj_out ([N] eps, [N] Delta, [N*4] hop).
-cbdg_status adjoint_run(cbdg_lattice *L, double T, int M) {
+// Reverse mode of the recursion over a set of start columns.  cols == NULL:
+// every site, the self-consistency map's source y_m = w_i (U_i/2) C_m h_i
+// (w = adj_w).  Otherwise the n_cols device sites `cols` with the source
+// table src [n_cols][M] (device) on the electron rows, y_m = src[c][m] e_i
+// (a loss on the LDOS); the Fermi coefficients are not needed then.
+cbdg_status adjoint_run(cbdg_lattice *L, double T, int M, const int32_t *cols = nullptr, int n_cols = 0,
+                        const double *src = nullptr) {
   const int N = L->N;
-  cbdg_status st = prepare(L, T, CBDG_JACKSON, 0.0, M, true);
+  const bool map_source = cols == nullptr;
+  if (map_source) {
+    cols = L->sites_all.as<int32_t>();
+    n_cols = N;
+  }
+  cbdg_status st = prepare(L, T, CBDG_JACKSON, 0.0, M, map_source);
   if (st != CBDG_OK) return st;
   std::vector<double> hC(M);
   CK(cudaMemcpyAsync(hC.data(), L->C.p, M * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
@@ -846,15 +857,15 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M) {
   int64_t max_cols = (static_cast<int64_t>(cap) / per_col / W) * W;
   if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
   if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for the adjoint");
-  const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((N + W - 1) / W) * W));
-  const int groups = adjoint_groups(L->Ly, ((std::min(chunk, N) + W - 1) / W) * W, W);
+  const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((n_cols + W - 1) / W) * W));
+  const int groups = adjoint_groups(L->Ly, ((std::min(chunk, n_cols) + W - 1) / W) * W, W);
   CK(L->adj_part.ensure(static_cast<size_t>(groups) * N * 12 * sizeof(double)));
   CK(cudaMemsetAsync(L->adj_part.p, 0, static_cast<size_t>(groups) * N * 12 * sizeof(double), L->stream));
   const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
   (void)tol;
 
-  for (int c0 = 0; c0 < N; c0 += chunk) {
-    const int ncols = std::min(chunk, N - c0);
+  for (int c0 = 0; c0 < n_cols; c0 += chunk) {
+    const int ncols = std::min(chunk, n_cols - c0);
     const int ld = ((ncols + W - 1) / W) * W;
     StepConfig cfg;
     if (!plan_step_real(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
@@ -871,7 +882,7 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M) {
     CK(L->dA.ensure(ld * sizeof(double2)));
     CK(L->acc_n.ensure(ld * sizeof(double)));
     CK(L->acc_d.ensure(ld * 4 * sizeof(double2)));
-    const int32_t *sites = L->sites_all.as<int32_t>() + c0;
+    const int32_t *sites = cols + c0;
     unsigned char *ck = L->adj_ck.as<unsigned char>();
     unsigned char *seg = L->adj_seg.as<unsigned char>();
     auto ckv = [&](int k, int which) { return ck + (2 * static_cast<size_t>(k) + which) * vb; };
@@ -948,8 +959,12 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M) {
           if (st != CBDG_OK) return st;
           std::swap(lam1, lam2);  // lam1 = lam_m, lam2 = lam_{m+1}
         }
-        CK(launch_adjoint_source(L->precision, L->Lx, L->Ly, ncols, W, sites, L->adj_w.as<double>(),
-                                 L->coupling_site(), halfU * hC[m], lam1, L->stream));
+        if (map_source)
+          CK(launch_adjoint_source(L->precision, L->Lx, L->Ly, ncols, W, sites, L->adj_w.as<double>(),
+                                   L->coupling_site(), halfU * hC[m], lam1, L->stream));
+        else
+          CK(launch_adjoint_source_table(L->precision, L->Lx, L->Ly, ncols, W, sites,
+                                         src + static_cast<size_t>(c0) * M, M, m, lam1, L->stream));
         CK(launch_adjoint_accumulate(L->precision, L->Lx, L->Ly, L->px, L->py, ld, W, groups, lam1,
                                      segv(m - 1 - k * S), m == 1 ? 1.0 : 2.0,
                                      L->adj_part.as<double>(), L->stream));
@@ -965,6 +980,36 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M) {
   return CBDG_OK;
 }
 
+}  // namespace
+
+namespace {
+// Hoppings of Eq. 2 as the recursion reads them: finite, zero across an open
+// edge, Hermitian pairs t_{j -> i} = conj(t_{i -> j}), real unless the
+// lattice has complex vectors.
+cbdg_status check_hop(const cbdg_lattice_desc *d, const std::vector<cbdg_complex> &hop) {
+  const int N = d->Lx * d->Ly;
+  for (size_t k = 0; k < hop.size(); ++k)
+    if (!finite_c(hop[k])) return fail(CBDG_ERR_INVALID_ARG, "hop[%zu] is not finite", k);
+  for (int i = 0; i < N; ++i) {
+    for (int dir = 0; dir < d->n_dirs; ++dir) {
+      const cbdg_complex t = hop[static_cast<size_t>(i) * d->n_dirs + dir];
+      const int j = host_neighbour(d, i, dir);
+      if (j < 0) {
+        if (t.re != 0.0 || t.im != 0.0)
+          return fail(CBDG_ERR_INVALID_ARG, "hop[%d][%d] crosses an open edge and must be 0", i, dir);
+        continue;
+      }
+      const cbdg_complex b = hop[static_cast<size_t>(j) * d->n_dirs + (dir ^ 1)];
+      const double tol = 1e-12 * (1.0 + hypot(t.re, t.im));
+      if (fabs(b.re - t.re) > tol || fabs(b.im + t.im) > tol)
+        return fail(CBDG_ERR_INVALID_ARG, "hop is not Hermitian at site %d dir %d", i, dir);
+    }
+  }
+  if (!d->complex_field)
+    for (auto &z : hop)
+      if (z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex hop with complex_field = 0");
+  return CBDG_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1005,24 +1050,13 @@ cbdg_status cbdg_build_lattice(const cbdg_lattice_desc *d, cbdg_stream stream,
   if ((e = host_copy(d->delta0, nd, delta)) != cudaSuccess) return cuda_fail(e, "reading delta0");
   for (int i = 0; i < N; ++i)
     if (!isfinite(eps[i])) return fail(CBDG_ERR_INVALID_ARG, "eps[%d] is not finite", i);
-  for (size_t k = 0; k < hop.size(); ++k)
-    if (!finite_c(hop[k])) return fail(CBDG_ERR_INVALID_ARG, "hop[%zu] is not finite", k);
   for (size_t k = 0; k < delta.size(); ++k)
     if (!finite_c(delta[k])) return fail(CBDG_ERR_INVALID_ARG, "delta0[%zu] is not finite", k);
+  {
+    cbdg_status hs = check_hop(d, hop);
+    if (hs != CBDG_OK) return hs;
+  }
   for (int i = 0; i < N; ++i) {
-    for (int dir = 0; dir < d->n_dirs; ++dir) {
-      const cbdg_complex t = hop[static_cast<size_t>(i) * d->n_dirs + dir];
-      const int j = host_neighbour(d, i, dir);
-      if (j < 0) {
-        if (t.re != 0.0 || t.im != 0.0)
-          return fail(CBDG_ERR_INVALID_ARG, "hop[%d][%d] crosses an open edge and must be 0", i, dir);
-        continue;
-      }
-      const cbdg_complex b = hop[static_cast<size_t>(j) * d->n_dirs + (dir ^ 1)];
-      const double tol = 1e-12 * (1.0 + hypot(t.re, t.im));
-      if (fabs(b.re - t.re) > tol || fabs(b.im + t.im) > tol)
-        return fail(CBDG_ERR_INVALID_ARG, "hop is not Hermitian at site %d dir %d", i, dir);
-    }
     if (d->pairing == CBDG_BOND_V) {
       for (int dir = 0; dir < 4; ++dir) {
         const cbdg_complex v = delta[static_cast<size_t>(i) * 4 + dir];
@@ -1040,8 +1074,6 @@ cbdg_status cbdg_build_lattice(const cbdg_lattice_desc *d, cbdg_stream stream,
     }
   }
   if (!d->complex_field) {
-    for (auto &z : hop)
-      if (z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex hop with complex_field = 0");
     for (auto &z : delta)
       if (z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex delta0 with complex_field = 0");
   }
@@ -1528,6 +1560,69 @@ cbdg_status cbdg_order_parameter_backward(cbdg_lattice *L, double T, int32_t M,
   return finish(L);
 }
 
+cbdg_status cbdg_ldos_backward(cbdg_lattice *L, const int32_t *sites, int32_t n_sites, int32_t M, int32_t kernel,
+                               double lambda, const double *energies, int32_t n_E, const double *dL_dldos,
+                               double *dL_deps, double *dL_dhop, double *dL_ddelta) {
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  if (mode_of(L) != kReal)
+    return fail(CBDG_ERR_UNSUPPORTED, "the adjoint handles real on-site pairing with 4 directions");
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  st = check_kernel(kernel, lambda);
+  if (st != CBDG_OK) return st;
+  if (n_sites < 1 || n_E < 1 || !sites || !energies || !dL_dldos)
+    return fail(CBDG_ERR_INVALID_ARG, "need n_sites >= 1, n_E >= 1 and non-NULL sites, energies, dL_dldos");
+  const int N = L->N;
+  std::vector<int32_t> hs;
+  std::vector<double> he;
+  cudaError_t e = host_copy(sites, n_sites, hs);
+  if (e != cudaSuccess) return cuda_fail(e, "reading sites");
+  e = host_copy(energies, n_E, he);
+  if (e != cudaSuccess) return cuda_fail(e, "reading energies");
+  for (int c = 0; c < n_sites; ++c)
+    if (hs[c] < 0 || hs[c] >= N) return fail(CBDG_ERR_INVALID_ARG, "site %d out of range", hs[c]);
+  const size_t ng = static_cast<size_t>(n_sites) * n_E;
+  const bool g_dev = is_device_ptr(dL_dldos);
+  std::vector<double> hg;
+  if (!g_dev) {
+    hg.assign(dL_dldos, dL_dldos + ng);
+    for (size_t k = 0; k < ng; ++k)
+      if (!isfinite(hg[k])) return fail(CBDG_ERR_INVALID_ARG, "dL_dldos is not finite");
+  }
+  // the rescale of the current Delta (adjoint_run computes the same a again)
+  st = prepare(L, 0.0, CBDG_JACKSON, 0.0, M, false);
+  if (st != CBDG_OK) return st;
+  double a = 0.0;
+  CK(cudaMemcpyAsync(&a, L->scal.as<double>() + kScalA, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  for (int k = 0; k < n_E; ++k)
+    if (!(fabs(he[k]) < a))
+      return fail(CBDG_ERR_INVALID_ARG, "energy %g outside the rescaled band (-a, a), a = %g", he[k], a);
+  // device copies: sites, energies, dL/dLDOS (unless on the device), W [n_E][M], S [n_sites][M]
+  auto r256 = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+  const size_t e_b = r256(static_cast<size_t>(n_E) * sizeof(double)), g_b = g_dev ? 0 : r256(ng * sizeof(double));
+  const size_t w_b = r256(static_cast<size_t>(n_E) * M * sizeof(double));
+  const size_t s_b = r256(static_cast<size_t>(n_sites) * M * sizeof(double));
+  CK(L->sites_user.ensure(n_sites * sizeof(int32_t)));
+  CK(L->stage.ensure(e_b + g_b + w_b + s_b));
+  unsigned char *sb = L->stage.as<unsigned char>();
+  double *dE = reinterpret_cast<double *>(sb), *dG = reinterpret_cast<double *>(sb + e_b);
+  double *dW = reinterpret_cast<double *>(sb + e_b + g_b), *dS = reinterpret_cast<double *>(sb + e_b + g_b + w_b);
+  CK(cudaMemcpyAsync(L->sites_user.p, hs.data(), n_sites * sizeof(int32_t), cudaMemcpyHostToDevice, L->stream));
+  CK(cudaMemcpyAsync(dE, he.data(), n_E * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  if (!g_dev) CK(cudaMemcpyAsync(dG, hg.data(), ng * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  CK(launch_ldos_source(n_sites, n_E, M, kernel, lambda, dE, L->scal.as<double>(), g_dev ? dL_dldos : dG, dW, dS,
+                        L->stream));
+  L->launches += 2;
+  st = adjoint_run(L, 0.0, M, L->sites_user.as<int32_t>(), n_sites, dS);
+  if (st != CBDG_OK) return st;
+  double *ge = L->adj_out.as<double>(), *gd = ge + N, *gh = ge + 2 * N;
+  CK(deliver(L, dL_deps, ge, N * sizeof(double)));
+  CK(deliver(L, dL_ddelta, gd, N * sizeof(double)));
+  CK(deliver(L, dL_dhop, gh, static_cast<size_t>(N) * 4 * sizeof(double)));
+  return finish(L);
+}
+
 cbdg_status cbdg_fixed_point_backward(cbdg_lattice *L, double T, int32_t M, double mix,
                                       const cbdg_complex *dL_ddelta, double tol, int32_t max_iter,
                                       double *dL_deps, double *dL_dhop, int32_t *iterations) {
@@ -1632,6 +1727,38 @@ cbdg_status cbdg_set_delta(cbdg_lattice *L, const cbdg_complex *delta) {
   return CBDG_OK;
 }
 
+cbdg_status cbdg_set_hamiltonian(cbdg_lattice *L, const double *eps, const cbdg_complex *hop) {
+  if (!L) return fail(CBDG_ERR_INVALID_ARG, "lattice is NULL");
+  CK(cudaSetDevice(L->device));
+  std::vector<double> he;
+  std::vector<cbdg_complex> hh;
+  if (eps) {
+    cudaError_t e = host_copy(eps, L->N, he);
+    if (e != cudaSuccess) return cuda_fail(e, "reading eps");
+    for (int i = 0; i < L->N; ++i)
+      if (!isfinite(he[i])) return fail(CBDG_ERR_INVALID_ARG, "eps[%d] is not finite", i);
+  }
+  if (hop) {
+    cudaError_t e = host_copy(hop, static_cast<size_t>(L->N) * L->n_dirs, hh);
+    if (e != cudaSuccess) return cuda_fail(e, "reading hop");
+    cbdg_lattice_desc d{};
+    d.Lx = L->Lx;
+    d.Ly = L->Ly;
+    d.periodic_x = L->px;
+    d.periodic_y = L->py;
+    d.n_dirs = L->n_dirs;
+    d.complex_field = L->cplx;
+    cbdg_status st = check_hop(&d, hh);
+    if (st != CBDG_OK) return st;
+  }
+  // validated host copies: upload (nothing changes on an invalid call)
+  if (eps) CK(cudaMemcpyAsync(L->eps.p, he.data(), L->N * sizeof(double), cudaMemcpyHostToDevice, L->stream));
+  if (hop)
+    CK(cudaMemcpyAsync(L->hop.p, hh.data(), hh.size() * sizeof(double2), cudaMemcpyHostToDevice, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  return CBDG_OK;
+}
+
 cbdg_status cbdg_set_coupling(cbdg_lattice *L, const double *coupling) {
   if (!L) return fail(CBDG_ERR_INVALID_ARG, "lattice is NULL");
   CK(cudaSetDevice(L->device));
@@ -1669,6 +1796,34 @@ cbdg_status cbdg_set_coupling(cbdg_lattice *L, const double *coupling) {
 cbdg_status cbdg_get_rescale(cbdg_lattice *L, double *a) {
   if (!L || !a) return fail(CBDG_ERR_INVALID_ARG, "NULL argument");
   *a = L->last_a;
+  return CBDG_OK;
+}
+
+// Lorentz damping (Eq. 16): g_n = sinh(lambda (1 - n/M)) / sinh(lambda) turns
+// each delta peak into a Lorentzian of half width lambda/M in the rescaled
+// energy (the paragraph after Eq. 16), i.e. a * lambda / M in energy at the
+// band centre.  lambda = broadening * M / a, with the a the next compute call
+// uses for the current Delta.
+cbdg_status cbdg_lorentz_lambda(cbdg_lattice *L, double broadening, int32_t M, double *lambda) {
+  if (!L || !lambda) return fail(CBDG_ERR_INVALID_ARG, "NULL argument");
+  if (!(broadening > 0.0) || !std::isfinite(broadening)) return fail(CBDG_ERR_INVALID_ARG, "broadening must be > 0");
+  if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
+  cbdg_status st = begin(L);
+  if (st != CBDG_OK) return st;
+  double a = 0.0;
+  if (L->fixed_a_pico > 0) {
+    a = static_cast<double>(L->fixed_a_pico) * 1e-12;
+  } else {
+    CK(L->scal.ensure(kScalars * sizeof(double)));
+    CK(launch_gershgorin(L->N, L->n_dirs, L->pairing, L->Lx, L->Ly, L->px, L->py, L->eps.as<double>(), L->mu,
+                         L->hop.as<double2>(), L->delta.as<double2>(), L->margin_milli / 1000.0,
+                         L->scal.as<double>(), L->stream));
+    L->launches += 2;
+    CK(cudaMemcpyAsync(&a, L->scal.as<double>() + kScalA, sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+  }
+  if (!(a > 0.0)) return fail(CBDG_ERR_SPECTRUM, "the rescale a is not positive (%g)", a);
+  *lambda = broadening * static_cast<double>(M) / a;
   return CBDG_OK;
 }
 

@@ -409,6 +409,66 @@ __global__ void split_tf32_kernel(int rows, int k, size_t ld, const T *__restric
   }
 }
 
+// Rate probe of the contraction's tensor-core instruction: one CTA per SM
+// issues `mmas` back-to-back tcgen05.mma kind::tf32 (M = 128, N = 256, K = 8,
+// the shape and descriptors of contract_kernel) from operand tiles resident
+// in shared memory into one FP32 accumulator in tensor memory.  No copies,
+// no drain: the time of a launch over its 2 M N K flops per MMA is the peak
+// the contraction's roofline is quoted against.  The tiles hold zeros (the
+// rate does not depend on the values).  The final wait is bounded; on expiry
+// the CTA records kFlagTimeout, waits once more (bounded) and frees its
+// tensor memory.
+constexpr unsigned kPeakCols = 256;
+constexpr size_t kPeakSmem = 120 * 1024;  // more than half an SM's shared memory: one CTA per SM
+static_assert(kPeakSmem >= 1024 + static_cast<size_t>(kATile) + kBTile, "probe tiles must fit");
+
+__global__ void __launch_bounds__(128, 1) tf32_peak_kernel(long long mmas, unsigned *flags) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *base = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) unsigned long long done_bar;
+  __shared__ unsigned tmem_slot;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kPeakCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  for (unsigned i = t * 16u; i < kATile + kBTile; i += 128u * 16u)
+    *reinterpret_cast<uint4 *>(base + i) = make_uint4(0u, 0u, 0u, 0u);
+  // the tensor cores read shared memory through the async proxy
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  if (t == 0) {
+    mbar_init(smem_addr(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
+  if (t == 0) {
+    const unsigned a = smem_addr(base), b = a + kATile;
+    for (long long i = 0; i < mmas; ++i) {
+      const unsigned off = static_cast<unsigned>(i & 1) * 32u;  // the two K = 8 halves of a 64-byte row
+      mma_tf32(tmem, smem_desc(a + off), smem_desc(b + off), i > 0 ? 1u : 0u);
+    }
+    tc_commit(smem_addr(&done_bar));
+    if (!mbar_wait_drain(smem_addr(&done_bar), 0u)) {
+      atomicOr(flags, kFlagTimeout);
+      mbar_wait_drain(smem_addr(&done_bar), 0u);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kPeakCols)
+                 : "memory");
+  }
+}
+
 // error word of the stand-alone contraction entry point
 static __device__ unsigned g_contract_flag;
 
@@ -486,6 +546,22 @@ cudaError_t contract_flag_address(unsigned **out) {
 }
 
 int contract_kp(int k) { return (k + 31) / 32 * 32; }
+
+double tf32_peak_flops_per_mma() { return 2.0 * kBM * kBN * 8; }
+
+cudaError_t launch_tf32_peak(int ctas, long long mmas, unsigned *flags, cudaStream_t s) {
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(tf32_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kPeakSmem));
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  tf32_peak_kernel<<<ctas, 128, kPeakSmem, s>>>(mmas, flags);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_split_tf32(const float *src, size_t ld, int rows, int k, int kp, float *hi, float *lo,
                               cudaStream_t s) {

@@ -217,6 +217,13 @@ cudaError_t launch_contract_planes(const float *a_hi, const float *a_lo, const f
 cudaError_t launch_adjoint_source(int precision, int Lx, int Ly, int ncols, int W,
                                   const int32_t *sites, const double *w, const double *U_site,
                                   double scale_m, void *lam, cudaStream_t s);
+// lam(e_i) += src[b * M + m] for column b (start site i = sites[b]).
+cudaError_t launch_adjoint_source_table(int precision, int Lx, int Ly, int ncols, int W, const int32_t *sites,
+                                        const double *src, int M, int m, void *lam, cudaStream_t s);
+// Source table of the LDOS-loss adjoint: W [n_E][M] (work) = the FP64 weights
+// of Eq. 17, S [n_sites][M] = G [n_sites][n_E] . W.
+cudaError_t launch_ldos_source(int n_sites, int n_E, int M, int kernel, double lambda, const double *energies,
+                               const double *scal, const double *G, double *W, double *S, cudaStream_t s);
 // Column groups of the accumulation for ld columns at slab width W on Ly rows.
 int adjoint_groups(int Ly, int ld, int W);
 cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int py, int ld, int W,
@@ -227,6 +234,11 @@ cudaError_t launch_fixed_point_update(int N, double mix, const double *g, const 
 cudaError_t launch_adjoint_final(int Lx, int Ly, int px, int py, int groups, const double *part,
                                  const double *scal, double *g_eps, double *g_hop, double *g_delta,
                                  cudaStream_t s);
+
+// Rate probe of tcgen05.mma kind::tf32 at the contraction's shape (M = 128,
+// N = 256, K = 8): `ctas` CTAs (one per SM) issue `mmas` MMAs each.
+cudaError_t launch_tf32_peak(int ctas, long long mmas, unsigned *flags, cudaStream_t s);
+double tf32_peak_flops_per_mma();
 
 // Device address of the stand-alone contraction's error word (this device).
 cudaError_t contract_flag_address(unsigned **out);

@@ -28,6 +28,8 @@
 // thread 0 lets its copies in flight land (bounded) and the pass returns false.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace cbdg {
@@ -79,17 +81,82 @@ struct Kahan {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// Plain FP32 accumulation of a1*b1 + a2*b2 (two FMAs): the LEAN pass keeps
-// these to fit three levels into the registers.  A thread sums one site's
-// Ly rows (128 on the bench lattice), so the relative error stays below
-// Ly * 2^-24 before the FP64 reduction across the CTA.
-struct PlainSum {
+// ChunkSum: plain FP32 accumulation of a1*b1 + a2*b2 (two FMAs), used by the
+// LEAN pass to fit three levels into the registers.  To keep its error
+// independent of the lattice height, the pass flushes it every kFlushRows
+// wavefronts (flush_sums below): the partials of the 8 lanes of a warp that
+// hold the same columns are added pairwise in FP32 and the result goes into
+// FP64, so no FP32 sum spans more than 4 kFlushRows + 3 roundings.
+struct ChunkSum {
   float s = 0.f;
   __device__ __forceinline__ void add2(float a1, float b1, float a2, float b2) {
     s = __fmaf_rn(a1, b1, __fmaf_rn(a2, b2, s));
   }
-  __device__ __forceinline__ double value() const { return (double)s; }
 };
+
+// Wavefronts between two flushes of ChunkSum accumulators: two iterations of
+// the pass's three-wavefront loop.  With two sites per thread a chunk holds at
+// most 4 kFlushRows FP32 roundings per lane, then three pairwise additions
+// across lanes: relative error (4 kFlushRows + 3) 2^-24 = 27 * 2^-24 of
+// sum |terms| for every lattice height.
+constexpr int kFlushRows = 6;
+
+// FP64 share of a warp's column sums: after each flush, lane l holds the sums
+// of entries [base(l), base(l) + PER) of the zero-padded list of K levels x 3
+// products x 4 columns of its column quad (l & 3).
+template <int K>
+struct FlushBank {
+  static constexpr int NV = K * 12, NVP = (NV + 7) / 8 * 8, PER = NVP / 8;
+  double d[PER];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) d[i] = 0.0;
+  }
+  // first list index held by lane l (lane bits 4, 3, 2 pick halves NVP/2, NVP/4, NVP/8)
+  __host__ __device__ static constexpr int base(int lane) {
+    return ((lane >> 4) & 1) * (NVP / 2) + ((lane >> 3) & 1) * (NVP / 4) + ((lane >> 2) & 1) * (NVP / 8);
+  }
+};
+
+// One halving stage of the reduce-scatter over lane bit `mask`: the lane with
+// the bit set keeps the upper half of v[0 .. 2H) and receives its partner's
+// upper half; the other keeps and receives the lower half.  Result in v[0 .. H).
+template <int H>
+__device__ __forceinline__ void scatter_stage(float *v, int mask, bool hi) {
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const float send = hi ? v[i] : v[H + i];
+    const float keep = hi ? v[H + i] : v[i];
+    v[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, mask));
+  }
+}
+
+// Moves every ChunkSum partial of the calling thread into the warp's FP64
+// bank and zeroes it.  All 32 lanes of the warp must call it together; lane
+// bits 0-1 select the column quad (4 quads per warp), bits 2-4 the x slot.
+template <int K>
+__device__ __forceinline__ void flush_sums(ChunkSum (&accA)[K][4], ChunkSum (&accB)[K][4],
+                                           ChunkSum (&accC)[K][4], FlushBank<K> &bank) {
+  using FB = FlushBank<K>;
+  float v[FB::NVP];
+#pragma unroll
+  for (int l = 0; l < K; ++l)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[l * 12 + 0 * 4 + j] = accA[l][j].s;
+      v[l * 12 + 1 * 4 + j] = accB[l][j].s;
+      v[l * 12 + 2 * 4 + j] = accC[l][j].s;
+      accA[l][j].s = accB[l][j].s = accC[l][j].s = 0.f;
+    }
+#pragma unroll
+  for (int i = FB::NV; i < FB::NVP; ++i) v[i] = 0.f;
+  const int lane = threadIdx.x & 31;
+  scatter_stage<FB::NVP / 2>(v, 16, (lane & 16) != 0);
+  scatter_stage<FB::NVP / 4>(v, 8, (lane & 8) != 0);
+  scatter_stage<FB::NVP / 8>(v, 4, (lane & 4) != 0);
+#pragma unroll
+  for (int i = 0; i < FB::PER; ++i) bank.d[i] += static_cast<double>(v[i]);
+}
 
 __device__ __forceinline__ float fc(const float4 &v, int j) { return reinterpret_cast<const float *>(&v)[j]; }
 
@@ -125,8 +192,11 @@ template <int W, int K, int D, int MAXX, int NT = kPassThreads, bool LEAN = fals
 __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__restrict__ par, int Lx, int Ly,
                                            float *smem, unsigned long long *bars, long long base,
                                            unsigned long long wait_ns, unsigned stall_tx, int *abort_flag,
-                                           Acc (&accA)[K][4], Acc (&accB)[K][4], Acc (&accC)[K][4]) {
+                                           Acc (&accA)[K][4], Acc (&accB)[K][4], Acc (&accC)[K][4],
+                                           FlushBank<K> *bank = nullptr) {
   using Sh = PassShape<W, K, D, NT, LEAN>;
+  constexpr bool kFlush = std::is_same<Acc, ChunkSum>::value;
+  static_assert(!kFlush || W / 4 == 4, "the chunk flush expects four column quads per warp");
   constexpr int VEC = Sh::VEC, QUADS = Sh::QUADS, XSLOTS = Sh::XSLOTS;
   constexpr int RQ = Sh::RQ, RP = Sh::RP, AS = Sh::AS, AR = Sh::AR;
   static_assert(W % VEC == 0 && NT % QUADS == 0 && K >= 2, "bad shape");
@@ -341,6 +411,12 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
           }
         }
       }
+    }
+    if constexpr (kFlush) {
+      // every lane arrives here (stop and G are uniform over the CTA); the
+      // last iteration always flushes, so the bank holds the whole sums
+      if (!stop && ((g0 / 3) % (kFlushRows / 3) == kFlushRows / 3 - 1 || g0 + 3 >= G))
+        flush_sums<K>(accA, accB, accC, *bank);
     }
   }
   if (*abort_flag) {

@@ -1,20 +1,25 @@
 // noalloc.cu -- cbdg_moments_noalloc: the moments of cbdg_moments without
 // any device allocation.
 //
-// Who needs it: callers that must not allocate device memory during their
-// run, e.g. code that records its work into a CUDA graph, a host program
-// that owns a fixed memory budget and hands out only the buffers it planned,
-// or a plug-in running inside another framework's allocator.  A lattice
-// handle allocates on build, so this entry point takes the problem directly
-// (all arrays in device memory) and keeps every intermediate -- stencil
-// parameters, the two recursion vectors, per-column sums and flags -- in one
-// file-scope device array of fixed size, reserved when the library is loaded.
+// Who needs it: callers that must not allocate device memory while they run,
+// e.g. a host program that owns a fixed memory budget and hands out only the
+// buffers it planned, or a plug-in running inside another framework's
+// allocator, where a cudaMalloc of ours would bypass (or break) the owner's
+// accounting.  A lattice handle allocates on build, so this entry point takes
+// the problem directly (all arrays in device memory) and keeps every
+// intermediate -- stencil parameters, the two recursion vectors, per-column
+// sums, a checked copy of the start sites and the flags -- in one file-scope
+// device array of fixed size, reserved when the library is loaded.
 //
 // That array is kNoallocScratchBytes (64 MiB) on every GPU that loads the
 // library and stays reserved until the process exits.  All calls share it;
 // each call clears what must start at zero and keeps nothing from earlier
 // calls, but two calls whose GPU work overlaps (different streams or host
 // threads) race on it and give wrong results: serialise them.
+//
+// Throughput: the recursion runs one CTA per 16- (FP32) or 4-column (FP64)
+// slab with no row split, so a call with few start sites occupies few SMs;
+// this entry point trades throughput for a fixed footprint.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -33,6 +38,21 @@ namespace {
 
 constexpr size_t kNoallocScratchBytes = static_cast<size_t>(64) << 20;
 constexpr int kMaxDevices = 64;
+// Error bit of this entry point only: a start site outside [0, N).
+constexpr unsigned kFlagBadSite = 4u;
+static_assert((kFlagBadSite & (kFlagSpectrum | kFlagTimeout)) == 0, "flag bits collide");
+
+// Copies the start sites of one chunk into the scratch; a site outside
+// [0, N) is replaced by site 0 (so that no later kernel indexes out of
+// bounds) and raises kFlagBadSite, which the call reports as an error.
+__global__ void noalloc_sites_kernel(int n, int N, const int32_t *sites, int32_t *out, unsigned *flags) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const int32_t i = sites[b];
+  const bool ok = i >= 0 && i < N;
+  out[b] = ok ? i : 0;
+  if (!ok) atomicOr(flags, kFlagBadSite);
+}
 
 // The scratch itself.  In host code this name is only a stand-in for the
 // device symbol; its device address comes from cudaGetSymbolAddress.
@@ -62,7 +82,10 @@ bool on_device(const void *p) {
 }
 
 // Device address of the scratch on the current device, looked up once per
-// device (first call on that device) with that device current.
+// device (first call on that device) with that device current.  The cached
+// address belongs to the CUDA context of that first call: after a
+// cudaDeviceReset it is stale, so the entry point must not be used again in
+// that process.
 cudaError_t scratch_address(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -124,8 +147,9 @@ extern "C" cbdg_status cbdg_moments_noalloc(const cbdg_lattice_desc *d, const in
                        round256(static_cast<size_t>(N) * kParamStride * es) +
                        round256(static_cast<size_t>(M) * sizeof(double));
   // per column: two vectors, three partial sums (one CTA per slab along y),
-  // mu_1, conj(Delta)/a and the two fold accumulators
-  const size_t per_col = 2 * rows * es + 3 * sizeof(double) + 2 * sizeof(double) + 2 * sizeof(double2);
+  // mu_1, conj(Delta)/a, the two fold accumulators and the checked start site
+  const size_t per_col =
+      2 * rows * es + 3 * sizeof(double) + 2 * sizeof(double) + 2 * sizeof(double2) + sizeof(int32_t);
   const int W0 = slab_width_default(prec);
   if (fixed + per_col * W0 + 8 * 256 > kNoallocScratchBytes)
     return nfail(CBDG_ERR_INVALID_ARG,
@@ -174,15 +198,18 @@ extern "C" cbdg_status cbdg_moments_noalloc(const cbdg_lattice_desc *d, const in
     double2 *dA = static_cast<double2 *>(cv.take(ld * sizeof(double2)));
     double *acc_n = static_cast<double *>(cv.take(ld * sizeof(double)));
     double2 *acc_d = static_cast<double2 *>(cv.take(ld * sizeof(double2)));
+    int32_t *csites = static_cast<int32_t *>(cv.take(ld * sizeof(int32_t)));
     if (cv.used > kNoallocScratchBytes)
       return nfail(CBDG_ERR_INVALID_ARG, "no-allocation scratch exhausted (%zu > %zu bytes)", cv.used,
                    kNoallocScratchBytes);
+    noalloc_sites_kernel<<<(ncols + 127) / 128, 128, 0, s>>>(ncols, N, sites + c0, csites, flags);
+    NCK(cudaGetLastError());
     NCK(cudaMemsetAsync(v0, 0, vbytes, s));
     NCK(cudaMemsetAsync(v1, 0, vbytes, s));
     double *mee = mu_ee ? mu_ee + static_cast<size_t>(c0) * M : nullptr;
     double2 *meh = eh ? eh + static_cast<size_t>(c0) * M : nullptr;
     NCK(launch_init_real(prec, d->Lx, d->Ly, d->periodic_x, d->periodic_y, ncols, cfg.slab_w,
-                         sites + c0, d->eps, d->mu, hop, delta, scal, C, M, v0, v1, mu1, dA, acc_n,
+                         csites, d->eps, d->mu, hop, delta, scal, C, M, v0, v1, mu1, dA, acc_n,
                          acc_d, mee, meh, 1, s));
     StepArgs a;
     a.params = params;
@@ -208,6 +235,8 @@ extern "C" cbdg_status cbdg_moments_noalloc(const cbdg_lattice_desc *d, const in
   unsigned hflags = 0;
   NCK(cudaMemcpyAsync(&hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   NCK(cudaStreamSynchronize(s));
+  if (hflags & kFlagBadSite)
+    return nfail(CBDG_ERR_INVALID_ARG, "a start site is outside [0, Lx*Ly); the moments are not valid");
   if (hflags & kFlagTimeout)
     return nfail(CBDG_ERR_CUDA, "a recursion kernel gave up waiting for a staged copy");
   if (hflags & kFlagSpectrum)

@@ -44,35 +44,58 @@ __global__ void __launch_bounds__(kThreads, 1) step_multi_kernel(StepArgs a) {
     abort_flag = 0;
   }
   __syncthreads();
-  using Acc = typename std::conditional<LEAN, mp::PlainSum, Kahan>::type;
+  using Acc = typename std::conditional<LEAN, mp::ChunkSum, Kahan>::type;
+  using FB = mp::FlushBank<K>;
   Acc accA[K][VEC], accB[K][VEC], accC[K][VEC];
+  FB bank;
+  bank.clear();
   const bool ok = mp::multi_pass<W, K, D, MAXX, kThreads, LEAN, Acc>(
       static_cast<float *>(a.prev) + slab, static_cast<float *>(const_cast<void *>(a.cur)) + slab,
       static_cast<const float *>(a.params), a.Lx, a.Ly, reinterpret_cast<float *>(smem_raw), bars, 0,
-      a.wait_ns, a.stall_tx, &abort_flag, accA, accB, accC);
+      a.wait_ns, a.stall_tx, &abort_flag, accA, accB, accC, &bank);
   if (!ok) {
     if (t == 0) atomicOr(a.flags, kFlagTimeout);
     return;
   }
   __syncthreads();
-  // per-level column sums -> partials[(lv * 3 + k) * ld + col] (fixed order, FP64)
   double *red = reinterpret_cast<double *>(smem_raw);
   const size_t c0 = static_cast<size_t>(blockIdx.x) * W;
-  for (int lv = 0; lv < K; ++lv) {
+  if constexpr (LEAN) {
+    // the pass flushed every sum into the warps' FP64 banks: lane l of warp w
+    // holds list entries [base(l), base(l) + PER) of column quad l & 3; add the
+    // warps in a fixed order -> partials[(lv * 3 + k) * ld + col]
+    constexpr int NWARP = kThreads / 32;
+    const int lane = t & 31, w = t >> 5;
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      red[(0 * XSLOTS + xs) * W + q * VEC + j] = accA[lv][j].value();
-      red[(1 * XSLOTS + xs) * W + q * VEC + j] = accB[lv][j].value();
-      red[(2 * XSLOTS + xs) * W + q * VEC + j] = accC[lv][j].value();
-    }
+    for (int i = 0; i < FB::PER; ++i) red[(w * 4 + (lane & 3)) * FB::NVP + FB::base(lane) + i] = bank.d[i];
     __syncthreads();
-    for (int idx = t; idx < 3 * W; idx += kThreads) {
-      const int k = idx / W, col = idx - k * W;
+    for (int idx = t; idx < K * 3 * W; idx += kThreads) {
+      const int lk = idx / W, col = idx - lk * W;  // lk = lv * 3 + k
+      const int lv = lk / 3, k = lk - lv * 3;
+      const int qd = col / VEC, j = col - qd * VEC;
       double s = 0.0;
-      for (int z = 0; z < XSLOTS; ++z) s += red[(k * XSLOTS + z) * W + col];
-      a.partials[(static_cast<size_t>(lv) * 3 + k) * a.ld + c0 + col] = s;
+      for (int z = 0; z < NWARP; ++z) s += red[(z * 4 + qd) * FB::NVP + lv * 12 + k * 4 + j];
+      a.partials[static_cast<size_t>(lk) * a.ld + c0 + col] = s;
     }
-    __syncthreads();
+    return;
+  } else {
+    // per-level column sums -> partials[(lv * 3 + k) * ld + col] (fixed order, FP64)
+    for (int lv = 0; lv < K; ++lv) {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        red[(0 * XSLOTS + xs) * W + q * VEC + j] = accA[lv][j].value();
+        red[(1 * XSLOTS + xs) * W + q * VEC + j] = accB[lv][j].value();
+        red[(2 * XSLOTS + xs) * W + q * VEC + j] = accC[lv][j].value();
+      }
+      __syncthreads();
+      for (int idx = t; idx < 3 * W; idx += kThreads) {
+        const int k = idx / W, col = idx - k * W;
+        double s = 0.0;
+        for (int z = 0; z < XSLOTS; ++z) s += red[(k * XSLOTS + z) * W + col];
+        a.partials[(static_cast<size_t>(lv) * 3 + k) * a.ld + c0 + col] = s;
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -81,7 +104,8 @@ constexpr int kMaxDynSmem = 227 * 1024 - 1024;
 template <int W, int K, int D, bool LEAN = false>
 size_t smem_bytes(int Lx) {
   const size_t ring = mp::PassShape<W, K, D, kThreads, LEAN>::smem_floats(Lx);
-  const size_t red = static_cast<size_t>(3) * (kThreads / (W / 4)) * W * sizeof(double) / sizeof(float);
+  const size_t red = LEAN ? static_cast<size_t>(kThreads / 32) * 4 * mp::FlushBank<K>::NVP * sizeof(double) / sizeof(float)
+                          : static_cast<size_t>(3) * (kThreads / (W / 4)) * W * sizeof(double) / sizeof(float);
   return std::max(ring, red) * sizeof(float);
 }
 

@@ -164,6 +164,8 @@ def test_sn_slab_full_size_sampled(precision):
     if precision == "fp64":
         return
     lam = lat.lorentz_lambda(p.extra["broadening"], p.M)
+    # the ABI's lambda = broadening * M / a (Eq. 16 and the paragraph after it) for the current Delta
+    assert lam == pytest.approx(p.extra["broadening"] * p.M / a, rel=1e-14)
     E = p.extra["energy_frac"] * 0.5 * a        # within +-0.025 a of the band centre
     surf = p.extra["surface_sites"][:3]
     rho = lat.ldos(surf, p.M, E, kernel="lorentz", lam=lam)

@@ -94,9 +94,9 @@ def test_option_range():
 @pytest.mark.parametrize("case", [(65, 7, 40), (100, 23, 33), (128, 2, 64), (128, 31, 129), (97, 64, 24)])
 def test_lean_three_steps_match_oracle(case):
     """Three steps per pass at two sites per thread (64 < Lx <= 128, slab 16):
-    level 0 read from its shared-memory ring, parameters through the
-    read-only cache, plain FP32 column sums.  Moments vs the oracle, and vs
-    one step per pass."""
+    level 0 read from its shared-memory ring, parameters in a ring of their
+    own, FP32 column sums flushed into FP64 every few rows.  Moments vs the
+    oracle, and vs one step per pass."""
     Lx, Ly, M = case
     p = rect(Lx, Ly, M, seed=Lx * 7 + Ly, periodic=0)
     sites = np.arange(p.N, dtype=np.int32)[::-1].copy()
@@ -146,6 +146,57 @@ def test_full_size_disordered_128_sampled(steps, slab):
     assert max_abs(d[sample], od) < TOL_DELTA, max_abs(d[sample], od)
     assert max_abs(n[sample], on) < TOL_DELTA, max_abs(n[sample], on)
     assert np.all(np.abs(d) <= 0.5 * p.coupling + 1e-9)
+
+
+def tall_disordered(Lx, Ly, M, seed):
+    """Open Lx x Ly s-wave lattice of the 128x128 workload's physics (eps_i ~
+    U[-0.5, 0.5], t = 1, mu = -0.5, U = 2, T = 0.01, Delta = 0.5)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N = Lx * Ly
+    return wl.Problem(name=f"tall{Lx}x{Ly}", Lx=Lx, Ly=Ly, periodic_x=0, periodic_y=0,
+                      eps=rng.uniform(-0.5, 0.5, size=N), mu=-0.5, hop=wl.square_hops(Lx, Ly, 0, 0),
+                      pairing=wl.ONSITE, coupling=2.0, delta0=np.full(N, 0.5 + 0j), T=0.01, M=M)
+
+
+@pytest.mark.parametrize("shape", [(128, 1024, 256), (128, 512, 1024), (96, 2048, 128)])
+def test_lean_pass_tall_lattices_match_oracle(shape):
+    """The lean three-step pass on lattices much taller than wide: each
+    thread's FP32 column sums are flushed into FP64 every few rows, so their
+    error does not grow with Ly.  Moments of 16 sampled start sites (among
+    them the first and last rows) vs the oracle at the FP32 moment tolerance;
+    at M = 1024 on 128 x 512 every start vector spreads over the whole
+    height."""
+    Lx, Ly, M = shape
+    p = tall_disordered(Lx, Ly, M, seed=Lx + Ly)
+    rng = np.random.default_rng(Ly)
+    sites = np.concatenate([[0, Lx - 1, p.N - Lx, p.N - 1, (Ly // 2) * Lx + Lx // 2],
+                            rng.choice(p.N, 11, replace=False)]).astype(np.int32)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3)
+    (ee, eh), launches = recursion_launches(lat, sites, M)
+    n_steps = (M + 1) // 2 - 1
+    assert launches == n_steps // 3 + n_steps % 3
+    assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL) == 3
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, M)
+    assert max_abs(ee, oee) < TOL_MOM, max_abs(ee, oee)
+    assert max_abs(eh, oeh) < TOL_MOM, max_abs(eh, oeh)
+    lat.close()
+
+
+def test_lean_pass_tall_lattice_order_parameter_sampled():
+    """Delta_out and n_i of one self-consistency map on the 128 x 512 lattice
+    at M = 1024 with all 65536 start vectors (the lean pass), at sampled sites
+    vs the oracle."""
+    p = tall_disordered(128, 512, 1024, seed=640)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3)
+    d, n = lat.order_parameter(p.T, p.M)
+    assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL) == 3
+    rng = np.random.default_rng(12)
+    sample = np.concatenate([[0, 127, 256 * 128 + 64, p.N - 1],
+                             rng.choice(p.N, 6, replace=False)]).astype(np.int32)
+    od, on = orc.order_parameter_sites(as_oracle(p), lat.rescale, p.T, p.M, K, sample)
+    assert max_abs(d[sample], od) < TOL_DELTA, max_abs(d[sample], od)
+    assert max_abs(n[sample], on) < TOL_DELTA, max_abs(n[sample], on)
+    lat.close()
 
 
 def test_lost_copy_times_out_in_the_two_step_kernel():
