@@ -27,7 +27,9 @@
  *     Van Loan, the symmetric Jacobi method with a phase rotation for the
  *     complex off-diagonal), used only as an independent exact check.
  *   - reverse-mode gradients, storing every j_n: of one self-consistency
- *     map (a loss on Delta_out) and of a loss on the LDOS, a frozen.
+ *     map (a loss on Delta_out; real lattices, and general ones with complex
+ *     hoppings, next-nearest neighbours and bond pairing) and of a loss on
+ *     the LDOS, a frozen.
  *   - nonlocal moments <alpha_t|T_n|e_i> at chosen target sites, the
  *     Green's function of gf1 built from them, and the bond currents of
  *     Eq. 20 from the one-body density matrix f(H).
@@ -918,6 +920,156 @@ int orc_ldos_gradient(const orc_lattice *L, double a, const int32_t *sites, int 
   reverse_mode(L, a, sites, n_sites, M, 0, src, g_eps, g_hop, g_delta);
   free(g);
   free(src);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode for general lattices: complex hoppings (Peierls phases),     */
+/* next-nearest neighbours, on-site or bond pairing (a and C_n frozen).      */
+/* ------------------------------------------------------------------------ */
+
+/* Forward map: Delta_out = orc_order_parameter (Eq. 19 through the direct
+ * recursion of Eq. 15).  For a real loss L with g[k] = dL/dRe Delta_out,k
+ * + i dL/dIm Delta_out,k ([N] on-site, [N*4] bond), L changes by
+ * Re sum_k conj(g_k) dDelta_out,k.  Column i (start vector e_i) carries
+ *   on-site:  Delta_out,i = (U_i/2) sum_m C_m conj(<h_i|j_m>), so the
+ *             source is y_m(h_i) = (U_i/2) C_m conj(g_i);
+ *   bond:     <h_j|j_m> (j = i + d, d < 4) enters Delta_out,(i,d) and
+ *             Delta_out,(j,d^1) with weight (V/8) C_m each (the
+ *             symmetrised singlet of the order-parameter routine), so
+ *             y_m(h_j) = (C_m/8) conj(V_{i,d} g_{i,d} + V_{j,d^1} g_{j,d^1}).
+ * With Phi = Re sum_m <y_m|j_m> the adjoint recursion is
+ *   lam_m = y_m + 2 H~ lam_{m+1} - lam_{m+2}   (H~ Hermitian),
+ * and dPhi = Re sum_rs G_rs dH~_rs with G_rs = sum_{m>=1} f_m conj(lam_m(r)) j_{m-1}(s)
+ * (f_1 = 1, f_m = 2).  Parameters, from the entries of Eq. 2 that each one
+ * sets (H~ = H/a), as complex gradients dL/dRe + i dL/dIm:
+ *   eps_i:        H_{e_i e_i} = eps - mu, H_{h_i h_i} = -(eps - mu)  (real)
+ *   t = t_{i,d}:  H_{e_i e_j} = -t, H_{h_i h_j} = conj(t), and its mirror
+ *                 H_{e_j e_i} = -conj(t), H_{h_j h_i} = t; g_hop[i,d] is
+ *                 the gradient with respect to t_{i,d}, g_hop[j,d^1] with
+ *                 respect to t_{j,d^1} = conj(t), i.e. its conjugate
+ *   Delta_i:      H_{e_i h_i} = Delta, H_{h_i e_i} = conj(Delta)
+ *   Delta_{i,d}:  H_{e_i h_j} = H_{e_j h_i} = Delta, H_{h_i e_j} = H_{h_j e_i}
+ *                 = conj(Delta) (symmetric), stored on both directed entries.
+ * Every j_m of a column is stored (no checkpoints).  g_hop [N*n_dirs],
+ * g_delta [N] or [N*4]. */
+
+/* G at the CSR position of (r, c), or 0 when the entry is not stored. */
+static cplx g_at(const orc_csr *H, const cplx *G, int r, int c) {
+  for (int k = H->rowptr[r]; k < H->rowptr[r + 1]; ++k)
+    if (H->col[k] == c) return G[k];
+  return 0.0;
+}
+
+int orc_map_gradient_general(const orc_lattice *L, double a, const double *C, int M, const cplx *g,
+                             double *g_eps, cplx *g_hop, cplx *g_delta) {
+  int N = L->Lx * L->Ly;
+  int n = 2 * N;
+  int nd = L->n_dirs;
+  orc_csr H = build_csr(L);
+  int nnz = H.rowptr[n];
+  cplx *G = (cplx *)calloc(nnz, sizeof(cplx));
+  int nthreads = 1;
+#ifdef _OPENMP
+  nthreads = omp_get_max_threads();
+#endif
+  cplx *Gt = (cplx *)calloc((size_t)nnz * nthreads, sizeof(cplx));
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    cplx *Gl = Gt + (size_t)nnz * tid;
+    cplx *J = (cplx *)malloc(sizeof(cplx) * (size_t)n * M);
+    cplx *lam = (cplx *)malloc(sizeof(cplx) * (size_t)n * (M + 2));
+    cplx *tmp = (cplx *)malloc(sizeof(cplx) * n);
+#pragma omp for schedule(dynamic, 1)
+    for (int i = 0; i < N; ++i) {
+      /* forward: j_0 = e_i, j_1 = H~ j_0, j_m = 2 H~ j_{m-1} - j_{m-2} */
+      memset(J, 0, sizeof(cplx) * n);
+      J[2 * i] = 1.0;
+      for (int m = 1; m < M; ++m) {
+        cplx *jm = J + (size_t)m * n, *j1 = J + (size_t)(m - 1) * n;
+        cplx *j2 = (m >= 2) ? J + (size_t)(m - 2) * n : NULL;
+        double sc = (m == 1) ? 1.0 / a : 2.0 / a;
+        for (int r = 0; r < n; ++r) {
+          cplx acc = 0.0;
+          for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k) acc += H.val[k] * j1[H.col[k]];
+          jm[r] = sc * acc - (j2 ? j2[r] : 0.0);
+        }
+      }
+      /* source rows and weights of this column: y_m(row) = C_m * w_row */
+      int srow[4];
+      cplx sw[4];
+      int ns = 0;
+      if (L->pairing == 0) {
+        srow[ns] = 2 * i + 1;
+        sw[ns++] = 0.5 * coupling_of(L, i) * conj(g[i]);
+      } else {
+        for (int d = 0; d < 4; ++d) {
+          int j = orc_neighbour(L, i, d);
+          if (j < 0) continue;
+          srow[ns] = 2 * j + 1;
+          sw[ns++] = 0.125 * conj(coupling_of(L, (size_t)i * 4 + d) * g[(size_t)i * 4 + d] +
+                                  coupling_of(L, (size_t)j * 4 + (d ^ 1)) * g[(size_t)j * 4 + (d ^ 1)]);
+        }
+      }
+      memset(lam, 0, sizeof(cplx) * (size_t)n * (M + 2));
+      for (int m = M - 1; m >= 1; --m) {
+        cplx *lm = lam + (size_t)m * n, *l1 = lam + (size_t)(m + 1) * n, *l2 = lam + (size_t)(m + 2) * n;
+        for (int r = 0; r < n; ++r) {
+          cplx acc = 0.0;
+          for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k) acc += H.val[k] * l1[H.col[k]];
+          tmp[r] = (m + 1 < M ? (2.0 / a) * acc : 0.0) - (m + 2 < M ? l2[r] : 0.0);
+        }
+        for (int r = 0; r < n; ++r) lm[r] = tmp[r];
+        for (int q = 0; q < ns; ++q) lm[srow[q]] += C[m] * sw[q];
+      }
+      for (int m = 1; m < M; ++m) {
+        double f = (m == 1) ? 1.0 : 2.0;
+        cplx *lm = lam + (size_t)m * n, *jp = J + (size_t)(m - 1) * n;
+        for (int r = 0; r < n; ++r) {
+          cplx lr = f * conj(lm[r]);
+          if (lr == 0.0) continue;
+          for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k) Gl[k] += lr * jp[H.col[k]];
+        }
+      }
+    }
+    free(J);
+    free(lam);
+    free(tmp);
+  }
+  for (int t = 0; t < nthreads; ++t)
+    for (int k = 0; k < nnz; ++k) G[k] += Gt[(size_t)nnz * t + k];
+  free(Gt);
+  for (int i = 0; i < N; ++i) {
+    int e = 2 * i, h = 2 * i + 1;
+    g_eps[i] = creal(g_at(&H, G, e, e) - g_at(&H, G, h, h)) / a;
+    if (L->pairing == 0) {
+      cplx geh = g_at(&H, G, e, h), ghe = g_at(&H, G, h, e);
+      g_delta[i] = (creal(geh + ghe) + I * (cimag(ghe) - cimag(geh))) / a;
+    }
+    for (int d = 0; d < nd; ++d) {
+      int j = orc_neighbour(L, i, d);
+      if (j < 0) {
+        g_hop[(size_t)i * nd + d] = 0.0;
+        if (L->pairing == 1 && d < 4) g_delta[(size_t)i * 4 + d] = 0.0;
+        continue;
+      }
+      int ej = 2 * j, hj = 2 * j + 1;
+      cplx a1 = g_at(&H, G, e, ej), a2 = g_at(&H, G, h, hj), a3 = g_at(&H, G, ej, e), a4 = g_at(&H, G, hj, h);
+      double gr = creal(-a1 + a2 - a3 + a4), gi = cimag(a1) + cimag(a2) - cimag(a3) - cimag(a4);
+      g_hop[(size_t)i * nd + d] = (gr + I * gi) / a;
+      if (L->pairing == 1 && d < 4) {
+        cplx b1 = g_at(&H, G, e, hj), b2 = g_at(&H, G, ej, h), b3 = g_at(&H, G, h, ej), b4 = g_at(&H, G, hj, e);
+        double dr = creal(b1 + b2 + b3 + b4), di = -cimag(b1) - cimag(b2) + cimag(b3) + cimag(b4);
+        g_delta[(size_t)i * 4 + d] = (dr + I * di) / a;
+      }
+    }
+  }
+  free(G);
+  free_csr(&H);
   return 0;
 }
 

@@ -115,6 +115,7 @@ def _load():
             lib.orc_jacobi_eigh.argtypes = [I, P, P, P, D, I]
             lib.orc_scf_map_gradient.argtypes = [P, D, P, I, P, P, P, P]
             lib.orc_ldos_gradient.argtypes = [P, D, P, I, I, I, D, P, I, P, P, P, P]
+            lib.orc_map_gradient_general.argtypes = [P, D, P, I, P, P, P, P]
             lib.orc_neighbour.argtypes = [P, I, I]
             lib.orc_green_moments.argtypes = [P, D, I, P, I, P, I, I, P, P]
             lib.orc_green_function.argtypes = [P, I, I, I, D, I, D, P, I, P]
@@ -333,6 +334,27 @@ def scf_map_gradient(lat: Lattice, a: float, C, w):
     _load().orc_scf_map_gradient(ctypes.byref(c), float(a), _ptr(C), C.size, _ptr(w),
                                  _ptr(g_eps), _ptr(g_hop), _ptr(g_delta))
     return g_eps, g_hop.reshape(lat.N, lat.n_dirs), g_delta
+
+
+def map_gradient_general(lat: Lattice, a: float, C, g):
+    """Reverse-mode gradient of the self-consistency map for any lattice
+    (complex hoppings, next-nearest neighbours, on-site or bond pairing), a
+    and C frozen.  g: dL/dRe Delta_out + i dL/dIm Delta_out ([N] or [N, 4]).
+
+    Returns (g_eps [N], g_hop [N, n_dirs] complex, g_delta [N] or [N, 4]
+    complex), each complex entry dL/dRe + i dL/dIm of that parameter."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.complex128).reshape(-1)
+    nd = lat.N * 4 if lat.pairing == 1 else lat.N
+    assert g.size == nd
+    g_eps = np.zeros(lat.N)
+    g_hop = np.zeros(lat.N * lat.n_dirs, dtype=np.complex128)
+    g_delta = np.zeros(nd, dtype=np.complex128)
+    c = lat._c()
+    _load().orc_map_gradient_general(ctypes.byref(c), float(a), _ptr(C), C.size, _ptr(g), _ptr(g_eps),
+                                     _ptr(g_hop), _ptr(g_delta))
+    return (g_eps, g_hop.reshape(lat.N, lat.n_dirs),
+            g_delta.reshape(lat.N, 4) if lat.pairing == 1 else g_delta)
 
 
 def ldos_gradient(lat: Lattice, a: float, sites, M: int, energies, dL_dldos, kernel: int = 0,

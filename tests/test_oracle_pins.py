@@ -530,6 +530,108 @@ def test_scf_map_gradient_vs_finite_differences():
         assert g_hop[j, d ^ 1] == pytest.approx(g_hop[i, d], rel=1e-12)
 
 
+def _general_loss(p, a, M, K, g):
+    """L = Re sum_k conj(g_k) Delta_out,k and a closure over perturbed arrays."""
+    def loss(eps=None, hop=None, delta=None):
+        l2 = orc.Lattice(p.Lx, p.Ly, p.periodic_x, p.periodic_y, p.eps if eps is None else eps, p.mu,
+                         p.hop if hop is None else hop, p.pairing, p.coupling,
+                         p.delta0 if delta is None else delta)
+        d, _ = orc.order_parameter(l2, a, p.T, M, K)
+        return float(np.real(np.conj(g) * d.reshape(g.shape)).sum())
+    return loss
+
+
+def _fd_check_general(p, M, g_seed, sites, bonds, pair_bonds):
+    K = 1 << 12
+    lat = as_oracle(p)
+    a = orc.rescale(lat)
+    C = orc.fold_coefficients(M, K, a, p.T)
+    rng = np.random.default_rng(g_seed)
+    shape = (p.N, 4) if p.pairing == wl.BOND else (p.N,)
+    g = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    if p.pairing == wl.BOND:
+        g = g * (np.abs(p.delta0) > 0)  # no output across a missing bond
+    g_eps, g_hop, g_delta = orc.map_gradient_general(lat, a, C, g)
+    loss = _general_loss(p, a, M, K, g)
+    h = 1e-6
+
+    def fd(**kw):
+        plus = {k: v[0] for k, v in kw.items()}
+        minus = {k: v[1] for k, v in kw.items()}
+        return (loss(**plus) - loss(**minus)) / (2 * h)
+
+    scale = max(np.abs(g_eps).max(), np.abs(g_hop).max(), np.abs(g_delta).max())
+    tol = dict(rel=1e-6, abs=1e-8 * scale)
+    for i in sites:
+        e1, e2 = p.eps.copy(), p.eps.copy()
+        e1[i] += h
+        e2[i] -= h
+        assert g_eps[i] == pytest.approx(fd(eps=(e1, e2)), **tol)
+        if p.pairing != wl.BOND:
+            for unit, part in ((1.0, np.real), (1j, np.imag)):
+                d1, d2 = p.delta0.copy(), p.delta0.copy()
+                d1[i] += unit * h
+                d2[i] -= unit * h
+                assert part(g_delta[i]) == pytest.approx(fd(delta=(d1, d2)), **tol)
+    hop = p.hop.reshape(p.N, -1)
+    for (i, d) in bonds:
+        j = orc.neighbour(lat, i, d)
+        for unit, part in ((1.0, np.real), (1j, np.imag)):
+            h1, h2 = hop.copy(), hop.copy()
+            h1[i, d] += unit * h          # t_{i,d} and its Hermitian mirror t_{j,d^1} = conj(t_{i,d})
+            h1[j, d ^ 1] += np.conj(unit) * h
+            h2[i, d] -= unit * h
+            h2[j, d ^ 1] -= np.conj(unit) * h
+            assert part(g_hop[i, d]) == pytest.approx(fd(hop=(h1, h2)), **tol)
+        assert g_hop[j, d ^ 1] == pytest.approx(np.conj(g_hop[i, d]), rel=1e-12, abs=1e-14)
+    for (i, d) in pair_bonds:
+        j = orc.neighbour(lat, i, d)
+        for unit, part in ((1.0, np.real), (1j, np.imag)):
+            d1, d2 = p.delta0.copy(), p.delta0.copy()
+            d1[i, d] += unit * h          # symmetric pairing: Delta_{j,d^1} moves with Delta_{i,d}
+            d1[j, d ^ 1] += unit * h
+            d2[i, d] -= unit * h
+            d2[j, d ^ 1] -= unit * h
+            assert part(g_delta[i, d]) == pytest.approx(fd(delta=(d1, d2)), **tol)
+        assert g_delta[j, d ^ 1] == pytest.approx(g_delta[i, d], rel=1e-12, abs=1e-14)
+    assert scale > 1e-3
+
+
+def test_general_map_gradient_field_nnn_onsite_vs_finite_differences():
+    """Complex hoppings (uniform field, Peierls phases), t' and complex Delta_i:
+    the general reverse mode vs central differences of the oracle's
+    order parameter (Re and Im of eps, every hopping kind, Delta)."""
+    p = wl.random_swave(4, 32, seed=84, periodic=1, complex_delta=True, flux_quanta=1.0, tp=-0.3, T=0.05)
+    _fd_check_general(p, 32, 5, sites=(0, 6, 15), bonds=((0, 0), (5, 2), (6, 4), (9, 7), (3, 1)),
+                      pair_bonds=())
+
+
+def test_general_map_gradient_dwave_bonds_vs_finite_differences():
+    """Bond pairing (d-wave, complex symmetric Delta_ij) with a field: gradients
+    for eps, the hoppings and each bond amplitude vs central differences."""
+    p = wl.random_dwave(4, 24, seed=85, flux_quanta=1.0)
+    p.T = 0.05
+    _fd_check_general(p, 24, 6, sites=(0, 7, 13), bonds=((0, 0), (5, 2), (6, 4), (10, 6)),
+                      pair_bonds=((0, 0), (5, 2), (7, 1), (12, 3)))
+
+
+def test_general_map_gradient_reduces_to_the_real_one():
+    """On a real lattice with a real g the general reverse mode gives the real
+    routine's gradients (independently pinned above), with zero imaginary
+    parts."""
+    M, K = 40, 1 << 12
+    p = wl.random_swave(5, M, seed=86, T=0.05)
+    lat = as_oracle(p)
+    a = orc.rescale(lat)
+    C = orc.fold_coefficients(M, K, a, p.T)
+    w = np.random.default_rng(8).normal(size=p.N)
+    ge, gh, gd = orc.scf_map_gradient(lat, a, C, w)
+    he, hh, hd = orc.map_gradient_general(lat, a, C, w.astype(np.complex128))
+    assert np.allclose(he, ge, rtol=1e-12, atol=1e-15)
+    assert np.allclose(hh.real, gh, rtol=1e-12, atol=1e-15) and np.abs(hh.imag).max() < 1e-15
+    assert np.allclose(hd.real, gd, rtol=1e-12, atol=1e-15) and np.abs(hd.imag).max() < 1e-15
+
+
 def _ldos_loss_lattice(seed):
     M = 40
     p = wl.random_swave(4, M, seed=seed, T=0.05)
