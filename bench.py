@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 METRIC = ("Chebyshev BdG steps/s (vectors×H-apps), FP32 vs FP64 at ≤1e-4 Δ error; HBM %")
 UNIT = "vector-steps/s"
 L, M, SEED = 128, 1024, 1001
-FP64_FLOPS_PER_ELEMENT_STEP = 20.0  # stencil 12 + moment products 8 (FMA = 2 flops)
+# per vector element and step: the stencil's 6 FMAs and half of a site's 6 product FMAs (FMA = 2 flops)
+FP64_FLOPS_PER_ELEMENT_STEP = 18.0
 
 
 def kernel_source_digest(sources):
@@ -596,21 +597,24 @@ def leg_currents(cbdg, wl, torch, stream, hbm):
 
 
 def leg_junction(cbdg, wl, torch, stream, hbm):
-    """The S/N slab after the paper's first example (64 x 320, U = 0 on the
-    top 20 rows, M = 2048, FP32): one self-consistency iteration (second call,
-    graph replay) and the surface LDOS (64 sites x 201 energies) with the
-    Lorentz kernel at a broadening of 0.001 t."""
+    """The S/N slab after the paper's first example (a 500-site periodic
+    plane x 320 layers, U = 0 on the top 20 layers, M = 2048, FP32): one
+    self-consistency iteration (second call, graph replay) with one start
+    site per layer (the plane's translations, cbdg_set_symmetry), and the
+    surface LDOS (64 surface sites x 201 energies) with the Lorentz kernel at
+    a broadening of 0.001 t."""
     import numpy as np
     p = wl.sn_slab()
     lat = cbdg.Lattice(p, precision="fp32", stream=stream)
     lat.set_coupling(p.extra["coupling_site"])
+    lat.set_symmetry(p.extra["symmetry"])
     lat.scf_step(p.T, p.M, p.mix)
     t0 = time.perf_counter()
     diff = lat.scf_step(p.T, p.M, p.mix)
     t1 = time.perf_counter()
     lam = lat.lorentz_lambda(p.extra["broadening"], p.M)
     E = p.extra["energy_frac"] * lat.rescale
-    sites = p.extra["surface_sites"]
+    sites = p.extra["surface_sites"][:64]
     lat.ldos(sites, p.M, E, kernel="lorentz", lam=lam)
     t2 = time.perf_counter()
     rho = lat.ldos(sites, p.M, E, kernel="lorentz", lam=lam)
@@ -623,15 +627,16 @@ def leg_junction(cbdg, wl, torch, stream, hbm):
     sms, sn, sb = cbdg.cbdg_profile_read(lat.handle)
     k = cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL)
     lat.close()
-    units = p.N * ((p.M + 1) // 2)
-    return {"lattice": "64x320, periodic x, open y, S rows 0-299 (U = 1.41), N rows 300-319 (U = 0)",
-            "M": p.M, "scf_iteration_s": t1 - t0, "vector_steps_per_s": units / (t1 - t0),
-            "max_abs_ddelta": diff, "delta_bulk": float(abs(d[64 * 150])), "delta_interface": float(abs(d[64 * 299])),
+    L = p.Lx
+    units = p.Ly * ((p.M + 1) // 2)
+    return {"lattice": f"{L}x{p.Ly}, periodic x (the plane), open y, S rows 0-299 (U = 1.41), N rows 300-319 (U = 0)",
+            "M": p.M, "start_vectors": int(p.Ly), "scf_iteration_s": t1 - t0, "vector_steps_per_s": units / (t1 - t0),
+            "max_abs_ddelta": diff, "delta_bulk": float(abs(d[L * 150])), "delta_interface": float(abs(d[L * 299])),
             "surface_ldos_s": t3 - t2, "lorentz_lambda": lam, "surface_ldos_at_0": float(rho[:, 100].mean()),
             "steps_per_pass": k, "recursion_launches": sn, "recursion_ms": sms,
             "roofline": {"bound": "hbm", "achieved": sb / (sms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": sb / (sms * 1e-3) / 1e9 / hbm,
-                         "note": "step_multi_kernel, 4 vector streams per pass of K steps (algorithmic bytes)"}}
+                         "note": "recursion kernels over their algorithmic bytes (one start site per layer)"}}
 
 
 def leg_green(cbdg, wl, torch, stream, fp64_peak=None):
@@ -791,8 +796,8 @@ def arith_peaks(cbdg, torch, stream, local=0):
     process.  TFLOP/s."""
     if _ARITH:
         return _ARITH
-    specs = (("fp64_fma", cbdg.CBDG_PEAK_FP64_FMA, 24000),
-             ("fp32_fma", cbdg.CBDG_PEAK_FP32_FMA, 1500000),
+    specs = (("fp64_fma", cbdg.CBDG_PEAK_FP64_FMA, 30000),
+             ("fp32_fma", cbdg.CBDG_PEAK_FP32_FMA, 750000),
              ("tf32_mma", cbdg.CBDG_PEAK_TF32_MMA, 1 << 20))
     out = {}
     with ClockSampler(local) as clk:
@@ -808,7 +813,7 @@ def arith_peaks(cbdg, torch, stream, local=0):
             ms = e0.elapsed_time(e1)
             out[name] = {"tflops": flops / (ms * 1e-3) / 1e12, "ms": ms, "flops": flops}
     out["clocks"] = clk.summary()
-    out["how"] = ("cbdg_measure_peak: FP64/FP32 -- 8 independent FMA chains per thread, 8 CTAs x 256 threads "
+    out["how"] = ("cbdg_measure_peak: FP64/FP32 -- 8/16 independent FMA chains per thread, 8 CTAs x 256 threads "
                   "per SM; TF32 -- tcgen05.mma kind::tf32 M=128 N=256 K=8 from shared memory into tensor "
                   "memory, one CTA per SM; one CUDA-event timed launch each after a warm-up")
     _ARITH.update(out)

@@ -215,24 +215,34 @@ cbdg_status cbdg_scf_step(cbdg_lattice *lat, double T, int32_t M, double mix,
                           double *max_abs_ddelta);
 
 /* Reverse-mode gradient of one self-consistency map Delta_out(eps, t, Delta_in)
- * (Eq. 19 through the recursion of Eq. 15) for real on-site pairing with
- * 4 directions, with the rescale a and the coefficients C_n frozen at their
+ * (Eq. 19 through the recursion of Eq. 15) for every lattice kind (real or
+ * complex Peierls hoppings, next-nearest neighbours, on-site or bond
+ * pairing), with the rescale a and the coefficients C_n frozen at their
  * values for the current Delta (a Gershgorin value, or the fixed one).
- * Given dL_ddelta_out [N] (real part used), writes
- *   dL_deps[i]         = dL/deps_i
- *   dL_dhop[i*4 + d]   = dL/dt for the undirected bond (i, i+d), moving both
- *                        directed entries together (stored on both; 0 across
- *                        an open edge)
- *   dL_ddelta_in[i]    = dL/dDelta_i  (the input Delta of the map)
- * Any output may be NULL.  The forward recursion runs without doubling,
- * keeps checkpoints of (j_{kS}, j_{kS+1}) every S = ceil(sqrt(M)) steps and
- * recomputes each segment during the reverse sweep
- *   lam_m = y_m + 2 H~ lam_{m+1} - lam_{m+2},  y_m = w_i (U/2) C_m h_i.
- * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Not in the paper (it has no
+ * Given dL_ddelta_out [nd] = dL/dRe Delta_out + i dL/dIm Delta_out
+ * (nd = N, or N*4 for bond pairing; host or device), writes
+ *   dL_deps[i]                = dL/deps_i (real)
+ *   dL_dhop[i*n_dirs + d]     = dL/dRe t + i dL/dIm t for t = t_{i,d}, the
+ *                               hopping of Eq. 2 with its Peierls phase; t
+ *                               and its Hermitian mirror t_{j,d^1} = conj(t)
+ *                               move together, so the mirror entry holds the
+ *                               conjugate (0 across an open edge)
+ *   dL_ddelta_in[k]           = dL/dRe Delta_k + i dL/dIm Delta_k of the input
+ *                               Delta (on-site [N], or bond [N*4] with
+ *                               Delta_{j,d^1} = Delta_{i,d} moving together)
+ * Any output may be NULL; outputs are host or device arrays.  Real lattices
+ * run the real recursion (imaginary parts 0), general ones complex vectors.
+ * The forward recursion runs without doubling, keeps checkpoints of
+ * (j_{kS}, j_{kS+1}) every S = ceil(sqrt(M)) steps and recomputes each
+ * segment during the reverse sweep
+ *   lam_m = y_m + 2 H~ lam_{m+1} - lam_{m+2},
+ * with the source y_m = (U_i/2) C_m conj(g_i) h_i (on-site) or
+ * (C_m/8) conj(V_{i,d} g_{i,d} + V_{j,d^1} g_{j,d^1}) h_j on each bond.
+ * Errors: INVALID_ARG, OOM, CUDA.  Not in the paper (it has no
  * derivatives); added for gradient-based inverse design on Delta. */
 cbdg_status cbdg_order_parameter_backward(cbdg_lattice *lat, double T, int32_t M,
                                           const cbdg_complex *dL_ddelta_out, double *dL_deps,
-                                          double *dL_dhop, double *dL_ddelta_in);
+                                          cbdg_complex *dL_dhop, cbdg_complex *dL_ddelta_in);
 
 /* Reverse-mode gradient of a loss on the up-spin LDOS of Eq. 17 (the
  * expansion of Eq. 10, as cbdg_ldos computes it) at the listed sites, for
@@ -300,6 +310,20 @@ cbdg_status cbdg_set_coupling(cbdg_lattice *lat, const double *coupling);
  * parameters (an optimiser, an autograd loop) reuse one lattice and its
  * buffers.  Errors: INVALID_ARG, CUDA. */
 cbdg_status cbdg_set_hamiltonian(cbdg_lattice *lat, const double *eps, const cbdg_complex *hop);
+
+/* Start-vector symmetry reduction.  rep [N] (host or device) maps every
+ * site to the representative of its orbit under a symmetry of the
+ * Hamiltonian and of the current and future Delta that the CALLER guarantees,
+ * e.g. the translations along a periodic direction of a lattice without
+ * disorder (rep[x + Lx*y] = Lx*y).  cbdg_order_parameter and cbdg_scf_step
+ * then run one recursion per distinct representative and give every site of
+ * an orbit its representative's Delta_out and n: each grid point's Green's
+ * function is computed separately (the paragraph after Eq. 20), and
+ * equivalent points have the same one.  Needs rep[rep[i]] == rep[i]; NULL
+ * restores every site as a start vector.  On-site pairing only (a bond fold
+ * reads the recursion of both ends).  Other calls (moments, LDOS, adjoints)
+ * are unaffected.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+cbdg_status cbdg_set_symmetry(cbdg_lattice *lat, const int32_t *rep);
 
 /* The rescale factor a used by the most recent compute call (0 before any). */
 cbdg_status cbdg_get_rescale(cbdg_lattice *lat, double *a);
@@ -446,9 +470,9 @@ cbdg_status cbdg_moments_noalloc(const cbdg_lattice_desc *desc, const int32_t *s
  * microbenchmarks: the denominators of the rooflines of the arithmetic-bound
  * kernels (the FP64 recursion, the FP64 Green's-function contraction, the
  * 3xTF32 LDOS contraction).  Not in the paper (it reports no timings).
- *   kind: CBDG_PEAK_FP64_FMA / CBDG_PEAK_FP32_FMA -- 8 independent FMA
- *         chains per thread, 8 CTAs of 256 threads per SM, `work` FMAs per
- *         chain; CBDG_PEAK_TF32_MMA -- one CTA per SM issuing `work`
+ *   kind: CBDG_PEAK_FP64_FMA / CBDG_PEAK_FP32_FMA -- 8 (FP64) or 16 (FP32)
+ *         independent FMA chains per thread, 8 CTAs of 256 threads per SM,
+ *         `work` FMAs per chain; CBDG_PEAK_TF32_MMA -- one CTA per SM issuing `work`
  *         tcgen05.mma kind::tf32 of M = 128, N = 256, K = 8 (the LDOS
  *         contraction's instruction) from shared memory into tensor memory.
  *   work: 1 .. 2^40.  *flops (host) receives the flops of the launch

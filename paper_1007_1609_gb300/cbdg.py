@@ -103,6 +103,7 @@ def load():
             "cbdg_get_delta": [P, P],
             "cbdg_set_delta": [P, P],
             "cbdg_set_hamiltonian": [P, P, P],
+            "cbdg_set_symmetry": [P, P],
             "cbdg_get_rescale": [P, P],
             "cbdg_lorentz_lambda": [P, D, I32, P],
             "cbdg_set_option": [P, I32, I64],
@@ -235,6 +236,10 @@ def cbdg_set_delta(lat, delta):
 
 def cbdg_set_hamiltonian(lat, eps, hop):
     _check(load().cbdg_set_hamiltonian(lat, _ptr(eps), _ptr(hop)))
+
+
+def cbdg_set_symmetry(lat, rep):
+    _check(load().cbdg_set_symmetry(lat, _ptr(rep)))
 
 
 def cbdg_get_rescale(lat):
@@ -534,6 +539,14 @@ class Lattice:
         self._cpl = np.ascontiguousarray(coupling, dtype=np.float64).reshape(-1)
         cbdg_set_coupling(self.handle, self._cpl)
 
+    def set_symmetry(self, rep):
+        """Representative site of every site's orbit ([N]; None: no reduction)."""
+        if rep is None:
+            cbdg_set_symmetry(self.handle, None)
+            return
+        self._rep = np.ascontiguousarray(rep, dtype=np.int32)
+        cbdg_set_symmetry(self.handle, self._rep)
+
     def lorentz_lambda(self, broadening, M):
         """lambda of the Lorentz kernel (Eq. 16) for an energy broadening at the
         band centre, with the rescale of the current Delta (cbdg_lorentz_lambda)."""
@@ -587,10 +600,13 @@ class Lattice:
         return ge, gh.reshape(self.N, 4), gd
 
     def backward(self, T, M, dL_ddelta_out):
-        """Gradients (eps [N], hop [N, 4], delta_in [N]) of one map (see the C ABI)."""
-        w = np.ascontiguousarray(dL_ddelta_out, dtype=np.complex128)
+        """Gradients of one map (see the C ABI): (eps [N] real, hop [N, n_dirs]
+        complex, delta_in [N] or [N, 4] complex), each complex entry
+        dL/dRe + i dL/dIm; dL_ddelta_out is [N] or [N, 4] (complex)."""
+        w = np.ascontiguousarray(dL_ddelta_out, dtype=np.complex128).reshape(-1)
         g_eps = np.zeros(self.N)
-        g_hop = np.zeros(self.N * 4)
-        g_delta = np.zeros(self.N)
+        g_hop = np.zeros(self.N * self.n_dirs, dtype=np.complex128)
+        g_delta = np.zeros(self.nd, dtype=np.complex128)
         cbdg_order_parameter_backward(self.handle, T, M, w, g_eps, g_hop, g_delta)
-        return g_eps, g_hop.reshape(self.N, 4), g_delta
+        return (g_eps, g_hop.reshape(self.N, self.n_dirs),
+                g_delta.reshape(self.N, 4) if self.pairing == CBDG_BOND_V else g_delta)

@@ -118,8 +118,11 @@ struct cbdg_lattice {
   DBuf eps, hop, delta, params, scal, flags, f, C, sites_all, sites_user;
   DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
   DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out, adj_fp;
+  DBuf adj_wc, adj_outc;  // general-lattice adjoint: dL/dDelta_out (complex) and the gradients
   DBuf params_c, g_acc, g_tgt, g_mom, g_w, g_out;  // nonlocal readout (green.cu)
   DBuf cpl;              // coupling per Delta entry (cbdg_set_coupling)
+  DBuf sym_rep, sym_list;  // cbdg_set_symmetry: representative of every site, distinct representatives
+  int sym_n = 0;           // number of representatives (0: no symmetry reduction)
   int site_cpl = 0;      // 1 while cpl replaces the scalar coupling
   const double *coupling_site() const { return site_cpl ? static_cast<const double *>(cpl.p) : nullptr; }
   // options
@@ -813,6 +816,14 @@ cbdg_status order_parameter_impl(cbdg_lattice *L, double T, int kernel, double l
   if (st != CBDG_OK) return st;
   CK(L->dout.ensure(static_cast<size_t>(L->nd) * sizeof(double2)));
   CK(L->nout.ensure(static_cast<size_t>(L->N) * sizeof(double)));
+  if (L->sym_n > 0) {
+    // one recursion per representative; its orbit copies Delta_out and n
+    st = run_columns(L, L->sym_list.as<int32_t>(), L->sym_n, M, nullptr, nullptr, 1, true);
+    if (st != CBDG_OK) return st;
+    CK(launch_orbit_fill(L->N, L->sym_rep.as<int32_t>(), L->dout.as<double2>(), L->nout.as<double>(), L->stream));
+    L->launches += 1;
+    return CBDG_OK;
+  }
   return run_columns(L, L->sites_all.as<int32_t>(), L->N, M, nullptr, nullptr, 1, true);
 }
 
@@ -1010,6 +1021,157 @@ cbdg_status check_hop(const cbdg_lattice_desc *d, const std::vector<cbdg_complex
       if (z.im != 0.0) return fail(CBDG_ERR_INVALID_ARG, "complex hop with complex_field = 0");
   return CBDG_OK;
 }
+// Adjoint of one self-consistency map for general lattices (complex vectors:
+// Peierls hoppings, next-nearest neighbours, on-site or bond pairing), with
+// g = dL/dRe Delta_out + i dL/dIm Delta_out [nd] already in L->adj_wc
+// (device).  The schedule of adjoint_run (sqrt(M) checkpoints of
+// (j_{kS}, j_{kS+1}), segment recomputation, reverse recursion) on the general
+// step kernel.  Leaves dL/dt [N * n_dirs] (complex), dL/dDelta_in [nd]
+// (complex) and dL/deps [N], in this order, in L->adj_outc.
+cbdg_status adjoint_run_cplx(cbdg_lattice *L, double T, int M) {
+  const int N = L->N;
+  const int bond = L->pairing == CBDG_BOND_V ? 1 : 0;
+  const int nd = L->n_dirs;
+  cbdg_status st = prepare(L, T, CBDG_JACKSON, 0.0, M, true);
+  if (st != CBDG_OK) return st;
+  std::vector<double> hC(M);
+  CK(cudaMemcpyAsync(hC.data(), L->C.p, M * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+
+  const size_t es = vec_elem_size(L);
+  const size_t rows = 2 * static_cast<size_t>(N);
+  const int W = slab_width_default_cplx(L->precision);
+  const int S = std::max(2, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(M)))));
+  const int nseg = (M + S - 1) / S;
+  const int64_t per_col = static_cast<int64_t>((2 * nseg + S + 4) * rows * es);
+  size_t cap;
+  if (L->ws_mb > 0) {
+    cap = static_cast<size_t>(L->ws_mb) << 20;
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    cap = static_cast<size_t>(0.5 * (fr + L->adj_ck.bytes + L->adj_seg.bytes + L->adj_lam.bytes +
+                                     L->vec0.bytes + L->vec1.bytes));
+  }
+  int64_t max_cols = (static_cast<int64_t>(cap) / per_col / W) * W;
+  if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
+  if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for the adjoint");
+  const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((N + W - 1) / W) * W));
+  const int groups = adjoint_groups(L->Ly, ((std::min(chunk, N) + W - 1) / W) * W, W);
+  const int KC = adjoint_cplx_sums(nd, bond);
+  const size_t part_bytes = static_cast<size_t>(groups) * N * 2 * KC * sizeof(double);
+  CK(L->adj_part.ensure(part_bytes));
+  CK(cudaMemsetAsync(L->adj_part.p, 0, part_bytes, L->stream));
+
+  for (int c0 = 0; c0 < N; c0 += chunk) {
+    const int ncols = std::min(chunk, N - c0);
+    const int ld = ((ncols + W - 1) / W) * W;
+    StepConfig cfg;
+    if (!plan_step_cplx(L->precision, L->Lx, L->Ly, ld, W, static_cast<int>(L->row_split),
+                        static_cast<int>(L->depth), &cfg) || cfg.slab_w != W)
+      return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d for the adjoint", L->Lx);
+    const size_t vb = rows * ld * es;
+    CK(L->vec0.ensure(vb));
+    CK(L->vec1.ensure(vb));
+    CK(L->adj_ck.ensure(2 * nseg * vb));
+    CK(L->adj_seg.ensure(static_cast<size_t>(S) * vb));
+    CK(L->adj_lam.ensure(2 * vb));
+    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 4 * ld * sizeof(double)));
+    CK(L->mu1.ensure(ld * sizeof(double)));
+    CK(L->dA.ensure(ld * sizeof(double2)));
+    CK(L->acc_n.ensure(ld * sizeof(double)));
+    CK(L->acc_d.ensure(ld * 4 * sizeof(double2)));
+    const int32_t *sites = L->sites_all.as<int32_t>() + c0;
+    unsigned char *ck = L->adj_ck.as<unsigned char>();
+    unsigned char *seg = L->adj_seg.as<unsigned char>();
+    auto ckv = [&](int k, int which) { return ck + (2 * static_cast<size_t>(k) + which) * vb; };
+    auto segv = [&](int r) { return seg + static_cast<size_t>(r) * vb; };
+    StepArgs a;
+    a.params = L->params.p;
+    a.partials = L->partials.as<double>();
+    a.flags = L->flags.as<unsigned int>();
+    a.wait_ns = static_cast<unsigned long long>(L->wait_ms) * 1000000ull;
+    a.stall_tx = L->stall ? 16u : 0u;
+    a.Lx = L->Lx;
+    a.Ly = L->Ly;
+    a.ld = ld;
+    a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+    auto step = [&](void *cur, void *prev_inout) -> cbdg_status {
+      a.cur = cur;
+      a.prev = prev_inout;
+      CK(launch_step_cplx(L->precision, nd == 8, bond, a, cfg, L->stream));
+      L->launches += 1;
+      return CBDG_OK;
+    };
+    CK(cudaMemsetAsync(L->vec0.p, 0, vb, L->stream));
+    CK(cudaMemsetAsync(L->vec1.p, 0, vb, L->stream));
+    CK(launch_init_cplx(L->precision, L->Lx, L->Ly, L->px, L->py, nd, L->pairing, ncols, W, sites,
+                        L->eps.as<double>(), L->mu, L->hop.as<double2>(), L->delta.as<double2>(),
+                        L->scal.as<double>(), L->C.as<double>(), M, L->vec0.p, L->vec1.p, L->mu1.as<double>(),
+                        L->dA.as<double2>(), L->acc_n.as<double>(), L->acc_d.as<double2>(), nullptr, nullptr, 1,
+                        L->stream));
+    L->launches += 1;
+    CK(cudaMemcpyAsync(ckv(0, 0), L->vec0.p, vb, cudaMemcpyDeviceToDevice, L->stream));
+    CK(cudaMemcpyAsync(ckv(0, 1), L->vec1.p, vb, cudaMemcpyDeviceToDevice, L->stream));
+    void *jm2 = L->vec0.p, *jm1 = L->vec1.p;
+    const int m_last = (nseg - 1) * S + 1;
+    for (int m = 2; m < M && m <= m_last; ++m) {
+      st = step(jm1, jm2);
+      if (st != CBDG_OK) return st;
+      std::swap(jm1, jm2);
+      if (m % S == 0) CK(cudaMemcpyAsync(ckv(m / S, 0), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+      if ((m - 1) % S == 0 && m - 1 >= S)
+        CK(cudaMemcpyAsync(ckv((m - 1) / S, 1), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+    }
+    void *lam1 = L->adj_lam.p;
+    void *lam2 = L->adj_lam.as<unsigned char>() + vb;
+    CK(cudaMemsetAsync(lam1, 0, vb, L->stream));
+    CK(cudaMemsetAsync(lam2, 0, vb, L->stream));
+    bool first = true;
+    for (int k = nseg - 1; k >= 0; --k) {
+      const int r_end = std::min(S, M - k * S);
+      CK(cudaMemcpyAsync(segv(0), ckv(k, 0), vb, cudaMemcpyDeviceToDevice, L->stream));
+      if (r_end > 1) CK(cudaMemcpyAsync(segv(1), ckv(k, 1), vb, cudaMemcpyDeviceToDevice, L->stream));
+      for (int r = 2; r < r_end; ++r) {
+        a.cur = segv(r - 1);
+        a.prev = segv(r - 2);
+        a.out = segv(r);
+        CK(launch_step_cplx(L->precision, nd == 8, bond, a, cfg, L->stream));
+        a.out = nullptr;
+        L->launches += 1;
+      }
+      const int m_hi = std::min(M - 1, k * S + r_end), m_lo = k * S + 1;
+      for (int m = m_hi; m >= m_lo; --m) {
+        if (first) {
+          first = false;
+        } else {
+          st = step(lam1, lam2);
+          if (st != CBDG_OK) return st;
+          std::swap(lam1, lam2);
+        }
+        CK(launch_adjoint_source_cplx(L->precision, L->Lx, L->Ly, L->px, L->py, ncols, W, sites, L->pairing,
+                                      L->adj_wc.as<double2>(), L->coupling_site(), L->coupling, hC[m], lam1,
+                                      L->stream));
+        CK(launch_adjoint_accumulate_cplx(L->precision, L->Lx, L->Ly, L->px, L->py, nd, bond, ld, W, groups, lam1,
+                                          segv(m - 1 - k * S), m == 1 ? 1.0 : 2.0, L->adj_part.as<double>(),
+                                          L->stream));
+        L->launches += 2;
+      }
+    }
+  }
+  const size_t out_bytes = static_cast<size_t>(N) * sizeof(double) +
+                           (static_cast<size_t>(N) * nd + static_cast<size_t>(L->nd)) * sizeof(double2);
+  CK(L->adj_outc.ensure(out_bytes));
+  // complex arrays first (16-byte aligned), then the N real dL/deps
+  double2 *gh = L->adj_outc.as<double2>();
+  double2 *gd = gh + static_cast<size_t>(N) * nd;
+  double *ge = reinterpret_cast<double *>(gd + L->nd);
+  CK(launch_adjoint_final_cplx(L->Lx, L->Ly, L->px, L->py, nd, bond, groups, L->adj_part.as<double>(),
+                               L->scal.as<double>(), ge, gh, gd, L->stream));
+  L->launches += 1;
+  return CBDG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1531,32 +1693,50 @@ cbdg_status cbdg_scf_step(cbdg_lattice *L, double T, int32_t M, double mix,
 
 cbdg_status cbdg_order_parameter_backward(cbdg_lattice *L, double T, int32_t M,
                                           const cbdg_complex *dL_ddelta_out, double *dL_deps,
-                                          double *dL_dhop, double *dL_ddelta_in) {
+                                          cbdg_complex *dL_dhop, cbdg_complex *dL_ddelta_in) {
   cbdg_status st = begin(L);
   if (st != CBDG_OK) return st;
-  if (mode_of(L) != kReal)
-    return fail(CBDG_ERR_UNSUPPORTED, "the adjoint handles real on-site pairing with 4 directions");
   if (!(T >= 0.0) || !isfinite(T)) return fail(CBDG_ERR_INVALID_ARG, "T must be finite and >= 0");
   if (M < 2) return fail(CBDG_ERR_INVALID_ARG, "M must be >= 2");
   if (!dL_ddelta_out) return fail(CBDG_ERR_INVALID_ARG, "dL_ddelta_out is NULL");
   const int N = L->N;
-  // w_i = Re dL/dDelta_out,i (Delta is real here)
   std::vector<cbdg_complex> hw;
-  cudaError_t e = host_copy(dL_ddelta_out, N, hw);
+  cudaError_t e = host_copy(dL_ddelta_out, L->nd, hw);
   if (e != cudaSuccess) return cuda_fail(e, "reading dL_ddelta_out");
-  std::vector<double> w(N);
-  for (int i = 0; i < N; ++i) {
-    if (!isfinite(hw[i].re)) return fail(CBDG_ERR_INVALID_ARG, "dL_ddelta_out is not finite");
-    w[i] = hw[i].re;
+  for (int k = 0; k < L->nd; ++k)
+    if (!finite_c(hw[k])) return fail(CBDG_ERR_INVALID_ARG, "dL_ddelta_out is not finite");
+  if (mode_of(L) != kReal) {
+    // general lattices: complex vectors, complex gradients
+    CK(L->adj_wc.ensure(static_cast<size_t>(L->nd) * sizeof(double2)));
+    CK(cudaMemcpyAsync(L->adj_wc.p, hw.data(), static_cast<size_t>(L->nd) * sizeof(double2), cudaMemcpyHostToDevice,
+                       L->stream));
+    st = adjoint_run_cplx(L, T, M);
+    if (st != CBDG_OK) return st;
+    double2 *gh = L->adj_outc.as<double2>();
+    double2 *gd = gh + static_cast<size_t>(N) * L->n_dirs;
+    double *ge = reinterpret_cast<double *>(gd + L->nd);
+    CK(deliver(L, dL_deps, ge, N * sizeof(double)));
+    CK(deliver(L, dL_dhop, gh, static_cast<size_t>(N) * L->n_dirs * sizeof(double2)));
+    CK(deliver(L, dL_ddelta_in, gd, static_cast<size_t>(L->nd) * sizeof(double2)));
+    return finish(L);
   }
+  // real lattices: the real recursion; w_i = Re dL/dDelta_out,i (Delta is real here)
+  std::vector<double> w(N);
+  for (int i = 0; i < N; ++i) w[i] = hw[i].re;
   CK(L->adj_w.ensure(N * sizeof(double)));
   CK(cudaMemcpyAsync(L->adj_w.p, w.data(), N * sizeof(double), cudaMemcpyHostToDevice, L->stream));
   st = adjoint_run(L, T, M);
   if (st != CBDG_OK) return st;
   double *ge = L->adj_out.as<double>(), *gd = ge + N, *gh = ge + 2 * N;
   CK(deliver(L, dL_deps, ge, N * sizeof(double)));
-  CK(deliver(L, dL_ddelta_in, gd, N * sizeof(double)));
-  CK(deliver(L, dL_dhop, gh, static_cast<size_t>(N) * 4 * sizeof(double)));
+  // complex outputs with zero imaginary parts
+  CK(L->adj_outc.ensure(static_cast<size_t>(N) * 5 * sizeof(double2)));
+  double2 *ch = L->adj_outc.as<double2>(), *cd = ch + static_cast<size_t>(N) * 4;
+  CK(launch_real_to_complex(N * 4, gh, ch, L->stream));
+  CK(launch_real_to_complex(N, gd, cd, L->stream));
+  L->launches += 2;
+  CK(deliver(L, dL_ddelta_in, cd, N * sizeof(double2)));
+  CK(deliver(L, dL_dhop, ch, static_cast<size_t>(N) * 4 * sizeof(double2)));
   return finish(L);
 }
 
@@ -1756,6 +1936,35 @@ cbdg_status cbdg_set_hamiltonian(cbdg_lattice *L, const double *eps, const cbdg_
   if (hop)
     CK(cudaMemcpyAsync(L->hop.p, hh.data(), hh.size() * sizeof(double2), cudaMemcpyHostToDevice, L->stream));
   CK(cudaStreamSynchronize(L->stream));
+  return CBDG_OK;
+}
+
+cbdg_status cbdg_set_symmetry(cbdg_lattice *L, const int32_t *rep) {
+  if (!L) return fail(CBDG_ERR_INVALID_ARG, "lattice is NULL");
+  CK(cudaSetDevice(L->device));
+  L->drop_graph();  // the captured iteration launches the recursion over the old site list
+  if (!rep) {
+    L->sym_n = 0;
+    return CBDG_OK;
+  }
+  if (L->pairing != CBDG_ONSITE_U)
+    return fail(CBDG_ERR_UNSUPPORTED, "symmetry reduction needs on-site pairing (a bond fold reads both ends)");
+  std::vector<int32_t> h;
+  cudaError_t e = host_copy(rep, L->N, h);
+  if (e != cudaSuccess) return cuda_fail(e, "reading rep");
+  std::vector<int32_t> list;
+  for (int i = 0; i < L->N; ++i) {
+    if (h[i] < 0 || h[i] >= L->N) return fail(CBDG_ERR_INVALID_ARG, "rep[%d] = %d out of range", i, h[i]);
+    if (h[h[i]] != h[i]) return fail(CBDG_ERR_INVALID_ARG, "rep[rep[%d]] != rep[%d]", i, i);
+    if (h[i] == i) list.push_back(i);
+  }
+  CK(L->sym_rep.ensure(static_cast<size_t>(L->N) * sizeof(int32_t)));
+  CK(L->sym_list.ensure(list.size() * sizeof(int32_t)));
+  CK(cudaMemcpyAsync(L->sym_rep.p, h.data(), static_cast<size_t>(L->N) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                     L->stream));
+  CK(cudaMemcpyAsync(L->sym_list.p, list.data(), list.size() * sizeof(int32_t), cudaMemcpyHostToDevice, L->stream));
+  CK(cudaStreamSynchronize(L->stream));
+  L->sym_n = static_cast<int>(list.size());
   return CBDG_OK;
 }
 

@@ -273,6 +273,23 @@ __global__ void finalize_onsite_kernel(int ncols, const int32_t *sites, double U
   if (nout) nout[i] = 1.0 + acc_n[b];
 }
 
+// dst[k] = (src[k], 0)
+__global__ void real_to_complex_kernel(int n, const double *src, double2 *dst) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[k] = make_double2(src[k], 0.0);
+}
+
+// Symmetry reduction: every site takes Delta_out and n of its orbit's
+// representative (rep[rep[i]] == rep[i], so representatives are only read).
+__global__ void orbit_fill_kernel(int N, const int32_t *rep, double2 *dout, double *nout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int r = rep[i];
+  if (r == i) return;
+  if (dout) dout[i] = dout[r];
+  if (nout) nout[i] = nout[r];
+}
+
 // Delta <- Delta + mix (Delta_out - Delta); max |Delta_out - Delta| by atomicMax.
 __global__ void mix_kernel(int n, double mix, const double2 *dout, double2 *delta, double *scal) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -360,6 +377,18 @@ cudaError_t launch_finalize_onsite(int ncols, const int32_t *sites, double U, co
   if (ncols <= 0) return cudaSuccess;
   finalize_onsite_kernel<<<blocks(ncols, 256), 256, 0, s>>>(ncols, sites, U, U_site, acc_n, acc_d, dout,
                                                             nout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_real_to_complex(int n, const double *src, double2 *dst, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  real_to_complex_kernel<<<blocks(n, 256), 256, 0, s>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_orbit_fill(int N, const int32_t *rep, double2 *dout, double *nout, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  orbit_fill_kernel<<<blocks(N, 256), 256, 0, s>>>(N, rep, dout, nout);
   return cudaGetLastError();
 }
 

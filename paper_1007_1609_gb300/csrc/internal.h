@@ -44,7 +44,7 @@ struct StepArgs {
   int Lx, Ly;
   int ld;               // columns (a multiple of the slab width)
   int rows_per_cta;     // lattice rows per CTA along y
-  void *out = nullptr;  // real one-step kernel only: j_{n+1} goes here when set (prev is kept)
+  void *out = nullptr;  // one-step kernels: j_{n+1} goes here when set (prev is kept)
 };
 
 struct StepConfig {
@@ -53,6 +53,7 @@ struct StepConfig {
   int row_split;        // CTAs per column slab along y
   int threads;
   size_t smem;
+  int pstage = 1;       // real one-step kernel: 0 = parameters through the read-only cache (wide lattices)
 };
 
 // Storage row of the electron (part 0) or hole (part 1) component of site s.
@@ -183,6 +184,10 @@ cudaError_t launch_finalize_onsite(int ncols, const int32_t *sites, double U, co
                                    double *nout, cudaStream_t s);
 cudaError_t launch_mix(int n, double mix, const double2 *dout, double2 *delta, double *scal,
                        cudaStream_t s);
+// dst[k] = (src[k], 0), k < n.
+cudaError_t launch_real_to_complex(int n, const double *src, double2 *dst, cudaStream_t s);
+// dout[i], nout[i] <- dout[rep[i]], nout[rep[i]] for every non-representative i.
+cudaError_t launch_orbit_fill(int N, const int32_t *rep, double2 *dout, double *nout, cudaStream_t s);
 cudaError_t launch_ldos_eval(int n_sites, int M, int kernel, double lambda, const double *mu_ee,
                              const double *energies, int n_E, const double *scal, float *ldos,
                              cudaStream_t s);
@@ -239,6 +244,22 @@ cudaError_t launch_adjoint_final(int Lx, int Ly, int px, int py, int groups, con
 // N = 256, K = 8): `ctas` CTAs (one per SM) issue `mmas` MMAs each.
 cudaError_t launch_tf32_peak(int ctas, long long mmas, unsigned *flags, cudaStream_t s);
 double tf32_peak_flops_per_mma();
+
+// Adjoint of the map for general lattices (adjoint_cplx.cu): complex vectors,
+// nd = 4 or 8 hopping directions, bond = nearest-neighbour pairing.
+// Sums per site of the accumulation (part is [groups][N][2 * sums]).
+int adjoint_cplx_sums(int nd, int bond);
+// lam(h_*) += Cm * (source weight of g) for every column (see adjoint_cplx.cu).
+cudaError_t launch_adjoint_source_cplx(int precision, int Lx, int Ly, int px, int py, int ncols, int W,
+                                       const int32_t *sites, int pairing, const double2 *g, const double *cpl,
+                                       double coupling, double Cm, void *lam, cudaStream_t s);
+cudaError_t launch_adjoint_accumulate_cplx(int precision, int Lx, int Ly, int px, int py, int nd, int bond, int ld,
+                                           int W, int groups, const void *lam, const void *j, double f, double *part,
+                                           cudaStream_t s);
+// g_eps [N] real; g_hop [N * nd], g_delta [N] or [N * 4] complex (dL/dRe + i dL/dIm).
+cudaError_t launch_adjoint_final_cplx(int Lx, int Ly, int px, int py, int nd, int bond, int groups,
+                                      const double *part, const double *scal, double *g_eps, double2 *g_hop,
+                                      double2 *g_delta, cudaStream_t s);
 
 // Device address of the stand-alone contraction's error word (this device).
 cudaError_t contract_flag_address(unsigned **out);

@@ -128,7 +128,11 @@ __device__ __forceinline__ void set_comp(V &v, int j, S x) {
   reinterpret_cast<S *>(&v)[j] = x;
 }
 
-template <typename S, int W, int NT, int MAXX, int D>
+// PST: stage each lattice row's parameters with its j_n row (TMA, one ring
+// slot per row); without it (wide lattices, whose rings would not fit in
+// shared memory) the computed row's parameters are read through the
+// read-only cache, where the 32-byte records of a row stay L2-resident.
+template <typename S, int W, int NT, int MAXX, int D, bool PST = true>
 __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
   using V = typename Vec<S>::T;
   constexpr int VEC = Vec<S>::N;
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
   S *const dst = a.out ? static_cast<S *>(a.out) + slab : prev;  // j_{n+1}
   const S *par = static_cast<const S *>(a.params);
   const unsigned row_bytes = static_cast<unsigned>(rowel * sizeof(S));
-  const unsigned par_bytes = static_cast<unsigned>(pel * sizeof(S));
+  const unsigned par_bytes = PST ? static_cast<unsigned>(pel * sizeof(S)) : 0u;
   const unsigned long long kWaitLimitNs = a.wait_ns;
 
   if (t == 0) {
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
     const unsigned bar = smem_addr(&bars[k % JS]);
     mbar_expect_tx(bar, row_bytes + par_bytes + (with_old ? row_bytes : 0u) + (k == 0 ? a.stall_tx : 0u));
     bulk_load(smem_addr(sj + (k % JS) * rowel), cur + static_cast<size_t>(y) * rowel, row_bytes, bar);
-    bulk_load(smem_addr(sp + (k % JS) * pel), par + static_cast<size_t>(y) * pel, par_bytes, bar);
+    if (PST) bulk_load(smem_addr(sp + (k % JS) * pel), par + static_cast<size_t>(y) * pel, par_bytes, bar);
     if (with_old)
       bulk_load(smem_addr(so + (r % OS) * rowel), prev + static_cast<size_t>(y0 + r) * rowel,
                 row_bytes, bar);
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
       const S *rc = sj + ((i + 1) % JS) * rowel;  // y
       const S *rp = sj + ((i + 2) % JS) * rowel;  // y + 1
       const S *ro = so + (i % OS) * rowel;        // j_{n-1} of y
-      const S *pc = sp + ((i + 1) % JS) * pel;
+      const S *pc = PST ? sp + ((i + 1) % JS) * pel : par + static_cast<size_t>(y0 + i) * pel;
       S *out = dst + static_cast<size_t>(y0 + i) * rowel;
       const int off = q * VEC;
       const int hb = Lx * W;  // hole rows follow the electron rows
@@ -237,7 +241,9 @@ __global__ void __launch_bounds__(NT, 1) step_real_kernel(StepArgs a) {
           const V uo = *reinterpret_cast<const V *>(ro + x * W + off);
           const V vo = *reinterpret_cast<const V *>(ro + hb + x * W + off);
           const S *pp = pc + x * kParamStride;
-          const S e = pp[0], d = pp[1], t0 = pp[2], t1 = pp[3], t2 = pp[4], t3 = pp[5];
+          const S e = PST ? pp[0] : __ldg(pp + 0), d = PST ? pp[1] : __ldg(pp + 1);
+          const S t0 = PST ? pp[2] : __ldg(pp + 2), t1 = PST ? pp[3] : __ldg(pp + 3);
+          const S t2 = PST ? pp[4] : __ldg(pp + 4), t3 = PST ? pp[5] : __ldg(pp + 5);
           V un, vn;
 #pragma unroll
           for (int j = 0; j < VEC; ++j) {
@@ -299,6 +305,7 @@ constexpr int kThreads = 256;
 // Dynamic shared memory cap: the 227 KB per-CTA opt-in limit less room for
 // the kernel's static mbarriers.
 constexpr int kMaxDynSmem = 227 * 1024 - 1024;
+constexpr int kUnstagedDepth = 2;  // rows in flight of the unstaged (wide-lattice) variant
 
 template <typename S, int W, int D>
 size_t smem_bytes(int Lx) {
@@ -311,9 +318,20 @@ size_t smem_bytes(int Lx) {
   return std::max(ring, red);
 }
 
-template <typename S, int W, int MAXX, int D>
+template <typename S, int W>
+size_t smem_bytes_unstaged(int Lx) {
+  constexpr int D = kUnstagedDepth;
+  constexpr int QUADS = W / Vec<S>::N;
+  constexpr int XSLOTS = kThreads / QUADS;
+  const size_t rowel = static_cast<size_t>(2) * Lx * W;
+  const size_t ring = ((3 + D) * rowel + (2 + D) * rowel) * sizeof(S);
+  const size_t red = static_cast<size_t>(3) * XSLOTS * W * sizeof(double);
+  return std::max(ring, red);
+}
+
+template <typename S, int W, int MAXX, int D, bool PST = true>
 cudaError_t launch_one(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
-  auto k = step_real_kernel<S, W, kThreads, MAXX, D>;
+  auto k = step_real_kernel<S, W, kThreads, MAXX, D, PST>;
   static int attr_dev = -1;  // set once per instantiation and device
   int dev = 0;
   cudaGetDevice(&dev);
@@ -335,6 +353,13 @@ int xslots() {
 template <typename S, int W, int D>
 cudaError_t dispatch_maxx(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
   const int xsl = xslots<S, W>();
+  if (!cfg.pstage) {
+    // wide lattices only (the staged rings fit up to xsl sites)
+    if (a.Lx <= 2 * xsl) return launch_one<S, W, 2, kUnstagedDepth, false>(a, cfg, s);
+    if (a.Lx <= 4 * xsl) return launch_one<S, W, 4, kUnstagedDepth, false>(a, cfg, s);
+    if (a.Lx <= 8 * xsl) return launch_one<S, W, 8, kUnstagedDepth, false>(a, cfg, s);
+    return cudaErrorInvalidValue;
+  }
   if (a.Lx <= 1 * xsl) return launch_one<S, W, 1, D>(a, cfg, s);
   if (a.Lx <= 2 * xsl) return launch_one<S, W, 2, D>(a, cfg, s);
   if (a.Lx <= 4 * xsl) return launch_one<S, W, 4, D>(a, cfg, s);
@@ -344,6 +369,7 @@ cudaError_t dispatch_maxx(const StepArgs &a, const StepConfig &cfg, cudaStream_t
 
 template <typename S, int W>
 cudaError_t dispatch_depth(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
+  if (!cfg.pstage) return dispatch_maxx<S, W, kUnstagedDepth>(a, cfg, s);
   switch (cfg.depth) {
     case 1: return dispatch_maxx<S, W, 1>(a, cfg, s);
     case 2: return dispatch_maxx<S, W, 2>(a, cfg, s);
@@ -377,6 +403,18 @@ int max_lx(int W) {
   return 8 * kThreads / (W / Vec<S>::N);
 }
 
+template <typename S>
+size_t smem_unstaged_dispatch(int W, int Lx) {
+  constexpr int V = Vec<S>::N;
+  switch (W) {
+    case V: return smem_bytes_unstaged<S, V>(Lx);
+    case 2 * V: return smem_bytes_unstaged<S, 2 * V>(Lx);
+    case 4 * V: return smem_bytes_unstaged<S, 4 * V>(Lx);
+    case 8 * V: return smem_bytes_unstaged<S, 8 * V>(Lx);
+  }
+  return 0;
+}
+
 }  // namespace
 
 int slab_width_default(int precision) { return precision == 1 ? 16 : 4; }
@@ -395,6 +433,7 @@ bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_
     const size_t b = smem(w, d);
     return b != 0 && b <= kMaxDynSmem && ld % w == 0 && Lx <= lxmax(w);
   };
+  bool pstage = true;
   while (!fits(W, D)) {
     if (D > 1) {
       D -= 1;
@@ -402,9 +441,25 @@ bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_
       W /= 2;
       D = d0;
     } else {
-      return false;
+      pstage = false;
+      break;
     }
   }
+  auto smem_u = [&](int w) {
+    return precision == 1 ? smem_unstaged_dispatch<float>(w, Lx) : smem_unstaged_dispatch<double>(w, Lx);
+  };
+  if (!pstage) {
+    // wide lattices (two or more sites per thread): parameters through the
+    // read-only cache, smaller rings
+    W = want_w > 0 ? want_w : slab_width_default(precision);
+    D = kUnstagedDepth;
+    while (!(smem_u(W) != 0 && smem_u(W) <= kMaxDynSmem && ld % W == 0 && Lx <= lxmax(W) &&
+             Lx > kThreads / (W / vecn))) {
+      if (W > vecn) W /= 2;
+      else return false;
+    }
+  }
+  const size_t smem_now = pstage ? smem(W, D) : smem_u(W);
   const int slabs = ld / W;
   int split = want_split;
   if (split <= 0) {
@@ -415,7 +470,7 @@ bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_
     cudaGetDevice(&dev);
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = static_cast<int>((228 * 1024) / (smem(W, D) + 1024));
+    int per_sm = static_cast<int>((228 * 1024) / (smem_now + 1024));
     per_sm = std::max(1, std::min(per_sm, 2048 / kThreads));
     const int slots = sms * per_sm;
     split = 1;
@@ -427,7 +482,8 @@ bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_
   cfg->depth = D;
   cfg->row_split = (Ly + rpc - 1) / rpc;
   cfg->threads = kThreads;
-  cfg->smem = smem(W, D);
+  cfg->smem = smem_now;
+  cfg->pstage = pstage ? 1 : 0;
   return true;
 }
 

@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
   const size_t slab = static_cast<size_t>(blockIdx.x) * (static_cast<size_t>(2) * Lx * Ly * W * 2);
   const S *cur = static_cast<const S *>(a.cur) + slab;
   S *prev = static_cast<S *>(a.prev) + slab;
+  S *const dst = a.out ? static_cast<S *>(a.out) + slab : prev;  // j_{n+1} (in place unless out is set)
   const S *par = static_cast<const S *>(a.params);
   const unsigned row_bytes = static_cast<unsigned>(rowel * sizeof(S));
   const unsigned par_bytes = PSTAGE ? static_cast<unsigned>(pel * sizeof(S)) : 0u;
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
       const S *rp = sj + ((i + 2) % JS) * rowel;
       const S *ro = so + (i % OS) * rowel;
       const int y = y0 + i;
-      S *out = prev + static_cast<size_t>(y) * rowel;
+      S *out = dst + static_cast<size_t>(y) * rowel;
       const int hb = Lx * W * 2;  // hole rows follow the electron rows (scalars)
       const int off = q * VC * 2;
 #pragma unroll

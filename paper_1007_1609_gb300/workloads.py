@@ -176,15 +176,17 @@ def currents_dwave(L=128, M=512, flux_quanta=2.0, xi=3.0):
                     0.005, M, mix=0.5, tol=1e-6, max_iter=100)
 
 
-def sn_slab(Lx=64, L_S=300, L_N=20, M=2048, U=1.41, mu=-0.5, T=0.005, broadening=0.001):
+def sn_slab(Lx=500, L_S=300, L_N=20, M=2048, U=1.41, mu=-0.5, T=0.005, broadening=0.001):
     """Planar S/N system after the paper's first example: superconductor (U)
     for rows y < L_S, normal metal (U = 0) for the L_N rows above it, open
-    along y (the slab normal) and periodic along x (the plane, Lx sites).
-    t = 1, no disorder; U = 1.41 at mu = -0.5 gives a bulk gap of about
-    0.1 t (coherence length about 7 sites).  Initial Delta 0.1 in S, 0 in N.
-    LDOS at the N surface (row y = L_S + L_N - 1) with the Lorentz kernel,
-    energy broadening ``broadening`` (in units of t).  Per-site couplings in
-    extra['coupling_site']."""
+    along y (the slab normal) and periodic along x (the plane, Lx = 500
+    sites: the printed L_y = 500 a).  t = 1, no disorder; U = 1.41 at
+    mu = -0.5 gives a bulk gap of about 0.1 t (coherence length about 7
+    sites).  Initial Delta 0.1 in S, 0 in N.  LDOS at the N surface (row
+    y = L_S + L_N - 1) with the Lorentz kernel, energy broadening
+    ``broadening`` (in units of t).  Per-site couplings in
+    extra['coupling_site']; the plane's translations map every site to the
+    site of its row at x = 0 (extra['symmetry'], for cbdg_set_symmetry)."""
     Ly = L_S + L_N
     N = Lx * Ly
     y = np.arange(N) // Lx
@@ -195,7 +197,8 @@ def sn_slab(Lx=64, L_S=300, L_N=20, M=2048, U=1.41, mu=-0.5, T=0.005, broadening
                 mu=mu, hop=np.ascontiguousarray(square_hops(Lx, Ly, 1, 0), dtype=np.complex128),
                 pairing=ONSITE, coupling=U, delta0=d0, T=T, M=M, mix=0.5, tol=1e-6, max_iter=200,
                 extra={"coupling_site": U_site, "surface_sites": surface, "broadening": broadening,
-                       "energy_frac": np.linspace(-0.05, 0.05, 201)})
+                       "energy_frac": np.linspace(-0.05, 0.05, 201),
+                       "symmetry": (Lx * y).astype(np.int32)})
     return p
 
 

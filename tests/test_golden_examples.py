@@ -24,6 +24,12 @@ def test_sn_slab_matches_the_printed_example():
     assert p.extra["broadening"] == g["broadening"]
     assert p.M >= g["moments_at_least"] - 48   # 2048: the next power of two above 2000
     assert p.periodic_x == 1 and p.periodic_y == 0
+    assert p.Lx == g["plane_width"]           # the plane (periodic) is the printed L_y
+    rep = p.extra["symmetry"]
+    assert np.array_equal(rep, (np.arange(p.N) // p.Lx) * p.Lx)
+    # the translations are a symmetry of the workload: every array is constant along a row
+    for arr in (p.eps, p.extra["coupling_site"], p.delta0):
+        assert np.array_equal(arr, arr[rep])
 
 
 def test_sn_slab_bulk_gap_is_the_printed_one():

@@ -3,9 +3,10 @@
 Per-site U_i (zero on normal-metal sites) and per-bond V_{i,d} enter Eq. 19
 through the fold; the order parameter, the self-consistency loop and the
 map gradient are compared with the oracle (same coupling array), on small
-lattices in both precisions and on the S/N slab at full size (64 x 320,
-M = 2048) on sampled sites, with its surface LDOS under the Lorentz kernel
-of Eq. 16.  Tolerances as in the other parity tests: Delta 1e-10 (FP64) and
+lattices in both precisions and on the S/N slab at full size (the printed
+500-site plane x 320 layers, M = 2048, one start site per layer through the
+plane's translation symmetry) on sampled sites, with its surface LDOS under
+the Lorentz kernel of Eq. 16.  Tolerances as in the other parity tests: Delta 1e-10 (FP64) and
 1e-4 (FP32); gradients 1e-9 relative (FP64); LDOS 1e-5 of the absolute
 series (3xTF32 contraction)."""
 import numpy as np
@@ -85,19 +86,52 @@ def test_site_coupling_order_parameter(case, precision, resident):
     assert max_abs(d0, od0) < TOL[precision]
 
 
+@pytest.mark.parametrize("symmetric", [0, 1])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_sn_slab_small_scf(precision):
+def test_sn_slab_small_scf(precision, symmetric):
     """Five mixed self-consistency iterations of a small S/N slab (graph
-    replay from the third call) against the oracle's loop."""
+    replay from the third call) against the oracle's loop, with every site a
+    start vector or one per layer (cbdg_set_symmetry with the plane's
+    translations)."""
     p = wl.sn_slab(Lx=8, L_S=12, L_N=4, M=128, T=0.02)
     cpl = p.extra["coupling_site"]
     lat = gpu_lattice(p, precision, cpl)
+    if symmetric:
+        lat.set_symmetry(p.extra["symmetry"])
     for _ in range(5):
         lat.scf_step(p.T, p.M, p.mix)
     ref, _, _, _ = orc.scf(oracle_lattice(p, cpl), p.T, p.M, K, p.mix, 0.0, 5)
     assert max_abs(lat.delta, ref) < TOL[precision], max_abs(lat.delta, ref)
     y = np.arange(p.N) // p.Lx
     assert np.all(lat.delta[y >= 12] == 0.0)
+
+
+def test_symmetry_reduction_equals_every_site():
+    """One recursion per representative gives the same Delta_out and n as one
+    per site (FP64, to round-off of the column reductions), also after
+    switching back; invalid maps and bond pairing are rejected."""
+    p = wl.sn_slab(Lx=10, L_S=9, L_N=5, M=96, T=0.02)
+    cpl = p.extra["coupling_site"]
+    full = gpu_lattice(p, "fp64", cpl)
+    d_all, n_all = full.order_parameter(p.T, p.M)
+    sym = gpu_lattice(p, "fp64", cpl)
+    sym.set_symmetry(p.extra["symmetry"])
+    cbdg.cbdg_launch_count(sym.handle, reset=True)
+    d_sym, n_sym = sym.order_parameter(p.T, p.M)
+    assert max_abs(d_sym, d_all) < 1e-13 and max_abs(n_sym, n_all) < 1e-13
+    sym.set_symmetry(None)
+    d_back, _ = sym.order_parameter(p.T, p.M)
+    assert max_abs(d_back, d_all) < 1e-13
+    bad = p.extra["symmetry"].copy()
+    bad[3] = 5  # 5 is not its own representative
+    with pytest.raises(cbdg.CbdgError) as ei:
+        sym.set_symmetry(bad)
+    assert ei.value.status == cbdg.CBDG_ERR_INVALID_ARG
+    q = wl.random_dwave(4, 16, seed=2)
+    lq = cbdg.Lattice(q, precision="fp64")
+    with pytest.raises(cbdg.CbdgError) as ei:
+        lq.set_symmetry(np.zeros(q.N, dtype=np.int32))
+    assert ei.value.status == cbdg.CBDG_ERR_UNSUPPORTED
 
 
 def test_site_coupling_gradient_matches_oracle():
@@ -146,21 +180,24 @@ def test_sns_junction_small_currents():
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_sn_slab_full_size_sampled(precision):
-    """The S/N slab workload (64 x 320, U = 0 on the top 20 rows, M = 2048):
-    one self-consistency iteration on the GPU, Delta_out at sampled sites
-    (bulk S, interface, N) against the oracle, and the surface LDOS with the
-    Lorentz kernel (broadening 0.001 t) against the oracle's."""
+    """The S/N slab workload (the printed 500-site plane, 320 layers, U = 0
+    on the top 20 rows, M = 2048): Delta_out of one self-consistency map on
+    the GPU with one start site per layer (the plane's translations), at
+    sampled sites (bulk S, interface, N) against the oracle, and the surface
+    LDOS with the Lorentz kernel (broadening 0.001 t) against the oracle's."""
     p = wl.sn_slab()
     cpl = p.extra["coupling_site"]
     lat = gpu_lattice(p, precision, cpl)
+    lat.set_symmetry(p.extra["symmetry"])
     d, _ = lat.order_parameter(p.T, p.M)
     ol = oracle_lattice(p, cpl)
     a = orc.rescale(ol)
     assert lat.rescale == pytest.approx(a, rel=1e-14)
-    sample = np.array([5, 64 * 150 + 7, 64 * 299 + 3, 64 * 300 + 3, 64 * 319 + 63], dtype=np.int32)
+    L = p.Lx
+    sample = np.array([5, L * 150 + 7, L * 299 + 3, L * 300 + 3, L * 319 + L - 1], dtype=np.int32)
     od, _ = orc.order_parameter_sites(ol, a, p.T, p.M, K, sample)
     assert max_abs(d[sample], od) < TOL[precision], max_abs(d[sample], od)
-    assert np.all(d[64 * 300:] == 0.0)
+    assert np.all(d[L * 300:] == 0.0)
     if precision == "fp64":
         return
     lam = lat.lorentz_lambda(p.extra["broadening"], p.M)
