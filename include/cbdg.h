@@ -372,11 +372,16 @@ enum {
                                     3 where each thread holds one lattice site (Lx <= 256 /
                                     (W / 4)) and at slab width 16 up to Lx = 128 (the lean
                                     pass), else 2.  Shapes the multi-step kernel does not
-                                    serve run one step per pass: periodic y, FP64, complex
-                                    fields, slab widths other than 8 and 16, Lx above 64 at
-                                    slab width 16 (128 for K = 2, and for K = 3 at pipeline
-                                    depth 1, the lean pass), above 128 at slab width 8 (256
-                                    for K = 2), and rings that do not fit in shared memory */
+                                    serve run one step per pass: periodic y, FP64, slab
+                                    widths other than 8 and 16, Lx above 64 at slab width
+                                    16 (128 for K = 2, and for K = 3 at pipeline depth 1,
+                                    the lean pass), above 128 at slab width 8 (256 for
+                                    K = 2), and rings that do not fit in shared memory.
+                                    General lattices (complex FP32 vectors: Peierls
+                                    hoppings, t', bond pairing; periodic or open): K >= 2
+                                    selects the two-step pass (slab width 2, Lx <= 256,
+                                    Ly >= 3, the default tile); 0 (default) keeps one step
+                                    per pass there, which measured faster */
   CBDG_OPT_GRAPH = 13,           /* 1 (default): cbdg_scf_step captures its iteration as a
                                     CUDA graph on the second call with the same (T, M, mix)
                                     and replays it afterwards (not while profiling,

@@ -421,6 +421,20 @@ cbdg_status autotune(cbdg_lattice *L, int mode, int n_sites, TuneVal *out) {
 // moments into per-column accumulators; optionally writes the moments
 // ([n_sites][M] and [n_sites][M][stride]).  With finalize, Delta_out and n
 // go to L->dout / L->nout; then the site list must be 0..N-1 in order
+// Whether the general (complex) recursion runs two steps per pass over the
+// vectors (step_cplx_multi.cu): only on request (CBDG_OPT_TEMPORAL_STEPS >= 2),
+// for FP32 vectors at the default tile; the pass takes slab width 2.  Not the
+// default: the general stencil keeps the one-step kernel near its HBM bound
+// with most issue slots busy, and the fused pass measured slower (latency-
+// bound at 8 warps per SM).
+bool use_cplx_multi(const cbdg_lattice *L) {
+  if (L->precision != CBDG_FP32_MIXED || L->slab_w != 0 || L->temporal < 2 || L->autotune ||
+      L->row_split != 0 || L->depth != 0)
+    return false;
+  StepConfig tmp;
+  return plan_step_cplx_multi(L->precision, L->Lx, L->Ly, 2, &tmp);
+}
+
 // (bond pairing pairs the accumulators of neighbouring start sites).
 cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int M,
                         double *mom_ee, double2 *mom_eh, int mom_stride, bool finalize) {
@@ -430,6 +444,8 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
   const int Wdef = mode == kReal ? slab_width_default(L->precision) : slab_width_default_cplx(L->precision);
   int W = L->slab_w > 0 ? static_cast<int>(L->slab_w) : Wdef;
   int want_split = static_cast<int>(L->row_split), want_depth = static_cast<int>(L->depth);
+  const bool cplx_multi = mode != kReal && use_cplx_multi(L);
+  if (cplx_multi) W = 2;
   // small real lattices: the whole recursion in shared memory, one launch
   const int Wres = (mode == kReal && L->resident && L->slab_w == 0 && L->row_split == 0 && L->depth == 0 &&
                     !L->autotune && !L->stall)
@@ -525,6 +541,9 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
           plan_step_multi(L->Lx, L->Ly, ld, cfg.slab_w, static_cast<int>(want_k), tuned_dm ? tuned_dm : want_depth,
                           &mcfg, &Kt)))
       Kt = 1;
+    if (mode != kReal) {
+      Kt = cplx_multi && plan_step_cplx_multi(L->precision, L->Lx, L->Ly, ld, &mcfg) ? 2 : 1;
+    }
     L->last_temporal = Kt;
     const int nsum = mode == kReal ? 3 : 4;
     const size_t vbytes = rows * ld * es;
@@ -596,6 +615,31 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     for (int n = 1; n <= steps;) {
       a.cur = cur;
       a.prev = prev;
+      if (mode != kReal && Kt == 2 && steps - n + 1 >= 2) {
+        // steps n, n+1 in one pass: j_{n+1} into prev, j_{n+2} into cur (no swap)
+        a.rows_per_cta = L->Ly;
+        if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx], L->stream));
+        CK(launch_step_cplx_multi(L->n_dirs == 8, mode == kDirect, a, mcfg, L->stream));
+        if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx + 1], L->stream));
+        if (mode == kCplx) {
+          for (int lv = 0; lv < 2; ++lv)
+            CK(launch_fold_cplx(n + lv, M, ncols, ld, 1, L->partials.as<double>() + static_cast<size_t>(lv) * 4 * ld,
+                                L->C.as<double>(), L->mu1.as<double>(), L->dA.as<double2>(), L->acc_n.as<double>(),
+                                L->acc_d.as<double2>(), mee, meh, mom_stride, L->flags.as<unsigned int>(), tol,
+                                L->stream));
+        } else {
+          CK(launch_gather(L->precision, n + 1, M, L->Lx, L->Ly, L->px, L->py, ncols, cfg.slab_w, sites + c0, prev,
+                           L->C.as<double>(), accn, accb, mee, meh, L->flags.as<unsigned int>(), tol, L->stream));
+          CK(launch_gather(L->precision, n + 2, M, L->Lx, L->Ly, L->px, L->py, ncols, cfg.slab_w, sites + c0, cur,
+                           L->C.as<double>(), accn, accb, mee, meh, L->flags.as<unsigned int>(), tol, L->stream));
+        }
+        L->launches += 3;
+        a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+        launch_bytes.push_back(4.0 * static_cast<double>(vbytes));
+        ++launch_idx;
+        n += 2;
+        continue;
+      }
       if (Kt >= 2 && steps - n + 1 >= Kt) {
         // steps n .. n+Kt-1 in one pass; (prev, cur) end as (j_{n+Kt-1}, j_{n+Kt})
         a.rows_per_cta = L->Ly;
@@ -710,7 +754,8 @@ cbdg_status run_targets(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
   const int Wdef = slab_width_default_cplx(L->precision);
   const bool w_ok = L->precision == CBDG_FP32_MIXED ? (L->slab_w == 2 || L->slab_w == 4 || L->slab_w == 8)
                                                      : (L->slab_w == 1 || L->slab_w == 2 || L->slab_w == 4);
-  const int W = w_ok ? static_cast<int>(L->slab_w) : Wdef;
+  const bool cplx_multi = !w_ok && use_cplx_multi(L);
+  const int W = w_ok ? static_cast<int>(L->slab_w) : (cplx_multi ? 2 : Wdef);
   size_t cap;
   if (L->ws_mb > 0) {
     cap = static_cast<size_t>(L->ws_mb) << 20;
@@ -733,11 +778,13 @@ cbdg_status run_targets(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
                         static_cast<int>(L->depth), &cfg))
       return fail(CBDG_ERR_UNSUPPORTED, "no recursion kernel fits Lx=%d with %d columns", L->Lx, ld);
     L->last_cfg = cfg;
-    L->last_temporal = 1;
+    StepConfig mcfg;
+    const bool two = cplx_multi && plan_step_cplx_multi(L->precision, L->Lx, L->Ly, ld, &mcfg);
+    L->last_temporal = two ? 2 : 1;
     const size_t vbytes = rows * ld * es;
     CK(L->vec0.ensure(vbytes));
     CK(L->vec1.ensure(vbytes));
-    CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 4 * ld * sizeof(double)));
+    CK(L->partials.ensure(static_cast<size_t>(std::max(cfg.row_split, 2)) * 4 * ld * sizeof(double)));
     CK(L->mu1.ensure(ld * sizeof(double)));
     CK(L->dA.ensure(ld * sizeof(double2)));
     CK(L->acc_n.ensure(ld * sizeof(double)));
@@ -778,28 +825,50 @@ cbdg_status run_targets(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
         L->events.push_back(ev);
       }
     }
-    // step n turns (j_{n-1}, j_n) into j_{n+1}, written over j_{n-1}
-    for (int n = 1; n + 1 < M; ++n) {
+    // step n turns (j_{n-1}, j_n) into j_{n+1}, written over j_{n-1}; the
+    // two-step pass turns them into (j_{n+1}, j_{n+2}) in place
+    std::vector<double> launch_bytes;
+    int launch_idx = 0;
+    for (int n = 1; n + 1 < M;) {
       a.cur = cur;
       a.prev = prev;
-      if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1)], L->stream));
+      if (two && n + 2 < M) {
+        a.rows_per_cta = L->Ly;
+        if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx], L->stream));
+        CK(launch_step_cplx_multi(L->n_dirs == 8, 1, a, mcfg, L->stream));
+        if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx + 1], L->stream));
+        for (int lv = 0; lv < 2; ++lv)
+          CK(launch_target_gather(L->precision, n + 1 + lv, M, L->Lx, L->Ly, L->px, L->py, ncols, W, sites + c0, n_t,
+                                  targets, lv == 0 ? prev : cur, L->C.as<double>(), acc_c, ae_c, ah_c,
+                                  L->flags.as<unsigned int>(), tol, L->stream));
+        L->launches += 3;
+        a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+        launch_bytes.push_back(4.0 * static_cast<double>(vbytes));
+        ++launch_idx;
+        n += 2;
+        continue;
+      }
+      if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx], L->stream));
       CK(launch_step_cplx(L->precision, L->n_dirs == 8, 1, a, cfg, L->stream));
-      if (L->profile) CK(cudaEventRecord(L->events[2 * (n - 1) + 1], L->stream));
+      if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx + 1], L->stream));
       CK(launch_target_gather(L->precision, n + 1, M, L->Lx, L->Ly, L->px, L->py, ncols, W, sites + c0, n_t,
                               targets, prev, L->C.as<double>(), acc_c, ae_c, ah_c, L->flags.as<unsigned int>(),
                               tol, L->stream));
       L->launches += 2;
+      launch_bytes.push_back(3.0 * static_cast<double>(vbytes));
+      ++launch_idx;
       std::swap(cur, prev);
+      ++n;
     }
-    if (L->profile && steps > 0) {
+    if (L->profile && launch_idx > 0) {
       CK(cudaStreamSynchronize(L->stream));
-      for (int k = 0; k < steps; ++k) {
+      for (int k = 0; k < launch_idx; ++k) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, L->events[2 * k], L->events[2 * k + 1]));
         L->prof_ms += ms;
-        L->prof_bytes += 3.0 * static_cast<double>(vbytes);
+        L->prof_bytes += launch_bytes[k];
       }
-      L->prof_launches += steps;
+      L->prof_launches += launch_idx;
     }
   }
   return CBDG_OK;

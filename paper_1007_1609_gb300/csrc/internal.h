@@ -118,6 +118,12 @@ cudaError_t launch_step_cplx(int precision, int nnn, int bond, const StepArgs &a
                              const StepConfig &cfg, cudaStream_t s);
 bool plan_step_cplx(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
                     int want_depth, StepConfig *cfg);
+// Two steps per pass over the vectors for the general lattice (FP32 complex,
+// step_cplx_multi.cu): j_{n+1} into prev, j_{n+2} into cur, both in place;
+// with on-site pairing the column sums of both steps in partials [2][4][ld].
+// Slab width 2, one CTA per slab; returns false when the shape does not fit.
+bool plan_step_cplx_multi(int precision, int Lx, int Ly, int ld, StepConfig *cfg);
+cudaError_t launch_step_cplx_multi(int nnn, int bond, const StepArgs &a, const StepConfig &cfg, cudaStream_t s);
 int slab_width_default_cplx(int precision);
 cudaError_t launch_params_cplx(int precision, int N, int Lx, int n_dirs, int pairing, const double *eps,
                                double mu, const double2 *hop, const double2 *delta,

@@ -29,10 +29,12 @@
 #include <algorithm>
 #include <cmath>
 
-#include "internal.h"
+#include "cplx_stencil.cuh"
 
 namespace cbdg {
 namespace {
+
+using namespace cx;
 
 template <typename S>
 struct CVec;
@@ -105,76 +107,6 @@ struct Acc<float> {
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
-
-template <typename S>
-struct Cx {
-  S re, im;
-};
-template <typename S>
-__device__ __forceinline__ Cx<S> cmul(Cx<S> a, Cx<S> b) {
-  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
-}
-template <typename S>
-__device__ __forceinline__ Cx<S> cmulc(Cx<S> a, Cx<S> b) {  // conj(a) * b
-  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
-}
-template <typename S>
-__device__ __forceinline__ Cx<S> cadd(Cx<S> a, Cx<S> b) {
-  return {a.re + b.re, a.im + b.im};
-}
-template <typename S>
-__device__ __forceinline__ Cx<S> csub(Cx<S> a, Cx<S> b) {
-  return {a.re - b.re, a.im - b.im};
-}
-
-__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
-// acc + a * b and acc + conj(a) * b, four FMAs each
-template <typename S>
-__device__ __forceinline__ Cx<S> cmac(Cx<S> acc, Cx<S> a, Cx<S> b) {
-  return {fma_rn(a.re, b.re, fma_rn(-a.im, b.im, acc.re)), fma_rn(a.re, b.im, fma_rn(a.im, b.re, acc.im))};
-}
-template <typename S>
-__device__ __forceinline__ Cx<S> cmacc(Cx<S> acc, Cx<S> a, Cx<S> b) {
-  return {fma_rn(a.re, b.re, fma_rn(a.im, b.im, acc.re)), fma_rn(a.re, b.im, fma_rn(-a.im, b.re, acc.im))};
-}
-template <typename S>
-__device__ __forceinline__ Cx<S> cneg(Cx<S> a) {
-  return {-a.re, -a.im};
-}
-
-template <typename V, typename S>
-__device__ __forceinline__ Cx<S> cget(const V &v, int j) {
-  const S *p = reinterpret_cast<const S *>(&v);
-  return {p[2 * j], p[2 * j + 1]};
-}
-template <typename V, typename S>
-__device__ __forceinline__ void cset(V &v, int j, Cx<S> z) {
-  S *p = reinterpret_cast<S *>(&v);
-  p[2 * j] = z.re;
-  p[2 * j + 1] = z.im;
-}
-
-template <typename S>
-struct Pair;
-template <>
-struct Pair<float> {
-  using T = float2;
-};
-template <>
-struct Pair<double> {
-  using T = double2;
-};
-// Complex field k of a site's parameters, one 8- or 16-byte load; p points at
-// field 0 of the site inside its lattice row, fields are 2 Lx scalars apart
-// (see internal.h).
-template <typename S, bool LDG>
-__device__ __forceinline__ Cx<S> pcx(const S *p, int k, int Lx) {
-  using P = typename Pair<S>::T;
-  const P *q = reinterpret_cast<const P *>(p + static_cast<size_t>(k) * 2 * Lx);
-  const P v = LDG ? __ldg(q) : *q;
-  return {v.x, v.y};
-}
 
 template <typename S, int W, int NT, int MAXX, int D, bool NNN, bool BOND, bool SUMS>
 __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
@@ -266,74 +198,13 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
         if (x < Lx) {
           const int xl = (x == 0) ? Lx - 1 : x - 1;
           const int xr = (x == Lx - 1) ? 0 : x + 1;
-          auto ld = [&](const S *row, int xx, int part) {
-            return *reinterpret_cast<const V *>(row + part * hb + xx * W * 2 + off);
-          };
           // parameter rows y (own, left neighbour) and y - 1 (lower neighbours)
           const S *py0 = PSTAGE ? sp + ((i + 1) % JS) * pel : par + static_cast<size_t>(y) * pel;
           const S *py1 = PSTAGE ? sp + (i % JS) * pel
                                 : par + static_cast<size_t>(y == 0 ? Ly - 1 : y - 1) * pel;
-          const S *pp = py0 + 2 * x;
-          const S e = pcx<S, !PSTAGE>(pp, kCpE, Lx).re;
-          const Cx<S> dl = pcx<S, !PSTAGE>(pp, kCpDelta, Lx);
-          auto conj_ = [](Cx<S> z) { return Cx<S>{z.re, -z.im}; };
-          // hopping of direction dd: forward from this site, backward from the neighbour
-          auto hop_of = [&](int dd) -> Cx<S> {
-            switch (dd) {
-              case 0: return pcx<S, !PSTAGE>(pp, kCpHop + 0, Lx);
-              case 1: return conj_(pcx<S, !PSTAGE>(py0 + 2 * xl, kCpHop + 0, Lx));
-              case 2: return pcx<S, !PSTAGE>(pp, kCpHop + 1, Lx);
-              case 3: return conj_(pcx<S, !PSTAGE>(py1 + 2 * x, kCpHop + 1, Lx));
-              case 4: return pcx<S, !PSTAGE>(pp, kCpHop + 2, Lx);
-              case 5: return conj_(pcx<S, !PSTAGE>(py1 + 2 * xl, kCpHop + 2, Lx));
-              case 6: return conj_(pcx<S, !PSTAGE>(py1 + 2 * xr, kCpHop + 3, Lx));
-              default: return pcx<S, !PSTAGE>(pp, kCpHop + 3, Lx);
-            }
-          };
-          auto bond_of = [&](int dd) -> Cx<S> {
-            switch (dd) {
-              case 0: return pcx<S, !PSTAGE>(pp, kCpBond + 0, Lx);
-              case 1: return pcx<S, !PSTAGE>(py0 + 2 * xl, kCpBond + 0, Lx);
-              case 2: return pcx<S, !PSTAGE>(pp, kCpBond + 1, Lx);
-              default: return pcx<S, !PSTAGE>(py1 + 2 * x, kCpBond + 1, Lx);
-            }
-          };
-          // neighbour rows/columns per direction 0:+x 1:-x 2:+y 3:-y 4:+x+y 5:-x-y 6:+x-y 7:-x+y
-          const S *nrow[8] = {rc, rc, rp, rm, rp, rm, rm, rp};
-          const int ncol[8] = {xr, xl, x, x, xr, xl, xr, xl};
-          const V u = ld(rc, x, 0), v = ld(rc, x, 1);
-          const V uo = ld(ro, x, 0), vo = ld(ro, x, 1);
-          V un, vn;
-          // start from -j_{n-1} and the on-site terms:
-          //   u' = e u + D v - u_old,  v' = conj(D) u - e v - v_old
-#pragma unroll
-          for (int j = 0; j < VC; ++j) {
-            const Cx<S> uj = cget<V, S>(u, j), vj = cget<V, S>(v, j);
-            const Cx<S> uoj = cget<V, S>(uo, j), voj = cget<V, S>(vo, j);
-            const Cx<S> hu = cmac(Cx<S>{fma_rn(e, uj.re, -uoj.re), fma_rn(e, uj.im, -uoj.im)}, dl, vj);
-            const Cx<S> hv = cmacc(Cx<S>{fma_rn(-e, vj.re, -voj.re), fma_rn(-e, vj.im, -voj.im)}, dl, uj);
-            cset<V, S>(un, j, hu);
-            cset<V, S>(vn, j, hv);
-          }
-#pragma unroll
-          for (int dd = 0; dd < (NNN ? 8 : 4); ++dd) {
-            const V ud = ld(nrow[dd], ncol[dd], 0), vd = ld(nrow[dd], ncol[dd], 1);
-            const Cx<S> td = hop_of(dd), ntd = cneg(td);
-            const Cx<S> bd = (BOND && dd < 4) ? bond_of(dd) : Cx<S>{0, 0};
-#pragma unroll
-            for (int j = 0; j < VC; ++j) {
-              Cx<S> hu = cget<V, S>(un, j), hv = cget<V, S>(vn, j);
-              // u' -= t_d u_d, v' += conj(t_d) v_d; bond pairing: u' += B_d v_d, v' += conj(B_d) u_d
-              hu = cmac(hu, ntd, cget<V, S>(ud, j));
-              hv = cmacc(hv, td, cget<V, S>(vd, j));
-              if (BOND && dd < 4) {
-                hu = cmac(hu, bd, cget<V, S>(vd, j));
-                hv = cmacc(hv, bd, cget<V, S>(ud, j));
-              }
-              cset<V, S>(un, j, hu);
-              cset<V, S>(vn, j, hv);
-            }
-          }
+          V u, v, un, vn;
+          cx::site_step<S, V, VC, W, NNN, BOND, !PSTAGE>(rm, rc, rp, ro, py0, py1, x, xl, xr, off, hb, Lx, u, v, un,
+                                                          vn);
 #pragma unroll
           for (int j = 0; j < VC; ++j) {
             const Cx<S> unj = cget<V, S>(un, j);
