@@ -91,6 +91,9 @@ cudaError_t launch_step_real(int precision, const StepArgs &a, const StepConfig 
 bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
                     int want_depth, StepConfig *cfg);
 int slab_width_default(int precision);
+// Lattice-row split of the one-step kernels: CTAs per column slab, chosen
+// from the SM count and how many CTAs of `smem` bytes fit on an SM.
+int choose_row_split(int slabs, int Ly, size_t smem, int threads);
 
 // K recursion steps per pass (temporal blocking) for real on-site FP32
 // lattices with open y edges; one CTA per slab (row split 1).  Partial sums

@@ -268,11 +268,16 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
   }
   const int G = Ly + K - 1;
   bool stop = false;
-  for (int g0 = 0; g0 < G && !stop; g0 += 3) {
+  // Three wavefronts g0 .. g0 + 2 (window slots are compile-time per phase).
+  // INNER: every level's row r and the rows r - 1, r + 1 it reads lie inside
+  // [0, Ly), so no edge test and no zero fill; FULL: every x slot of every
+  // thread holds a lattice site (Lx = MAXX * XSLOTS), so no x test either.
+  auto three_waves = [&](const int g0, auto inner_c, auto full_c) {
+    constexpr bool INNER = decltype(inner_c)::value, FULL = decltype(full_c)::value;
 #pragma unroll
     for (int ph = 0; ph < 3; ++ph) {
       const int g = g0 + ph;
-      if (stop || g >= G) break;
+      if (stop || (!INNER && g >= G)) break;
       // rows up to g + 1 must have landed (LEAN: parameter rows up to g)
       for (; ok && waited <= min(g + 1, Ly - 1); ++waited)
         if (!mbar_wait(bar_of(waited), par_of(waited), wait_ns))
@@ -307,7 +312,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
         for (int k = 0; k < MAXX; ++k) {
           const int x = xs + k * XSLOTS;
           float4 nu = zero4(), nv = zero4();
-          if (x < Lx && g + 1 < Ly) {
+          if ((FULL || x < Lx) && (INNER || g + 1 < Ly)) {
             const float *src = sq + ((g + 1) % RQ) * rowel;
             nu = lds4(src + x * W + off);
             nv = lds4(src + hb + x * W + off);
@@ -320,7 +325,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
       for (int lv = 1; lv <= K; ++lv) {
         const int r = g - lv + 1;
         const int sm = (ph - lv + 6) % 3, sc = (ph - lv + 7) % 3, su = (ph - lv + 8) % 3;
-        if (r >= 0 && r < Ly) {
+        if (INNER || (r >= 0 && r < Ly)) {
           const float *nb = lv == 1 ? sq + (r % RQ) * rowel : sl + ((lv - 2) * 2 + (r & 1)) * rowel;
           const float *po = sp + (r % RP) * rowel;
           const float *pc = LEAN ? sa + ((base + r) % (AR > 0 ? AR : 1)) * pel : sa + (r % (AS > 0 ? AS : 1)) * pel;
@@ -328,7 +333,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
 #pragma unroll
           for (int k = 0; k < MAXX; ++k) {
             const int x = xs + k * XSLOTS;
-            if (x < Lx) {
+            if (FULL || x < Lx) {
               const int xl = (x == 0) ? Lx - 1 : x - 1;
               const int xr = (x == Lx - 1) ? 0 : x + 1;
               float4 u, v, uu, vu, ud, vd;
@@ -337,16 +342,24 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
                 const float *rc = sq + (r % RQ) * rowel;
                 u = lds4(rc + x * W + off);
                 v = lds4(rc + hb + x * W + off);
-                uu = vu = ud = vd = zero4();
-                if (r + 1 < Ly) {
-                  const float *rp = sq + ((r + 1) % RQ) * rowel;
+                if (INNER) {
+                  const float *rp = sq + ((r + 1) % RQ) * rowel, *rm = sq + ((r - 1) % RQ) * rowel;
                   uu = lds4(rp + x * W + off);
                   vu = lds4(rp + hb + x * W + off);
-                }
-                if (r >= 1) {
-                  const float *rm = sq + ((r - 1) % RQ) * rowel;
                   ud = lds4(rm + x * W + off);
                   vd = lds4(rm + hb + x * W + off);
+                } else {
+                  uu = vu = ud = vd = zero4();
+                  if (r + 1 < Ly) {
+                    const float *rp = sq + ((r + 1) % RQ) * rowel;
+                    uu = lds4(rp + x * W + off);
+                    vu = lds4(rp + hb + x * W + off);
+                  }
+                  if (r >= 1) {
+                    const float *rm = sq + ((r - 1) % RQ) * rowel;
+                    ud = lds4(rm + x * W + off);
+                    vd = lds4(rm + hb + x * W + off);
+                  }
                 }
               } else {
                 u = wu[lv - 1][sc][k], v = wv[lv - 1][sc][k];
@@ -402,7 +415,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
               }
             }
           }
-        } else if (lv < K) {
+        } else if (!INNER && lv < K) {
           // rows outside [0, Ly) are zero (open edges)
 #pragma unroll
           for (int k = 0; k < MAXX; ++k) {
@@ -411,6 +424,20 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
           }
         }
       }
+    }
+  };
+  const bool xfull = Lx == MAXX * XSLOTS;
+  for (int g0 = 0; g0 < G && !stop; g0 += 3) {
+    // wavefronts K .. Ly - 2: level t's row g - t + 1 and its neighbours
+    // g - t .. g - t + 2 lie inside the lattice, and so does row g + 1 (K = 4
+    // keeps the one checked copy: a second copy of its body spills)
+    if (K <= 3 && g0 >= K && g0 + 2 <= Ly - 2) {
+      if constexpr (K <= 3) {
+        if (xfull) three_waves(g0, std::true_type{}, std::true_type{});
+        else three_waves(g0, std::true_type{}, std::false_type{});
+      }
+    } else {
+      three_waves(g0, std::false_type{}, std::false_type{});
     }
     if constexpr (kFlush) {
       // every lane arrives here (stop and G are uniform over the CTA); the

@@ -419,6 +419,44 @@ size_t smem_unstaged_dispatch(int W, int Lx) {
 
 int slab_width_default(int precision) { return precision == 1 ? 16 : 4; }
 
+int choose_row_split(int slabs, int Ly, size_t smem, int threads) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = static_cast<int>((228 * 1024) / (smem + 1024));
+  per_sm = std::max(1, std::min(per_sm, 2048 / threads));
+  const int slots = sms * per_sm;
+  if (per_sm > 1) {
+    // several CTAs per SM share its bandwidth: split only to reach two waves
+    int split = 1;
+    while (slabs * split < 2 * slots && (Ly + 2 * split - 1) / (2 * split) >= 8) split *= 2;
+    return split;
+  }
+  // One CTA per SM: the CTAs run in ceil(slabs * split / slots) waves, each
+  // as long as one CTA's rows -- three vector streams per row, plus two halo
+  // rows of j_n and a pipeline fill of a few rows -- so take the split with
+  // the least waves x (3 rows + 8), at least 8 rows per CTA, if it beats one
+  // CTA per slab by 5% (the model is coarse; splitting re-reads halos).
+  auto cost = [&](int n, int rpc) {
+    return ((static_cast<long long>(slabs) * n + slots - 1) / slots) * (3LL * rpc + 8);
+  };
+  const long long whole = cost(1, Ly);
+  int best = 1;
+  long long best_cost = whole;
+  for (int split = 2; split <= Ly; ++split) {
+    const int rpc = (Ly + split - 1) / split;
+    if (rpc < 8) break;
+    const int n = (Ly + rpc - 1) / rpc;
+    const long long c = cost(n, rpc);
+    if (c < best_cost) {
+      best_cost = c;
+      best = n;
+    }
+  }
+  return 20 * best_cost <= 19 * whole ? best : 1;
+}
+
 bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_split,
                     int want_depth, StepConfig *cfg) {
   const int vecn = precision == 1 ? 4 : 2;
@@ -462,20 +500,7 @@ bool plan_step_real(int precision, int Lx, int Ly, int ld, int want_w, int want_
   const size_t smem_now = pstage ? smem(W, D) : smem_u(W);
   const int slabs = ld / W;
   int split = want_split;
-  if (split <= 0) {
-    // One CTA per slab marches over all rows (no halo re-reads) unless that
-    // leaves the GPU with fewer than two waves of CTAs; then split rows, but
-    // keep at least 8 rows per CTA.
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = static_cast<int>((228 * 1024) / (smem_now + 1024));
-    per_sm = std::max(1, std::min(per_sm, 2048 / kThreads));
-    const int slots = sms * per_sm;
-    split = 1;
-    while (slabs * split < 2 * slots && (Ly + 2 * split - 1) / (2 * split) >= 8) split *= 2;
-  }
+  if (split <= 0) split = choose_row_split(slabs, Ly, smem_now, kThreads);
   split = std::max(1, std::min(split, Ly));
   const int rpc = (Ly + split - 1) / split;
   cfg->slab_w = W;

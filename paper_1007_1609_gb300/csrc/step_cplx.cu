@@ -368,17 +368,7 @@ bool plan_step_cplx(int precision, int Lx, int Ly, int ld, int want_w, int want_
   }
   const int slabs = ld / W;
   int split = want_split;
-  if (split <= 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = static_cast<int>((228 * 1024) / (smem(W, D) + 1024));
-    per_sm = std::max(1, std::min(per_sm, 2048 / kThreads));
-    const int slots = sms * per_sm;
-    split = 1;
-    while (slabs * split < 2 * slots && (Ly + 2 * split - 1) / (2 * split) >= 8) split *= 2;
-  }
+  if (split <= 0) split = choose_row_split(slabs, Ly, smem(W, D), kThreads);
   split = std::max(1, std::min(split, Ly));
   const int rpc = (Ly + split - 1) / split;
   cfg->slab_w = W;

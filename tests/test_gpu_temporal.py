@@ -91,16 +91,19 @@ def test_option_range():
     assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_OPT_TEMPORAL_STEPS) == 3
 
 
-@pytest.mark.parametrize("case", [(65, 7, 40), (100, 23, 33), (128, 2, 64), (128, 31, 129), (97, 64, 24)])
-def test_lean_three_steps_match_oracle(case):
-    """Three steps per pass at two sites per thread (64 < Lx <= 128, slab 16):
-    level 0 read from its shared-memory ring, parameters in a ring of their
-    own, FP32 column sums flushed into FP64 every few rows.  Moments vs the
-    oracle, and vs one step per pass."""
+@pytest.mark.parametrize("slab", [16, 8])
+@pytest.mark.parametrize("case", [(65, 7, 40), (100, 23, 33), (128, 2, 64), (128, 31, 129), (97, 64, 24),
+                                  (64, 19, 37), (33, 40, 26)])
+def test_lean_three_steps_match_oracle(case, slab):
+    """Three steps per pass: at slab 16 and 64 < Lx <= 128 the lean pass
+    (two sites per thread, level 0 read from its shared-memory ring,
+    parameters in a ring of their own, FP32 column sums flushed into FP64
+    every few rows), otherwise one site per thread with every level in
+    register windows.  Moments vs the oracle, and vs one step per pass."""
     Lx, Ly, M = case
     p = rect(Lx, Ly, M, seed=Lx * 7 + Ly, periodic=0)
     sites = np.arange(p.N, dtype=np.int32)[::-1].copy()
-    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3, slab_width=slab)
     (ee, eh), launches = recursion_launches(lat, sites, M)
     n_steps = (M + 1) // 2 - 1
     assert launches == n_steps // 3 + n_steps % 3
@@ -112,13 +115,15 @@ def test_lean_three_steps_match_oracle(case):
     assert max_abs(ee, one[0]) < 5e-6 and max_abs(eh, one[1]) < 5e-6
 
 
-def test_lost_copy_times_out_in_the_lean_pass():
-    """The bounded waits of the lean three-step pass: a copy that never
-    arrives makes the call report CBDG_ERR_CUDA, and the lattice then
-    computes correct moments."""
-    p = rect(100, 12, 40, seed=52, periodic=0)
+@pytest.mark.parametrize("Lx,slab", [(100, 16), (100, 8), (40, 8)])
+def test_lost_copy_times_out_in_the_lean_pass(Lx, slab):
+    """The bounded waits of the three-step pass (the lean pass at slab 16,
+    one site per thread at slab 8): a copy that never arrives makes the call
+    report CBDG_ERR_CUDA, and the lattice then computes correct moments."""
+    p = rect(Lx, 12, 40, seed=52, periodic=0)
     sites = np.arange(p.N, dtype=np.int32)
-    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3, wait_limit_ms=20, test_stall_copy=1)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3, wait_limit_ms=20, test_stall_copy=1,
+                      slab_width=slab)
     with pytest.raises(cbdg.CbdgError) as ei:
         lat.moments(sites, p.M)
     assert ei.value.status == cbdg.CBDG_ERR_CUDA and "gave up waiting" in str(ei.value)
@@ -158,11 +163,13 @@ def tall_disordered(Lx, Ly, M, seed):
                       pairing=wl.ONSITE, coupling=2.0, delta0=np.full(N, 0.5 + 0j), T=0.01, M=M)
 
 
+@pytest.mark.parametrize("slab", [16, 8])
 @pytest.mark.parametrize("shape", [(128, 1024, 256), (128, 512, 1024), (96, 2048, 128)])
-def test_lean_pass_tall_lattices_match_oracle(shape):
-    """The lean three-step pass on lattices much taller than wide: each
-    thread's FP32 column sums are flushed into FP64 every few rows, so their
-    error does not grow with Ly.  Moments of 16 sampled start sites (among
+def test_lean_pass_tall_lattices_match_oracle(shape, slab):
+    """Three steps per pass on lattices much taller than wide: in the lean
+    pass (slab 16) each thread's FP32 column sums are flushed into FP64 every
+    few rows, at slab 8 (one site per thread) they are Kahan-compensated, so
+    in neither does their error grow with Ly.  Moments of 16 sampled start sites (among
     them the first and last rows) vs the oracle at the FP32 moment tolerance;
     at M = 1024 on 128 x 512 every start vector spreads over the whole
     height."""
@@ -171,7 +178,7 @@ def test_lean_pass_tall_lattices_match_oracle(shape):
     rng = np.random.default_rng(Ly)
     sites = np.concatenate([[0, Lx - 1, p.N - Lx, p.N - 1, (Ly // 2) * Lx + Lx // 2],
                             rng.choice(p.N, 11, replace=False)]).astype(np.int32)
-    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3)
+    lat = gpu_lattice(p, "fp32", resident=0, temporal_steps=3, slab_width=slab)
     (ee, eh), launches = recursion_launches(lat, sites, M)
     n_steps = (M + 1) // 2 - 1
     assert launches == n_steps // 3 + n_steps % 3
