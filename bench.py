@@ -494,25 +494,41 @@ def leg_ensemble(cbdg, wl, stream, samples=256):
             "algorithmic_bytes": algo_bytes}
 
 
-def adjoint_streams(M):
+def adjoint_streams(M, multi=False):
     """Vector streams (reads + writes of one 2N x B vector) of one adjoint run
     as the library schedules it: forward with checkpoints every S = ceil(sqrt M)
     steps, per segment the checkpoint copies and the recomputation, the
     reverse recursion (3 streams per step) and the gradient accumulation
-    (lambda_m and j_(m-1): 2 streams per moment)."""
+    (lambda_m and j_(m-1): 2 streams per moment).  multi: the forward,
+    recomputed and reverse recursions run three steps per pass where three
+    remain in the segment (else two, else one): in place a pass moves 4
+    vectors, with every level written 2 + K."""
     import math
     S = max(2, math.ceil(math.sqrt(M)))
     nseg = (M + S - 1) // S
-    m_last = (nseg - 1) * S + 1
-    # steps m = 2 .. min(M - 1, m_last); copies (2 streams each) of j_0, j_1 and of j_kS, j_kS+1
-    fwd = 3 * max(0, min(M - 1, m_last) - 1) + 2 * 2
-    fwd += 2 * sum(1 for k in range(1, nseg) if k * S <= min(M - 1, m_last))
-    fwd += 2 * sum(1 for k in range(1, nseg) if k * S + 1 <= min(M - 1, m_last))
-    rec = 0
-    for k in range(nseg):
+
+    def run(n, to, out_of_place):
+        s = 0
+        while n < to:
+            k = 3 if multi and to - n >= 3 else (2 if multi and to - n >= 2 else 1)
+            s += (2 + k if out_of_place else 4) if k > 1 else 3
+            n += k
+        return s
+    fwd, n = 2 * 2, 1  # copies of j_0, j_1 into checkpoint 0
+    for k in range(1, nseg):
+        to = k * S + 1 if k * S + 1 < M else k * S
+        fwd += run(n, to, False) + 2 * (2 if to == k * S + 1 else 1)
+        n = to
+    rec, rev, m = 0, 0, M
+    for k in reversed(range(nseg)):
         r_end = min(S, M - k * S)
-        rec += 2 + (2 if r_end > 1 else 0) + 3 * max(0, r_end - 2)
-    rev = 3 * (M - 2) + 2 * (M - 1)
+        rec += 2 + (2 if r_end > 1 else 0) + run(1, max(1, r_end - 1), True)
+        # lam_(m-1) .. lam_(kS+1), every level written (the first, lam_(M-1), is its source alone)
+        if m == M:
+            m = M - 1
+        rev += run(k * S + 1, m, True)
+        m = k * S + 1
+    rev += 2 * (M - 1)  # accumulation: lam_m and j_(m-1) for m = M-1 .. 1
     return fwd + rec + rev
 
 
@@ -534,11 +550,14 @@ def leg_adjoint(cbdg, wl, stream, hbm):
         lg.close()
         if prec == "fp32":
             vb = 2 * pg.N * pg.N * es
-            gbs = adjoint_streams(pg.M) * vb / dt / 1e9
+            streams = adjoint_streams(pg.M, multi=True)
+            gbs = streams * vb / dt / 1e9
             out["fp32_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                    "frac": gbs / hbm, "streams": adjoint_streams(pg.M), "vector_bytes": vb,
-                                    "note": "whole backward call (forward with checkpoints, recomputation, "
-                                            "reverse recursion, accumulation) over its algorithmic bytes"}
+                                    "frac": gbs / hbm, "streams": streams, "vector_bytes": vb,
+                                    "streams_one_step_per_pass": adjoint_streams(pg.M),
+                                    "note": "whole backward call (forward with checkpoints, recomputation and "
+                                            "reverse recursion three steps per pass, accumulation) over its "
+                                            "algorithmic bytes"}
     return out
 
 

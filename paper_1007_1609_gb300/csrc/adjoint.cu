@@ -139,6 +139,15 @@ __global__ void __launch_bounds__(256) adjoint_accumulate_kernel(int Lx, int Ly,
             acc[k].add(p);
           }
         };
+        // every load of the slab first (one memory round trip per slab): a
+        // missing neighbour reads the site itself and is not summed
+        P de[4], dh[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          const size_t ne = has[d] ? static_cast<size_t>(2 * Lx * ny[d] + nx[d]) * W + off : re;
+          de[d] = *reinterpret_cast<const P *>(jb + ne);
+          dh[d] = *reinterpret_cast<const P *>(jb + ne + static_cast<size_t>(Lx) * W);
+        }
         dot(0, le, je);
         dot(1, lh, jh);
         dot(2, le, jh);
@@ -146,11 +155,8 @@ __global__ void __launch_bounds__(256) adjoint_accumulate_kernel(int Lx, int Ly,
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
           if (!has[d]) continue;
-          const size_t ne = static_cast<size_t>(2 * Lx * ny[d] + nx[d]) * W + off;
-          const P de = *reinterpret_cast<const P *>(jb + ne);
-          const P dh = *reinterpret_cast<const P *>(jb + ne + static_cast<size_t>(Lx) * W);
-          dot(4 + d, le, de);
-          dot(8 + d, lh, dh);
+          dot(4 + d, le, de[d]);
+          dot(8 + d, lh, dh[d]);
         }
       }
     }
@@ -167,6 +173,178 @@ __global__ void __launch_bounds__(256) adjoint_accumulate_kernel(int Lx, int Ly,
       double *pp = part + (static_cast<size_t>(g) * N + static_cast<size_t>(y) * Lx + x) * 12;
 #pragma unroll
       for (int k = 0; k < 12; ++k) pp[k] += f * tot[k];
+    }
+  }
+}
+
+// FP32 accumulation with staged rows: one CTA per (lattice row y, group of
+// column slabs); per slab, bulk copies (cp.async.bulk on mbarriers) bring
+// the lam row y and the j rows y-1, y, y+1 of that slab into one stage of a
+// kAccStages ring, the copies of the next slabs in flight while the sums of
+// this one read every neighbour from shared memory.  MAXX x slots per thread
+// (Lx <= 64 MAXX); same sums, order and compensation as the unstaged kernel.
+constexpr int kAccStages = 3, kAccThreads = 256, kAccW = 16;
+
+__device__ __forceinline__ unsigned acc_smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool acc_mbar_wait(unsigned bar, unsigned parity, unsigned long long limit_ns) {
+  auto try_once = [&]() {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+  };
+  if (try_once()) return true;
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+  for (unsigned it = 0;; ++it) {
+    if (try_once()) return true;
+    if ((it & 255u) == 255u) {
+      unsigned long long t1;
+      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t1));
+      if (t1 - t0 > limit_ns) return false;
+    }
+  }
+}
+
+template <int MAXX>
+__global__ void __launch_bounds__(kAccThreads) adjoint_accumulate_staged_kernel(
+    int Lx, int Ly, int px, int py, int ld, int spg, const float *__restrict__ lam, const float *__restrict__ j,
+    double f, double *part, unsigned long long wait_ns, unsigned *flags) {
+  constexpr int W = kAccW, VEC = 4, QUADS = W / VEC, XSLOTS = kAccThreads / QUADS, R = kAccStages;
+  using P = Pack<float, VEC>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[R];
+  __shared__ int abort_flag;
+  const int N = Lx * Ly, y = blockIdx.x, g = blockIdx.y;
+  const int t = threadIdx.x, q = t % QUADS, xs = t / QUADS, off = q * VEC;
+  const size_t slab_el = static_cast<size_t>(2) * N * W;
+  const int rowel = 2 * Lx * W;  // floats of one lattice row: electron then hole part
+  const int s0 = g * spg, ns = min(ld / W, s0 + spg) - s0;
+  // rows y - 1 and y + 1 (-1: beyond an open edge)
+  const int ym = y > 0 ? y - 1 : (py ? Ly - 1 : -1), yp = y + 1 < Ly ? y + 1 : (py ? 0 : -1);
+  float *sm = reinterpret_cast<float *>(smem_raw);  // [R][4][rowel]: lam y, j y-1, j y, j y+1
+  if (t == 0) {
+    for (int k = 0; k < R; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(acc_smem_addr(&bars[k])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  const unsigned row_bytes = static_cast<unsigned>(rowel) * 4u;
+  auto copy = [&](float *dst, const float *src, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            acc_smem_addr(dst)),
+        "l"(src), "r"(row_bytes), "r"(bar)
+        : "memory");
+  };
+  auto issue = [&](int i) {
+    const int st = i % R;
+    const unsigned bar = acc_smem_addr(&bars[st]);
+    const unsigned n_rows = 2u + (ym >= 0 ? 1u : 0u) + (yp >= 0 ? 1u : 0u);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(n_rows * row_bytes)
+                 : "memory");
+    const float *lb = lam + (s0 + i) * slab_el, *jb = j + (s0 + i) * slab_el;
+    float *d = sm + static_cast<size_t>(st) * 4 * rowel;
+    copy(d, lb + static_cast<size_t>(y) * rowel, bar);
+    copy(d + 2 * rowel, jb + static_cast<size_t>(y) * rowel, bar);
+    if (ym >= 0) copy(d + rowel, jb + static_cast<size_t>(ym) * rowel, bar);
+    if (yp >= 0) copy(d + 3 * rowel, jb + static_cast<size_t>(yp) * rowel, bar);
+  };
+  int issued = min(ns, R);
+  if (t == 0)
+    for (int i = 0; i < issued; ++i) issue(i);
+  // neighbours along x of each x slot (-1: beyond an open edge)
+  int xl[MAXX], xr[MAXX];
+#pragma unroll
+  for (int k = 0; k < MAXX; ++k) {
+    const int x = xs + k * XSLOTS;
+    xl[k] = x > 0 ? x - 1 : (px ? Lx - 1 : -1);
+    xr[k] = x + 1 < Lx ? x + 1 : (px ? 0 : -1);
+  }
+  SumOf<float> acc[MAXX][12];
+  auto dot = [](SumOf<float> &a, const P &u, const P &v) {
+    float p = u.v[0] * v.v[0];
+#pragma unroll
+    for (int l = 1; l < VEC; ++l) p = fmaf(u.v[l], v.v[l], p);
+    a.add(p);
+  };
+  const int hb = Lx * W;
+  for (int i = 0; i < ns; ++i) {
+    const int st = i % R;
+    if (!acc_mbar_wait(acc_smem_addr(&bars[st]), static_cast<unsigned>((i / R) & 1), wait_ns)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    const float *d = sm + static_cast<size_t>(st) * 4 * rowel;
+    const float *sl = d, *jm = d + rowel, *jc = d + 2 * rowel, *jp = d + 3 * rowel;
+#pragma unroll
+    for (int k = 0; k < MAXX; ++k) {
+      const int x = xs + k * XSLOTS;
+      if (x >= Lx) continue;
+      const int e = x * W + off;
+      const P le = *reinterpret_cast<const P *>(sl + e), lh = *reinterpret_cast<const P *>(sl + hb + e);
+      const P je = *reinterpret_cast<const P *>(jc + e), jh = *reinterpret_cast<const P *>(jc + hb + e);
+      dot(acc[k][0], le, je);
+      dot(acc[k][1], lh, jh);
+      dot(acc[k][2], le, jh);
+      dot(acc[k][3], lh, je);
+      // directions +x, -x, +y, -y
+      if (xr[k] >= 0) {
+        const int n = xr[k] * W + off;
+        dot(acc[k][4], le, *reinterpret_cast<const P *>(jc + n));
+        dot(acc[k][8], lh, *reinterpret_cast<const P *>(jc + hb + n));
+      }
+      if (xl[k] >= 0) {
+        const int n = xl[k] * W + off;
+        dot(acc[k][5], le, *reinterpret_cast<const P *>(jc + n));
+        dot(acc[k][9], lh, *reinterpret_cast<const P *>(jc + hb + n));
+      }
+      if (yp >= 0) {
+        dot(acc[k][6], le, *reinterpret_cast<const P *>(jp + e));
+        dot(acc[k][10], lh, *reinterpret_cast<const P *>(jp + hb + e));
+      }
+      if (ym >= 0) {
+        dot(acc[k][7], le, *reinterpret_cast<const P *>(jm + e));
+        dot(acc[k][11], lh, *reinterpret_cast<const P *>(jm + hb + e));
+      }
+    }
+    __syncthreads();  // stage st is free
+    if (i + R < ns) {
+      if (t == 0) issue(i + R);
+      issued = i + R + 1;
+    }
+  }
+  if (abort_flag) {
+    if (t == 0) {
+      atomicOr(flags, kFlagTimeout);
+      // let the copies in flight land before the CTA's shared memory goes away
+      for (int i = 0; i < issued; ++i)
+        if (!acc_mbar_wait(acc_smem_addr(&bars[i % R]), static_cast<unsigned>((i / R) & 1), wait_ns)) break;
+    }
+    return;
+  }
+  // combine the QUADS column lanes of each site (adjacent lanes), FP64
+#pragma unroll
+  for (int k = 0; k < MAXX; ++k) {
+    const int x = xs + k * XSLOTS;
+    double tot[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      double v = acc[k][c].value();
+#pragma unroll
+      for (int o = 1; o < QUADS; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      tot[c] = v;
+    }
+    if (x < Lx && q == 0) {
+      double *pp = part + (static_cast<size_t>(g) * N + static_cast<size_t>(y) * Lx + x) * 12;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) pp[c] += f * tot[c];
     }
   }
 }
@@ -289,9 +467,51 @@ cudaError_t accumulate_s(int Lx, int Ly, int px, int py, int ld, int W, int grou
   return cudaErrorInvalidValue;
 }
 
+namespace {
+bool accumulate_staged(int precision, int Lx, int W) {
+  return precision == 1 && W == kAccW && Lx <= 2 * (kAccThreads / (kAccW / 4));
+}
+size_t staged_smem(int Lx) { return static_cast<size_t>(kAccStages) * 4 * 2 * Lx * kAccW * sizeof(float); }
+
+template <int MAXX>
+cudaError_t launch_staged(int Lx, int Ly, int px, int py, int ld, int groups, const void *lam, const void *j,
+                          double f, double *part, unsigned long long wait_ns, unsigned *flags, cudaStream_t s) {
+  auto k = adjoint_accumulate_staged_kernel<MAXX>;
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  const int slabs = ld / kAccW, spg = (slabs + groups - 1) / groups;
+  k<<<dim3(Ly, groups), kAccThreads, staged_smem(Lx), s>>>(Lx, Ly, px, py, ld, spg, static_cast<const float *>(lam),
+                                                         static_cast<const float *>(j), f, part, wait_ns, flags);
+  return cudaGetLastError();
+}
+}  // namespace
+
+int adjoint_groups_real(int precision, int Lx, int Ly, int ld, int W) {
+  if (!accumulate_staged(precision, Lx, W)) return adjoint_groups(Ly, ld, W);
+  // staged CTAs: about two waves of the resident CTAs, at least 4 slabs per group
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = std::max(1, std::min(8, static_cast<int>((228 * 1024) / (staged_smem(Lx) + 1024))));
+  const int slabs = std::max(1, ld / W);
+  return std::max(1, std::min(slabs / 4, (2 * sms * per_sm) / Ly));
+}
+
 cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int py, int ld, int W,
                                       int groups, const void *lam, const void *j, double f,
-                                      double *part, cudaStream_t s) {
+                                      double *part, unsigned long long wait_ns, unsigned *flags,
+                                      cudaStream_t s) {
+  if (accumulate_staged(precision, Lx, W)) {
+    if (Lx <= kAccThreads / (kAccW / 4))
+      return launch_staged<1>(Lx, Ly, px, py, ld, groups, lam, j, f, part, wait_ns, flags, s);
+    return launch_staged<2>(Lx, Ly, px, py, ld, groups, lam, j, f, part, wait_ns, flags, s);
+  }
   return precision == 1 ? accumulate_s<float>(Lx, Ly, px, py, ld, W, groups, lam, j, f, part, s)
                         : accumulate_s<double>(Lx, Ly, px, py, ld, W, groups, lam, j, f, part, s);
 }

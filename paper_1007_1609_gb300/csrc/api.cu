@@ -923,8 +923,10 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M, const int32_t *cols = 
   const int W = slab_width_default(L->precision);
   const int S = std::max(2, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(M)))));
   const int nseg = (M + S - 1) / S;
-  // per column: 2 checkpoint vectors per segment, S segment vectors, 2 forward, 2 adjoint
-  const int64_t per_col = static_cast<int64_t>((2 * nseg + S + 4) * rows * es);
+  // per column: 2 checkpoint vectors per segment, S segment vectors, 2 forward,
+  // 5 adjoint (2 inputs and 3 outputs of a multi-step pass; 2 with one step)
+  const int n_lam = L->precision == CBDG_FP32_MIXED && !L->py && L->temporal != 1 ? 5 : 2;
+  const int64_t per_col = static_cast<int64_t>((2 * nseg + S + 4 + n_lam - 2) * rows * es);
   size_t cap;
   if (L->ws_mb > 0) {
     cap = static_cast<size_t>(L->ws_mb) << 20;
@@ -938,7 +940,7 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M, const int32_t *cols = 
   if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
   if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for the adjoint");
   const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((n_cols + W - 1) / W) * W));
-  const int groups = adjoint_groups(L->Ly, ((std::min(chunk, n_cols) + W - 1) / W) * W, W);
+  const int groups = adjoint_groups_real(L->precision, L->Lx, L->Ly, ((std::min(chunk, n_cols) + W - 1) / W) * W, W);
   CK(L->adj_part.ensure(static_cast<size_t>(groups) * N * 12 * sizeof(double)));
   CK(cudaMemsetAsync(L->adj_part.p, 0, static_cast<size_t>(groups) * N * 12 * sizeof(double), L->stream));
   const double tol = L->precision == CBDG_FP32_MIXED ? 1e-4 : 1e-6;
@@ -956,7 +958,7 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M, const int32_t *cols = 
     CK(L->vec1.ensure(vb));
     CK(L->adj_ck.ensure(2 * nseg * vb));
     CK(L->adj_seg.ensure(static_cast<size_t>(S) * vb));
-    CK(L->adj_lam.ensure(2 * vb));
+    CK(L->adj_lam.ensure(n_lam * vb));
     CK(L->partials.ensure(static_cast<size_t>(cfg.row_split) * 3 * ld * sizeof(double)));
     CK(L->mu1.ensure(ld * sizeof(double)));
     CK(L->dA.ensure(ld * sizeof(double2)));
@@ -985,6 +987,28 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M, const int32_t *cols = 
       L->launches += 1;
       return CBDG_OK;
     };
+    // Several steps per pass (real FP32, open y edges; not with one step per
+    // pass asked for): a pass reads (j_{n-1}, j_n) and writes each level it
+    // is given an output vector for, no column sums.
+    StepConfig mcfg3, mcfg2;
+    int k3 = 0, k2 = 0;
+    const bool multi = L->precision == CBDG_FP32_MIXED && !L->py && L->temporal != 1;
+    const bool multi3 = multi && plan_step_multi(L->Lx, L->Ly, ld, W, 3, 1, &mcfg3, &k3) && k3 == 3 &&
+                        mcfg3.depth == 1;
+    const bool multi2 = multi && plan_step_multi(L->Lx, L->Ly, ld, W, 2, 1, &mcfg2, &k2) && k2 == 2 &&
+                        mcfg2.depth == 1;
+    auto pass = [&](int K, void *prev, void *cur, void *o1, void *o2, void *o3) -> cbdg_status {
+      a.prev = prev;
+      a.cur = cur;
+      a.lvout[0] = o1;
+      a.lvout[1] = o2;
+      a.lvout[2] = o3;
+      const cudaError_t e = launch_step_multi(a, K == 3 ? mcfg3 : mcfg2, K, L->stream);
+      a.lvout[0] = a.lvout[1] = a.lvout[2] = nullptr;
+      CK(e);
+      L->launches += 1;
+      return CBDG_OK;
+    };
     // ---- forward with checkpoints (j_{kS}, j_{kS+1})
     CK(cudaMemsetAsync(L->vec0.p, 0, vb, L->stream));
     CK(cudaMemsetAsync(L->vec1.p, 0, vb, L->stream));
@@ -997,58 +1021,147 @@ cbdg_status adjoint_run(cbdg_lattice *L, double T, int M, const int32_t *cols = 
     // checkpoint k holds j_{kS} (slot 0) and j_{kS+1} (slot 1, when kS+1 < M)
     CK(cudaMemcpyAsync(ckv(0, 0), L->vec0.p, vb, cudaMemcpyDeviceToDevice, L->stream));
     CK(cudaMemcpyAsync(ckv(0, 1), L->vec1.p, vb, cudaMemcpyDeviceToDevice, L->stream));
-    void *jm2 = L->vec0.p, *jm1 = L->vec1.p;  // j_{m-2}, j_{m-1} before step m
-    const int m_last = (nseg - 1) * S + 1;     // no later j is ever needed from the forward pass
-    for (int m = 2; m < M && m <= m_last; ++m) {
-      st = step(jm1, jm2);  // jm2 <- j_m
-      if (st != CBDG_OK) return st;
-      std::swap(jm1, jm2);  // jm1 = j_m
-      if (m % S == 0) CK(cudaMemcpyAsync(ckv(m / S, 0), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
-      if ((m - 1) % S == 0 && m - 1 >= S)
-        CK(cudaMemcpyAsync(ckv((m - 1) / S, 1), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+    void *jm2 = L->vec0.p, *jm1 = L->vec1.p;  // (j_{n-1}, j_n)
+    int n = 1;
+    // advance the forward recursion in place until jm1 = j_to
+    auto advance = [&](int to) -> cbdg_status {
+      while (n < to) {
+        const int left = to - n;
+        if (multi3 && left >= 3) {
+          st = pass(3, jm2, jm1, nullptr, jm2, jm1);
+          n += 3;
+        } else if (multi2 && left >= 2) {
+          st = pass(2, jm2, jm1, jm2, jm1, nullptr);
+          n += 2;
+        } else {
+          st = step(jm1, jm2);  // jm2 <- j_{n+1}
+          std::swap(jm1, jm2);
+          n += 1;
+        }
+        if (st != CBDG_OK) return st;
+      }
+      return CBDG_OK;
+    };
+    // checkpoint k: j_{kS} and, when kS + 1 < M, j_{kS+1}; no later j is
+    // ever needed from the forward pass
+    for (int k = 1; k < nseg; ++k) {
+      if (k * S + 1 < M) {
+        st = advance(k * S + 1);
+        if (st != CBDG_OK) return st;
+        CK(cudaMemcpyAsync(ckv(k, 0), jm2, vb, cudaMemcpyDeviceToDevice, L->stream));
+        CK(cudaMemcpyAsync(ckv(k, 1), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+      } else {
+        st = advance(k * S);
+        if (st != CBDG_OK) return st;
+        CK(cudaMemcpyAsync(ckv(k, 0), jm1, vb, cudaMemcpyDeviceToDevice, L->stream));
+      }
     }
     // ---- reverse: lam_m for m = M-1 .. 1, gradient f_m lam_m (x) j_{m-1}
-    void *lam1 = L->adj_lam.p;                                  // lam_{m+1}
-    void *lam2 = L->adj_lam.as<unsigned char>() + vb;          // lam_{m+2}
-    CK(cudaMemsetAsync(lam1, 0, vb, L->stream));
-    CK(cudaMemsetAsync(lam2, 0, vb, L->stream));
+    // lam[iq] = lam_m (the newest), lam[ip] = lam_{m+1}; a multi-step pass
+    // writes lam_{m-1} .. lam_{m-K} into free buffers, adding each level's
+    // source y in the pass
+    void *lam[5];
+    for (int b = 0; b < n_lam; ++b) lam[b] = L->adj_lam.as<unsigned char>() + static_cast<size_t>(b) * vb;
+    int ip = 0, iq = 1;
+    CK(cudaMemsetAsync(lam[ip], 0, vb, L->stream));
+    CK(cudaMemsetAsync(lam[iq], 0, vb, L->stream));
     const double halfU = L->site_cpl ? 0.5 : 0.5 * L->coupling;
-    bool first = true;
+    PassSource psrc;
+    psrc.sites = sites;
+    psrc.ncols = ncols;
+    if (map_source) {
+      // y_m = w_i (U_i / 2) C_m on the hole row
+      psrc.w = L->adj_w.as<double>();
+      psrc.u = L->coupling_site();
+      psrc.tab = L->C.as<double>();
+      psrc.stride = 0;
+      psrc.scale = halfU;
+      psrc.part = 1;
+    } else {
+      // y_m = src[c][m] on the electron row
+      psrc.tab = src + static_cast<size_t>(c0) * M;
+      psrc.stride = M;
+      psrc.scale = 1.0;
+      psrc.part = 0;
+    }
+    auto source = [&](int m, void *v) -> cbdg_status {
+      if (map_source)
+        CK(launch_adjoint_source(L->precision, L->Lx, L->Ly, ncols, W, sites, L->adj_w.as<double>(),
+                                 L->coupling_site(), halfU * hC[m], v, L->stream));
+      else
+        CK(launch_adjoint_source_table(L->precision, L->Lx, L->Ly, ncols, W, sites,
+                                       src + static_cast<size_t>(c0) * M, M, m, v, L->stream));
+      L->launches += 1;
+      return CBDG_OK;
+    };
+    int m = M;  // lam[iq] = lam_m; none computed yet
     for (int k = nseg - 1; k >= 0; --k) {
       // recompute j_{kS} .. j_{kS+S-1} (those below M) into the segment
       const int r_end = std::min(S, M - k * S);
       CK(cudaMemcpyAsync(segv(0), ckv(k, 0), vb, cudaMemcpyDeviceToDevice, L->stream));
       if (r_end > 1) CK(cudaMemcpyAsync(segv(1), ckv(k, 1), vb, cudaMemcpyDeviceToDevice, L->stream));
-      for (int r = 2; r < r_end; ++r) {
-        // j_r = 2 H~ j_{r-1} - j_{r-2}, out of place (the segment keeps j_{r-2})
-        a.cur = segv(r - 1);
-        a.prev = segv(r - 2);
-        a.out = segv(r);
-        CK(launch_step_real(L->precision, a, cfg, L->stream));
-        a.out = nullptr;
-        L->launches += 1;
-      }
-      // m - 1 in [kS, kS + r_end - 1]  ->  m in [kS + 1, kS + r_end], m <= M - 1
-      const int m_hi = std::min(M - 1, k * S + r_end), m_lo = k * S + 1;
-      for (int m = m_hi; m >= m_lo; --m) {
-        if (first) {
-          // lam_{M-1} = y_{M-1}
-          first = false;
+      for (int r = 2; r < r_end;) {
+        // j_r = 2 H~ j_{r-1} - j_{r-2}, out of place (the segment keeps every j)
+        if (multi3 && r_end - r >= 3) {
+          st = pass(3, segv(r - 2), segv(r - 1), segv(r), segv(r + 1), segv(r + 2));
+          r += 3;
+        } else if (multi2 && r_end - r >= 2) {
+          st = pass(2, segv(r - 2), segv(r - 1), segv(r), segv(r + 1), nullptr);
+          r += 2;
         } else {
-          st = step(lam1, lam2);  // lam2 <- 2 H~ lam_{m+1} - lam_{m+2} = lam_m without source
-          if (st != CBDG_OK) return st;
-          std::swap(lam1, lam2);  // lam1 = lam_m, lam2 = lam_{m+1}
+          a.cur = segv(r - 1);
+          a.prev = segv(r - 2);
+          a.out = segv(r);
+          const cudaError_t e = launch_step_real(L->precision, a, cfg, L->stream);
+          a.out = nullptr;
+          CK(e);
+          L->launches += 1;
+          r += 1;
         }
-        if (map_source)
-          CK(launch_adjoint_source(L->precision, L->Lx, L->Ly, ncols, W, sites, L->adj_w.as<double>(),
-                                   L->coupling_site(), halfU * hC[m], lam1, L->stream));
-        else
-          CK(launch_adjoint_source_table(L->precision, L->Lx, L->Ly, ncols, W, sites,
-                                         src + static_cast<size_t>(c0) * M, M, m, lam1, L->stream));
-        CK(launch_adjoint_accumulate(L->precision, L->Lx, L->Ly, L->px, L->py, ld, W, groups, lam1,
-                                     segv(m - 1 - k * S), m == 1 ? 1.0 : 2.0,
-                                     L->adj_part.as<double>(), L->stream));
-        L->launches += 2;
+        if (st != CBDG_OK) return st;
+      }
+      // this segment holds j_{m-1} for m in [kS + 1, kS + r_end] (m <= M - 1)
+      const int m_lo = k * S + 1;
+      auto accumulate = [&](int mm, void *v) -> cbdg_status {
+        CK(launch_adjoint_accumulate(L->precision, L->Lx, L->Ly, L->px, L->py, ld, W, groups, v,
+                                     segv(mm - 1 - k * S), mm == 1 ? 1.0 : 2.0, L->adj_part.as<double>(),
+                                     a.wait_ns, L->flags.as<unsigned int>(), L->stream));
+        L->launches += 1;
+        return CBDG_OK;
+      };
+      while (m - 1 >= m_lo) {
+        if (m == M) {
+          // lam_{M-1} = y_{M-1} (lam_M = 0)
+          m = M - 1;
+          st = source(m, lam[iq]);
+          if (st == CBDG_OK) st = accumulate(m, lam[iq]);
+        } else {
+          const int left = m - m_lo;  // lam_{m-1} .. lam_{m_lo} remain in this segment
+          const int K = multi3 && left >= 3 ? 3 : (multi2 && left >= 2 ? 2 : 1);
+          if (K == 1) {
+            st = step(lam[iq], lam[ip]);  // lam[ip] <- 2 H~ lam_m - lam_{m+1}
+            if (st != CBDG_OK) return st;
+            std::swap(ip, iq);
+            m -= 1;
+            st = source(m, lam[iq]);
+            if (st == CBDG_OK) st = accumulate(m, lam[iq]);
+          } else {
+            int o[3], nf = 0;
+            for (int b = 0; b < n_lam && nf < K; ++b)
+              if (b != ip && b != iq) o[nf++] = b;
+            psrc.m0 = m;
+            psrc.dm = -1;
+            a.src = psrc;
+            st = pass(K, lam[ip], lam[iq], lam[o[0]], lam[o[1]], K == 3 ? lam[o[2]] : nullptr);
+            a.src = PassSource{};
+            if (st != CBDG_OK) return st;
+            for (int t = 1; t <= K && st == CBDG_OK; ++t) st = accumulate(m - t, lam[o[t - 1]]);
+            ip = o[K - 2];
+            iq = o[K - 1];
+            m -= K;
+          }
+        }
+        if (st != CBDG_OK) return st;
       }
     }
   }

@@ -33,6 +33,24 @@ constexpr int kCpE = 0, kCpDelta = 1, kCpHop = 2, kCpBond = 6;
 // (row r, column b) sits at (b / W) * 2N*W + r*W + (b % W).  Rows go lattice
 // row by lattice row; inside lattice row y the Lx electron rows come first,
 // then the Lx hole rows (vector_row below).
+// One-element sources of a multi-step pass with per-level outputs (the
+// adjoint's reverse recursion, lam_m = y_m + 2 H~ lam_{m+1} - lam_{m+2}):
+// level t adds to column c, at the electron (part 0) or hole (part 1) row of
+// its start site i = sites[c], the value
+//     w[i] u[i] (scale tab[stride c + m]),   m = m0 + dm t,
+// with w, u taken as 1 where null.  sites == nullptr: no sources.
+struct PassSource {
+  const int32_t *sites = nullptr;
+  int ncols = 0;  // columns with a start site (the rest are padding)
+  const double *w = nullptr;
+  const double *u = nullptr;
+  const double *tab = nullptr;
+  int stride = 0;
+  double scale = 1.0;
+  int m0 = 0, dm = -1;
+  int part = 1;
+};
+
 struct StepArgs {
   const void *cur;      // j_n
   void *prev;           // j_{n-1} on entry, j_{n+1} on exit (in place)
@@ -45,6 +63,11 @@ struct StepArgs {
   int ld;               // columns (a multiple of the slab width)
   int rows_per_cta;     // lattice rows per CTA along y
   void *out = nullptr;  // one-step kernels: j_{n+1} goes here when set (prev is kept)
+  // multi-step kernels: when lvout[K-1] is set, level t (j_{n+t}) goes to
+  // lvout[t-1] where that is set, (prev, cur) are only read and no column
+  // sums are formed
+  void *lvout[4] = {nullptr, nullptr, nullptr, nullptr};
+  PassSource src;       // sources of the per-level-output passes
 };
 
 struct StepConfig {
@@ -240,9 +263,13 @@ cudaError_t launch_ldos_source(int n_sites, int n_E, int M, int kernel, double l
                                const double *scal, const double *G, double *W, double *S, cudaStream_t s);
 // Column groups of the accumulation for ld columns at slab width W on Ly rows.
 int adjoint_groups(int Ly, int ld, int W);
+// column-slab groups of launch_adjoint_accumulate (the FP32 kernel with staged
+// rows, slab width 16, Lx <= 128, sizes its own grid)
+int adjoint_groups_real(int precision, int Lx, int Ly, int ld, int W);
 cudaError_t launch_adjoint_accumulate(int precision, int Lx, int Ly, int px, int py, int ld, int W,
                                       int groups, const void *lam, const void *j, double f,
-                                      double *part, cudaStream_t s);
+                                      double *part, unsigned long long wait_ns, unsigned *flags,
+                                      cudaStream_t s);
 cudaError_t launch_fixed_point_update(int N, double mix, const double *g, const double *gd, double *lam,
                                       double *w, double *scal, cudaStream_t s);
 cudaError_t launch_adjoint_final(int Lx, int Ly, int px, int py, int groups, const double *part,

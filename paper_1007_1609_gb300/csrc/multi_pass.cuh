@@ -21,6 +21,11 @@
 // 3 per step.  Rows -1 and Ly do not exist (open edges), which is what makes
 // the single wavefront possible.
 //
+// LVOUT: the levels go to vectors of their own instead of (P, Q), which are
+// then only read, and no column sums are formed; level t may add a
+// one-element source per column at its start site (PassSource) -- the
+// adjoint's forward, recomputed and reverse recursions.
+//
 // Staging: TMA bulk copies on mbarriers; load l (rows l of Q and P and the
 // parameters of lattice row l) completes on bars[(base + l) % NB] in phase
 // ((base + l) / NB) & 1, so consecutive passes on the same barriers continue
@@ -92,6 +97,19 @@ struct ChunkSum {
   __device__ __forceinline__ void add2(float a1, float b1, float a2, float b2) {
     s = __fmaf_rn(a1, b1, __fmaf_rn(a2, b2, s));
   }
+};
+
+// No column sums (passes whose moments nobody reads, e.g. the adjoint's
+// forward and recomputed recursions).
+struct NoSum {
+  __device__ __forceinline__ void add2(float, float, float, float) {}
+  __device__ __forceinline__ double value() const { return 0.0; }
+};
+
+// Per-level outputs of a pass (LVOUT): level t's rows go to p[t - 1] when it
+// is set, and P and Q are only read.
+struct LevelOut {
+  float *p[4];
 };
 
 // Wavefronts between two flushes of ChunkSum accumulators: two iterations of
@@ -188,12 +206,15 @@ struct PassShape {
   }
 };
 
-template <int W, int K, int D, int MAXX, int NT = kPassThreads, bool LEAN = false, typename Acc = Kahan>
+template <int W, int K, int D, int MAXX, int NT = kPassThreads, bool LEAN = false, typename Acc = Kahan,
+          bool LVOUT = false>
 __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__restrict__ par, int Lx, int Ly,
                                            float *smem, unsigned long long *bars, long long base,
                                            unsigned long long wait_ns, unsigned stall_tx, int *abort_flag,
                                            Acc (&accA)[K][4], Acc (&accB)[K][4], Acc (&accC)[K][4],
-                                           FlushBank<K> *bank = nullptr) {
+                                           FlushBank<K> *bank = nullptr, LevelOut lo = LevelOut{},
+                                           const PassSource *src = nullptr, int col0 = 0) {
+  static_assert(K <= 4, "LevelOut holds four levels");
   using Sh = PassShape<W, K, D, NT, LEAN>;
   constexpr bool kFlush = std::is_same<Acc, ChunkSum>::value;
   static_assert(!kFlush || W / 4 == 4, "the chunk flush expects four column quads per warp");
@@ -242,6 +263,43 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
 
   const int hb = Lx * W;
   const int off = q * VEC;
+  // LVOUT sources: bit j of smask when column col0 + off + j has its start
+  // site at one of this thread's x slots (slot s_k, row s_r)
+  int smask = 0, s_k[VEC], s_r[VEC], s_i[VEC];
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) s_k[j] = s_r[j] = s_i[j] = 0;
+  if constexpr (LVOUT) {
+    if (src != nullptr && src->sites != nullptr) {
+#pragma unroll
+      for (int j = 0; j < VEC; ++j) {
+        const int c = col0 + off + j;
+        if (c < src->ncols) {
+          const int i = src->sites[c], rx = i % Lx;
+          if (rx % XSLOTS == xs) {
+            smask |= 1 << j;
+            s_k[j] = rx / XSLOTS;
+            s_r[j] = i / Lx;
+            s_i[j] = i;
+          }
+        }
+      }
+    }
+  }
+  // adds the level-lv sources of this thread's columns whose start site is
+  // (slot k, row r)
+  auto add_sources = [&](int lv, int r, int k, float4 &un, float4 &vn) {
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      if (((smask >> j) & 1) && s_r[j] == r && s_k[j] == k) {
+        const int i = s_i[j];
+        const double wv = (src->w ? src->w[i] : 1.0) * (src->u ? src->u[i] : 1.0);
+        const double val =
+            wv * (src->scale * src->tab[static_cast<size_t>(src->stride) * (col0 + off + j) + src->m0 + src->dm * lv]);
+        float *e = reinterpret_cast<float *>(src->part == 0 ? &un : &vn) + j;
+        *e = static_cast<float>(static_cast<double>(*e) + val);
+      }
+    }
+  };
   float4 wu[K][3][MAXX], wv[K][3][MAXX];
 #pragma unroll
   for (int l = 0; l < K; ++l)
@@ -397,14 +455,24 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
                 accB[lv - 1][j].add2(unj, uj, vnj, vj);
                 accC[lv - 1][j].add2(unj, vj, -vnj, uj);
               }
+              if constexpr (LVOUT) {
+                if (smask != 0) add_sources(lv, r, k, un, vn);
+              }
               if (lv < K) {
                 wu[lv < K ? lv : 0][sc][k] = un;
                 wv[lv < K ? lv : 0][sc][k] = vn;
                 *reinterpret_cast<float4 *>(dl + x * W + off) = un;
                 *reinterpret_cast<float4 *>(dl + hb + x * W + off) = vn;
               }
-              // levels K-1 and K become the new (P, Q); their HBM rows are no longer read
-              if (lv == K - 1) {
+              if constexpr (LVOUT) {
+                // every level to its own vector, when given; P and Q are only read
+                if (lo.p[lv - 1] != nullptr) {
+                  float *o = lo.p[lv - 1] + static_cast<size_t>(r) * rowel;
+                  __stcs(reinterpret_cast<float4 *>(o + x * W + off), un);
+                  __stcs(reinterpret_cast<float4 *>(o + hb + x * W + off), vn);
+                }
+              } else if (lv == K - 1) {
+                // levels K-1 and K become the new (P, Q); their HBM rows are no longer read
                 float *o = P + static_cast<size_t>(r) * rowel;
                 __stcs(reinterpret_cast<float4 *>(o + x * W + off), un);
                 __stcs(reinterpret_cast<float4 *>(o + hb + x * W + off), vn);

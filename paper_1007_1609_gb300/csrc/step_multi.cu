@@ -27,8 +27,8 @@ namespace {
 using mp::Kahan;
 constexpr int kThreads = mp::kPassThreads;
 
-template <int W, int K, int D, int MAXX, bool LEAN>
-__global__ void __launch_bounds__(kThreads, 1) step_multi_kernel(StepArgs a) {
+template <int W, int K, int D, int MAXX, bool LEAN, bool LVOUT = false>
+__global__ void __launch_bounds__(kThreads, LVOUT && MAXX == 1 ? 2 : 1) step_multi_kernel(StepArgs a) {
   using Sh = mp::PassShape<W, K, D, kThreads, LEAN>;
   constexpr int VEC = Sh::VEC, XSLOTS = Sh::XSLOTS, NB = Sh::NB;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -44,19 +44,26 @@ __global__ void __launch_bounds__(kThreads, 1) step_multi_kernel(StepArgs a) {
     abort_flag = 0;
   }
   __syncthreads();
-  using Acc = typename std::conditional<LEAN, mp::ChunkSum, Kahan>::type;
+  using Acc = typename std::conditional<LVOUT, mp::NoSum,
+                                        typename std::conditional<LEAN, mp::ChunkSum, Kahan>::type>::type;
   using FB = mp::FlushBank<K>;
   Acc accA[K][VEC], accB[K][VEC], accC[K][VEC];
   FB bank;
   bank.clear();
-  const bool ok = mp::multi_pass<W, K, D, MAXX, kThreads, LEAN, Acc>(
+  mp::LevelOut lo{};
+  if constexpr (LVOUT) {
+#pragma unroll
+    for (int l = 0; l < K; ++l) lo.p[l] = a.lvout[l] ? static_cast<float *>(a.lvout[l]) + slab : nullptr;
+  }
+  const bool ok = mp::multi_pass<W, K, D, MAXX, kThreads, LEAN, Acc, LVOUT>(
       static_cast<float *>(a.prev) + slab, static_cast<float *>(const_cast<void *>(a.cur)) + slab,
       static_cast<const float *>(a.params), a.Lx, a.Ly, reinterpret_cast<float *>(smem_raw), bars, 0,
-      a.wait_ns, a.stall_tx, &abort_flag, accA, accB, accC, &bank);
+      a.wait_ns, a.stall_tx, &abort_flag, accA, accB, accC, &bank, lo, &a.src, static_cast<int>(blockIdx.x) * W);
   if (!ok) {
     if (t == 0) atomicOr(a.flags, kFlagTimeout);
     return;
   }
+  if constexpr (LVOUT) return;
   __syncthreads();
   double *red = reinterpret_cast<double *>(smem_raw);
   const size_t c0 = static_cast<size_t>(blockIdx.x) * W;
@@ -109,14 +116,17 @@ size_t smem_bytes(int Lx) {
   return std::max(ring, red) * sizeof(float);
 }
 
-template <int W, int K, int D, int MAXX, bool LEAN = false>
+template <int W, int K, int D, int MAXX, bool LEAN = false, bool LVOUT = false>
 cudaError_t launch_one(const StepArgs &a, size_t smem, cudaStream_t s) {
-  auto k = step_multi_kernel<W, K, D, MAXX, LEAN>;
+  auto k = step_multi_kernel<W, K, D, MAXX, LEAN, LVOUT>;
   static int attr_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (attr_dev != dev) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    // the per-level-output kernels at one site per thread fit two CTAs per SM
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
@@ -149,6 +159,19 @@ cudaError_t dispatch_lean(const StepArgs &a, cudaStream_t s) {
   constexpr int xsl = kThreads / (kLeanW / 4);
   if (a.Lx <= xsl || a.Lx > 2 * xsl) return cudaErrorInvalidValue;
   return launch_one<kLeanW, kLeanK, kLeanD, 2, true>(a, smem_bytes<kLeanW, kLeanK, kLeanD, true>(a.Lx), s);
+}
+
+// Per-level outputs and no column sums (the adjoint's forward and recomputed
+// recursions): slab width 16 at depth 1, K = 2 or 3.
+cudaError_t dispatch_lvout(const StepArgs &a, const StepConfig &cfg, int K, cudaStream_t s) {
+  constexpr int xsl = kThreads / 4;
+  if (cfg.slab_w != 16 || cfg.depth != 1) return cudaErrorInvalidValue;
+  if (K == 3 && a.Lx <= xsl) return launch_one<16, 3, 1, 1, false, true>(a, smem_bytes<16, 3, 1>(a.Lx), s);
+  if (K == 3 && a.Lx <= 2 * xsl)
+    return launch_one<16, 3, 1, 2, true, true>(a, smem_bytes<16, 3, 1, true>(a.Lx), s);
+  if (K == 2 && a.Lx <= xsl) return launch_one<16, 2, 1, 1, false, true>(a, smem_bytes<16, 2, 1>(a.Lx), s);
+  if (K == 2 && a.Lx <= 2 * xsl) return launch_one<16, 2, 1, 2, false, true>(a, smem_bytes<16, 2, 1>(a.Lx), s);
+  return cudaErrorInvalidValue;
 }
 
 template <int W, int K>
@@ -204,6 +227,7 @@ bool plan_step_multi(int Lx, int Ly, int ld, int want_w, int want_k, int want_de
 }
 
 cudaError_t launch_step_multi(const StepArgs &a, const StepConfig &cfg, int K, cudaStream_t s) {
+  if (K >= 2 && K <= 4 && a.lvout[K - 1] != nullptr) return dispatch_lvout(a, cfg, K, s);
   if (cfg.slab_w == kLeanW && K == kLeanK && cfg.depth == kLeanD && a.Lx > kThreads / (kLeanW / 4))
     return dispatch_lean(a, s);
 #define CBDG_MULTI_CASE(w, k, d) \

@@ -36,6 +36,42 @@ def test_backward_matches_oracle_gradient(precision, tol, L, M, periodic):
     assert rel(ge, oe) < tol and rel(gh, oh) < tol and rel(gd, od) < tol, (rel(ge, oe), rel(gh, oh), rel(gd, od))
 
 
+def rect_swave(Lx, Ly, M, seed):
+    """Open Lx x Ly disordered s-wave lattice with a random real Delta_i."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N = Lx * Ly
+    return wl.Problem(name=f"adj{Lx}x{Ly}", Lx=Lx, Ly=Ly, periodic_x=0, periodic_y=0,
+                      eps=rng.uniform(-0.5, 0.5, N), mu=-0.5, hop=wl.square_hops(Lx, Ly, 0, 0),
+                      pairing=wl.ONSITE, coupling=2.0,
+                      delta0=rng.uniform(0.2, 0.8, N).astype(np.complex128), T=0.05, M=M)
+
+
+@pytest.mark.parametrize("Lx,Ly,M", [(20, 13, 40), (70, 9, 64), (33, 17, 101), (16, 40, 50), (128, 3, 23)])
+def test_fp32_backward_with_multi_step_passes(Lx, Ly, M):
+    """The FP32 adjoint runs its forward and recomputed recursions three (or
+    two) steps per pass, each level written to its own vector, the reverse
+    recursion one step per launch.  Segment lengths of 7, 8, 11, 8 and 5
+    steps exercise every remainder; Lx = 70 and 128 the lean pass.  Against
+    the oracle's reverse mode (1e-3 of the gradient's scale) and against the
+    same adjoint with one step per pass (FP32 rounding only)."""
+    p = rect_swave(Lx, Ly, M, seed=Lx + Ly + M)
+    w = np.random.default_rng(M).normal(size=p.N)
+    out = {}
+    for steps in (0, 1):
+        lat = cbdg.Lattice(p, precision="fp32")
+        cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_QUADRATURE_NODES, K)
+        cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_TEMPORAL_STEPS, steps)
+        out[steps] = lat.backward(p.T, M, w.astype(np.complex128))
+        a = lat.rescale
+        lat.close()
+    ol = as_oracle(p)
+    oe, oh, od = orc.scf_map_gradient(ol, a, orc.fold_coefficients(M, K, a, p.T), w)
+    ge, gh, gd = out[0]
+    assert rel(ge, oe) < 1e-3 and rel(gh.real, oh) < 1e-3 and rel(gd.real, od) < 1e-3
+    for x, y in zip(out[0], out[1]):
+        assert rel(x, y) < 2e-5, rel(x, y)
+
+
 def test_gradient_loss_full_size_vs_finite_differences():
     """The differentiation workload: 64x64 open, M = 512, L = sum (Delta_out -
     target)^2 with a Gaussian bump target.  Adjoint (FP64) vs central
