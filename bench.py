@@ -486,12 +486,15 @@ def leg_ensemble(cbdg, wl, stream, samples=256):
     t2 = time.perf_counter()
     ens.close()
     units = sum(p.N for p in probs) * 256
-    # 255 doubled steps per column: 127 two-step passes (4 vector streams of 2N x 4 B each)
-    # and one single step (3 streams)
-    algo_bytes = sum((127 * 4 + 3) * 2 * p.N * 4 * p.N for p in probs)
+    # 255 doubled steps per column: three-step passes (4 vector streams of 2N x 4 B each)
+    # while three remain, then single steps (3 streams)
+    steps = (512 + 1) // 2 - 1
+    streams = 4 * (steps // 3) + 3 * (steps % 3)
+    algo_bytes = sum(streams * 2 * p.N * 4 * p.N for p in probs)
     return {"samples": len(probs), "s_per_iteration": t2 - t1, "first_call_s": t1 - t0,
             "vector_steps_per_s": units / (t2 - t1), "algorithmic_gbs": algo_bytes / (t2 - t1) / 1e9,
-            "algorithmic_bytes": algo_bytes}
+            "algorithmic_bytes": algo_bytes, "streams_per_column": streams,
+            "streams_per_column_one_step_per_pass": 3 * steps}
 
 
 def adjoint_streams(M, multi=False):

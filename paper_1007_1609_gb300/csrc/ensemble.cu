@@ -7,8 +7,10 @@
 // sample first and handed out through an atomic counter.  A CTA owns an item
 // from j_0 to the last moment: its two vectors live in a per-CTA scratch
 // block (slab-blocked [2N][W], electron rows then hole rows per lattice row),
-// every step marches the lattice rows with TMA bulk copies on mbarriers (the
-// same pipeline as step.cu), and the step dependencies stay inside the CTA,
+// three steps per pass (the lean mp::multi_pass) while three remain, the
+// rest one step at a time; every pass marches the lattice rows with TMA bulk
+// copies on mbarriers (the same pipeline as step.cu), and the step
+// dependencies stay inside the CTA,
 // so no grid-wide synchronisation is needed.  Moments are folded per column
 // in FP64 as they appear (doubling identities of the real s-wave case), and
 // the item ends with Delta_out and n of its W sites.  Per-sample Gershgorin
@@ -60,7 +62,7 @@ struct EnsArgs {
   double *nout;                     // [total]
   unsigned *queue;                  // item counter
   unsigned *flags;
-  int multi;                        // 1: two steps per pass (mp::multi_pass) while two remain
+  int multi;                        // 1: three steps per pass (mp::multi_pass, lean) while three remain
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
@@ -119,8 +121,11 @@ template <int MAXX, int NT>
 __global__ void __launch_bounds__(NT, 1) ensemble_recursion_kernel(EnsArgs a) {
   constexpr int W = kEnsW, VEC = 4, QUADS = W / VEC, XSLOTS = NT / QUADS;
   constexpr int JS = kEnsJS, OS = kEnsOS, D = kEnsD;
+  using Lean = mp::PassShape<W, 3, 1, NT, true>;  // the three-step pass
+  using FB = mp::FlushBank<3>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long bars[JS];
+  __shared__ __align__(8) unsigned long long bars[JS];         // the one-step march
+  __shared__ __align__(8) unsigned long long pbars[Lean::NB];  // the three-step pass
   __shared__ int abort_flag;
   __shared__ int item_s;
   // per-thread column sums, [3][XSLOTS][W], in the ring's space: written and
@@ -136,12 +141,15 @@ __global__ void __launch_bounds__(NT, 1) ensemble_recursion_kernel(EnsArgs a) {
   if (t == 0) {
     for (int k = 0; k < JS; ++k)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&bars[k])) : "memory");
+    for (int k = 0; k < Lean::NB; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&pbars[k])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     abort_flag = 0;
   }
   __syncthreads();
 
-  long long G = 0;  // loads issued by this CTA so far (slot = G % JS, parity = (G / JS) & 1)
+  long long G = 0;   // march loads issued by this CTA so far (slot = G % JS, parity = (G / JS) & 1)
+  long long Gp = 0;  // rows the three-step passes staged so far (their barriers' phase base)
   for (;;) {
     if (t == 0) item_s = static_cast<int>(atomicAdd(a.queue, 1u));
     __syncthreads();
@@ -197,7 +205,20 @@ __global__ void __launch_bounds__(NT, 1) ensemble_recursion_kernel(EnsArgs a) {
 
     const int steps = (a.M + 1) / 2 - 1;
     float *cur = bufB, *prev = bufA;
-    // fixed-order FP64 column sums of one step -> moments 2n, 2n+1 -> fold
+    // column t's sums of step n (|j_n|^2, <j_{n+1}|j_n>, symplectic) -> moments 2n, 2n+1 -> fold
+    auto fold = [&](int n, double A, double B, double Cs) {
+      const int m0 = 2 * n, m1 = 2 * n + 1;
+      const double e0 = 2.0 * A - 1.0, e1 = 2.0 * B - m1s[t];
+      const double sgn = (n & 1) ? 1.0 : -1.0;
+      const double h1 = 2.0 * sgn * Cs - dAs[t];
+      if (m0 < a.M) accn[t] -= C[m0] * e0;
+      if (m1 < a.M) {
+        accn[t] -= C[m1] * e1;
+        accd[t] += C[m1] * h1;
+      }
+      if (!(fabs(e0) <= 1.0 + 1e-4) || !(fabs(e1) <= 1.0 + 1e-4)) atomicOr(a.flags, kFlagSpectrum);
+    };
+    // fixed-order FP64 column sums of one step -> fold
     auto reduce_fold = [&](int n, auto &sA, auto &sB, auto &sC) {
 #pragma unroll
       for (int j = 0; j < VEC; ++j) {
@@ -213,32 +234,51 @@ __global__ void __launch_bounds__(NT, 1) ensemble_recursion_kernel(EnsArgs a) {
           B += red[1][z][t];
           Cs += red[2][z][t];
         }
-        const int m0 = 2 * n, m1 = 2 * n + 1;
-        const double e0 = 2.0 * A - 1.0, e1 = 2.0 * B - m1s[t];
-        const double sgn = (n & 1) ? 1.0 : -1.0;
-        const double h1 = 2.0 * sgn * Cs - dAs[t];
-        if (m0 < a.M) accn[t] -= C[m0] * e0;
-        if (m1 < a.M) {
-          accn[t] -= C[m1] * e1;
-          accd[t] += C[m1] * h1;
+        fold(n, A, B, Cs);
+      }
+      __syncthreads();
+    };
+    // the three-step pass's sums are in the warps' FP64 banks: lane l of warp
+    // w holds list entries [base(l), base(l) + PER) of column quad l & 3; add
+    // the warps in a fixed order and fold steps n, n + 1, n + 2
+    auto reduce_fold_bank = [&](int n, const FB &bank) {
+      double *rb = reinterpret_cast<double *>(smem_raw);
+      const int lane = t & 31, w = t >> 5;
+#pragma unroll
+      for (int i = 0; i < FB::PER; ++i) rb[(w * 4 + (lane & 3)) * FB::NVP + FB::base(lane) + i] = bank.d[i];
+      __syncthreads();
+      if (t < cols) {
+        const int qd = t / VEC, j = t % VEC;
+        for (int lv = 0; lv < 3; ++lv) {
+          double A = 0.0, B = 0.0, Cs = 0.0;
+          for (int z = 0; z < NT / 32; ++z) {
+            const double *r = rb + (z * 4 + qd) * FB::NVP + lv * 12 + j;
+            A += r[0];
+            B += r[4];
+            Cs += r[8];
+          }
+          fold(n + lv, A, B, Cs);
         }
-        if (!(fabs(e0) <= 1.0 + 1e-4) || !(fabs(e1) <= 1.0 + 1e-4)) atomicOr(a.flags, kFlagSpectrum);
       }
       __syncthreads();
     };
     int n = 1;
     if (a.multi && Ly >= 2) {
-      // two steps per pass over the item's vectors; (prev, cur) end as (j_{n+1}, j_{n+2})
-      for (; n + 1 <= steps && !abort_flag; n += 2) {
-        mp::Kahan pA[2][VEC], pB[2][VEC], pC[2][VEC];
-        if (!mp::multi_pass<W, 2, D, MAXX, NT>(prev, cur, par, Lx, Ly, reinterpret_cast<float *>(smem_raw), bars, G,
-                                           kWaitNs, 0u, &abort_flag, pA, pB, pC))
+      // three steps per pass over the item's vectors (the lean pass: FP32
+      // column sums flushed into FP64 every few rows); (prev, cur) end as
+      // (j_{n+2}, j_{n+3})
+      for (; n + 2 <= steps && !abort_flag; n += 3) {
+        mp::ChunkSum pA[3][VEC], pB[3][VEC], pC[3][VEC];
+        FB bank;
+        bank.clear();
+        if (!mp::multi_pass<W, 3, 1, MAXX, NT, true, mp::ChunkSum>(prev, cur, par, Lx, Ly,
+                                                                   reinterpret_cast<float *>(smem_raw), pbars, Gp,
+                                                                   kWaitNs, 0u, &abort_flag, pA, pB, pC, &bank))
           break;
-        G += Ly;
+        Gp += Ly;
         // the new rows were stored by this thread; the next pass reads them through TMA
         asm volatile("fence.proxy.async;\n" ::: "memory");
-        reduce_fold(n, pA[0], pB[0], pC[0]);
-        reduce_fold(n + 1, pA[1], pB[1], pC[1]);
+        reduce_fold_bank(n, bank);
       }
     }
     for (; n <= steps && !abort_flag; ++n) {
@@ -538,10 +578,10 @@ size_t ens_smem(int Lmax) {
   const size_t rowel = static_cast<size_t>(2) * Lmax * kEnsW;
   return ((kEnsJS + kEnsOS) * rowel + kEnsJS * static_cast<size_t>(Lmax) * kParamStride) * sizeof(float);
 }
-// shared memory of the two-step pass (its barriers are the kEnsJS of the one-step march)
+// shared memory of the three-step (lean) pass and of its FP64 sums' reduction
 size_t ens_multi_smem(int Lmax) {
-  static_assert(mp::PassShape<kEnsW, 2, kEnsD>::NB == kEnsJS, "the pass and the march share the barriers");
-  return mp::PassShape<kEnsW, 2, kEnsD>::smem_floats(Lmax) * sizeof(float);
+  const size_t bank = static_cast<size_t>(kEnsThreads / 32) * 4 * mp::FlushBank<3>::NVP * sizeof(double);
+  return std::max(mp::PassShape<kEnsW, 3, 1, kEnsThreads, true>::smem_floats(Lmax) * sizeof(float), bank);
 }
 // the per-thread column sums [3][XSLOTS][W] doubles share the ring's space
 size_t ens_red_smem(int Lmax);

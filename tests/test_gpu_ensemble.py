@@ -45,6 +45,33 @@ def test_ensemble_matches_single_lattice_path():
         assert max_abs(ens.delta(s), lat.delta) < 1e-5
 
 
+@pytest.mark.parametrize("M", [64, 66, 68])
+def test_uneven_members_match_the_oracle_for_every_step_remainder(M):
+    """Members of uneven shape -- tall, wide (two sites per thread), two and
+    one rows, a ragged last column slab -- through three-step passes while
+    three steps remain, then single steps (M = 64, 66, 68: 31, 32 and 33
+    steps).  Delta_out of one iteration (2 Delta_1 - Delta_0) vs the oracle
+    at every site, and vs the single-lattice FP32 path."""
+    from tests.test_gpu_parity import rect
+    shapes = [(96, 5), (5, 96), (70, 2), (13, 1), (33, 17), (1, 40)]
+    probs = [rect(lx, ly, M, seed=lx * 31 + ly + M, periodic=0) for lx, ly in shapes]
+    ens = cbdg.Ensemble(probs)
+    ens.set_option(cbdg.CBDG_OPT_QUADRATURE_NODES, K)
+    ok, it, mask = ens.scf(0.02, M, 0.5, 0.0, 1)
+    assert it == 1
+    for s, p in enumerate(probs):
+        ol = as_oracle(p)
+        a = orc.rescale(ol)
+        od, _ = orc.order_parameter(ol, a, p.T, M, K)
+        dout = 2 * ens.delta(s) - p.delta0
+        assert max_abs(dout, od) < 1e-5, (p.name, max_abs(dout, od))
+        lat = cbdg.Lattice(p, precision="fp32")
+        cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_QUADRATURE_NODES, K)
+        lat.scf_step(p.T, M, 0.5)
+        assert max_abs(ens.delta(s), lat.delta) < 1e-5
+        lat.close()
+
+
 def test_full_ensemble_first_iteration_sampled():
     """The full ensemble workload (256 samples, sides 32..96, M = 512) for one
     iteration: Delta_out = 2 Delta_1 - Delta_0 at sampled sites of sampled
