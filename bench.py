@@ -537,10 +537,28 @@ def adjoint_streams(M, multi=False):
 
 def leg_adjoint(cbdg, wl, stream, hbm):
     """Gradient of one self-consistency map, 64x64, M = 512 (FP64 and FP32),
-    with the algorithmic bytes of the implemented schedule (adjoint_streams)."""
+    with the algorithmic bytes of the implemented schedule (adjoint_streams);
+    and of the general-lattice map (64x64 periodic d-wave lattice with field,
+    t' and two vortices: complex64 vectors, one step per launch), FP32."""
     import numpy as np
-    pg = wl.gradient_case()
     out = {}
+    pc = wl.currents_dwave(64, 512)
+    lc = cbdg.Lattice(pc, precision="fp32", complex_field=True, stream=stream)
+    lc.order_parameter(pc.T, pc.M)
+    gc = (np.random.default_rng(1).normal(size=(pc.N, 4)) * (np.abs(pc.delta0) > 0)).astype(np.complex128)
+    lc.backward(pc.T, pc.M, gc)
+    t0 = time.perf_counter()
+    lc.backward(pc.T, pc.M, gc)
+    dt = time.perf_counter() - t0
+    lc.close()
+    vb = 2 * pc.N * pc.N * 8
+    gbs = adjoint_streams(pc.M) * vb / dt / 1e9
+    out["general_fp32_s"] = dt
+    out["general_fp32_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                    "streams": adjoint_streams(pc.M), "vector_bytes": vb,
+                                    "note": "64x64 d-wave vortex lattice (bond pairing, t', field), complex64; "
+                                            "whole backward call over its algorithmic bytes"}
+    pg = wl.gradient_case()
     for prec, es in (("fp64", 8), ("fp32", 4)):
         lg = cbdg.Lattice(pg, precision=prec, stream=stream)
         d, _ = lg.order_parameter(pg.T, pg.M)

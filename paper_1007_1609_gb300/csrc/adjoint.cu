@@ -276,11 +276,13 @@ __global__ void __launch_bounds__(kAccThreads) adjoint_accumulate_staged_kernel(
     a.add(p);
   };
   const int hb = Lx * W;
+  int landed = 0;  // slabs whose copies have all landed
   for (int i = 0; i < ns; ++i) {
     const int st = i % R;
     if (!acc_mbar_wait(acc_smem_addr(&bars[st]), static_cast<unsigned>((i / R) & 1), wait_ns)) abort_flag = 1;
     __syncthreads();
     if (abort_flag) break;
+    landed = i + 1;
     const float *d = sm + static_cast<size_t>(st) * 4 * rowel;
     const float *sl = d, *jm = d + rowel, *jc = d + 2 * rowel, *jp = d + 3 * rowel;
 #pragma unroll
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(kAccThreads) adjoint_accumulate_staged_kernel(
     if (t == 0) {
       atomicOr(flags, kFlagTimeout);
       // let the copies in flight land before the CTA's shared memory goes away
-      for (int i = 0; i < issued; ++i)
+      for (int i = landed; i < issued; ++i)
         if (!acc_mbar_wait(acc_smem_addr(&bars[i % R]), static_cast<unsigned>((i / R) & 1), wait_ns)) break;
     }
     return;

@@ -172,6 +172,165 @@ __global__ void __launch_bounds__(256) adjoint_accumulate_cplx_kernel(int Lx, in
   }
 }
 
+// FP32 accumulation with staged rows (slab width 4): one CTA per (lattice
+// row y, block of up to kCaXB sites of it, group of column slabs), one thread
+// per (site, column).  Per slab, bulk copies (cp.async.bulk on mbarriers)
+// bring the lam row y and the j rows y - 1, y, y + 1 (whole rows, electron
+// then hole part) into one stage of a kCaStages ring; the sums read every
+// neighbour from shared memory.  The sums are plain FP32 over at most
+// kCaMaxSpg slabs per launch (relative error below kCaMaxSpg 2^-24 of the sum
+// of |terms|), then FP64.
+constexpr int kCaW = 4, kCaXB = 64, kCaThreads = kCaW * kCaXB, kCaStages = 3, kCaMaxSpg = 64;
+constexpr int kCaSite = kCaW * 2;  // floats of one site's W complex entries
+
+__device__ __forceinline__ unsigned ca_smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool ca_mbar_wait(unsigned bar, unsigned parity, unsigned long long limit_ns) {
+  auto try_once = [&]() {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+  };
+  if (try_once()) return true;
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+  for (unsigned it = 0;; ++it) {
+    if (try_once()) return true;
+    if ((it & 255u) == 255u) {
+      unsigned long long t1;
+      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t1));
+      if (t1 - t0 > limit_ns) return false;
+    }
+  }
+}
+
+template <int NDIR, bool BOND>
+__global__ void __launch_bounds__(kCaThreads) adjoint_accumulate_cplx_staged_kernel(
+    int Lx, int Ly, int px, int py, int ld, int spg, int nxb, const float *__restrict__ lam,
+    const float *__restrict__ j, double f, double *part, unsigned long long wait_ns, unsigned *flags) {
+  constexpr int KC = 4 + 2 * NDIR + (BOND ? 8 : 0), W = kCaW, R = kCaStages;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[R];
+  __shared__ int abort_flag;
+  float *sm = reinterpret_cast<float *>(smem_raw);
+  const int N = Lx * Ly, y = blockIdx.x / nxb, g = blockIdx.y;
+  const int t = threadIdx.x, lane = t % W, x = (blockIdx.x % nxb) * kCaXB + t / W;
+  const bool valid = x < Lx;
+  const size_t slab_el = static_cast<size_t>(2) * N * kCaSite;  // floats of one slab
+  const int rowf = 2 * Lx * kCaSite;                            // floats of one lattice row
+  const int s0 = g * spg, ns = min(ld / W, s0 + spg) - s0;
+  // staged rows: 0 lam y, 1 j y-1, 2 j y, 3 j y+1 (-1: beyond an open edge)
+  const int yrow[4] = {y, y > 0 ? y - 1 : (py ? Ly - 1 : -1), y, y + 1 < Ly ? y + 1 : (py ? 0 : -1)};
+  if (t == 0) {
+    for (int k = 0; k < R; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ca_smem_addr(&bars[k])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  const unsigned row_bytes = static_cast<unsigned>(rowf) * 4u;
+  const unsigned stage_bytes = row_bytes * (2u + (yrow[1] >= 0 ? 1u : 0u) + (yrow[3] >= 0 ? 1u : 0u));
+  auto issue = [&](int i) {
+    const int st = i % R;
+    const unsigned bar = ca_smem_addr(&bars[st]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(stage_bytes) : "memory");
+    for (int r = 0; r < 4; ++r) {
+      if (yrow[r] < 0) continue;
+      const float *src = (r == 0 ? lam : j) + static_cast<size_t>(s0 + i) * slab_el + static_cast<size_t>(yrow[r]) * rowf;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+              ca_smem_addr(sm + (static_cast<size_t>(st) * 4 + r) * rowf)),
+          "l"(src), "r"(row_bytes), "r"(bar)
+          : "memory");
+    }
+  };
+  int issued = min(ns, R);
+  if (t == 0)
+    for (int i = 0; i < issued; ++i) issue(i);
+  // neighbour d of this thread's site: offset in a stage (row y + dy, site x + dx), -1: none
+  int noff[NDIR];
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d) {
+    const int dx = (d == 0 || d == 4 || d == 6) ? 1 : (d == 1 || d == 5 || d == 7) ? -1 : 0;
+    const int dy = (d == 2 || d == 4 || d == 7) ? 1 : (d == 3 || d == 5 || d == 6) ? -1 : 0;
+    const bool ok = valid && neighbour_site(Lx, Ly, px, py, y * Lx + x, d) >= 0;
+    const int nx = (x + dx + Lx) % Lx;
+    noff[d] = ok ? (2 + dy) * rowf + nx * kCaSite + 2 * lane : -1;
+  }
+  float re[KC], im[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) re[k] = im[k] = 0.f;
+  const int own = x * kCaSite + 2 * lane, hp = Lx * kCaSite;  // hole part offset within a row
+  int landed = 0;  // slabs whose copies have all landed
+  for (int i = 0; i < ns; ++i) {
+    const int st = i % R;
+    if (!ca_mbar_wait(ca_smem_addr(&bars[st]), static_cast<unsigned>((i / R) & 1), wait_ns)) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    landed = i + 1;
+    if (valid) {
+      const float *d = sm + static_cast<size_t>(st) * 4 * rowf;
+      auto ld2 = [&](int off) { return *reinterpret_cast<const float2 *>(d + off); };
+      const float2 le = ld2(own), lh = ld2(own + hp), je = ld2(2 * rowf + own), jh = ld2(2 * rowf + own + hp);
+      // conj(l) v = (lr vr + li vi) + i (lr vi - li vr)
+      auto acc = [&](int k, float2 l, float2 v) {
+        re[k] = fmaf(l.x, v.x, fmaf(l.y, v.y, re[k]));
+        im[k] = fmaf(l.x, v.y, fmaf(-l.y, v.x, im[k]));
+      };
+      acc(0, le, je);
+      acc(1, lh, jh);
+      acc(2, le, jh);
+      acc(3, lh, je);
+#pragma unroll
+      for (int dd = 0; dd < NDIR; ++dd) {
+        if (noff[dd] < 0) continue;
+        const float2 ne = ld2(noff[dd]), nh = ld2(noff[dd] + hp);
+        acc(4 + 2 * dd, le, ne);
+        acc(5 + 2 * dd, lh, nh);
+        if (BOND && dd < 4) {
+          acc(4 + 2 * NDIR + 2 * dd, le, nh);
+          acc(5 + 2 * NDIR + 2 * dd, lh, ne);
+        }
+      }
+    }
+    __syncthreads();  // stage st is free
+    if (i + R < ns) {
+      if (t == 0) issue(i + R);
+      issued = i + R + 1;
+    }
+  }
+  if (abort_flag) {
+    if (t == 0) {
+      atomicOr(flags, kFlagTimeout);
+      // let the copies in flight land before the CTA's shared memory goes away
+      for (int i = landed; i < issued; ++i)
+        if (!ca_mbar_wait(ca_smem_addr(&bars[i % R]), static_cast<unsigned>((i / R) & 1), wait_ns)) break;
+    }
+    return;
+  }
+  // combine the W column lanes of each site (adjacent lanes), FP64
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    double vr = re[k], vi = im[k];
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+      vr += __shfl_xor_sync(0xffffffffu, vr, o);
+      vi += __shfl_xor_sync(0xffffffffu, vi, o);
+    }
+    if (valid && lane == 0) {
+      double *pp = part + (static_cast<size_t>(g) * N + static_cast<size_t>(y) * Lx + x) * 2 * KC + 2 * k;
+      pp[0] += f * vr;
+      pp[1] += f * vi;
+    }
+  }
+}
+
 __global__ void adjoint_final_cplx_kernel(int Lx, int Ly, int px, int py, int nd, int bond, int groups,
                                           const double *part, const double *scal, double *g_eps, double2 *g_hop,
                                           double2 *g_delta) {
@@ -237,9 +396,45 @@ cudaError_t accumulate_kind(int Lx, int Ly, int px, int py, int nd, int bond, in
               : accumulate_c<S, W, 4, false>(Lx, Ly, px, py, ld, groups, lam, j, f, part, s);
 }
 
+size_t cplx_staged_smem(int Lx) { return static_cast<size_t>(kCaStages) * 4 * 2 * Lx * kCaSite * sizeof(float); }
+bool cplx_staged(int precision, int Lx, int W) {
+  return precision == 1 && W == kCaW && cplx_staged_smem(Lx) <= 200 * 1024;
+}
+
+template <int NDIR, bool BOND>
+cudaError_t launch_cplx_staged(int Lx, int Ly, int px, int py, int ld, int groups, const void *lam, const void *j,
+                               double f, double *part, unsigned long long wait_ns, unsigned *flags, cudaStream_t s) {
+  auto k = adjoint_accumulate_cplx_staged_kernel<NDIR, BOND>;
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  const int slabs = ld / kCaW, spg = (slabs + groups - 1) / groups, nxb = (Lx + kCaXB - 1) / kCaXB;
+  k<<<dim3(Ly * nxb, groups), kCaThreads, cplx_staged_smem(Lx), s>>>(
+      Lx, Ly, px, py, ld, spg, nxb, static_cast<const float *>(lam), static_cast<const float *>(j), f, part, wait_ns,
+      flags);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int adjoint_cplx_sums(int nd, int bond) { return cplx_sums(nd, bond); }
+
+int adjoint_groups_cplx(int precision, int Lx, int Ly, int ld, int W) {
+  if (!cplx_staged(precision, Lx, W)) return adjoint_groups(Ly, ld, W);
+  // about two waves of two resident CTAs per SM (128 registers a thread), and
+  // at most kCaMaxSpg slabs per group (the FP32 sums' error bound)
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int slabs = std::max(1, ld / W), rows = Ly * ((Lx + kCaXB - 1) / kCaXB);
+  const int want = std::max(1, (2 * 2 * sms + rows - 1) / rows);
+  return std::max((slabs + kCaMaxSpg - 1) / kCaMaxSpg, std::min(want, std::max(1, slabs / 4)));
+}
 
 cudaError_t launch_adjoint_source_cplx(int precision, int Lx, int Ly, int px, int py, int ncols, int W,
                                        const int32_t *sites, int pairing, const double2 *g, const double *cpl,
@@ -256,7 +451,14 @@ cudaError_t launch_adjoint_source_cplx(int precision, int Lx, int Ly, int px, in
 
 cudaError_t launch_adjoint_accumulate_cplx(int precision, int Lx, int Ly, int px, int py, int nd, int bond, int ld,
                                            int W, int groups, const void *lam, const void *j, double f, double *part,
-                                           cudaStream_t s) {
+                                           unsigned long long wait_ns, unsigned *flags, cudaStream_t s) {
+  if (cplx_staged(precision, Lx, W)) {
+    if (nd == 8)
+      return bond ? launch_cplx_staged<8, true>(Lx, Ly, px, py, ld, groups, lam, j, f, part, wait_ns, flags, s)
+                  : launch_cplx_staged<8, false>(Lx, Ly, px, py, ld, groups, lam, j, f, part, wait_ns, flags, s);
+    return bond ? launch_cplx_staged<4, true>(Lx, Ly, px, py, ld, groups, lam, j, f, part, wait_ns, flags, s)
+                : launch_cplx_staged<4, false>(Lx, Ly, px, py, ld, groups, lam, j, f, part, wait_ns, flags, s);
+  }
   if (precision == 1) {
     switch (W) {
       case 1: return accumulate_kind<float, 1>(Lx, Ly, px, py, nd, bond, ld, groups, lam, j, f, part, s);

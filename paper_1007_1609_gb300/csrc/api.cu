@@ -1239,7 +1239,7 @@ cbdg_status adjoint_run_cplx(cbdg_lattice *L, double T, int M) {
   if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
   if (max_cols < W) return fail(CBDG_ERR_OOM, "workspace too small for the adjoint");
   const int chunk = static_cast<int>(std::min<int64_t>(max_cols, ((N + W - 1) / W) * W));
-  const int groups = adjoint_groups(L->Ly, ((std::min(chunk, N) + W - 1) / W) * W, W);
+  const int groups = adjoint_groups_cplx(L->precision, L->Lx, L->Ly, ((std::min(chunk, N) + W - 1) / W) * W, W);
   const int KC = adjoint_cplx_sums(nd, bond);
   const size_t part_bytes = static_cast<size_t>(groups) * N * 2 * KC * sizeof(double);
   CK(L->adj_part.ensure(part_bytes));
@@ -1336,7 +1336,7 @@ cbdg_status adjoint_run_cplx(cbdg_lattice *L, double T, int M) {
                                       L->stream));
         CK(launch_adjoint_accumulate_cplx(L->precision, L->Lx, L->Ly, L->px, L->py, nd, bond, ld, W, groups, lam1,
                                           segv(m - 1 - k * S), m == 1 ? 1.0 : 2.0, L->adj_part.as<double>(),
-                                          L->stream));
+                                          a.wait_ns, L->flags.as<unsigned int>(), L->stream));
         L->launches += 2;
       }
     }

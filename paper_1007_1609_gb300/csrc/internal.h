@@ -289,9 +289,12 @@ int adjoint_cplx_sums(int nd, int bond);
 cudaError_t launch_adjoint_source_cplx(int precision, int Lx, int Ly, int px, int py, int ncols, int W,
                                        const int32_t *sites, int pairing, const double2 *g, const double *cpl,
                                        double coupling, double Cm, void *lam, cudaStream_t s);
+// column-slab groups of launch_adjoint_accumulate_cplx (the FP32 kernel with
+// staged rows, slab width 4, sizes its own grid)
+int adjoint_groups_cplx(int precision, int Lx, int Ly, int ld, int W);
 cudaError_t launch_adjoint_accumulate_cplx(int precision, int Lx, int Ly, int px, int py, int nd, int bond, int ld,
                                            int W, int groups, const void *lam, const void *j, double f, double *part,
-                                           cudaStream_t s);
+                                           unsigned long long wait_ns, unsigned *flags, cudaStream_t s);
 // g_eps [N] real; g_hop [N * nd], g_delta [N] or [N * 4] complex (dL/dRe + i dL/dIm).
 cudaError_t launch_adjoint_final_cplx(int Lx, int Ly, int px, int py, int nd, int bond, int groups,
                                       const double *part, const double *scal, double *g_eps, double2 *g_hop,
