@@ -379,6 +379,9 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
           wv[0][(ph + 1) % 3][k] = nv;
         }
       }
+      // LEAN: level 1's j_n row r - 1 at this x (row g - 1) is level 2's
+      // j_n row r at this wavefront; kept from level 1's loads
+      float4 q_ud[MAXX], q_vd[MAXX];
 #pragma unroll
       for (int lv = 1; lv <= K; ++lv) {
         const int r = g - lv + 1;
@@ -406,6 +409,8 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
                   vu = lds4(rp + hb + x * W + off);
                   ud = lds4(rm + x * W + off);
                   vd = lds4(rm + hb + x * W + off);
+                  q_ud[k] = ud;
+                  q_vd[k] = vd;
                 } else {
                   uu = vu = ud = vd = zero4();
                   if (r + 1 < Ly) {
@@ -431,10 +436,15 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
                 uo = lds4(po + x * W + off);
                 vo = lds4(po + hb + x * W + off);
               } else if (LEAN && lv == 2) {
-                // level 0 row r from the j_n ring
-                const float *rc = sq + (r % RQ) * rowel;
-                uo = lds4(rc + x * W + off);
-                vo = lds4(rc + hb + x * W + off);
+                // level 0 row r: interior wavefronts kept it from level 1
+                if (INNER) {
+                  uo = q_ud[k];
+                  vo = q_vd[k];
+                } else {
+                  const float *rc = sq + (r % RQ) * rowel;
+                  uo = lds4(rc + x * W + off);
+                  vo = lds4(rc + hb + x * W + off);
+                }
               } else {
                 uo = wu[lv >= 2 ? lv - 2 : 0][sc][k];
                 vo = wv[lv >= 2 ? lv - 2 : 0][sc][k];
