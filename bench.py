@@ -666,6 +666,7 @@ def leg_junction(cbdg, wl, torch, stream, hbm):
     lat.order_parameter(p.T, p.M)
     sms, sn, sb = cbdg.cbdg_profile_read(lat.handle)
     k = cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL)
+    tile = lat.last_tile()
     lat.close()
     L = p.Lx
     units = p.Ly * ((p.M + 1) // 2)
@@ -673,7 +674,7 @@ def leg_junction(cbdg, wl, torch, stream, hbm):
             "M": p.M, "start_vectors": int(p.Ly), "scf_iteration_s": t1 - t0, "vector_steps_per_s": units / (t1 - t0),
             "max_abs_ddelta": diff, "delta_bulk": float(abs(d[L * 150])), "delta_interface": float(abs(d[L * 299])),
             "surface_ldos_s": t3 - t2, "lorentz_lambda": lam, "surface_ldos_at_0": float(rho[:, 100].mean()),
-            "steps_per_pass": k, "recursion_launches": sn, "recursion_ms": sms,
+            "steps_per_pass": k, "tile": list(tile), "recursion_launches": sn, "recursion_ms": sms,
             "roofline": {"bound": "hbm", "achieved": sb / (sms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": sb / (sms * 1e-3) / 1e9 / hbm,
                          "note": "recursion kernels over their algorithmic bytes (one start site per layer)"}}
