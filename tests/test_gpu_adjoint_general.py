@@ -92,3 +92,33 @@ def test_real_lattice_gradients_are_complex_with_zero_imaginary_parts():
     a = orc.rescale(ol)
     oe, oh, od = orc.scf_map_gradient(ol, a, orc.fold_coefficients(p.M, K, a, p.T), w)
     assert rel(ge, oe) < 1e-9 and rel(gh.real, oh) < 1e-9 and rel(gd.real, od) < 1e-9
+
+
+@pytest.mark.parametrize("shape", [(70, 5, 24, 1, True), (130, 3, 20, 1, False), (66, 4, 18, 0, True)])
+def test_fp32_general_backward_wide_rows(shape):
+    """The FP32 gradient sums of general lattices run one CTA per block of
+    64 sites of a lattice row (whole rows staged); rows wider than 64 sites
+    take several blocks, with the periodic x wrap between the first and the
+    last.  Against the oracle's reverse mode (1e-3) and the FP64 path (1e-3)."""
+    from tests.test_gpu_temporal_cplx import rect_general
+    Lx, Ly, M, periodic, bond = shape
+    p = rect_general(Lx, Ly, M, seed=Lx + Ly, periodic=periodic, flux=1.0 if periodic else 0.0, tp=-0.3, bond=bond)
+    rng = np.random.default_rng(Lx)
+    shp = (p.N, 4) if bond else (p.N,)
+    g = rng.normal(size=shp) + 1j * rng.normal(size=shp)
+    if bond:
+        g = g * (np.abs(p.delta0) > 0)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        lat = cbdg.Lattice(p, precision=prec, complex_field=True)
+        cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_QUADRATURE_NODES, K)
+        out[prec] = lat.backward(p.T, M, g)
+        a = lat.rescale
+        lat.close()
+    ol = as_oracle(p)
+    oe, oh, od = orc.map_gradient_general(ol, a, orc.fold_coefficients(M, K, a, p.T), g)
+    for got, ref in zip(out["fp32"], (oe, oh, od)):
+        assert rel(got, ref) < 1e-3, rel(got, ref)
+    for got, ref in zip(out["fp64"], (oe, oh, od)):
+        assert rel(got, ref) < 1e-9, rel(got, ref)
+
