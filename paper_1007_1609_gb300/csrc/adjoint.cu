@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) adjoint_accumulate_kernel(int Lx, int Ly,
 // kAccStages ring, the copies of the next slabs in flight while the sums of
 // this one read every neighbour from shared memory.  MAXX x slots per thread
 // (Lx <= 64 MAXX); same sums, order and compensation as the unstaged kernel.
-constexpr int kAccStages = 3, kAccThreads = 256, kAccW = 16;
+constexpr int kAccStages = 2, kAccThreads = 256, kAccW = 16;
 
 __device__ __forceinline__ unsigned acc_smem_addr(const void *p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
