@@ -376,7 +376,12 @@ enum {
                                     widths other than 8 and 16, Lx above 64 at slab width
                                     16 (128 for K = 2, and for K = 3 at pipeline depth 1,
                                     the lean pass), above 128 at slab width 8 (256 for
-                                    K = 2), and rings that do not fit in shared memory.
+                                    K = 2), and rings that do not fit in shared memory;
+                                    except that K = 2 requested explicitly on a lattice
+                                    128 < Lx <= 512 at slab width 4 or 8 runs the two-step
+                                    pass over row blocks (each block recomputes its halo
+                                    rows, the new vectors are written to two more vector
+                                    buffers: four vectors of workspace instead of two).
                                     General lattices (complex FP32 vectors: Peierls
                                     hoppings, t', bond pairing; periodic or open): K >= 2
                                     selects the two-step pass (slab width 2, Lx <= 256,

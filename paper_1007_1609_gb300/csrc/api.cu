@@ -117,6 +117,7 @@ struct cbdg_lattice {
   int nd = 0;  // number of Delta entries (N or 4N)
   DBuf eps, hop, delta, params, scal, flags, f, C, sites_all, sites_user;
   DBuf vec0, vec1, partials, mu1, dA, acc_n, acc_d, dout, nout, mom_ee, mom_eh, stage;
+  DBuf vec2, vec3;  // the out-of-place outputs of the row-block passes
   DBuf acc_site_n, acc_site_b, adj_ck, adj_seg, adj_lam, adj_part, adj_w, adj_out, adj_fp;
   DBuf adj_wc, adj_outc;  // general-lattice adjoint: dL/dDelta_out (complex) and the gradients
   DBuf params_c, g_acc, g_tgt, g_mom, g_w, g_out;  // nonlocal readout (green.cu)
@@ -466,16 +467,20 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     L->tuned_d = tv.D;
     L->tuned_split = tv.split;
   }
-  // column chunk: bounded by the workspace cap (two vectors)
+  // row-block passes (two steps per pass, out of place) for real FP32
+  // lattices with open y edges too wide for the whole-column pass
+  const bool blocked_candidate = mode == kReal && L->precision == CBDG_FP32_MIXED && !L->py && !Wres &&
+                                 L->temporal >= 2 && L->Lx > 128 && L->Lx <= 512 && !L->autotune;
+  // column chunk: bounded by the workspace cap (two vectors, four for row blocks)
   size_t cap;
   if (L->ws_mb > 0) {
     cap = static_cast<size_t>(L->ws_mb) << 20;
   } else {
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
-    cap = static_cast<size_t>(0.6 * (fr + L->vec0.bytes + L->vec1.bytes));
+    cap = static_cast<size_t>(0.6 * (fr + L->vec0.bytes + L->vec1.bytes + L->vec2.bytes + L->vec3.bytes));
   }
-  int64_t per_col = static_cast<int64_t>(2 * rows * es);
+  int64_t per_col = static_cast<int64_t>((blocked_candidate ? 4 : 2) * rows * es);
   int64_t max_cols = static_cast<int64_t>(cap) / per_col;
   max_cols = (max_cols / W) * W;
   if (L->chunk > 0) max_cols = std::min<int64_t>(max_cols, ((L->chunk + W - 1) / W) * W);
@@ -544,12 +549,27 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
     if (mode != kReal) {
       Kt = cplx_multi && plan_step_cplx_multi(L->precision, L->Lx, L->Ly, ld, &mcfg) ? 2 : 1;
     }
+    // row blocks with recomputed halos where the whole-column pass does not
+    // fit: only on request (CBDG_OPT_TEMPORAL_STEPS = 2); on the 500-wide S/N
+    // slab (slab width 4, two sites per thread) the pass measured 0.91x the
+    // one-step kernel, latency-bound like the other passes at 8 warps per SM
+    bool blocked = false;
+    if (Kt == 1 && blocked_candidate && L->temporal >= 2 &&
+        plan_step_multi_blocked(L->Lx, L->Ly, ld, cfg.slab_w, &mcfg)) {
+      blocked = true;
+      Kt = 2;
+    }
     L->last_temporal = Kt;
     const int nsum = mode == kReal ? 3 : 4;
     const size_t vbytes = rows * ld * es;
     CK(L->vec0.ensure(vbytes));
     CK(L->vec1.ensure(vbytes));
-    CK(L->partials.ensure(static_cast<size_t>(std::max(cfg.row_split, Kt)) * nsum * ld * sizeof(double)));
+    if (blocked) {
+      CK(L->vec2.ensure(vbytes));
+      CK(L->vec3.ensure(vbytes));
+    }
+    CK(L->partials.ensure(static_cast<size_t>(std::max(cfg.row_split, Kt * (blocked ? mcfg.row_split : 1))) *
+                          nsum * ld * sizeof(double)));
     CK(L->mu1.ensure(ld * sizeof(double)));
     CK(L->dA.ensure(ld * sizeof(double2)));
     CK(L->acc_n.ensure(ld * sizeof(double)));
@@ -591,6 +611,7 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
       }
     }
     void *cur = L->vec1.p, *prev = L->vec0.p;
+    void *out_prev = L->vec2.p, *out_cur = L->vec3.p;  // row-block passes: the next (j_{n+1}, j_{n+2})
     std::vector<double> launch_bytes;
     // doubling: step n yields moments 2n, 2n+1; direct: step n yields j_{n+1}
     const int steps = mode == kDirect ? M - 2 : (M + 1) / 2 - 1;
@@ -635,6 +656,29 @@ cbdg_status run_columns(cbdg_lattice *L, const int32_t *sites, int n_sites, int 
         }
         L->launches += 3;
         a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+        launch_bytes.push_back(4.0 * static_cast<double>(vbytes));
+        ++launch_idx;
+        n += 2;
+        continue;
+      }
+      if (blocked && steps - n + 1 >= 2) {
+        // steps n, n+1 over row blocks: j_{n+1}, j_{n+2} into (out_prev, out_cur)
+        const int nblk = mcfg.row_split;
+        a.rows_per_cta = (L->Ly + nblk - 1) / nblk;
+        a.lvout[0] = out_prev;
+        a.lvout[1] = out_cur;
+        if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx], L->stream));
+        const cudaError_t e = launch_step_multi(a, mcfg, 2, L->stream);
+        if (L->profile) CK(cudaEventRecord(L->events[2 * launch_idx + 1], L->stream));
+        a.lvout[0] = a.lvout[1] = nullptr;
+        CK(e);
+        CK(launch_fold(n, M, ncols, ld, nblk, L->partials.as<double>(), L->C.as<double>(), L->mu1.as<double>(),
+                       L->dA.as<double2>(), L->acc_n.as<double>(), L->acc_d.as<double2>(), mee, meh, mom_stride,
+                       L->flags.as<unsigned int>(), tol, L->stream, 2));
+        L->launches += 2;
+        a.rows_per_cta = (L->Ly + cfg.row_split - 1) / cfg.row_split;
+        std::swap(prev, out_prev);
+        std::swap(cur, out_cur);
         launch_bytes.push_back(4.0 * static_cast<double>(vbytes));
         ++launch_idx;
         n += 2;

@@ -77,6 +77,7 @@ struct StepConfig {
   int threads;
   size_t smem;
   int pstage = 1;       // real one-step kernel: 0 = parameters through the read-only cache (wide lattices)
+  int blocked = 0;      // multi-step pass over row blocks of row_split lattice rows, out of place
 };
 
 // Storage row of the electron (part 0) or hole (part 1) component of site s.
@@ -124,6 +125,10 @@ int choose_row_split(int slabs, int Ly, size_t smem, int threads);
 // instantiation or the rings do not fit in shared memory.
 bool plan_step_multi(int Lx, int Ly, int ld, int want_w, int want_k, int want_depth,
                      StepConfig *cfg, int *k_out);
+// Two steps per pass over row blocks with recomputed halos (real FP32, open
+// y edges, slab width 4 or 8): for lattices too wide for the whole-column
+// pass.  Fills cfg (row_split = blocks per slab); false if it does not fit.
+bool plan_step_multi_blocked(int Lx, int Ly, int ld, int W, StepConfig *cfg);
 cudaError_t launch_step_multi(const StepArgs &a, const StepConfig &cfg, int K, cudaStream_t s);
 
 // Whole recursion in shared memory for small real on-site lattices

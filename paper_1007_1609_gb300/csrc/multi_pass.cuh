@@ -22,9 +22,13 @@
 // the single wavefront possible.
 //
 // LVOUT: the levels go to vectors of their own instead of (P, Q), which are
-// then only read, and no column sums are formed; level t may add a
-// one-element source per column at its start site (PassSource) -- the
-// adjoint's forward, recomputed and reverse recursions.
+// then only read; level t may add a one-element source per column at its
+// start site (PassSource) -- the adjoint's forward, recomputed and reverse
+// recursions, whose kernel forms no column sums.
+//
+// BLOCKED (with LVOUT): the CTA owns a block of lattice rows instead of all
+// of them and recomputes K - t halo rows of level t on either side, so
+// blocks need no exchange; the sums and outputs cover its own rows only.
 //
 // Staging: TMA bulk copies on mbarriers; load l (rows l of Q and P and the
 // parameters of lattice row l) completes on bars[(base + l) % NB] in phase
@@ -207,14 +211,16 @@ struct PassShape {
 };
 
 template <int W, int K, int D, int MAXX, int NT = kPassThreads, bool LEAN = false, typename Acc = Kahan,
-          bool LVOUT = false>
+          bool LVOUT = false, bool BLOCKED = false>
 __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__restrict__ par, int Lx, int Ly,
                                            float *smem, unsigned long long *bars, long long base,
                                            unsigned long long wait_ns, unsigned stall_tx, int *abort_flag,
                                            Acc (&accA)[K][4], Acc (&accB)[K][4], Acc (&accC)[K][4],
                                            FlushBank<K> *bank = nullptr, LevelOut lo = LevelOut{},
-                                           const PassSource *src = nullptr, int col0 = 0) {
+                                           const PassSource *src = nullptr, int col0 = 0, int rb = 0,
+                                           int re = -1) {
   static_assert(K <= 4, "LevelOut holds four levels");
+  static_assert(!BLOCKED || LVOUT, "a row block writes its levels out of place");
   using Sh = PassShape<W, K, D, NT, LEAN>;
   constexpr bool kFlush = std::is_same<Acc, ChunkSum>::value;
   static_assert(!kFlush || W / 4 == 4, "the chunk flush expects four column quads per warp");
@@ -223,6 +229,19 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
   static_assert(W % VEC == 0 && NT % QUADS == 0 && K >= 2, "bad shape");
   const int rowel = 2 * Lx * W;
   const int pel = Lx * kParamStride;
+  // BLOCKED: the CTA owns lattice rows [rb, re) and computes level t on them
+  // and on K - t halo rows either side (none beyond the lattice edges), which
+  // it recomputes instead of exchanging; it loads rows r0 .. r0 + NR - 1, and
+  // every row index below is relative to r0.  Otherwise it owns all rows.
+  if (!BLOCKED || re < 0) re = Ly;
+  if (!BLOCKED) rb = 0;
+  const int r0 = BLOCKED ? max(0, rb - K) : 0, NR = BLOCKED ? min(Ly, re + K) - r0 : Ly;
+  P += static_cast<size_t>(r0) * rowel;
+  Q += static_cast<size_t>(r0) * rowel;
+  par += static_cast<size_t>(r0) * pel;
+  // rows of level t this CTA computes: [clo(t), chi(t))
+  auto clo = [&](int t) { return BLOCKED ? max(0, rb - K + t) - r0 : 0; };
+  auto chi = [&](int t) { return BLOCKED ? min(Ly, re + K - t) - r0 : Ly; };
   float *sq = smem;                       // [RQ][rowel]  j_n
   float *sp = sq + RQ * rowel;            // [RP][rowel]  j_{n-1}
   float *sl = sp + RP * rowel;            // [K-1][2][rowel] levels 1..K-1
@@ -254,8 +273,8 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
     bulk_load(smem_addr(sa + (AR > 0 ? (base + l) % AR : 0) * pel), par + static_cast<size_t>(l) * pel, par_bytes,
               bar);
   };
-  int issued = min(Ly, 2 + D);
-  int pissued = LEAN ? min(Ly, 2) : 0;  // rows 0, 1 before the first wavefront
+  int issued = min(NR, 2 + D);
+  int pissued = LEAN ? min(NR, 2) : 0;  // rows 0, 1 before the first wavefront
   if (t == 0) {
     for (int l = 0; l < issued; ++l) issue(l);
     for (int l = 0; l < pissued; ++l) issue_par(l);
@@ -278,7 +297,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
           if (rx % XSLOTS == xs) {
             smask |= 1 << j;
             s_k[j] = rx / XSLOTS;
-            s_r[j] = i / Lx;
+            s_r[j] = i / Lx - r0;
             s_i[j] = i;
           }
         }
@@ -324,7 +343,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
       }
     }
   }
-  const int G = Ly + K - 1;
+  const int G = NR + K - 1;
   bool stop = false;
   // Three wavefronts g0 .. g0 + 2 (window slots are compile-time per phase).
   // INNER: every level's row r and the rows r - 1, r + 1 it reads lie inside
@@ -337,11 +356,11 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
       const int g = g0 + ph;
       if (stop || (!INNER && g >= G)) break;
       // rows up to g + 1 must have landed (LEAN: parameter rows up to g)
-      for (; ok && waited <= min(g + 1, Ly - 1); ++waited)
+      for (; ok && waited <= min(g + 1, NR - 1); ++waited)
         if (!mbar_wait(bar_of(waited), par_of(waited), wait_ns))
           ok = false;
       if constexpr (LEAN)
-        for (; ok && pwaited <= min(g, Ly - 1); ++pwaited)
+        for (; ok && pwaited <= min(g, NR - 1); ++pwaited)
           if (!mbar_wait(pbar_of(pwaited), ppar_of(pwaited), wait_ns))
             ok = false;
       if (!ok) *abort_flag = 1;
@@ -352,14 +371,14 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
       }
       // the slots of rows g - 1 (j_{n-1}) and g - 1 (j_n; LEAN: g - 2) are free:
       // every read of them happened before the barrier
-      if (g + 2 + D < Ly) {
+      if (g + 2 + D < NR) {
         if (t == 0) issue(g + 2 + D);
         issued = g + 3 + D;
       }
       // LEAN: the parameter slot of row g - K is free (its last reader, level K,
       // ran at wavefront g - 1): parameter row g + 1 goes there
       if constexpr (LEAN) {
-        if (g + 1 < Ly && g + 1 >= pissued) {
+        if (g + 1 < NR && g + 1 >= pissued) {
           if (t == 0) issue_par(g + 1);
           pissued = g + 2;
         }
@@ -370,7 +389,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
         for (int k = 0; k < MAXX; ++k) {
           const int x = xs + k * XSLOTS;
           float4 nu = zero4(), nv = zero4();
-          if ((FULL || x < Lx) && (INNER || g + 1 < Ly)) {
+          if ((FULL || x < Lx) && (INNER || g + 1 < NR)) {
             const float *src = sq + ((g + 1) % RQ) * rowel;
             nu = lds4(src + x * W + off);
             nv = lds4(src + hb + x * W + off);
@@ -386,7 +405,9 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
       for (int lv = 1; lv <= K; ++lv) {
         const int r = g - lv + 1;
         const int sm = (ph - lv + 6) % 3, sc = (ph - lv + 7) % 3, su = (ph - lv + 8) % 3;
-        if (INNER || (r >= 0 && r < Ly)) {
+        // sums and output rows: the block's own rows only
+        const bool own = !BLOCKED || (r0 + r >= rb && r0 + r < re);
+        if (INNER || (r >= clo(lv) && r < chi(lv))) {
           const float *nb = lv == 1 ? sq + (r % RQ) * rowel : sl + ((lv - 2) * 2 + (r & 1)) * rowel;
           const float *po = sp + (r % RP) * rowel;
           const float *pc = LEAN ? sa + ((base + r) % (AR > 0 ? AR : 1)) * pel : sa + (r % (AS > 0 ? AS : 1)) * pel;
@@ -413,7 +434,7 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
                   q_vd[k] = vd;
                 } else {
                   uu = vu = ud = vd = zero4();
-                  if (r + 1 < Ly) {
+                  if (r + 1 < NR) {
                     const float *rp = sq + ((r + 1) % RQ) * rowel;
                     uu = lds4(rp + x * W + off);
                     vu = lds4(rp + hb + x * W + off);
@@ -461,9 +482,11 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
                                       __fmaf_rn(t1, fc(vl, j), __fmaf_rn(t0, fc(vr, j), -fc(vo, j)))))));
                 reinterpret_cast<float *>(&un)[j] = unj;
                 reinterpret_cast<float *>(&vn)[j] = vnj;
-                accA[lv - 1][j].add2(uj, uj, vj, vj);
-                accB[lv - 1][j].add2(unj, uj, vnj, vj);
-                accC[lv - 1][j].add2(unj, vj, -vnj, uj);
+                if (own) {
+                  accA[lv - 1][j].add2(uj, uj, vj, vj);
+                  accB[lv - 1][j].add2(unj, uj, vnj, vj);
+                  accC[lv - 1][j].add2(unj, vj, -vnj, uj);
+                }
               }
               if constexpr (LVOUT) {
                 if (smask != 0) add_sources(lv, r, k, un, vn);
@@ -476,8 +499,8 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
               }
               if constexpr (LVOUT) {
                 // every level to its own vector, when given; P and Q are only read
-                if (lo.p[lv - 1] != nullptr) {
-                  float *o = lo.p[lv - 1] + static_cast<size_t>(r) * rowel;
+                if (own && lo.p[lv - 1] != nullptr) {
+                  float *o = lo.p[lv - 1] + static_cast<size_t>(r0 + r) * rowel;
                   __stcs(reinterpret_cast<float4 *>(o + x * W + off), un);
                   __stcs(reinterpret_cast<float4 *>(o + hb + x * W + off), vn);
                 }
@@ -494,7 +517,8 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
             }
           }
         } else if (!INNER && lv < K) {
-          // rows outside [0, Ly) are zero (open edges)
+          // rows outside [0, Ly) are zero (open edges); a block's rows beyond
+          // its halo are never read
 #pragma unroll
           for (int k = 0; k < MAXX; ++k) {
             wu[lv < K ? lv : 0][sc][k] = zero4();
@@ -506,10 +530,11 @@ __device__ __forceinline__ bool multi_pass(float *P, float *Q, const float *__re
   };
   const bool xfull = Lx == MAXX * XSLOTS;
   for (int g0 = 0; g0 < G && !stop; g0 += 3) {
-    // wavefronts K .. Ly - 2: level t's row g - t + 1 and its neighbours
-    // g - t .. g - t + 2 lie inside the lattice, and so does row g + 1 (K = 4
-    // keeps the one checked copy: a second copy of its body spills)
-    if (K <= 3 && g0 >= K && g0 + 2 <= Ly - 2) {
+    // wavefronts K .. NR - 2 (a block: 2K - 1 .. NR - 2): level t's row
+    // g - t + 1 is one it computes, its neighbours g - t .. g - t + 2 lie
+    // inside the rows computed or loaded, and so does row g + 1 (K = 4 keeps
+    // the one checked copy: a second copy of its body spills)
+    if (K <= 3 && g0 >= (BLOCKED ? 2 * K - 1 : K) && g0 + 2 <= NR - 2) {
       if constexpr (K <= 3) {
         if (xfull) three_waves(g0, std::true_type{}, std::true_type{});
         else three_waves(g0, std::true_type{}, std::false_type{});

@@ -27,16 +27,24 @@ namespace {
 using mp::Kahan;
 constexpr int kThreads = mp::kPassThreads;
 
-template <int W, int K, int D, int MAXX, bool LEAN, bool LVOUT = false>
-__global__ void __launch_bounds__(kThreads, LVOUT && MAXX == 1 ? 2 : 1) step_multi_kernel(StepArgs a) {
+// LVOUT: per-level outputs, no column sums (the adjoint).  BLK: row blocks
+// of a.rows_per_cta lattice rows with recomputed halos, the last two levels
+// written out of place to a.lvout[K - 2], a.lvout[K - 1], column sums per
+// block (partials [level][block][3][ld]).
+template <int W, int K, int D, int MAXX, bool LEAN, bool LVOUT = false, bool BLK = false>
+__global__ void __launch_bounds__(kThreads, LVOUT && !BLK && MAXX == 1 ? 2 : 1) step_multi_kernel(StepArgs a) {
   using Sh = mp::PassShape<W, K, D, kThreads, LEAN>;
   constexpr int VEC = Sh::VEC, XSLOTS = Sh::XSLOTS, NB = Sh::NB;
+  // FP32 chunk sums flushed into FP64 need four column quads per warp
+  constexpr bool kChunk = LEAN && W / VEC == 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long bars[NB];
   __shared__ int abort_flag;
   const int t = threadIdx.x;
   const int q = t % Sh::QUADS, xs = t / Sh::QUADS;
-  const size_t slab = static_cast<size_t>(blockIdx.x) * (static_cast<size_t>(2) * a.Lx * a.Ly * W);
+  const int nblk = BLK ? (a.Ly + a.rows_per_cta - 1) / a.rows_per_cta : 1;
+  const int sl = static_cast<int>(blockIdx.x) / nblk, blk = static_cast<int>(blockIdx.x) % nblk;
+  const size_t slab = static_cast<size_t>(sl) * (static_cast<size_t>(2) * a.Lx * a.Ly * W);
   if (t == 0) {
     for (int k = 0; k < NB; ++k)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mp::smem_addr(&bars[k])) : "memory");
@@ -44,8 +52,8 @@ __global__ void __launch_bounds__(kThreads, LVOUT && MAXX == 1 ? 2 : 1) step_mul
     abort_flag = 0;
   }
   __syncthreads();
-  using Acc = typename std::conditional<LVOUT, mp::NoSum,
-                                        typename std::conditional<LEAN, mp::ChunkSum, Kahan>::type>::type;
+  using Acc = typename std::conditional<LVOUT && !BLK, mp::NoSum,
+                                        typename std::conditional<kChunk, mp::ChunkSum, Kahan>::type>::type;
   using FB = mp::FlushBank<K>;
   Acc accA[K][VEC], accB[K][VEC], accC[K][VEC];
   FB bank;
@@ -55,22 +63,25 @@ __global__ void __launch_bounds__(kThreads, LVOUT && MAXX == 1 ? 2 : 1) step_mul
 #pragma unroll
     for (int l = 0; l < K; ++l) lo.p[l] = a.lvout[l] ? static_cast<float *>(a.lvout[l]) + slab : nullptr;
   }
-  const bool ok = mp::multi_pass<W, K, D, MAXX, kThreads, LEAN, Acc, LVOUT>(
+  const int rb = blk * a.rows_per_cta, re = min(a.Ly, rb + a.rows_per_cta);
+  const bool ok = mp::multi_pass<W, K, D, MAXX, kThreads, LEAN, Acc, LVOUT, BLK>(
       static_cast<float *>(a.prev) + slab, static_cast<float *>(const_cast<void *>(a.cur)) + slab,
       static_cast<const float *>(a.params), a.Lx, a.Ly, reinterpret_cast<float *>(smem_raw), bars, 0,
-      a.wait_ns, a.stall_tx, &abort_flag, accA, accB, accC, &bank, lo, &a.src, static_cast<int>(blockIdx.x) * W);
+      a.wait_ns, a.stall_tx, &abort_flag, accA, accB, accC, &bank, lo, &a.src, sl * W, rb, re);
   if (!ok) {
     if (t == 0) atomicOr(a.flags, kFlagTimeout);
     return;
   }
-  if constexpr (LVOUT) return;
+  if constexpr (LVOUT && !BLK) return;
   __syncthreads();
   double *red = reinterpret_cast<double *>(smem_raw);
-  const size_t c0 = static_cast<size_t>(blockIdx.x) * W;
-  if constexpr (LEAN) {
+  const size_t c0 = static_cast<size_t>(sl) * W;
+  // level lv's sums of this block: partials[((lv * nblk + blk) * 3 + k) * ld + col]
+  auto part_at = [&](int lv, int k) { return a.partials + ((static_cast<size_t>(lv) * nblk + blk) * 3 + k) * a.ld; };
+  if constexpr (kChunk) {
     // the pass flushed every sum into the warps' FP64 banks: lane l of warp w
     // holds list entries [base(l), base(l) + PER) of column quad l & 3; add the
-    // warps in a fixed order -> partials[(lv * 3 + k) * ld + col]
+    // warps in a fixed order -> part_at(lv, k)[col]
     constexpr int NWARP = kThreads / 32;
     const int lane = t & 31, w = t >> 5;
 #pragma unroll
@@ -82,11 +93,11 @@ __global__ void __launch_bounds__(kThreads, LVOUT && MAXX == 1 ? 2 : 1) step_mul
       const int qd = col / VEC, j = col - qd * VEC;
       double s = 0.0;
       for (int z = 0; z < NWARP; ++z) s += red[(z * 4 + qd) * FB::NVP + lv * 12 + k * 4 + j];
-      a.partials[static_cast<size_t>(lk) * a.ld + c0 + col] = s;
+      part_at(lv, k)[c0 + col] = s;
     }
     return;
   } else {
-    // per-level column sums -> partials[(lv * 3 + k) * ld + col] (fixed order, FP64)
+    // per-level column sums -> part_at(lv, k)[col] (fixed order, FP64)
     for (int lv = 0; lv < K; ++lv) {
 #pragma unroll
       for (int j = 0; j < VEC; ++j) {
@@ -99,7 +110,7 @@ __global__ void __launch_bounds__(kThreads, LVOUT && MAXX == 1 ? 2 : 1) step_mul
         const int k = idx / W, col = idx - k * W;
         double s = 0.0;
         for (int z = 0; z < XSLOTS; ++z) s += red[(k * XSLOTS + z) * W + col];
-        a.partials[(static_cast<size_t>(lv) * 3 + k) * a.ld + c0 + col] = s;
+        part_at(lv, k)[c0 + col] = s;
       }
       __syncthreads();
     }
@@ -111,14 +122,15 @@ constexpr int kMaxDynSmem = 227 * 1024 - 1024;
 template <int W, int K, int D, bool LEAN = false>
 size_t smem_bytes(int Lx) {
   const size_t ring = mp::PassShape<W, K, D, kThreads, LEAN>::smem_floats(Lx);
-  const size_t red = LEAN ? static_cast<size_t>(kThreads / 32) * 4 * mp::FlushBank<K>::NVP * sizeof(double) / sizeof(float)
+  const size_t red = LEAN && W == 16
+                          ? static_cast<size_t>(kThreads / 32) * 4 * mp::FlushBank<K>::NVP * sizeof(double) / sizeof(float)
                           : static_cast<size_t>(3) * (kThreads / (W / 4)) * W * sizeof(double) / sizeof(float);
   return std::max(ring, red) * sizeof(float);
 }
 
-template <int W, int K, int D, int MAXX, bool LEAN = false, bool LVOUT = false>
+template <int W, int K, int D, int MAXX, bool LEAN = false, bool LVOUT = false, bool BLK = false>
 cudaError_t launch_one(const StepArgs &a, size_t smem, cudaStream_t s) {
-  auto k = step_multi_kernel<W, K, D, MAXX, LEAN, LVOUT>;
+  auto k = step_multi_kernel<W, K, D, MAXX, LEAN, LVOUT, BLK>;
   static int attr_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -130,7 +142,8 @@ cudaError_t launch_one(const StepArgs &a, size_t smem, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
-  k<<<a.ld / W, kThreads, smem, s>>>(a);
+  const int nblk = BLK ? (a.Ly + a.rows_per_cta - 1) / a.rows_per_cta : 1;
+  k<<<a.ld / W * nblk, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -159,6 +172,23 @@ cudaError_t dispatch_lean(const StepArgs &a, cudaStream_t s) {
   constexpr int xsl = kThreads / (kLeanW / 4);
   if (a.Lx <= xsl || a.Lx > 2 * xsl) return cudaErrorInvalidValue;
   return launch_one<kLeanW, kLeanK, kLeanD, 2, true>(a, smem_bytes<kLeanW, kLeanK, kLeanD, true>(a.Lx), s);
+}
+
+// Row blocks with recomputed halos, two steps per pass: lattices too wide
+// for a whole-column pass (rows of up to 2 x 256 sites at slab width 4, 2 x
+// 128 at 8), the parameters in the lean pass's ring, Kahan column sums, the
+// new vectors out of place.
+template <int W>
+size_t smem_blocked(int Lx) {
+  return smem_bytes<W, 2, 1, true>(Lx);
+}
+
+template <int W>
+cudaError_t dispatch_blocked(const StepArgs &a, cudaStream_t s) {
+  constexpr int xsl = kThreads / (W / 4);
+  if (a.Lx <= xsl) return launch_one<W, 2, 1, 1, true, true, true>(a, smem_blocked<W>(a.Lx), s);
+  if (a.Lx <= 2 * xsl) return launch_one<W, 2, 1, 2, true, true, true>(a, smem_blocked<W>(a.Lx), s);
+  return cudaErrorInvalidValue;
 }
 
 // Per-level outputs and no column sums (the adjoint's forward and recomputed
@@ -226,7 +256,26 @@ bool plan_step_multi(int Lx, int Ly, int ld, int want_w, int want_k, int want_de
   return true;
 }
 
+bool plan_step_multi_blocked(int Lx, int Ly, int ld, int W, StepConfig *cfg) {
+  if ((W != 4 && W != 8) || Ly < 2 || ld % W != 0 || Lx > 2 * (kThreads / (W / 4))) return false;
+  const size_t b = W == 4 ? smem_blocked<4>(Lx) : smem_blocked<8>(Lx);
+  if (b > static_cast<size_t>(kMaxDynSmem)) return false;
+  cfg->slab_w = W;
+  cfg->depth = 1;
+  cfg->threads = kThreads;
+  cfg->smem = b;
+  cfg->blocked = 1;
+  cfg->row_split = choose_row_split(ld / W, Ly, b, kThreads);
+  return true;
+}
+
 cudaError_t launch_step_multi(const StepArgs &a, const StepConfig &cfg, int K, cudaStream_t s) {
+  if (cfg.blocked) {
+    if (K != 2 || a.lvout[0] == nullptr || a.lvout[1] == nullptr) return cudaErrorInvalidValue;
+    if (cfg.slab_w == 4) return dispatch_blocked<4>(a, s);
+    if (cfg.slab_w == 8) return dispatch_blocked<8>(a, s);
+    return cudaErrorInvalidValue;
+  }
   if (K >= 2 && K <= 4 && a.lvout[K - 1] != nullptr) return dispatch_lvout(a, cfg, K, s);
   if (cfg.slab_w == kLeanW && K == kLeanK && cfg.depth == kLeanD && a.Lx > kThreads / (kLeanW / 4))
     return dispatch_lean(a, s);

@@ -222,3 +222,57 @@ def test_lost_copy_times_out_in_the_two_step_kernel():
     assert launches == 19 // 2 + 19 % 2  # the two-step kernel ran
     oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, p.M)
     assert max_abs(ee, oee) < TOL_MOM and max_abs(eh, oeh) < TOL_MOM
+
+
+@pytest.mark.parametrize("case", [(150, 50, 40, 8, 16), (150, 12, 40, 4, 37), (300, 33, 33, 4, 20),
+                                  (500, 19, 24, 4, 12), (200, 3, 17, 8, 24), (140, 64, 21, 4, 300)])
+def test_row_blocks_match_oracle_and_one_step(case):
+    """Lattices too wide for the whole-column pass run two steps per pass over
+    row blocks on request (CBDG_OPT_TEMPORAL_STEPS = 2): each CTA recomputes
+    K - t halo rows of level t on either side of its rows, writes the two new
+    vectors out of place and sums its own rows only.  Few start sites, so the rows split into several blocks (ragged last
+    block, blocks shorter than the halo at Ly = 3).  Moments vs the oracle
+    and vs one step per pass."""
+    Lx, Ly, M, slab, n_sites = case
+    p = rect(Lx, Ly, M, seed=Lx + Ly, periodic=0)
+    rng = np.random.default_rng(Lx)
+    sites = np.sort(rng.choice(p.N, min(n_sites, p.N), replace=False)).astype(np.int32)
+    lat = gpu_lattice(p, "fp32", resident=0, slab_width=slab, temporal_steps=2)
+    (ee, eh), launches = recursion_launches(lat, sites, M)
+    n_steps = (M + 1) // 2 - 1
+    assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL) == 2
+    assert launches == n_steps // 2 + n_steps % 2
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, M)
+    assert max_abs(ee, oee) < TOL_MOM, max_abs(ee, oee)
+    assert max_abs(eh, oeh) < TOL_MOM, max_abs(eh, oeh)
+    one = gpu_lattice(p, "fp32", resident=0, slab_width=slab, temporal_steps=1).moments(sites, M)
+    assert max_abs(ee, one[0]) < 5e-6 and max_abs(eh, one[1]) < 5e-6
+
+
+def test_row_blocks_order_parameter():
+    """Delta_out and n of every site through row-block passes (all sites as
+    start vectors on a 160 x 24 lattice at slab width 8) vs the oracle."""
+    p = rect(160, 24, 48, seed=77, periodic=0)
+    lat = gpu_lattice(p, "fp32", resident=0, slab_width=8, temporal_steps=2)
+    d, n = lat.order_parameter(p.T, p.M)
+    assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL) == 2
+    od, on = orc.order_parameter(as_oracle(p), lat.rescale, p.T, p.M, K)
+    assert max_abs(d, od) < TOL_DELTA and max_abs(n, on) < TOL_DELTA
+
+
+def test_lost_copy_times_out_in_row_blocks():
+    """The bounded waits of the row-block pass: a copy that never arrives
+    makes the call report CBDG_ERR_CUDA; the lattice then computes correct
+    moments."""
+    p = rect(150, 20, 30, seed=53, periodic=0)
+    sites = np.arange(0, p.N, 97, dtype=np.int32)
+    lat = gpu_lattice(p, "fp32", resident=0, slab_width=4, temporal_steps=2, wait_limit_ms=20, test_stall_copy=1)
+    with pytest.raises(cbdg.CbdgError) as ei:
+        lat.moments(sites, p.M)
+    assert ei.value.status == cbdg.CBDG_ERR_CUDA and "gave up waiting" in str(ei.value)
+    lat.set_option(cbdg.CBDG_OPT_TEST_STALL_COPY, 0)
+    ee, eh = lat.moments(sites, p.M)
+    assert cbdg.cbdg_get_option(lat.handle, cbdg.CBDG_INFO_LAST_TEMPORAL) == 2
+    oee, oeh = orc.moments(as_oracle(p), lat.rescale, sites, p.M)
+    assert max_abs(ee, oee) < TOL_MOM and max_abs(eh, oeh) < TOL_MOM
+
