@@ -426,14 +426,26 @@ int adjoint_cplx_sums(int nd, int bond) { return cplx_sums(nd, bond); }
 
 int adjoint_groups_cplx(int precision, int Lx, int Ly, int ld, int W) {
   if (!cplx_staged(precision, Lx, W)) return adjoint_groups(Ly, ld, W);
-  // about two waves of two resident CTAs per SM (128 registers a thread), and
-  // at most kCaMaxSpg slabs per group (the FP32 sums' error bound)
+  // at most kCaMaxSpg slabs per group (the FP32 sums' error bound); among
+  // those, the group count whose CTAs (two resident per SM at 128 registers a
+  // thread) run in the fewest waves x slabs per group
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long slots = 2LL * sms;
   const int slabs = std::max(1, ld / W), rows = Ly * ((Lx + kCaXB - 1) / kCaXB);
-  const int want = std::max(1, (2 * 2 * sms + rows - 1) / rows);
-  return std::max((slabs + kCaMaxSpg - 1) / kCaMaxSpg, std::min(want, std::max(1, slabs / 4)));
+  const int gmin = (slabs + kCaMaxSpg - 1) / kCaMaxSpg, gmax = std::max(gmin, std::min(slabs, 4 * gmin));
+  int best = gmin;
+  long long best_cost = -1;
+  for (int g = gmin; g <= gmax; ++g) {
+    const long long spg = (slabs + g - 1) / g;
+    const long long cost = ((static_cast<long long>(rows) * g + slots - 1) / slots) * spg;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = g;
+    }
+  }
+  return best;
 }
 
 cudaError_t launch_adjoint_source_cplx(int precision, int Lx, int Ly, int px, int py, int ncols, int W,
