@@ -1,0 +1,27 @@
+"""The algorithmic-byte accounting behind the bench's rooflines (CPU only):
+vector streams of the adjoint schedule, counted by hand for small M."""
+import pytest
+
+import bench
+
+
+def test_adjoint_streams_one_step_per_launch_m5():
+    # M = 5: S = 3, two segments.  Forward: copies of j0, j1 (4 streams), steps
+    # j2, j3, j4 (3 x 3), checkpoint 1 = (j3, j4) copied (4) -> 17.  Recompute:
+    # segment 1 copies j3, j4 (4); segment 0 copies j0, j1 (4) and one step
+    # for j2 (3) -> 11.  Reverse: lam4 is its source; lam3, lam2, lam1 are
+    # three steps (9) and lam4 .. lam1 four accumulations (8) -> 17.
+    assert bench.adjoint_streams(5) == 17 + 11 + 17
+
+
+def test_adjoint_streams_multi_step_m5():
+    # Forward: copies (4), one three-step pass in place j1 -> j4 (4 streams),
+    # checkpoint copies (4) -> 12.  Recompute: 4 + (4 + 3) -> 11.  Reverse:
+    # lam3, lam2, lam1 in one pass writing three levels (2 + 3) and four
+    # accumulations (8) -> 13.
+    assert bench.adjoint_streams(5, multi=True) == 12 + 11 + 13
+
+
+@pytest.mark.parametrize("M", [2, 3, 7, 40, 64, 101, 512])
+def test_multi_step_schedule_never_moves_more(M):
+    assert bench.adjoint_streams(M, multi=True) <= bench.adjoint_streams(M)

@@ -72,6 +72,28 @@ def test_fp32_backward_with_multi_step_passes(Lx, Ly, M):
         assert rel(x, y) < 2e-5, rel(x, y)
 
 
+def test_lost_copy_times_out_in_the_adjoint():
+    """Failure detection without a fault in the FP32 adjoint's multi-step
+    passes: with the stall hook the first staged row of every CTA expects
+    bytes that never arrive, the bounded waits run out (20 ms) and the call
+    reports CBDG_ERR_CUDA; the same lattice then gives the oracle's gradient."""
+    p = rect_swave(20, 13, 40, seed=7)
+    w = np.random.default_rng(3).normal(size=p.N).astype(np.complex128)
+    lat = cbdg.Lattice(p, precision="fp32")
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_QUADRATURE_NODES, K)
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_WAIT_LIMIT_MS, 20)
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_TEST_STALL_COPY, 1)
+    with pytest.raises(cbdg.CbdgError) as ei:
+        lat.backward(p.T, p.M, w)
+    assert ei.value.status == cbdg.CBDG_ERR_CUDA and "gave up waiting" in str(ei.value)
+    cbdg.cbdg_set_option(lat.handle, cbdg.CBDG_OPT_TEST_STALL_COPY, 0)
+    ge, gh, gd = lat.backward(p.T, p.M, w)
+    a = lat.rescale
+    lat.close()
+    oe, oh, od = orc.scf_map_gradient(as_oracle(p), a, orc.fold_coefficients(p.M, K, a, p.T), w.real)
+    assert rel(ge, oe) < 1e-3 and rel(gh.real, oh) < 1e-3 and rel(gd.real, od) < 1e-3
+
+
 def test_gradient_loss_full_size_vs_finite_differences():
     """The differentiation workload: 64x64 open, M = 512, L = sum (Delta_out -
     target)^2 with a Gaussian bump target.  Adjoint (FP64) vs central
