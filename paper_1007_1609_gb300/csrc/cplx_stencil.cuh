@@ -11,8 +11,8 @@
 // (step_cplx.cu) and the two-step pass (step_cplx_multi.cu).
 //
 // FP32: a complex64 element (re, im) is one packed pair of the f32x2
-// instructions (fma.rn.f32x2, sub.rn.f32x2; sm_100 and later), two FP32
-// operations each.  A product c z with a complex coefficient c splits into
+// instructions (f32x2.cuh), two FP32 operations each.  A product c z with a
+// complex coefficient c splits into
 // A += (c.re, c.re) z and S += (c.im, c.im) z, combined once per element at
 // the end: c z = (A.x - S.y, A.y + S.x) and conj(c) z = (A.x + S.y, A.y - S.x).
 // Half the FMA instructions of four scalar FMAs per complex multiply-add, and
@@ -21,6 +21,7 @@
 
 #include <type_traits>
 
+#include "f32x2.cuh"
 #include "internal.h"
 
 namespace cbdg {
@@ -173,28 +174,6 @@ __device__ __forceinline__ void site_step_scalar(const S *rm, const S *rc, const
     }
 }
 
-// packed FP32 pairs: lo = first float (the real part of a complex64 element)
-using F2 = unsigned long long;
-__device__ __forceinline__ F2 f2pack(float lo, float hi) {
-  F2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(F2 p, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
-}
-__device__ __forceinline__ F2 f2fma(F2 a, F2 b, F2 c) {  // a * b + c, both halves
-  F2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ F2 f2sub(F2 a, F2 b) {
-  F2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ F2 f2bcast(float x) { return f2pack(x, x); }
-
 // The FP32 update of site_step_scalar with packed pairs (two complex64
 // columns per float4).  Per element j of this thread:
 //   u' = P_u - N_u with P_u = e u + D v + sum_{d<4} B_d v_d and
@@ -208,8 +187,8 @@ __device__ __forceinline__ void site_step_f32x2(const float *rm, const float *rc
   auto ld = [&](const float *row, int xx, int part) {
     return *reinterpret_cast<const float4 *>(row + part * hb + xx * W * 2 + off);
   };
-  auto lo = [](const float4 &q) { return f2pack(q.x, q.y); };
-  auto hi = [](const float4 &q) { return f2pack(q.z, q.w); };
+  auto lo = [](const float4 &q) { return f2lo(q); };
+  auto hi = [](const float4 &q) { return f2hi(q); };
   const float *pp = py0 + 2 * x;
   const float e = pcx<float, LDG>(pp, kCpE, Lx).re;
   const Cx<float> dl = pcx<float, LDG>(pp, kCpDelta, Lx);
