@@ -255,6 +255,10 @@ __global__ void __launch_bounds__(NT, 1) step_cplx_kernel(StepArgs a) {
 }
 
 constexpr int kThreads = 256;
+// FP32 rows of at most kNarrowLx sites at slab width 4 run 128-thread CTAs:
+// 64 x slots, so every thread holds a site (256 threads would leave half of
+// them idle) and twice the CTAs fit on an SM.
+constexpr int kNarrowThreads = 128, kNarrowLx = 64;
 constexpr int kMaxDynSmem = 227 * 1024 - 1024;
 
 template <typename S, int W, int D>
@@ -268,9 +272,9 @@ size_t smem_bytes(int Lx) {
   return std::max(ring, red);
 }
 
-template <typename S, int W, int MAXX, int D, bool NNN, bool BOND, bool SUMS>
+template <typename S, int W, int MAXX, int D, bool NNN, bool BOND, bool SUMS, int NT = kThreads>
 cudaError_t launch_one(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
-  auto k = step_cplx_kernel<S, W, kThreads, MAXX, D, NNN, BOND, SUMS>;
+  auto k = step_cplx_kernel<S, W, NT, MAXX, D, NNN, BOND, SUMS>;
   static int attr_dev = -1;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -280,13 +284,20 @@ cudaError_t launch_one(const StepArgs &a, const StepConfig &cfg, cudaStream_t s)
     attr_dev = dev;
   }
   dim3 grid(a.ld / W, cfg.row_split);
-  k<<<grid, kThreads, cfg.smem, s>>>(a);
+  k<<<grid, NT, cfg.smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename S, int W, int D, bool NNN, bool BOND, bool SUMS>
 cudaError_t dispatch_maxx(const StepArgs &a, const StepConfig &cfg, cudaStream_t s) {
   const int xsl = kThreads / (W / CVec<S>::N);
+  if constexpr (sizeof(S) == 4 && W == 4) {
+    if (cfg.threads == kNarrowThreads) {
+      if (a.Lx > kNarrowLx) return cudaErrorInvalidValue;
+      return launch_one<S, W, 1, D, NNN, BOND, SUMS, kNarrowThreads>(a, cfg, s);
+    }
+  }
+  if (cfg.threads != kThreads) return cudaErrorInvalidValue;
   if (a.Lx <= 1 * xsl) return launch_one<S, W, 1, D, NNN, BOND, SUMS>(a, cfg, s);
   if (a.Lx <= 2 * xsl) return launch_one<S, W, 2, D, NNN, BOND, SUMS>(a, cfg, s);
   if (a.Lx <= 4 * xsl) return launch_one<S, W, 4, D, NNN, BOND, SUMS>(a, cfg, s);
@@ -368,13 +379,14 @@ bool plan_step_cplx(int precision, int Lx, int Ly, int ld, int want_w, int want_
   }
   const int slabs = ld / W;
   int split = want_split;
-  if (split <= 0) split = choose_row_split(slabs, Ly, smem(W, D), kThreads);
+  const int threads = precision == 1 && W == 4 && Lx <= kNarrowLx ? kNarrowThreads : kThreads;
+  if (split <= 0) split = choose_row_split(slabs, Ly, smem(W, D), threads);
   split = std::max(1, std::min(split, Ly));
   const int rpc = (Ly + split - 1) / split;
   cfg->slab_w = W;
   cfg->depth = D;
   cfg->row_split = (Ly + rpc - 1) / rpc;
-  cfg->threads = kThreads;
+  cfg->threads = threads;
   cfg->smem = smem(W, D);
   return true;
 }
