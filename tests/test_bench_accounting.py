@@ -25,3 +25,34 @@ def test_adjoint_streams_multi_step_m5():
 @pytest.mark.parametrize("M", [2, 3, 7, 40, 64, 101, 512])
 def test_multi_step_schedule_never_moves_more(M):
     assert bench.adjoint_streams(M, multi=True) <= bench.adjoint_streams(M)
+
+
+def test_headline_traffic_record_matches_the_kernel_source():
+    """The bench reports the dominant kernel's DRAM traffic from the committed
+    ncu summary only while the kernel's source is the one those counters were
+    taken with; a change to the three-step pass without a recapture shows up
+    here rather than as a silent null in the bench line."""
+    traffic, src = bench.recorded_traffic(("step_multi.cu", "multi_pass.cuh"), "step_multi_kernel_fp32_*.md")
+    assert src is not None and src.startswith("profiles/")
+    # four vector streams of 2N x B x 4 B per launch (128 x 128, all 16384 columns): within 1%
+    algorithmic = 4 * 2 * 16384 * 16384 * 4
+    assert abs(traffic / algorithmic - 1.0) < 0.01
+
+
+def test_profiles_hold_text_summaries_with_unlocked_clocks():
+    """profiles/ holds short text summaries; every ncu command in them leaves
+    the clocks alone (--clock-control none) and names committed files only."""
+    import glob
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    paths = sorted(glob.glob(os.path.join(root, "profiles", "*")))
+    assert paths
+    for path in paths:
+        assert path.endswith((".md", ".txt")), path
+        assert os.path.getsize(path) < 64 * 1024, path
+        text = open(path).read()
+        assert "_work" not in text, path
+        # an ncu command may continue over backslash-ended lines
+        for cmd in re.findall(r"(?m)^\s*ncu\b(?:[^\n]*\\\n)*[^\n]*", text):
+            assert "--clock-control none" in cmd, (path, cmd)
