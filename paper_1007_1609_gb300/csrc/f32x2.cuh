@@ -1,10 +1,8 @@
-// f32x2.cuh -- packed FP32 pairs for the fma.rn / sub.rn / mul.rn .f32x2
+// f32x2.cuh -- packed FP32 pairs for the fma.rn.f32x2 and sub.rn.f32x2
 // instructions of sm_100 and later.  Each does two independent FP32
 // operations with the rounding of the scalar instruction, so a sequence of
 // packed operations gives, in each half, bit for bit the result of the same
-// scalar sequence; multiplying by (-1, -1) is an exact negation (the sign of
-// a zero included).  Shared by the complex stencil (cplx_stencil.cuh) and the
-// multi-step pass (multi_pass.cuh).
+// scalar sequence.  Used by the complex stencil (cplx_stencil.cuh).
 #pragma once
 
 namespace cbdg {
@@ -27,11 +25,6 @@ __device__ __forceinline__ F2 f2fma(F2 a, F2 b, F2 c) {  // a * b + c, both halv
 __device__ __forceinline__ F2 f2sub(F2 a, F2 b) {
   F2 d;
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ F2 f2mul(F2 a, F2 b) {
-  F2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
 __device__ __forceinline__ F2 f2bcast(float x) { return f2pack(x, x); }
